@@ -1,0 +1,446 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test names the passage it checks.  None of them re-types the oracle's
+formulas: the references are the paper's printed numbers (tests/golden), an
+independent derivation of the filters from the lifting steps (Table 2.1), exact
+identities (perfect reconstruction, polynomial reproduction, moment
+conservation) and a dense whole-grid wavelet transform assembled in this file
+from the 1D primitives.
+"""
+from fractions import Fraction as Fr
+
+import numpy as np
+import pytest
+
+from conftest import golden
+from paper_2112_07537_gb300 import inputs as I
+
+WAVELETS = [(2, 0), (2, 2), (4, 0), (4, 2), (6, 0), (6, 2)]
+
+
+# --------------------------------------------------------------- filters
+def _dual_lifting(N):
+    """Table 2.1: dual-lifting coefficients S~_i, i = -(N/2-1)..N/2."""
+    t = {2: [Fr(-1, 2), Fr(-1, 2)],
+         4: [Fr(1, 16), Fr(-9, 16), Fr(-9, 16), Fr(1, 16)],
+         6: [Fr(-3, 256), Fr(25, 256), Fr(-75, 128), Fr(-75, 128), Fr(25, 256), Fr(-3, 256)]}[N]
+    return {i - (N // 2 - 1): c for i, c in enumerate(t)}
+
+
+def _lifting_matrices(N, Nt, n=32):
+    """Analysis (split, dual lift, primal lift with S = -1/2 S~ of order Nt)
+    and its inverse, as exact rational matrices on a periodic signal of n
+    samples, built from the lifting steps of Sec. 2.1.4 only."""
+    St = _dual_lifting(N)
+    S = {k: -Fr(1, 2) * c for k, c in _dual_lifting(2).items()} if Nt == 2 else {}
+    m = n // 2
+    rows_lam, rows_gam = [], []
+    for k in range(m):
+        g = [Fr(0)] * n
+        g[(2 * k + 1) % n] += 1
+        for i, c in St.items():
+            g[(2 * (k + i)) % n] += c
+        rows_gam.append(g)
+    for k in range(m):
+        lam = [Fr(0)] * n
+        lam[(2 * k) % n] += 1
+        # primal lift: lambda_k += S_{k,m} gamma_m, S acting on gamma_{k-1}, gamma_k
+        for i, c in S.items():
+            mm = (k - 1 + i) % m  # i in {0,1} -> gamma_{k-1}, gamma_k
+            for j in range(n):
+                lam[j] += c * rows_gam[mm][j]
+        rows_lam.append(lam)
+    return rows_lam, rows_gam
+
+
+@pytest.mark.parametrize("N,Nt", WAVELETS)
+def test_analysis_filters_match_lifting_construction(oracle_mod, N, Nt):
+    """Tables SM1/SM2 H^a and G^a equal split + dual lift (Table 2.1) + primal
+    lift S = -1/2 S~ (Sec. 2.1.4), derived here in exact arithmetic."""
+    n = 32
+    lam, gam = _lifting_matrices(N, Nt, n)
+    for which, rows, centre in (("Ha", lam, 0), ("Ga", gam, 1)):
+        off, c, _ = oracle_mod.filter_taps(N, Nt, which)
+        k = 8
+        expect = {((j - (2 * k + centre) + n // 2) % n) - n // 2: v for j, v in enumerate(rows[k]) if v}
+        got = {int(o): Fr(float(v)).limit_denominator(1 << 20) for o, v in zip(off, c) if v}
+        assert got == expect, (which, got, expect)
+
+
+@pytest.mark.parametrize("N,Nt", WAVELETS)
+def test_perfect_reconstruction(oracle_mod, N, Nt):
+    """P3: synthesis(J^s, K^s) o analysis(H^a, G^a) = identity (eqs 2.9-2.10),
+    bit-exact on dyadic data."""
+    rng = np.random.default_rng(7)
+    x = I.dyadic_random(256, rng)
+    lam = oracle_mod.restrict_1d(N, Nt, x)
+    gam = oracle_mod.detail_1d(N, Nt, x)
+    assert np.array_equal(oracle_mod.synth_1d(N, Nt, lam, gam), x)
+
+
+@pytest.mark.parametrize("N,Nt", WAVELETS)
+def test_interpolating_reproduces_polynomials_1d(oracle_mod, N, Nt):
+    """Sec. 2.1.3: refinement with zero details reproduces polynomials of degree
+    < N exactly (eq 2.13); details of such polynomials vanish."""
+    n = 64
+    k = np.arange(n, dtype=float)
+    for deg in range(N):
+        # non-periodic polynomial: check away from the periodic seam
+        coarse = (k / n - 0.4) ** deg
+        fine = oracle_mod.synth_1d(N, Nt, coarse)
+        x = np.arange(2 * n) / (2.0 * n)
+        sl = slice(2 * N, 2 * n - 2 * N)
+        assert np.allclose(fine[sl], ((x - 0.4) ** deg)[sl], atol=1e-13, rtol=0)
+        d = oracle_mod.detail_1d(N, Nt, (x - 0.4) ** deg)
+        assert np.abs(d[N:n - N]).max() < 1e-13
+
+
+def _e3(a, b):
+    """max over i,j,k of |a_i a_j a_k - b_i b_j b_k| (separable 3D E_inf)."""
+    idx = np.nonzero(np.abs(a) + np.abs(b) > 1e-14)[0]
+    A, B = a[idx], b[idx]
+    AA, BB = np.outer(A, A), np.outer(B, B)
+    # |A_i AA - B_i BB| <= |A_i - B_i| max|AA| + |B_i| max|AA - BB|: visit the
+    # rows in decreasing bound order and stop once no row can beat the best
+    ub = np.abs(A - B) * np.abs(AA).max() + np.abs(B) * np.abs(AA - BB).max()
+    best = 0.0
+    for i in np.argsort(-ub):
+        if ub[i] < best:
+            break
+        best = max(best, np.abs(A[i] * AA - B[i] * BB).max())
+    return best
+
+
+@pytest.mark.parametrize("row", golden("epsilon_plateaus.txt"), ids=lambda r: f"{int(r[0])}.{int(r[1])}-L{int(r[2])}")
+def test_epsilon_test_plateaus(oracle_mod, row):
+    """P1: the epsilon test's uniform plateaus (Sec. 4.1 figure data) --
+    coarsen the Gaussian sigma=2/15 from level 5 to Lc with H^a, refine back
+    with zero details, E_inf over the 3D grid; the Gaussian and both
+    operators are separable, so 1D arrays give the exact 3D value."""
+    N, Nt, Lc, ref = int(row[0]), int(row[1]), int(row[2]), row[3]
+    nb = 24
+    h = 1.0 / (nb * 32)
+    x = np.arange(2 * nb * 32) * h
+    a = np.exp(-(x - 1) ** 2 / (2 / 15) ** 2)
+    b = a.copy()
+    for _ in range(5 - Lc):
+        b = oracle_mod.restrict_1d(N, Nt, b)
+    for _ in range(5 - Lc):
+        b = oracle_mod.synth_1d(N, Nt, b)
+    assert _e3(a, b) == pytest.approx(ref, rel=1e-10)
+
+
+def test_table22_ghost_requirements(oracle_mod):
+    """P6: Table 2.2 -- coarsening ghosts (H^a reach under the vertex layout),
+    coarse region extension, update-step ghosts (reach of the detail filters
+    from the extended region) and refinement ghosts (J^s/K^s reach)."""
+    for r in golden("table22_ghosts.txt"):
+        N, Nt = int(r[0]), int(r[1])
+        _, ha, ext = oracle_mod.filter_taps(N, Nt, "Ha")
+        hw = (len(ha) - 1) // 2
+        assert (hw, max(hw - 1, 0)) == (r[2], r[3])
+        assert ext == (r[4], r[5])
+        assert oracle_mod.detail_reach(N, Nt) == (r[6], r[7])
+        _, ks, _ = oracle_mod.filter_taps(N, Nt, "Ks")
+        # refinement: odd child 2k+1 reads coarse k-(N/2-1)..k+N/2
+        lam_taps = [o for o, v in zip(range(-(len(ks) // 2), len(ks) // 2 + 1), ks) if v and o % 2]
+        assert (-(min(lam_taps) + 1) // 2, (max(lam_taps) + 1) // 2) == (r[8], r[9])
+
+
+# ------------------------------------------------------------ 3D ghosts
+def _poly_grid(oracle_mod, N, Nt, nb):
+    nt, tl = (4, 4, 4), 0.25
+    lev, anc = I.uniform_leaves(nt, 0)
+    lev, anc = I.refine_leaves(lev, anc, np.all((anc >= 1) & (anc <= 2), axis=1))
+    lev, anc = I.refine_leaves(lev, anc, (lev == 1) & np.all(anc == 3, axis=1))
+    lev, anc = I.balance(nt, lev, anc)
+    return oracle_mod.Grid(nt, tl, nb, N, Nt, 0, 4, lev, anc)
+
+
+@pytest.mark.parametrize("N,Nt", [(2, 0), (2, 2), (4, 0), (4, 2), (6, 0), (6, 2)])
+def test_ghost_fill_reproduces_polynomials(oracle_mod, N, Nt):
+    """P2: on a 3-level 2:1 tree, ghost reconstruction (refinement of the
+    coarse buffer, substitution, coarsening of finer neighbours) is exact for
+    polynomials of degree < N (degree <= 1 for lifted H^a), and substitution
+    leaves such data unchanged (Sec. 2.1.3, 2.2.2, 2.2.4)."""
+    nb = 16 if N < 6 else 24
+    g = _poly_grid(oracle_mod, N, Nt, nb)
+    G = 3
+    deg = N - 1 if Nt == 0 else 1
+    co = np.random.default_rng(1).normal(size=64)
+    xyz = I.point_coords(g.nt, g.tree_len, nb, g.lev, g.anc)
+    f = I.polynomial(xyz, co, deg)
+    pad, sub = oracle_mod.ghost_fill(g, f, G)
+    assert np.abs(sub - f).max() < 1e-13
+    h = g.tree_len / (nb * (1 << g.lev.astype(np.int64)))
+    ii = np.arange(-G, nb + G)
+    checked = 0
+    for b in range(g.nleaf):
+        x0 = g.anc[b] * nb * h[b]
+        if np.any(x0 - G * h[b] < 0) or np.any(x0 + (nb + G) * h[b] > 1.0):
+            continue  # padded region crosses the periodic seam
+        X, Y, Z = [(g.anc[b][d] * nb + ii) * h[b] for d in range(3)]
+        Zg, Yg, Xg = np.meshgrid(Z, Y, X, indexing="ij")
+        assert np.abs(pad[b] - I.polynomial([Xg, Yg, Zg], co, deg)).max() < 1e-12
+        checked += 1
+    assert checked > 20
+
+
+def test_substitution_enforces_zero_details(oracle_mod):
+    """Sec. 2.2.4: after substitution, the details of the band points next to
+    a coarser neighbour vanish (N.0: G^a along odd dimensions is the full
+    detail), while points outside the band keep their values."""
+    N, Nt, nb = 4, 0, 16
+    g = _poly_grid(oracle_mod, N, Nt, nb)
+    rng = np.random.default_rng(3)
+    f = rng.normal(size=(g.nleaf, nb, nb, nb))
+    G = oracle_mod.adapt_shell(N, Nt)
+    pad, sub = oracle_mod.ghost_fill(g, f, G)
+    _, _, (ef, eb) = oracle_mod.filter_taps(N, Nt, "Ha")
+    # a level-1 leaf whose -x face neighbour is a level-0 leaf
+    lvl1 = [b for b in range(g.nleaf) if g.lev[b] == 1 and g.anc[b][0] == 2 and
+            1 <= g.anc[b][1] <= 4 and 1 <= g.anc[b][2] <= 4]
+    b = lvl1[0]
+    d = oracle_mod.filter_taps(N, Nt, "Ga")
+    ga = dict(zip(d[0], d[1]))
+    P = pad[b]
+    # 1-degree detail in y at (x=0, y odd, z even) -> zero after substitution
+    for y in range(1, nb - 4, 2):
+        for z in range(2, nb - 4, 2):
+            det = sum(c * P[z + G, y + G + o, 0 + G] for o, c in ga.items())
+            assert abs(det) < 1e-12
+    # far from every coarse face (x in the middle) nothing changed
+    assert np.array_equal(sub[b][:, :, eb + 2:nb - ef - 2][4:-4, 4:-4], f[b][:, :, eb + 2:nb - ef - 2][4:-4, 4:-4])
+
+
+# ------------------------------------------------------ adaptation, moments
+def _dense(nb, lev, anc, phi, L, nt=2):
+    n = nt * nb << L
+    D = np.zeros((n, n, n))
+    for b in range(len(lev)):
+        s = nb << (L - lev[b])
+        a = anc[b] * s
+        if lev[b] == L:
+            D[a[2]:a[2] + s, a[1]:a[1] + s, a[0]:a[0] + s] = phi[b]
+    return D
+
+
+def _transform(oracle_mod, N, Nt, X, inverse=False):
+    U = X.copy()
+    for ax in range(3):
+        U = np.moveaxis(U, ax, -1)
+        sh = U.shape
+        V = U.reshape(-1, sh[-1])
+        W = np.empty_like(V)
+        for r in range(V.shape[0]):
+            if inverse:
+                W[r] = oracle_mod.synth_1d(N, Nt, V[r, 0::2], V[r, 1::2])
+            else:
+                W[r, 0::2] = oracle_mod.restrict_1d(N, Nt, V[r])
+                W[r, 1::2] = oracle_mod.detail_1d(N, Nt, V[r])
+        U = np.moveaxis(W.reshape(sh), -1, ax)
+    return U
+
+
+@pytest.mark.parametrize("N,Nt", [(2, 2), (4, 2), (2, 0), (4, 0)])
+def test_adapt_equals_dense_transform_with_discarded_details(oracle_mod, N, Nt):
+    """Coarsening + update step (eq 2.22) + refinement back to the uniform
+    level reproduce exactly the dense 3D wavelet synthesis of the original
+    field with the discarded details (the coarsened regions, and the
+    coarse-extension bands of the fine blocks, Sec. 2.2.2-2.2.4) set to zero.
+    Lifted wavelets then conserve M0 and M1 (eq 2.19, P4) to round-off."""
+    # 2x2x2 trees, uniform level 2; the blob sits in the middle of one sibling
+    # group, far enough from the periodic seam that no stencil wrapping around
+    # it sees the field (first moments would pick up the coordinate jump)
+    nt, tl, nb = (2, 2, 2), 0.5, 8
+    lev, anc = I.uniform_leaves(nt, 2)
+    g = oracle_mod.Grid(nt, tl, nb, N, Nt, 0, 2, lev, anc)
+    phi = I.gaussian(I.point_coords(nt, tl, nb, lev, anc), (0.375, 0.375, 0.375), 0.04)
+    X = _dense(nb, lev, anc, phi, 2)
+    g2, phi2, _ = oracle_mod.adapt(g, phi, 1e9, 1e-4, allow_refine=False)
+    assert set(np.unique(g2.lev)) == {1, 2}
+    g3, phi3, _ = oracle_mod.adapt(g2, phi2, 0.0, -1.0, allow_coarsen=False)
+    assert np.all(g3.lev == 2)
+    X3 = _dense(nb, g3.lev, g3.anc, phi3, 2)
+    # dense reference
+    n = 2 * nb << 2
+    _, _, (ef, eb) = oracle_mod.filter_taps(N, Nt, "Ha")
+    levmap = np.zeros((n, n, n), int)
+    for b in range(g2.nleaf):
+        s = nb << (2 - g2.lev[b])
+        a = g2.anc[b] * s
+        levmap[a[2]:a[2] + s, a[1]:a[1] + s, a[0]:a[0] + s] = g2.lev[b]
+    disc = levmap == 1
+    for b in np.nonzero(g2.lev == 2)[0]:
+        a = g2.anc[b] * nb
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    dd = (dx, dy, dz)
+                    if dd == (0, 0, 0):
+                        continue
+                    p = [(a[d] + (-1 if dd[d] < 0 else nb if dd[d] > 0 else 0)) % n for d in range(3)]
+                    if levmap[p[2], p[1], p[0]] < 2:
+                        sl = [slice(a[d] + (0 if dd[d] <= 0 else nb - ef),
+                                    a[d] + (eb if dd[d] < 0 else nb)) for d in range(3)]
+                        disc[sl[2], sl[1], sl[0]] = True
+    ii = np.arange(n)
+    odd = (ii[:, None, None] | ii[None, :, None] | ii[None, None, :]) & 1
+    U = _transform(oracle_mod, N, Nt, X)
+    U[disc & (odd > 0)] = 0.0
+    Xp = _transform(oracle_mod, N, Nt, U, inverse=True)
+    assert np.abs(X3 - Xp).max() < 1e-14
+    m0, m1 = oracle_mod.moments(g, phi)
+    n0, n1 = oracle_mod.moments(g3, phi3)
+    if Nt == 2:
+        # round-off of the quadrature sums; non-lifted wavelets miss by >1e-8
+        assert abs(n0 - m0) < 1e-10 * abs(m0)
+        assert np.abs(n1 - m1).max() < 1e-10 * abs(m0)
+    else:
+        assert abs(n0 - m0) > 1e-8 * abs(m0)  # non-lifted: moments not conserved
+
+
+def test_compression_error_bounded_by_eps(oracle_mod):
+    """P5 (eq 2.21): coarsening by eps_c then refining back keeps
+    ||f - f_eps||_inf <= C1 eps_c with C1 = O(1)."""
+    nt, tl, nb = (2, 2, 2), 0.5, 8
+    lev, anc = I.uniform_leaves(nt, 2)
+    for N, Nt in [(4, 0), (4, 2)]:
+        g = oracle_mod.Grid(nt, tl, nb, N, Nt, 0, 2, lev, anc)
+        phi = I.gaussian(I.point_coords(nt, tl, nb, lev, anc), (0.375, 0.375, 0.375), 0.06)
+        for eps in (1e-3, 1e-5):
+            g2, phi2, _ = oracle_mod.adapt(g, phi, 1e9, eps, allow_refine=False)
+            g3, phi3, _ = oracle_mod.adapt(g2, phi2, 0.0, -1.0, allow_coarsen=False)
+            err = np.abs(_dense(nb, g3.lev, g3.anc, phi3, 2) - _dense(nb, lev, anc, phi, 2)).max()
+            assert err <= 10 * eps
+
+
+def test_status_thresholds_and_policy(oracle_mod):
+    """Alg. SM3 step 3 (ties: >= eps_r refines, <= eps_c coarsens) and the
+    policy of step 4 on a random balanced tree: the new tree stays 2:1
+    balanced, coarsening only happens for complete sibling groups, and the
+    result does not depend on the order of the leaves."""
+    from oracle import FINER, SAME, COARSER
+    assert oracle_mod.status(1e-4, 1e-4, 1e-6) == FINER
+    assert oracle_mod.status(1e-6, 1e-4, 1e-6) == COARSER
+    assert oracle_mod.status(5e-5, 1e-4, 1e-6) == SAME
+    rng = np.random.default_rng(11)
+    nt = (2, 2, 2)
+    lev, anc = I.random_tree(nt, 1, 12, rng, 4)
+    g = oracle_mod.Grid(nt, 1.0, 16, 4, 0, 1, 4, lev, anc)
+    st = rng.integers(-1, 2, size=g.nleaf).astype(np.int8)
+    out = oracle_mod.policy(g, st)
+    perm = rng.permutation(g.nleaf)
+    gp = g.with_leaves(lev[perm], anc[perm])
+    outp = oracle_mod.policy(gp, st[perm])
+    assert np.array_equal(outp, out[perm])
+    assert np.all(out >= np.minimum(st, 0))  # statuses only rise
+    # build the new tree and check balance
+    new_l, new_a = [], []
+    for b in range(g.nleaf):
+        if out[b] == FINER:
+            for c in range(8):
+                new_l.append(lev[b] + 1)
+                new_a.append([2 * anc[b][0] + (c & 1), 2 * anc[b][1] + ((c >> 1) & 1), 2 * anc[b][2] + (c >> 2)])
+        elif out[b] == COARSER:
+            sib = [i for i in range(g.nleaf) if lev[i] == lev[b] and np.all(anc[i] // 2 == anc[b] // 2)]
+            assert len(sib) == 8 and all(out[i] == COARSER for i in sib)
+            if np.all(anc[b] % 2 == 0):
+                new_l.append(lev[b] - 1)
+                new_a.append(list(anc[b] // 2))
+        else:
+            new_l.append(lev[b])
+            new_a.append(list(anc[b]))
+    nl, na = np.asarray(new_l, np.int32), np.asarray(new_a, np.int32)
+    bl, ba = I.balance(nt, nl, na)
+    assert len(bl) == len(nl)  # already balanced
+
+
+# ---------------------------------------------------------- RHS and RK3
+def test_uniform_cons3_translation_matches_paper(oracle_mod):
+    """P8: Sec. 5.1 uniform-grid line: Gaussian sigma=1/5 advected a distance 3
+    at u=(0,0,1), CONS-3 + RK3-TVD, CFL 1/4, h=1/48: E_inf 0.01540 (figure
+    data).  The field is constant across x and y, so a one-block-thick slab of
+    trees gives the 3D result exactly."""
+    h_ref, e_ref = golden("translation_cons3.txt")[0]
+    nb, tl, nt = 8, 1 / 6.0, (1, 1, 36)
+    lev, anc = I.uniform_leaves(nt, 0)
+    g = oracle_mod.Grid(nt, tl, nb, 4, 0, 0, 0, lev, anc)
+    _, _, Z = I.point_coords(nt, tl, nb, lev, anc)
+    phi = np.exp(-(Z - 1.5) ** 2 / 0.2 ** 2)
+    h = tl / nb
+    assert h == pytest.approx(h_ref)
+    dt = oracle_mod.dt_cfl(g, 0.25, (0.0, 0.0, 1.0))
+    assert dt == pytest.approx(0.25 * h)
+    for _ in range(int(round(3.0 / dt))):
+        phi = oracle_mod.rk3_step(g, phi, dt, oracle_mod.CONS3, (0.0, 0.0, 1.0))
+    err = np.abs(phi - np.exp(-(Z - 4.5) ** 2 / 0.2 ** 2)).max()
+    assert err == pytest.approx(e_ref, rel=0.01)
+
+
+@pytest.mark.parametrize("scheme,order", [(1, 5), (2, 5), (0, 3)])
+def test_rhs_design_order(oracle_mod, scheme, order):
+    """The CONS-3 / CONS-5 / WENO-Z5 right-hand sides (Tables SM3/SM4)
+    converge at their design order on a smooth periodic field, in every
+    direction at once (u = (1, -0.5, 0.25))."""
+    errs = []
+    u = (1.0, -0.5, 0.25)
+    for L in (1, 2):
+        nt, tl, nb = (1, 1, 1), 1.0, 8
+        lev, anc = I.uniform_leaves(nt, L)
+        g = oracle_mod.Grid(nt, tl, nb, 4, 0, 0, L, lev, anc)
+        X, Y, Z = I.point_coords(nt, tl, nb, lev, anc)
+        k = 2 * np.pi
+        f = np.sin(k * X) * np.cos(k * Y) * np.sin(k * Z + 0.3)
+        ex = -(u[0] * k * np.cos(k * X) * np.cos(k * Y) * np.sin(k * Z + 0.3)
+               - u[1] * k * np.sin(k * X) * np.sin(k * Y) * np.sin(k * Z + 0.3)
+               + u[2] * k * np.sin(k * X) * np.cos(k * Y) * np.cos(k * Z + 0.3))
+        pad, _ = oracle_mod.ghost_fill(g, f, 3)
+        r = oracle_mod.rhs(g, pad, 3, scheme, u)
+        errs.append(np.abs(r - ex).max())
+    assert np.log2(errs[0] / errs[1]) > order - 0.6
+
+
+@pytest.mark.parametrize("N,lo,hi", [(4, 2.6, 3.6), (6, 4.4, 5.8)])
+def test_two_level_rhs_order_across_jump(oracle_mod, N, lo, hi):
+    """P7 (Sec. 4.3): across a resolution jump (one level-1 octant refined,
+    face, edge and corner jumps) the CONS-5 advection error converges as
+    h^min(5, N-1): 3rd order with 4.0 ghosts, 5th order with 6.0."""
+    errs = []
+    for nb in (16, 32):
+        nt, tl = (1, 1, 1), 1.0
+        lev, anc = I.uniform_leaves(nt, 1)
+        lev, anc = I.refine_leaves(lev, anc, np.all(anc == 0, axis=1))
+        g = oracle_mod.Grid(nt, tl, nb, N, 0, 0, 2, lev, anc)
+        xyz = I.point_coords(nt, tl, nb, lev, anc)
+        c, s = (0.45, 0.45, 0.45), 0.1  # nearest-image kink below 1e-10
+        f = I.gaussian(xyz, c, s)
+        d = [I.periodic_delta(xyz[i], c[i], 1.0) for i in range(3)]
+        ex = -sum(-2 * d[i] / s ** 2 for i in range(3)) * f  # u = (1,1,1)
+        pad, _ = oracle_mod.ghost_fill(g, f, 3)
+        r = oracle_mod.rhs(g, pad, 3, oracle_mod.CONS5, (1.0, 1.0, 1.0))
+        errs.append(np.abs(r - ex).max())
+    p = np.log2(errs[0] / errs[1])
+    assert lo < p < hi, (errs, p)
+
+
+def test_rk3_gaussian_translate_converges(oracle_mod):
+    """P9: periodic Gaussian advected by u=(1,1,1) on the two-level tree of
+    the tiny configuration matches the exact periodic translate, and the
+    error falls under refinement of the whole grid."""
+    errs = []
+    for nb in (8, 16):
+        nt, tl = (2, 2, 2), 0.5
+        lev, anc = I.tree_config1()
+        g = oracle_mod.Grid(nt, tl, nb, 4, 0, 0, 1, lev, anc)
+        xyz = I.point_coords(nt, tl, nb, lev, anc)
+        phi = I.gaussian_images(xyz, (0.5, 0.5, 0.5), 0.1, nimg=1)
+        dt = oracle_mod.dt_cfl(g, 0.5, (1, 1, 1))
+        T = 0.05
+        n = int(round(T / dt))
+        dt = T / n
+        for _ in range(n):
+            phi = oracle_mod.rk3_step(g, phi, dt, oracle_mod.CONS5, (1.0, 1.0, 1.0))
+        ex = I.gaussian_images(xyz, (0.5 + T, 0.5 + T, 0.5 + T), 0.1, nimg=1)
+        errs.append(np.abs(phi - ex).max())
+    assert errs[1] < errs[0] / 6, errs
