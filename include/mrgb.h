@@ -1,0 +1,211 @@
+/*
+ * mrgb.h -- C ABI of the GB300 multiresolution stencil library.
+ *
+ * The library advances scalar advection on a periodic forest of octrees of
+ * collocated nb^3 blocks with interpolating-wavelet grid adaptation, after
+ * T. Gillis and W. M. van Rees, "MURPHY - A scalable multiresolution
+ * framework for scientific computing on 3D block-structured collocated
+ * grids" (arXiv 2112.07537).  All compute runs in CUDA kernels on the device
+ * the grid was created on; nothing here falls back to the CPU.
+ *
+ * Conventions shared by every call
+ *  - Return value: MR_OK (0) or a negative MR_ERR_* code.  No call throws or
+ *    aborts.  MR_ERR_CUDA means a CUDA runtime call failed; the message of
+ *    the last failure is available from mr_last_error().
+ *  - Asynchrony: calls enqueue work on the grid's stream and return, except
+ *    where a call's comment says it synchronises (those that return host
+ *    values: mr_grid_leaves, mr_adapt, mr_query, mr_field_copy_out to host).
+ *  - Ownership: the caller owns host buffers and the device workspace passed
+ *    to mr_grid_create (for example a torch uint8 tensor); the grid carves all
+ *    its device arrays (block pool, octree tables, scratch) out of that
+ *    workspace and never calls cudaMalloc.  The workspace must outlive the grid.
+ *  - Leaves: a leaf is (level L, anchor a[3]) with 0 <= a[d] < ntree[d]*2^L,
+ *    in units of level-L blocks.  The grid keeps its leaves sorted by Morton
+ *    key (anchor scaled to lmax, bits interleaved x lowest); the block pool
+ *    slot of a leaf is its rank in that order.
+ *  - Field layout: leaf-major in slot order, nb^3 values per leaf, x fastest
+ *    (v[slot*nb^3 + i + nb*(j + nb*k)]); point i of a level-L leaf with
+ *    anchor a sits at x = (a*nb + i) * tree_len / (nb * 2^L) (vertex-aligned,
+ *    Sec. 2.2: coarse point k coincides with fine point 2k); periodic in every
+ *    direction.  Element type: float for MR_F32, double for MR_F64.
+ *  - Padded layout (ghost fill output): per leaf (nb+2G)^3 values over
+ *    [-G, nb+G)^3, x fastest.
+ */
+#ifndef MRGB_H
+#define MRGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MR_OK 0
+#define MR_ERR_INVALID (-1)     /* bad argument or descriptor */
+#define MR_ERR_NOMEM (-2)       /* workspace or leaf capacity too small */
+#define MR_ERR_CUDA (-3)        /* a CUDA runtime call failed */
+#define MR_ERR_TIMEOUT (-4)     /* a bounded device/host loop hit its cap */
+#define MR_ERR_UNSUPPORTED (-5) /* valid request outside what is built */
+#define MR_ERR_BALANCE (-6)     /* leaves are not 2:1 balanced, or a ghost
+                                   shell reaches beyond the +-1 level ring */
+
+#define MR_F32 0
+#define MR_F64 1
+
+/* right-hand side schemes (supplementary "Finite differences scheme") */
+#define MR_CONS3 0  /* Table SM3 with the ideal weights 1/3, 2/3 */
+#define MR_CONS5 1  /* Table SM4 with the ideal weights 1/10, 3/5, 3/10 */
+#define MR_WENOZ5 2 /* Table SM4 with WENO-Z weights (Borges et al. 2008) */
+
+/* analytic initial fields for mr_field_set */
+#define MR_INIT_GAUSSIAN 0    /* params: cx cy cz sigma amp; nearest image  */
+#define MR_INIT_TANH_SPHERE 1 /* params: cx cy cz radius width             */
+#define MR_INIT_TAYLOR_GREEN 2 /* params: component(0,1,2) scale phase    */
+
+/* adaptation flags */
+#define MR_ADAPT_REFINE 1
+#define MR_ADAPT_COARSEN 2
+
+typedef struct {
+  int ntree[3];     /* trees per direction (the forest tiles the domain)   */
+  double tree_len;  /* edge of one tree                                    */
+  int nb;           /* points per block edge: even, 8..32                  */
+  int lmin, lmax;   /* level bounds used by the adaptation policy          */
+  int wav_N;        /* interpolation order N: 2, 4 or 6                    */
+  int wav_Nt;       /* lifting order N~: 0 or 2                            */
+  int precision;    /* MR_F32 or MR_F64                                    */
+  int nfields;      /* user fields held in the block pool (>= 1)           */
+  int capacity;     /* maximum number of leaves                            */
+  void *stream;     /* cudaStream_t the grid enqueues on (NULL: legacy)    */
+} mr_grid_desc;
+
+typedef struct {
+  int nleaf;
+  int count_per_level[32];
+  int min_level, max_level;
+} mr_stats;
+
+typedef struct mr_grid mr_grid;
+
+/* Last error message recorded by any call in this process (static string). */
+const char *mr_last_error(void);
+
+/* Device workspace (bytes) a grid with this descriptor needs.  Covers the
+ * block pool (nfields user fields, two RK temporaries, and the second pool
+ * adaptation writes into), the padded ghost buffers for the widest shell the
+ * adaptation uses (Table 2.2), and the octree tables (the owner map holds
+ * prod_d ntree[d]*2^lmax int32 entries). */
+int mr_workspace_size(const mr_grid_desc *desc, size_t *bytes);
+
+/* Create a grid on the current CUDA device.  workspace: device pointer,
+ * 256-byte aligned, at least mr_workspace_size bytes, owned by the caller.
+ * lev/anc: host arrays of nleaf leaves (any order) forming a 2:1-balanced
+ * complete forest (face, edge and corner neighbours differ by <= 1 level).
+ * Synchronises.  Errors: MR_ERR_INVALID (bad descriptor, overlapping or
+ * missing leaves), MR_ERR_NOMEM (capacity/workspace), MR_ERR_BALANCE.      */
+int mr_grid_create(const mr_grid_desc *desc, void *workspace, size_t workspace_bytes,
+                   const int32_t *lev, const int32_t *anc, int nleaf, mr_grid **out);
+int mr_grid_destroy(mr_grid *grid);
+
+/* Current leaves in slot (Morton) order and their Morton keys (keys may be
+ * NULL).  Synchronises.  cap: capacity of the host arrays.                 */
+int mr_grid_leaves(mr_grid *grid, int32_t *lev, int32_t *anc, uint64_t *keys, int cap,
+                   int *nleaf);
+
+/* Copy a whole field in (from host or device memory) or out, in the field
+ * layout above with the current leaf count.  Copies to host synchronise.   */
+int mr_field_copy_in(mr_grid *grid, int fid, const void *src, int src_on_device);
+int mr_field_copy_out(mr_grid *grid, int fid, void *dst, int dst_on_device);
+
+/* Evaluate an analytic field on the device at every point (MR_INIT_*). */
+int mr_field_set(mr_grid *grid, int fid, int kind, const double *params, int nparams);
+
+/*
+ * Ghost reconstruction (Alg. SM1 then Alg. SM2, Sec. 2.2.2 and 2.2.4) of
+ * field fid with a shell of G points:
+ *   1. every leaf takes same-level points as copies, points inside a coarser
+ *      leaf from the zero-detail refinement (J^s, K^s) of the coarse-level
+ *      values, points inside a finer leaf as the coincident value;
+ *   2. leaves next to a coarser leaf substitute their band (Table 2.2 coarse
+ *      region extension, mirrored) degree by degree (eqs 2.23, 2.27-2.29);
+ *      the substituted values overwrite the field;
+ *   3. points inside a finer leaf F become the tensor H^a coarsening of F's
+ *      data from steps 1-2.
+ * padded: device buffer of nleaf*(nb+2G)^3 elements receiving the padded
+ * blocks, or NULL (only the substitution of the field happens then).
+ * G: 1..MR_MAX_SHELL(=12) and G <= nb/2 (MR_ERR_BALANCE otherwise).        */
+int mr_ghost_fill(mr_grid *grid, int fid, int G, void *padded);
+
+/* As mr_ghost_fill, but the padded blocks are computed and returned in FP64
+ * (from the stored field values, FP32 fields upcast): the path the
+ * adaptation uses, so that refinement and coarsening decisions do not depend
+ * on FP32 rounding.  padded: nleaf*(nb+2G)^3 doubles or NULL.             */
+int mr_ghost_fill64(mr_grid *grid, int fid, int G, double *padded);
+
+/* Wait for the grid's stream and report device-side errors recorded by the
+ * kernels since the last check (MR_ERR_BALANCE: a ghost point was owned by
+ * a leaf more than one level away, or a shell exceeded the stored padding). */
+int mr_sync(mr_grid *grid);
+
+/* rhs = -sum_d (F_{i+1/2} - F_{i-1/2}) / h for d(phi)/dt + div(u phi) = 0,
+ * with u = u_const (host, 3 doubles).  Includes the ghost fill of phi (and
+ * its substitution).  scheme: MR_CONS3 / MR_CONS5 / MR_WENOZ5.             */
+int mr_rhs_advect(mr_grid *grid, int phi_fid, const double *u_const, int out_fid, int scheme);
+
+/* RK3-TVD stage (supplementary "Time integration scheme"):
+ *   stage 0: out = y + dt*rhs
+ *   stage 1: out = 3/4 u + 1/4 (y + dt*rhs)
+ *   stage 2: out = 1/3 u + 2/3 (y + dt*rhs)
+ * elementwise over the current leaves; out may alias u or y.               */
+int mr_rk_stage(mr_grid *grid, int stage, double dt, int u_fid, int y_fid, int rhs_fid,
+                int out_fid);
+
+/* One RK3 step of phi (in place): three times ghost fill + fused rhs/stage,
+ * using the grid's two internal temporaries.  Constant velocity u_const.   */
+int mr_step(mr_grid *grid, int phi_fid, double dt, const double *u_const, int scheme);
+
+/* Per-leaf max |detail| over the block and its coarse-region extension
+ * (Sec. 2.2.5, eqs 2.24-2.26), computed in FP64 from the field as stored,
+ * after a ghost fill with the adaptation shell.  maxdet: device array of
+ * nleaf doubles.                                                           */
+int mr_criterion(mr_grid *grid, int fid, double *maxdet);
+
+/* Grid adaptation (Alg. SM3) of every field, driven by field crit_fid, run
+ * until no leaf changes (at most 64 iterations, else MR_ERR_TIMEOUT).
+ * flags: MR_ADAPT_REFINE | MR_ADAPT_COARSEN.  Synchronises once per
+ * iteration; *n_changed (may be NULL) receives the total number of leaves
+ * that refined or coarsened.                                               */
+int mr_adapt(mr_grid *grid, int crit_fid, double eps_refine, double eps_coarsen, int flags,
+             int *n_changed);
+
+/* One iteration of mr_adapt; *n_changed receives the leaves changed. */
+int mr_adapt_iter(mr_grid *grid, int crit_fid, double eps_refine, double eps_coarsen,
+                  int flags, int *n_changed);
+
+/* Sum over leaves of h^3 * sum(phi) in FP64 (eq 2.18 with p = 0), written
+ * to *mass (host).  Synchronises.                                          */
+int mr_mass(mr_grid *grid, int fid, double *mass);
+
+/* Leaf counts.  Synchronises. */
+int mr_query(mr_grid *grid, mr_stats *stats);
+
+/* Launch registry (the per-operation timers of the library).
+ * mr_profile(grid, 1) clears the records and brackets every following kernel
+ * launch with CUDA events on the grid's stream (up to 4096 launches);
+ * mr_profile(grid, 0) stops recording.  mr_profile_read synchronises and
+ * returns, for kernel id kid (0 .. MR_NUM_KERNELS-1), the summed device time
+ * of its recorded launches, their number and the kernel's name (static
+ * string).  mr_launch_count returns every kernel launch since creation.    */
+#define MR_NUM_KERNELS 18
+int mr_profile(mr_grid *grid, int enable);
+int mr_profile_read(mr_grid *grid, int kid, double *total_ms, int *nlaunch, const char **name);
+int mr_launch_count(mr_grid *grid, long long *n);
+
+/* Device pointer of field fid (slot-major layout above). */
+int mr_field_ptr(mr_grid *grid, int fid, void **ptr);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MRGB_H */

@@ -1,0 +1,339 @@
+// ghost.cu -- ghost-point reconstruction on the device (Alg. SM1 / SM2).
+//
+// Three kernels, one CTA per leaf:
+//   part1: padded block = interior + same-level copies + zero-detail
+//          refinement of the coarse-level values where a coarser leaf owns
+//          the point + the coincident value where a finer leaf owns it; then
+//          the degree-ordered substitution of the band next to coarser
+//          leaves (Sec. 2.2.4, eqs 2.27-2.29) on the padded block;
+//   part2: points owned by a finer leaf F <- tensor H^a of F's padded block
+//          (written to a side buffer, so every read sees the part1 state);
+//   merge: side buffer -> padded block; substituted interior -> field.
+// The wavelet arithmetic uses explicitly rounded multiply/add in the same
+// order as a plain nested-loop evaluation, so the FP64 instantiation is
+// reproducible bit for bit.
+#include <cstdio>
+
+#include "mr_internal.cuh"
+
+namespace mr {
+
+template <typename T>
+__device__ __forceinline__ T ld(const T *p) { return __ldg(p); }
+
+// Value stored by leaf o (level Lo >= L or a coarse grid point) at level-L
+// point g; flags a balance error through *err when g is not on o's grid.
+template <typename TI>
+__device__ __forceinline__ double leaf_value(const Tree &t, const TI *phi, int o, int L, int gx,
+                                             int gy, int gz, int *err) {
+  const int Lo = __ldg(t.lev + o);
+  const int lx = local_index(t, o, Lo, L, gx, 0);
+  const int ly = local_index(t, o, Lo, L, gy, 1);
+  const int lz = local_index(t, o, Lo, L, gz, 2);
+  const int nb = t.nb;
+  if (lx < 0 || ly < 0 || lz < 0 || lx >= nb || ly >= nb || lz >= nb) {
+    atomicOr(err, 1);
+    return 0.0;
+  }
+  return (double)ld(phi + (size_t)o * nb * nb * nb + lx + nb * (ly + nb * lz));
+}
+
+// Zero-detail refinement at level-L point g from the level-(L-1) values
+// (J^s on even, K^s on odd coordinates; taps landing on details skipped).
+template <typename TI, typename TP, int N, int NT>
+__device__ TP refine_point(const Tree &t, const TI *phi, int L, int gx, int gy, int gz, int *err) {
+  using W = Wav<N, NT>;
+  const bool odx = gx & 1, ody = gy & 1, odz = gz & 1;
+  const int hx = odx ? W::hwK : W::hwJ, hy = ody ? W::hwK : W::hwJ, hz = odz ? W::hwK : W::hwJ;
+  TP s = TP(0);
+  for (int oz = -hz; oz <= hz; ++oz) {
+    if ((gz + oz) & 1) continue;
+    const TP wz = TP(odz ? W::K(oz) : W::J(oz));
+    for (int oy = -hy; oy <= hy; ++oy) {
+      if ((gy + oy) & 1) continue;
+      const TP wy = TP(ody ? W::K(oy) : W::J(oy));
+      for (int ox = -hx; ox <= hx; ++ox) {
+        if ((gx + ox) & 1) continue;
+        const TP wx = TP(odx ? W::K(ox) : W::J(ox));
+        const TP wgt = rmul(rmul(wx, wy), wz);
+        if (wgt == TP(0)) continue;
+        const int qx = (gx + ox) / 2, qy = (gy + oy) / 2, qz = (gz + oz) / 2;
+        const int o = owner(t, L - 1, qx, qy, qz);
+        if (__ldg(t.lev + o) < L - 1) {
+          atomicOr(err, 2);
+          continue;
+        }
+        const TP v = TP(leaf_value(t, phi, o, L - 1, qx, qy, qz, err));
+        s = radd(s, rmul(wgt, v));
+      }
+    }
+  }
+  return s;
+}
+
+__device__ __forceinline__ bool in_band(int mask, int i, int j, int k, int nb, int ef, int eb) {
+  for (int m = 0; m < 27; ++m) {
+    if (!((mask >> m) & 1)) continue;
+    const int d0 = m % 3 - 1, d1 = (m / 3) % 3 - 1, d2 = m / 9 - 1;
+    bool ok = (d0 < 0 ? i < eb : d0 > 0 ? i >= nb - ef : true) &&
+              (d1 < 0 ? j < eb : d1 > 0 ? j >= nb - ef : true) &&
+              (d2 < 0 ? k < eb : d2 > 0 ? k >= nb - ef : true);
+    if (ok) return true;
+  }
+  return false;
+}
+
+// Directions (27-bit mask) toward a coarser neighbour of leaf b.
+__device__ int coarse_mask_dir(const Tree &t, int b, int m, int *err) {
+  if (m == 13) return 0;
+  const int L = __ldg(t.lev + b), nb = t.nb;
+  const int dd[3] = {m % 3 - 1, (m / 3) % 3 - 1, m / 9 - 1};
+  int g[3];
+  for (int d = 0; d < 3; ++d)
+    g[d] = __ldg(t.anc + 3 * b + d) * nb + (dd[d] < 0 ? -1 : dd[d] > 0 ? nb : 0);
+  const int o = owner(t, L, g[0], g[1], g[2]);
+  const int Lo = __ldg(t.lev + o);
+  if (Lo < L - 1 || Lo > L + 1) atomicOr(err, 4);
+  return Lo < L ? (1 << m) : 0;
+}
+
+template <typename TI, typename TP, int N, int NT>
+__global__ void __launch_bounds__(256) k_part1(Tree t, const TI *__restrict__ phi, TP *__restrict__ P,
+                                               int Gi, int *cmask_out, int *err) {
+  using W = Wav<N, NT>;
+  const int b = blockIdx.x;
+  const int nb = t.nb, Wd = nb + 2 * Gi;
+  const size_t np = (size_t)Wd * Wd * Wd;
+  const int L = __ldg(t.lev + b);
+  const int ax = __ldg(t.anc + 3 * b) * nb, ay = __ldg(t.anc + 3 * b + 1) * nb,
+            az = __ldg(t.anc + 3 * b + 2) * nb;
+  __shared__ int cmask;
+  if (threadIdx.x == 0) cmask = 0;
+  __syncthreads();
+  if (threadIdx.x < 27) {
+    int m = coarse_mask_dir(t, b, threadIdx.x, err);
+    if (m) atomicOr(&cmask, m);
+  }
+  TP *Pb = P + (size_t)b * np;
+  const TI *phib = phi + (size_t)b * nb * nb * nb;
+  for (size_t p = threadIdx.x; p < np; p += blockDim.x) {
+    const int i = (int)(p % Wd) - Gi, j = (int)((p / Wd) % Wd) - Gi, k = (int)(p / ((size_t)Wd * Wd)) - Gi;
+    TP v;
+    if (i >= 0 && i < nb && j >= 0 && j < nb && k >= 0 && k < nb) {
+      v = TP(ld(phib + i + nb * (j + nb * k)));
+    } else {
+      const int gx = ax + i, gy = ay + j, gz = az + k;
+      const int o = owner(t, L, gx, gy, gz);
+      const int Lo = __ldg(t.lev + o);
+      if (Lo >= L) {
+        v = TP(leaf_value(t, phi, o, L, gx, gy, gz, err));
+      } else if (Lo == L - 1) {
+        v = refine_point<TI, TP, N, NT>(t, phi, L, gx, gy, gz, err);
+      } else {
+        atomicOr(err, 8);
+        v = TP(0);
+      }
+    }
+    Pb[p] = v;
+  }
+  __syncthreads();
+  const int mask = cmask;
+  if (threadIdx.x == 0 && cmask_out) cmask_out[b] = mask;
+  if (!mask) return;
+  // substitution, degree by degree (points of one degree never read each other)
+  for (int deg = 1; deg <= 3; ++deg) {
+    for (int p = threadIdx.x; p < nb * nb * nb; p += blockDim.x) {
+      const int i = p % nb, j = (p / nb) % nb, k = p / (nb * nb);
+      const int o0 = i & 1, o1 = j & 1, o2 = k & 1;
+      if (o0 + o1 + o2 != deg) continue;
+      if (!in_band(mask, i, j, k, nb, W::ext_f, W::ext_b)) continue;
+      const int hx = o0 ? W::hwG : 0, hy = o1 ? W::hwG : 0, hz = o2 ? W::hwG : 0;
+      TP s = TP(0);
+      for (int tz = -hz; tz <= hz; ++tz)
+        for (int ty = -hy; ty <= hy; ++ty)
+          for (int tx = -hx; tx <= hx; ++tx) {
+            if (!tx && !ty && !tz) continue;
+            const TP wgt = rmul(rmul(TP(o0 ? W::G(tx) : 1.0), TP(o1 ? W::G(ty) : 1.0)),
+                                TP(o2 ? W::G(tz) : 1.0));
+            if (wgt == TP(0)) continue;
+            s = radd(s, rmul(wgt, Pb[(i + tx + Gi) + Wd * ((j + ty + Gi) + (size_t)Wd * (k + tz + Gi))]));
+          }
+      Pb[(i + Gi) + Wd * ((j + Gi) + (size_t)Wd * (k + Gi))] = -s;
+    }
+    __syncthreads();
+  }
+}
+
+// Part 2: ghost points (shell G) owned by a finer leaf F <- tensor H^a of
+// F's padded block, nearest periodic image.  Writes Q only.
+template <typename TP, int N, int NT>
+__global__ void __launch_bounds__(256) k_part2(Tree t, const TP *__restrict__ P, TP *__restrict__ Q,
+                                               int Gi, int G, int *err) {
+  using W = Wav<N, NT>;
+  const int b = blockIdx.x;
+  const int nb = t.nb, Wd = nb + 2 * Gi, Wg = nb + 2 * G;
+  const size_t np = (size_t)Wd * Wd * Wd;
+  const int L = __ldg(t.lev + b);
+  const int a[3] = {__ldg(t.anc + 3 * b) * nb, __ldg(t.anc + 3 * b + 1) * nb, __ldg(t.anc + 3 * b + 2) * nb};
+  for (int p = threadIdx.x; p < Wg * Wg * Wg; p += blockDim.x) {
+    const int i = p % Wg - G, j = (p / Wg) % Wg - G, k = p / (Wg * Wg) - G;
+    if (i >= 0 && i < nb && j >= 0 && j < nb && k >= 0 && k < nb) continue;
+    const int g[3] = {a[0] + i, a[1] + j, a[2] + k};
+    const int F = owner(t, L, g[0], g[1], g[2]);
+    const int LF = __ldg(t.lev + F);
+    if (LF <= L) continue;
+    if (LF > L + 1) {
+      atomicOr(err, 16);
+      continue;
+    }
+    int fl[3];
+    for (int d = 0; d < 3; ++d) {
+      const int Pn = npts(t, L + 1, d);
+      int off = pwrap(2 * g[d] - __ldg(t.anc + 3 * F + d) * nb, Pn);
+      if (off >= Pn / 2) off -= Pn;
+      fl[d] = off;
+    }
+    const TP *PF = P + (size_t)F * np;
+    TP s = TP(0);
+    bool bad = false;
+    for (int tz = -W::hwH; tz <= W::hwH; ++tz)
+      for (int ty = -W::hwH; ty <= W::hwH; ++ty)
+        for (int tx = -W::hwH; tx <= W::hwH; ++tx) {
+          const TP wgt = rmul(rmul(TP(W::H(tx)), TP(W::H(ty))), TP(W::H(tz)));
+          if (wgt == TP(0)) continue;
+          const int qx = fl[0] + tx, qy = fl[1] + ty, qz = fl[2] + tz;
+          if (qx < -Gi || qx >= nb + Gi || qy < -Gi || qy >= nb + Gi || qz < -Gi || qz >= nb + Gi) {
+            bad = true;
+            continue;
+          }
+          s = radd(s, rmul(wgt, PF[(qx + Gi) + Wd * ((qy + Gi) + (size_t)Wd * (qz + Gi))]));
+        }
+    if (bad) atomicOr(err, 32);
+    Q[(size_t)b * np + (i + Gi) + Wd * ((j + Gi) + (size_t)Wd * (k + Gi))] = s;
+  }
+}
+
+// Merge the part-2 values into P and write the substituted interior back to
+// the field of leaves that have a coarser neighbour.
+template <typename TO, typename TP>
+__global__ void __launch_bounds__(256) k_merge(Tree t, TP *__restrict__ P, const TP *__restrict__ Q,
+                                               int Gi, int G, const int *__restrict__ cmask,
+                                               TO *__restrict__ phi_out) {
+  const int b = blockIdx.x;
+  const int nb = t.nb, Wd = nb + 2 * Gi, Wg = nb + 2 * G;
+  const size_t np = (size_t)Wd * Wd * Wd;
+  const int L = __ldg(t.lev + b);
+  const int a[3] = {__ldg(t.anc + 3 * b) * nb, __ldg(t.anc + 3 * b + 1) * nb, __ldg(t.anc + 3 * b + 2) * nb};
+  for (int p = threadIdx.x; p < Wg * Wg * Wg; p += blockDim.x) {
+    const int i = p % Wg - G, j = (p / Wg) % Wg - G, k = p / (Wg * Wg) - G;
+    if (i >= 0 && i < nb && j >= 0 && j < nb && k >= 0 && k < nb) continue;
+    const int F = owner(t, L, a[0] + i, a[1] + j, a[2] + k);
+    if (__ldg(t.lev + F) != L + 1) continue;
+    const size_t q = (size_t)b * np + (i + Gi) + Wd * ((j + Gi) + (size_t)Wd * (k + Gi));
+    P[q] = Q[q];
+  }
+  if (phi_out && cmask[b]) {
+    for (int p = threadIdx.x; p < nb * nb * nb; p += blockDim.x) {
+      const int i = p % nb, j = (p / nb) % nb, k = p / (nb * nb);
+      if (!((i | j | k) & 1)) continue;  // 0-degree points are never substituted
+      phi_out[(size_t)b * nb * nb * nb + p] =
+          TO(P[(size_t)b * np + (i + Gi) + Wd * ((j + Gi) + (size_t)Wd * (k + Gi))]);
+    }
+  }
+}
+
+template <typename TO, typename TP>
+__global__ void k_crop(const TP *__restrict__ P, int Gi, TO *__restrict__ out, int G, int nb) {
+  const int b = blockIdx.x;
+  const int Wd = nb + 2 * Gi, Wg = nb + 2 * G;
+  const size_t np = (size_t)Wd * Wd * Wd, ng = (size_t)Wg * Wg * Wg;
+  for (size_t p = threadIdx.x; p < ng; p += blockDim.x) {
+    const int i = (int)(p % Wg), j = (int)((p / Wg) % Wg), k = (int)(p / ((size_t)Wg * Wg));
+    out[(size_t)b * ng + p] =
+        TO(P[(size_t)b * np + (i - G + Gi) + Wd * ((j - G + Gi) + (size_t)Wd * (k - G + Gi))]);
+  }
+}
+
+// internal shell: the requested one, the substitution reach, and what the
+// part-2 coarsening of a finer neighbour reads
+static int internal_shell(int N, int Nt, int G, int nb) {
+  const int hwH = Nt ? N : 0, hwG = N - 1;
+  int gi = G;
+  if (hwH > gi) gi = hwH;
+  if (hwG > gi) gi = hwG;
+  if (2 * G + hwH - nb > gi) gi = 2 * G + hwH - nb;
+  return gi;
+}
+
+template <typename TI, typename TP, int N, int NT>
+static int ghost_impl(mr_grid *g, const TI *phi_in, TI *phi_out, int G, TP *P, TP *Q, int Gi) {
+  Tree t = tree_view(g);
+  const int n = g->nleaf;
+  int *err = g->counter + 1;
+  int *cm = g->cmask;
+  MR_LAUNCH(g, MRK_PART1, k_part1<TI, TP, N, NT><<<n, 256, 0, g->stream>>>(t, phi_in, P, Gi, cm, err));
+  if (check_cuda(cudaGetLastError(), "k_part1")) return MR_ERR_CUDA;
+  MR_LAUNCH(g, MRK_PART2, k_part2<TP, N, NT><<<n, 256, 0, g->stream>>>(t, P, Q, Gi, G, err));
+  if (check_cuda(cudaGetLastError(), "k_part2")) return MR_ERR_CUDA;
+  MR_LAUNCH(g, MRK_MERGE, k_merge<TI, TP><<<n, 256, 0, g->stream>>>(t, P, Q, Gi, G, cm, phi_out));
+  if (check_cuda(cudaGetLastError(), "k_merge")) return MR_ERR_CUDA;
+  return MR_OK;
+}
+
+template <typename TI, typename TP>
+static int ghost_dispatch(mr_grid *g, const TI *phi_in, TI *phi_out, int G, TP *P, TP *Q, int Gi) {
+  const int N = g->desc.wav_N, Nt = g->desc.wav_Nt;
+#define MR_GCASE(n_, nt_) \
+  if (N == n_ && Nt == nt_) return ghost_impl<TI, TP, n_, nt_>(g, phi_in, phi_out, G, P, Q, Gi);
+  MR_GCASE(2, 0) MR_GCASE(2, 2) MR_GCASE(4, 0) MR_GCASE(4, 2) MR_GCASE(6, 0) MR_GCASE(6, 2)
+#undef MR_GCASE
+  return MR_ERR_UNSUPPORTED;
+}
+
+// Ghost fill of phi_in with requested shell G.  fp64: padded buffers in FP64
+// (the adaptation path), else in the field's element type.  On return *P is
+// the padded buffer (internal shell *Gi).
+int launch_ghost(mr_grid *g, const void *phi_in, void *phi_out, int G, bool fp64, void **P, int *Gi) {
+  const int nb = g->desc.nb;
+  if (G < 1 || G > MR_MAX_SHELL) return MR_ERR_INVALID;
+  if (G > nb / 2) return MR_ERR_BALANCE;
+  const int gi = internal_shell(g->desc.wav_N, g->desc.wav_Nt, G, nb);
+  const int cap = fp64 ? g->shell_ad : g->shell_rk;
+  if (gi > cap) return MR_ERR_UNSUPPORTED;
+  *Gi = gi;
+  const bool f32 = g->desc.precision == MR_F32;
+  if (fp64) {
+    *P = g->padP64;
+    if (f32)
+      return ghost_dispatch<float, double>(g, (const float *)phi_in, (float *)phi_out, G, g->padP64,
+                                           g->padQ64, gi);
+    return ghost_dispatch<double, double>(g, (const double *)phi_in, (double *)phi_out, G, g->padP64,
+                                          g->padQ64, gi);
+  }
+  *P = g->padP;
+  if (f32)
+    return ghost_dispatch<float, float>(g, (const float *)phi_in, (float *)phi_out, G,
+                                        (float *)g->padP, (float *)g->padQ, gi);
+  return ghost_dispatch<double, double>(g, (const double *)phi_in, (double *)phi_out, G,
+                                        (double *)g->padP, (double *)g->padQ, gi);
+}
+
+int launch_crop64(mr_grid *g, const double *P, int Gi, double *out, int G) {
+  MR_LAUNCH(g, MRK_CROP, k_crop<double, double><<<g->nleaf, 256, 0, g->stream>>>(P, Gi, out, G, g->desc.nb));
+  return check_cuda(cudaGetLastError(), "k_crop64") ? MR_ERR_CUDA : MR_OK;
+}
+
+int launch_crop(mr_grid *g, const void *P, int Gi, void *out, int G, bool fp64_src) {
+  const int n = g->nleaf, nb = g->desc.nb;
+  const bool f32 = g->desc.precision == MR_F32;
+  if (fp64_src) {
+    if (f32) MR_LAUNCH(g, MRK_CROP, k_crop<float, double><<<n, 256, 0, g->stream>>>((const double *)P, Gi, (float *)out, G, nb));
+    else MR_LAUNCH(g, MRK_CROP, k_crop<double, double><<<n, 256, 0, g->stream>>>((const double *)P, Gi, (double *)out, G, nb));
+  } else {
+    if (f32) MR_LAUNCH(g, MRK_CROP, k_crop<float, float><<<n, 256, 0, g->stream>>>((const float *)P, Gi, (float *)out, G, nb));
+    else MR_LAUNCH(g, MRK_CROP, k_crop<double, double><<<n, 256, 0, g->stream>>>((const double *)P, Gi, (double *)out, G, nb));
+  }
+  return check_cuda(cudaGetLastError(), "k_crop") ? MR_ERR_CUDA : MR_OK;
+}
+
+}  // namespace mr

@@ -1,0 +1,219 @@
+// mr_internal.cuh -- device-side data structures and wavelet filters shared
+// by the CUDA translation units of the library (not by the CPU oracle).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mrgb.h"
+
+#define MR_MAX_SHELL 12
+#define MR_MAX_LEVEL 16
+
+namespace mr {
+
+// ---------------------------------------------------------------------------
+// Interpolating-wavelet filters, Tables SM1 (N.0) and SM2 (N.2), indexed by
+// the fine-grid offset o from the filter centre.  Every filter of the family
+// is symmetric.  All coefficients are dyadic rationals, exact in FP32.
+// ---------------------------------------------------------------------------
+template <int N, int NT>
+struct Wav {
+  static constexpr int hwH = (NT == 0) ? 0 : N;       // H^a half-width
+  static constexpr int hwG = N - 1;                   // G^a half-width
+  static constexpr int hwJ = (NT == 0) ? 0 : 1;       // J^s half-width
+  static constexpr int hwK = (NT == 0) ? N - 1 : N;   // K^s half-width
+  // Table 2.2 "coarse region extension", 3D column
+  static constexpr int ext_f = (NT == 0) ? N - 2 : N - 1;
+  static constexpr int ext_b = ext_f + 1;
+  static constexpr int hmax = hwH > hwG ? hwH : hwG;
+
+  __host__ __device__ static constexpr double H(int o) {
+    const int a = o < 0 ? -o : o;
+    if (NT == 0) return a == 0 ? 1.0 : 0.0;
+    if (N == 2) return a == 0 ? 3.0 / 4 : a == 1 ? 1.0 / 4 : a == 2 ? -1.0 / 8 : 0.0;
+    if (N == 4)
+      return a == 0 ? 23.0 / 32 : a == 1 ? 1.0 / 4 : a == 2 ? -1.0 / 8 : a == 4 ? 1.0 / 64 : 0.0;
+    return a == 0 ? 181.0 / 256 : a == 1 ? 1.0 / 4 : a == 2 ? -125.0 / 1024
+         : a == 4 ? 11.0 / 512 : a == 6 ? -3.0 / 1024 : 0.0;
+  }
+  __host__ __device__ static constexpr double G(int o) {
+    const int a = o < 0 ? -o : o;
+    if (a == 0) return 1.0;
+    if (N == 2) return a == 1 ? -1.0 / 2 : 0.0;
+    if (N == 4) return a == 1 ? -9.0 / 16 : a == 3 ? 1.0 / 16 : 0.0;
+    return a == 1 ? -75.0 / 128 : a == 3 ? 25.0 / 256 : a == 5 ? -3.0 / 256 : 0.0;
+  }
+  __host__ __device__ static constexpr double J(int o) {
+    const int a = o < 0 ? -o : o;
+    if (NT == 0) return a == 0 ? 1.0 : 0.0;
+    return a == 0 ? 1.0 : a == 1 ? -1.0 / 4 : 0.0;
+  }
+  __host__ __device__ static constexpr double K(int o) {
+    const int a = o < 0 ? -o : o;
+    if (NT == 0) {
+      if (a == 0) return 1.0;
+      if (N == 2) return a == 1 ? 1.0 / 2 : 0.0;
+      if (N == 4) return a == 1 ? 9.0 / 16 : a == 3 ? -1.0 / 16 : 0.0;
+      return a == 1 ? 75.0 / 128 : a == 3 ? -25.0 / 256 : a == 5 ? 3.0 / 256 : 0.0;
+    }
+    if (N == 2) return a == 0 ? 3.0 / 4 : a == 1 ? 1.0 / 2 : a == 2 ? -1.0 / 8 : 0.0;
+    if (N == 4)
+      return a == 0 ? 23.0 / 32 : a == 1 ? 9.0 / 16 : a == 2 ? -1.0 / 8 : a == 3 ? -1.0 / 16
+           : a == 4 ? 1.0 / 64 : 0.0;
+    return a == 0 ? 181.0 / 256 : a == 1 ? 75.0 / 128 : a == 2 ? -125.0 / 1024
+         : a == 3 ? -25.0 / 256 : a == 4 ? 11.0 / 512 : a == 5 ? 3.0 / 256
+         : a == 6 ? -3.0 / 1024 : 0.0;
+  }
+};
+
+// Rounded (never fused) arithmetic for the wavelet paths: the FP64 ghost
+// fill and criterion reproduce a fixed evaluation order bit for bit.
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+
+// ---------------------------------------------------------------------------
+// Device view of the octree: leaves in Morton order (slot = rank) and a dense
+// owner map at level M (the grid's lmax): map[cell] = slot of the leaf whose
+// region contains that level-M block cell.
+// ---------------------------------------------------------------------------
+struct Tree {
+  int nt[3];
+  int nb;
+  int M;          // level of the owner map
+  int nleaf;
+  int mdim[3];    // nt[d] << M
+  const int *lev; // [slot]
+  const int *anc; // [3*slot + d], anchor at the leaf's own level
+  const int *map; // mdim[0]*mdim[1]*mdim[2]
+  double tree_len;
+};
+
+__device__ __forceinline__ int pwrap(int g, int P) {
+  int r = g % P;
+  return r < 0 ? r + P : r;
+}
+
+// points along dimension d at level L
+__device__ __forceinline__ int npts(const Tree &t, int L, int d) { return (t.nt[d] * t.nb) << L; }
+
+// slot owning level-L point g (any integers; wrapped periodically)
+__device__ __forceinline__ int owner(const Tree &t, int L, int gx, int gy, int gz) {
+  const int s = t.M - L;
+  int cx = (pwrap(gx, npts(t, L, 0)) << s) / t.nb;
+  int cy = (pwrap(gy, npts(t, L, 1)) << s) / t.nb;
+  int cz = (pwrap(gz, npts(t, L, 2)) << s) / t.nb;
+  return __ldg(t.map + cx + t.mdim[0] * (cy + t.mdim[1] * cz));
+}
+
+// local index (in leaf o, level Lo >= L... or grid point of a coarser leaf)
+// of level-L point g along dimension d; returns -1 if not a grid point.
+__device__ __forceinline__ int local_index(const Tree &t, int o, int Lo, int L, int g, int d) {
+  int gg = pwrap(g, npts(t, L, d));
+  int q;
+  if (Lo >= L) {
+    q = gg << (Lo - L);
+  } else {
+    int s = L - Lo;
+    if (gg & ((1 << s) - 1)) return -1;
+    q = gg >> s;
+  }
+  return q - __ldg(t.anc + 3 * o + d) * t.nb;
+}
+
+}  // namespace mr
+
+// ---------------------------------------------------------------------------
+// Host-side grid object (opaque to the C ABI)
+// ---------------------------------------------------------------------------
+struct mr_grid {
+  mr_grid_desc desc;
+  cudaStream_t stream;
+  int dev;
+  int nleaf;
+  int M;
+  size_t nb3;
+  size_t esize;           // sizeof element
+  // workspace carving
+  char *ws;
+  size_t ws_bytes;
+  // tree tables (two copies: current and next during adaptation)
+  int *lev[2], *anc[2];
+  int cur;                // which tree copy is current
+  int *maps[2];           // owner maps of the two tree copies
+  int *map;               // maps[cur]
+  size_t map_cells;
+  unsigned long long *keys[2];
+  // fields: nfields user + 2 temporaries, two pools (current/next)
+  void *pool[2];          // each: (nfields+2) * capacity * nb3 elements
+  int pool_cur;
+  // ghost buffers: padded P and part-2 Q, FP64 (adaptation) and element type
+  void *padP;             // capacity * W^3 * esize (RK shell)
+  void *padQ;
+  double *padP64;         // capacity * Wa^3 doubles (adaptation shell)
+  double *padQ64;
+  int shell_rk;           // internal shell of padP
+  int shell_ad;           // internal shell of padP64
+  // per-leaf scratch
+  double *maxdet;         // capacity
+  int8_t *status;         // capacity
+  int *refined;           // capacity (two copies)
+  int *refined2;
+  int *scan;              // capacity + 1
+  int *newsrc;            // 8*capacity: source mapping of new leaves
+  int *counter;           // device words: [0] changed count, [1] error bits, [2..] scratch
+  double *dscratch;       // reduction scratch
+  int *cmask;             // per-leaf coarse-direction masks (ghost fill)
+  // launch registry: counts every kernel launch; with profiling on, brackets
+  // each launch with CUDA events on the grid's stream
+  long long launches[32];
+  int profiling;
+  int nrec;
+  int rec_kid[4096];
+  cudaEvent_t ev[2][4096];
+  int ev_ready;
+};
+
+// kernel ids of the launch registry
+enum {
+  MRK_PART1 = 0, MRK_PART2, MRK_MERGE, MRK_CROP, MRK_RHS, MRK_COMBINE, MRK_FIELDSET, MRK_MASS,
+  MRK_MAP, MRK_BALANCE, MRK_CRITERION, MRK_STATUS, MRK_POLICY, MRK_SCAN, MRK_EMIT, MRK_INTERP,
+  MRK_UPDATE, MRK_MISC, MRK_COUNT
+};
+
+// helpers implemented in the .cu files
+namespace mr {
+void kt_begin(mr_grid *g, int kid);
+void kt_end(mr_grid *g);
+#define MR_LAUNCH(g, kid, ...)    \
+  do {                            \
+    mr::kt_begin((g), (kid));     \
+    __VA_ARGS__;                  \
+    mr::kt_end((g));              \
+  } while (0)
+mr::Tree tree_view(const mr_grid *g);
+int set_error(const char *msg);
+int check_cuda(cudaError_t e, const char *where);
+void *field_ptr(mr_grid *g, int fid);      // fid >= nfields: temporaries
+void *next_field_ptr(mr_grid *g, int fid);
+
+// ghost.cu
+int launch_ghost(mr_grid *g, const void *phi_in, void *phi_out, int G, bool fp64, void **P,
+                 int *Gi);
+int launch_crop(mr_grid *g, const void *P, int Gi, void *out, int G, bool fp64_src);
+int launch_crop64(mr_grid *g, const double *P, int Gi, double *out, int G);
+int adapt_shell(int N, int Nt);
+// stencil.cu
+int launch_rhs_stage(mr_grid *g, const void *P, int Gi, const void *u, void *out, int stage,
+                     double dt, const double *uc, int scheme, bool rhs_only);
+int launch_rk_combine(mr_grid *g, int stage, double dt, const void *u, const void *y,
+                      const void *r, void *out);
+int launch_field_set(mr_grid *g, void *f, int kind, const double *p, int np);
+int launch_mass(mr_grid *g, const void *f, double *host_out);
+// adapt.cu
+int launch_criterion(mr_grid *g, const double *P64, int Gi, double *maxdet);
+int adapt_iteration(mr_grid *g, int crit_fid, double er, double ec, int flags, int *nch);
+int build_map(mr_grid *g);
+int check_balance(mr_grid *g);
+}  // namespace mr

@@ -1,0 +1,255 @@
+// stencil.cu -- advection right-hand side fused with the RK3-TVD stage,
+// analytic field initialisation and the FP64 mass reduction.
+#include <cmath>
+
+#include "mr_internal.cuh"
+
+namespace mr {
+
+// WENO-Z: tau5 = |b0 - b2|, alpha_k = gamma_k (1 + r_k^2), r_k = tau5/(b_k+eps)
+// capped at 1e15 so r_k^2 stays finite in FP32.
+template <typename T>
+struct WenoC {
+  static constexpr double eps = 1e-30;
+  static constexpr double rcap = 1e15;
+};
+
+// Interface flux F_{i+1/2} from f[0..5] = f_{i-2..i+3} (Tables SM3 / SM4).
+template <typename T, int SCHEME>
+__device__ __forceinline__ T iface_flux(const T *f, bool left) {
+  if (SCHEME == MR_CONS3) {
+    if (left) {
+      const T s0 = T(-0.5) * f[1] + T(1.5) * f[2], s1 = T(0.5) * f[2] + T(0.5) * f[3];
+      return T(1.0 / 3) * s0 + T(2.0 / 3) * s1;
+    }
+    const T s0 = T(0.5) * f[2] + T(0.5) * f[3], s1 = T(1.5) * f[3] - T(0.5) * f[4];
+    return T(2.0 / 3) * s0 + T(1.0 / 3) * s1;
+  }
+  T a, b, c, d, e, g0, g1, g2, s0, s1, s2;
+  if (left) {
+    a = f[0], b = f[1], c = f[2], d = f[3], e = f[4];
+    s0 = T(1.0 / 3) * a - T(7.0 / 6) * b + T(11.0 / 6) * c;
+    s1 = T(-1.0 / 6) * b + T(5.0 / 6) * c + T(1.0 / 3) * d;
+    s2 = T(1.0 / 3) * c + T(5.0 / 6) * d - T(1.0 / 6) * e;
+    g0 = T(0.1), g1 = T(0.6), g2 = T(0.3);
+  } else {
+    a = f[1], b = f[2], c = f[3], d = f[4], e = f[5];
+    s0 = T(-1.0 / 6) * a + T(5.0 / 6) * b + T(1.0 / 3) * c;
+    s1 = T(1.0 / 3) * b + T(5.0 / 6) * c - T(1.0 / 6) * d;
+    s2 = T(11.0 / 6) * c - T(7.0 / 6) * d + T(1.0 / 3) * e;
+    g0 = T(0.3), g1 = T(0.6), g2 = T(0.1);
+  }
+  if (SCHEME == MR_CONS5) return g0 * s0 + g1 * s1 + g2 * s2;
+  const T t0 = a - T(4) * b + T(3) * c, u0 = a - T(2) * b + c;
+  const T t1 = d - b, u1 = b - T(2) * c + d;
+  const T t2 = T(-3) * c + T(4) * d - e, u2 = c - T(2) * d + e;
+  const T b0 = T(0.25) * t0 * t0 + T(13.0 / 12) * u0 * u0;
+  const T b1 = T(0.25) * t1 * t1 + T(13.0 / 12) * u1 * u1;
+  const T b2 = T(0.25) * t2 * t2 + T(13.0 / 12) * u2 * u2;
+  const T tau = fabs(b0 - b2);
+  const T eps = T(WenoC<T>::eps), cap = T(WenoC<T>::rcap);
+  T r0 = tau / (b0 + eps), r1 = tau / (b1 + eps), r2 = tau / (b2 + eps);
+  r0 = r0 > cap ? cap : r0;
+  r1 = r1 > cap ? cap : r1;
+  r2 = r2 > cap ? cap : r2;
+  const T a0 = g0 * (T(1) + r0 * r0), a1 = g1 * (T(1) + r1 * r1), a2 = g2 * (T(1) + r2 * r2);
+  return (a0 * s0 + a1 * s1 + a2 * s2) / (a0 + a1 + a2);
+}
+
+// One CTA per leaf: rhs from the padded block P (shell Gi >= 3), then the RK
+// stage combination (or the bare rhs).  u: u^n (stages 1, 2), may alias out.
+template <typename T, int SCHEME>
+__global__ void __launch_bounds__(256) k_rhs_stage(Tree t, const T *__restrict__ P, int Gi,
+                                                   const T *u, T *out, int stage, T dt, T ux, T uy,
+                                                   T uz, int rhs_only) {
+  const int b = blockIdx.x;
+  const int nb = t.nb, Wd = nb + 2 * Gi;
+  const size_t np = (size_t)Wd * Wd * Wd;
+  const T h = T(t.tree_len / ((double)nb * (double)(1 << __ldg(t.lev + b))));
+  const T *Pb = P + (size_t)b * np;
+  const T uc[3] = {ux, uy, uz};
+  const int stride[3] = {1, Wd, Wd * Wd};
+  for (int p = threadIdx.x; p < nb * nb * nb; p += blockDim.x) {
+    const int i = p % nb, j = (p / nb) % nb, k = p / (nb * nb);
+    const size_t c = (i + Gi) + Wd * ((j + Gi) + (size_t)Wd * (k + Gi));
+    T acc = T(0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (uc[d] == T(0)) continue;
+      T f[7];
+#pragma unroll
+      for (int m = 0; m < 7; ++m) f[m] = uc[d] * Pb[c + (ptrdiff_t)(m - 3) * stride[d]];
+      const bool left = uc[d] >= T(0);
+      acc += iface_flux<T, SCHEME>(f + 1, left) - iface_flux<T, SCHEME>(f, left);
+    }
+    const T r = -acc / h;
+    const size_t q = (size_t)b * nb * nb * nb + p;
+    if (rhs_only) {
+      out[q] = r;
+    } else {
+      const T v = Pb[c] + dt * r;
+      T o;
+      if (stage == 0) o = v;
+      else if (stage == 1) o = T(0.75) * u[q] + T(0.25) * v;
+      else o = T(1.0 / 3) * u[q] + T(2.0 / 3) * v;
+      out[q] = o;
+    }
+  }
+}
+
+template <typename T>
+static int rhs_dispatch(mr_grid *g, const T *P, int Gi, const T *u, T *out, int stage, double dt,
+                        const double *uc, int scheme, bool rhs_only) {
+  Tree t = tree_view(g);
+  const int n = g->nleaf;
+  const T ux = T(uc[0]), uy = T(uc[1]), uz = T(uc[2]);
+  if (scheme == MR_CONS3)
+    MR_LAUNCH(g, MRK_RHS, k_rhs_stage<T, MR_CONS3><<<n, 256, 0, g->stream>>>(t, P, Gi, u, out, stage, T(dt), ux, uy, uz, rhs_only));
+  else if (scheme == MR_CONS5)
+    MR_LAUNCH(g, MRK_RHS, k_rhs_stage<T, MR_CONS5><<<n, 256, 0, g->stream>>>(t, P, Gi, u, out, stage, T(dt), ux, uy, uz, rhs_only));
+  else if (scheme == MR_WENOZ5)
+    MR_LAUNCH(g, MRK_RHS, k_rhs_stage<T, MR_WENOZ5><<<n, 256, 0, g->stream>>>(t, P, Gi, u, out, stage, T(dt), ux, uy, uz, rhs_only));
+  else
+    return MR_ERR_INVALID;
+  return check_cuda(cudaGetLastError(), "k_rhs_stage") ? MR_ERR_CUDA : MR_OK;
+}
+
+int launch_rhs_stage(mr_grid *g, const void *P, int Gi, const void *u, void *out, int stage,
+                     double dt, const double *uc, int scheme, bool rhs_only) {
+  if (Gi < 3) return MR_ERR_INVALID;
+  if (g->desc.precision == MR_F32)
+    return rhs_dispatch<float>(g, (const float *)P, Gi, (const float *)u, (float *)out, stage, dt, uc,
+                               scheme, rhs_only);
+  return rhs_dispatch<double>(g, (const double *)P, Gi, (const double *)u, (double *)out, stage, dt,
+                              uc, scheme, rhs_only);
+}
+
+template <typename T>
+__global__ void k_rk_combine(size_t n, int stage, T dt, const T *u, const T *y, const T *r, T *out) {
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+    const T v = y[q] + dt * r[q];
+    T o;
+    if (stage == 0) o = v;
+    else if (stage == 1) o = T(0.75) * u[q] + T(0.25) * v;
+    else o = T(1.0 / 3) * u[q] + T(2.0 / 3) * v;
+    out[q] = o;
+  }
+}
+
+int launch_rk_combine(mr_grid *g, int stage, double dt, const void *u, const void *y, const void *r,
+                      void *out) {
+  const size_t n = (size_t)g->nleaf * g->nb3;
+  const int blocks = 152 * 8;
+  if (g->desc.precision == MR_F32)
+    MR_LAUNCH(g, MRK_COMBINE, k_rk_combine<float><<<blocks, 256, 0, g->stream>>>(n, stage, (float)dt, (const float *)u,
+                                                        (const float *)y, (const float *)r, (float *)out));
+  else
+    MR_LAUNCH(g, MRK_COMBINE, k_rk_combine<double><<<blocks, 256, 0, g->stream>>>(n, stage, dt, (const double *)u,
+                                                         (const double *)y, (const double *)r,
+                                                         (double *)out));
+  return check_cuda(cudaGetLastError(), "k_rk_combine") ? MR_ERR_CUDA : MR_OK;
+}
+
+// ---------------------------------------------------------------- analytic
+struct InitParams {
+  double p[8];
+};
+
+__device__ __forceinline__ double pdelta(double x, double c, double ext) {
+  double d = x - c;
+  return d - ext * rint(d / ext);
+}
+
+template <typename T>
+__global__ void k_field_set(Tree t, T *f, int kind, InitParams ip) {
+  const int b = blockIdx.x, nb = t.nb;
+  const int L = __ldg(t.lev + b);
+  const double h = t.tree_len / ((double)nb * (double)(1 << L));
+  const double ext[3] = {t.nt[0] * t.tree_len, t.nt[1] * t.tree_len, t.nt[2] * t.tree_len};
+  for (int p = threadIdx.x; p < nb * nb * nb; p += blockDim.x) {
+    const int i = p % nb, j = (p / nb) % nb, k = p / (nb * nb);
+    const double x[3] = {(__ldg(t.anc + 3 * b) * nb + i) * h, (__ldg(t.anc + 3 * b + 1) * nb + j) * h,
+                         (__ldg(t.anc + 3 * b + 2) * nb + k) * h};
+    double v = 0.0;
+    if (kind == MR_INIT_GAUSSIAN) {
+      double r2 = 0.0;
+      for (int d = 0; d < 3; ++d) {
+        const double dd = pdelta(x[d], ip.p[d], ext[d]);
+        r2 += dd * dd;
+      }
+      v = ip.p[4] * exp(-r2 / (ip.p[3] * ip.p[3]));
+    } else if (kind == MR_INIT_TANH_SPHERE) {
+      double r2 = 0.0;
+      for (int d = 0; d < 3; ++d) {
+        const double dd = pdelta(x[d], ip.p[d], ext[d]);
+        r2 += dd * dd;
+      }
+      v = 0.5 * (1.0 - tanh((sqrt(r2) - ip.p[3]) / ip.p[4]));
+    } else if (kind == MR_INIT_TAYLOR_GREEN) {
+      const double w = 2.0 * M_PI, s = ip.p[1], ph = ip.p[2];
+      const int comp = (int)ip.p[0];
+      if (comp == 0) v = s * sin(w * x[0] + ph) * cos(w * x[1]) * cos(w * x[2]);
+      else if (comp == 1) v = -s * cos(w * x[0] + ph) * sin(w * x[1]) * cos(w * x[2]);
+      else v = 0.0;
+    }
+    f[(size_t)b * nb * nb * nb + p] = T(v);
+  }
+}
+
+int launch_field_set(mr_grid *g, void *f, int kind, const double *p, int np) {
+  InitParams ip{};
+  for (int i = 0; i < np && i < 8; ++i) ip.p[i] = p[i];
+  Tree t = tree_view(g);
+  if (g->desc.precision == MR_F32)
+    MR_LAUNCH(g, MRK_FIELDSET, k_field_set<float><<<g->nleaf, 256, 0, g->stream>>>(t, (float *)f, kind, ip));
+  else
+    MR_LAUNCH(g, MRK_FIELDSET, k_field_set<double><<<g->nleaf, 256, 0, g->stream>>>(t, (double *)f, kind, ip));
+  return check_cuda(cudaGetLastError(), "k_field_set") ? MR_ERR_CUDA : MR_OK;
+}
+
+// FP64 mass: per-leaf sums (fixed order within a CTA), then one CTA sums the
+// per-leaf partials in slot order: deterministic for a given leaf count.
+template <typename T>
+__global__ void k_mass_leaf(Tree t, const T *f, double *part) {
+  const int b = blockIdx.x, nb = t.nb;
+  const double h = t.tree_len / ((double)nb * (double)(1 << __ldg(t.lev + b)));
+  double s = 0.0;
+  for (int p = threadIdx.x; p < nb * nb * nb; p += blockDim.x) s += (double)f[(size_t)b * nb * nb * nb + p];
+  __shared__ double red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[b] = red[0] * h * h * h;
+}
+
+__global__ void k_sum_serial(const double *part, int n, double *out) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+int launch_mass(mr_grid *g, const void *f, double *host_out) {
+  Tree t = tree_view(g);
+  if (g->desc.precision == MR_F32)
+    MR_LAUNCH(g, MRK_MASS, k_mass_leaf<float><<<g->nleaf, 256, 0, g->stream>>>(t, (const float *)f, g->maxdet));
+  else
+    MR_LAUNCH(g, MRK_MASS, k_mass_leaf<double><<<g->nleaf, 256, 0, g->stream>>>(t, (const double *)f, g->maxdet));
+  MR_LAUNCH(g, MRK_MASS, k_sum_serial<<<1, 256, 0, g->stream>>>(g->maxdet, g->nleaf, g->dscratch));
+  if (check_cuda(cudaGetLastError(), "k_mass")) return MR_ERR_CUDA;
+  if (check_cuda(cudaMemcpyAsync(host_out, g->dscratch, sizeof(double), cudaMemcpyDeviceToHost, g->stream),
+                 "mass copy"))
+    return MR_ERR_CUDA;
+  return check_cuda(cudaStreamSynchronize(g->stream), "mass sync") ? MR_ERR_CUDA : MR_OK;
+}
+
+}  // namespace mr

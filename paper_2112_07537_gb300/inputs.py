@@ -99,7 +99,7 @@ def tree_sphere(nt, tree_len, base, radii, centre=(0.5, 0.5, 0.5)):
     lev, anc = uniform_leaves(nt, base)
     for k, r in enumerate(radii):
         lev, anc = refine_in_ball(nt, tree_len, lev, anc, centre, r, base + k)
-        lev, anc = balance(nt, lev, anc)
+        lev, anc = balance_fast(nt, lev, anc)
     return lev, anc
 
 
@@ -195,3 +195,57 @@ def polynomial(xyz, coeffs, degree, x0=(0.5, 0.5, 0.5)):
 def dyadic_random(shape, rng, bits=10):
     """Random values on a dyadic grid k/2^bits (exact in FP32 and FP64)."""
     return rng.integers(-(1 << bits), 1 << bits, size=shape).astype(np.float64) / (1 << bits)
+
+
+# ------------------------------------------------------ large-tree helpers
+def _level_map(nt, lev, anc, M):
+    """Dense map at level M of the level of the leaf covering each cell."""
+    D = np.zeros((nt[2] << M, nt[1] << M, nt[0] << M), np.int8)
+    for L in np.unique(lev):
+        s = 1 << (M - L)
+        a = anc[lev == L]
+        V = np.zeros((nt[2] << L, nt[1] << L, nt[0] << L), np.int8)
+        V[a[:, 2], a[:, 1], a[:, 0]] = L + 1
+        D = np.maximum(D, np.repeat(np.repeat(np.repeat(V, s, 0), s, 1), s, 2))
+    return D - 1
+
+
+def balance_fast(nt, lev, anc, max_iter=32):
+    """2:1 balance (face, edge, corner; periodic) with a dense level map:
+    refine every leaf that touches a leaf two or more levels finer."""
+    from scipy.ndimage import maximum_filter
+    for _ in range(max_iter):
+        M = int(lev.max())
+        D = _level_map(nt, lev, anc, M)
+        Dn = maximum_filter(D, size=3, mode="wrap")
+        need = np.zeros(len(lev), bool)
+        for L in np.unique(lev):
+            s = 1 << (M - L)
+            Z, Y, X = Dn.shape
+            B = Dn.reshape(Z // s, s, Y // s, s, X // s, s).max(axis=(1, 3, 5))
+            idx = np.nonzero(lev == L)[0]
+            a = anc[idx]
+            need[idx] = B[a[:, 2], a[:, 1], a[:, 0]] > L + 1
+        if not need.any():
+            return lev, anc
+        lev, anc = refine_leaves(lev, anc, need)
+    raise RuntimeError("balance did not converge")
+
+
+def tree_shell(nt, tree_len, base, top, radius, widths, centre=(0.5, 0.5, 0.5)):
+    """Uniform at `base`; then at each level L < top refine the leaves whose
+    box comes within widths[L-base] of the sphere |x - c| = radius
+    (periodic); 2:1 balanced."""
+    lev, anc = uniform_leaves(nt, base)
+    ext = np.asarray(nt, float) * tree_len
+    for k, L in enumerate(range(base, top)):
+        c, size = block_centres(nt, tree_len, lev, anc)
+        d = np.abs(c - np.asarray(centre))
+        d = np.minimum(d, ext - d)
+        half = 0.5 * size[:, None]
+        near = np.sqrt((np.maximum(d - half, 0.0) ** 2).sum(1))
+        far = np.sqrt(((d + half) ** 2).sum(1))
+        hit = (near <= radius + widths[k]) & (far >= radius - widths[k]) & (lev == L)
+        lev, anc = refine_leaves(lev, anc, hit)
+        lev, anc = balance_fast(nt, lev, anc)
+    return lev, anc

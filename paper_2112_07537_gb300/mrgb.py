@@ -1,0 +1,266 @@
+"""Python binding of the C ABI in include/mrgb.h (argument marshalling only).
+
+Every numerical step runs in the CUDA library ``_lib/libmrgb.so``; this module
+only converts arguments.  PyTorch supplies device memory (the grid workspace
+is a torch uint8 tensor) and the stream.  If the library is missing or fails
+to load, ``load()`` raises: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libmrgb.so")
+
+MR_OK = 0
+F32, F64 = 0, 1
+CONS3, CONS5, WENOZ5 = 0, 1, 2
+INIT_GAUSSIAN, INIT_TANH_SPHERE, INIT_TAYLOR_GREEN = 0, 1, 2
+ADAPT_REFINE, ADAPT_COARSEN = 1, 2
+NUM_KERNELS = 18
+
+# every entry point include/mrgb.h declares
+EXPORTS = ["mr_last_error", "mr_workspace_size", "mr_grid_create", "mr_grid_destroy",
+           "mr_grid_leaves", "mr_field_copy_in", "mr_field_copy_out", "mr_field_set",
+           "mr_ghost_fill", "mr_ghost_fill64", "mr_sync", "mr_rhs_advect", "mr_rk_stage",
+           "mr_step", "mr_criterion", "mr_adapt", "mr_adapt_iter", "mr_mass", "mr_query",
+           "mr_field_ptr", "mr_profile", "mr_profile_read", "mr_launch_count"]
+
+
+class MRError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"mrgb error {code}: {msg}")
+        self.code = code
+
+
+class Desc(C.Structure):
+    _fields_ = [("ntree", C.c_int * 3), ("tree_len", C.c_double), ("nb", C.c_int),
+                ("lmin", C.c_int), ("lmax", C.c_int), ("wav_N", C.c_int), ("wav_Nt", C.c_int),
+                ("precision", C.c_int), ("nfields", C.c_int), ("capacity", C.c_int),
+                ("stream", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("nleaf", C.c_int), ("count_per_level", C.c_int * 32), ("min_level", C.c_int),
+                ("max_level", C.c_int)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library (raises if it is missing: no CPU fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError(f"CUDA library not built: {path} (run paper_2112_07537_gb300.build)")
+        L = C.CDLL(path)
+        vp, ip, dp = C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_double)
+        L.mr_last_error.restype = C.c_char_p
+        L.mr_workspace_size.argtypes = [C.POINTER(Desc), C.POINTER(C.c_size_t)]
+        L.mr_grid_create.argtypes = [C.POINTER(Desc), vp, C.c_size_t, ip, ip, C.c_int,
+                                     C.POINTER(vp)]
+        L.mr_grid_destroy.argtypes = [vp]
+        L.mr_grid_leaves.argtypes = [vp, ip, ip, C.POINTER(C.c_uint64), C.c_int,
+                                     C.POINTER(C.c_int)]
+        L.mr_field_copy_in.argtypes = [vp, C.c_int, vp, C.c_int]
+        L.mr_field_copy_out.argtypes = [vp, C.c_int, vp, C.c_int]
+        L.mr_field_set.argtypes = [vp, C.c_int, C.c_int, dp, C.c_int]
+        L.mr_ghost_fill.argtypes = [vp, C.c_int, C.c_int, vp]
+        L.mr_ghost_fill64.argtypes = [vp, C.c_int, C.c_int, vp]
+        L.mr_sync.argtypes = [vp]
+        L.mr_rhs_advect.argtypes = [vp, C.c_int, dp, C.c_int, C.c_int]
+        L.mr_rk_stage.argtypes = [vp, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int]
+        L.mr_step.argtypes = [vp, C.c_int, C.c_double, dp, C.c_int]
+        L.mr_criterion.argtypes = [vp, C.c_int, vp]
+        L.mr_adapt.argtypes = [vp, C.c_int, C.c_double, C.c_double, C.c_int, C.POINTER(C.c_int)]
+        L.mr_adapt_iter.argtypes = [vp, C.c_int, C.c_double, C.c_double, C.c_int,
+                                    C.POINTER(C.c_int)]
+        L.mr_mass.argtypes = [vp, C.c_int, dp]
+        L.mr_query.argtypes = [vp, C.POINTER(Stats)]
+        L.mr_field_ptr.argtypes = [vp, C.c_int, C.POINTER(vp)]
+        L.mr_profile.argtypes = [vp, C.c_int]
+        L.mr_profile_read.argtypes = [vp, C.c_int, dp, C.POINTER(C.c_int), C.POINTER(C.c_char_p)]
+        L.mr_launch_count.argtypes = [vp, C.POINTER(C.c_longlong)]
+        _lib = L
+    return _lib
+
+
+def _chk(code):
+    if code != MR_OK:
+        raise MRError(code, load().mr_last_error().decode())
+    return code
+
+
+def _u3(u):
+    return (C.c_double * 3)(*[float(v) for v in u])
+
+
+def _ptr(x):
+    """Raw pointer of a torch tensor or numpy array (argument marshalling)."""
+    if hasattr(x, "data_ptr"):
+        return C.c_void_p(x.data_ptr())
+    return C.c_void_p(x.ctypes.data)
+
+
+def _on_dev(x):
+    return int(hasattr(x, "is_cuda") and x.is_cuda)
+
+
+class Grid:
+    """A periodic forest of octrees of nb^3 blocks on one GPU (mr_grid)."""
+
+    def __init__(self, ntree, tree_len, nb, lmin, lmax, N, Nt, lev, anc, precision=F32,
+                 nfields=1, capacity=None, device="cuda", stream=None):
+        import torch
+        L = load()
+        lev = np.ascontiguousarray(lev, np.int32)
+        anc = np.ascontiguousarray(np.asarray(anc).reshape(-1, 3), np.int32)
+        cap = int(capacity or len(lev))
+        self.torch = torch
+        self.device = torch.device(device)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.stream = s
+        d = Desc()
+        d.ntree[:] = list(ntree)
+        d.tree_len, d.nb, d.lmin, d.lmax = float(tree_len), nb, lmin, lmax
+        d.wav_N, d.wav_Nt, d.precision, d.nfields, d.capacity = N, Nt, precision, nfields, cap
+        d.stream = s.cuda_stream
+        self.desc = d
+        nbytes = C.c_size_t()
+        _chk(L.mr_workspace_size(C.byref(d), C.byref(nbytes)))
+        self.ws = torch.empty(nbytes.value + 256, dtype=torch.uint8, device=self.device)
+        base = self.ws.data_ptr()
+        self._off = (-base) % 256
+        h = C.c_void_p()
+        _chk(L.mr_grid_create(C.byref(d), C.c_void_p(base + self._off), nbytes.value,
+                              lev.ctypes.data_as(C.POINTER(C.c_int32)),
+                              anc.ctypes.data_as(C.POINTER(C.c_int32)), len(lev), C.byref(h)))
+        self.h = h
+        self.nb, self.N, self.Nt = nb, N, Nt
+        self.ntree, self.tree_len, self.lmin, self.lmax = tuple(ntree), float(tree_len), lmin, lmax
+        self.precision = precision
+        self.dtype = torch.float32 if precision == F32 else torch.float64
+        self.np_dtype = np.float32 if precision == F32 else np.float64
+        self.nfields = nfields
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                load().mr_grid_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ queries
+    @property
+    def nleaf(self):
+        n = C.c_int()
+        _chk(load().mr_grid_leaves(self.h, None, None, None, 0, C.byref(n)))
+        return n.value
+
+    def leaves(self):
+        n = self.nleaf
+        lev = np.empty(n, np.int32)
+        anc = np.empty((n, 3), np.int32)
+        keys = np.empty(n, np.uint64)
+        nn = C.c_int()
+        _chk(load().mr_grid_leaves(self.h, lev.ctypes.data_as(C.POINTER(C.c_int32)),
+                                   anc.ctypes.data_as(C.POINTER(C.c_int32)),
+                                   keys.ctypes.data_as(C.POINTER(C.c_uint64)), n, C.byref(nn)))
+        return lev, anc, keys
+
+    def query(self):
+        st = Stats()
+        _chk(load().mr_query(self.h, C.byref(st)))
+        return st
+
+    def sync(self):
+        _chk(load().mr_sync(self.h))
+
+    def field_view(self, fid):
+        """Torch view (nleaf, nb, nb, nb) of field fid inside the workspace."""
+        p = C.c_void_p()
+        _chk(load().mr_field_ptr(self.h, fid, C.byref(p)))
+        off = p.value - self.ws.data_ptr()
+        n = self.nleaf * self.nb ** 3
+        es = 4 if self.precision == F32 else 8
+        return self.ws[off:off + n * es].view(self.dtype).view(self.nleaf, self.nb, self.nb, self.nb)
+
+    # ------------------------------------------------------------- fields
+    def field_copy_in(self, fid, src):
+        if not _on_dev(src):
+            src = np.ascontiguousarray(src, self.np_dtype)
+        elif src.dtype != self.dtype or not src.is_contiguous():
+            raise ValueError("device source must be contiguous and of the grid's dtype")
+        _chk(load().mr_field_copy_in(self.h, fid, _ptr(src), _on_dev(src)))
+        self._keep = src
+
+    def field_copy_out(self, fid, dst=None):
+        if dst is None:
+            dst = np.empty((self.nleaf, self.nb, self.nb, self.nb), self.np_dtype)
+        _chk(load().mr_field_copy_out(self.h, fid, _ptr(dst), _on_dev(dst)))
+        return dst
+
+    def field_set(self, fid, kind, params):
+        p = (C.c_double * len(params))(*params)
+        _chk(load().mr_field_set(self.h, fid, kind, p, len(params)))
+
+    # ------------------------------------------------------------ the path
+    def ghost_fill(self, fid, G, padded=None):
+        _chk(load().mr_ghost_fill(self.h, fid, G, _ptr(padded) if padded is not None else None))
+        return padded
+
+    def ghost_fill64(self, fid, G, padded=None):
+        _chk(load().mr_ghost_fill64(self.h, fid, G, _ptr(padded) if padded is not None else None))
+        return padded
+
+    def rhs_advect(self, phi_fid, u, out_fid, scheme):
+        _chk(load().mr_rhs_advect(self.h, phi_fid, _u3(u), out_fid, scheme))
+
+    def rk_stage(self, stage, dt, u_fid, y_fid, rhs_fid, out_fid):
+        _chk(load().mr_rk_stage(self.h, stage, float(dt), u_fid, y_fid, rhs_fid, out_fid))
+
+    def step(self, phi_fid, dt, u, scheme):
+        _chk(load().mr_step(self.h, phi_fid, float(dt), _u3(u), scheme))
+
+    def criterion(self, fid, maxdet):
+        _chk(load().mr_criterion(self.h, fid, _ptr(maxdet)))
+        return maxdet
+
+    def adapt(self, crit_fid, eps_r, eps_c, flags=ADAPT_REFINE | ADAPT_COARSEN):
+        n = C.c_int()
+        _chk(load().mr_adapt(self.h, crit_fid, float(eps_r), float(eps_c), flags, C.byref(n)))
+        return n.value
+
+    def adapt_iter(self, crit_fid, eps_r, eps_c, flags=ADAPT_REFINE | ADAPT_COARSEN):
+        n = C.c_int()
+        _chk(load().mr_adapt_iter(self.h, crit_fid, float(eps_r), float(eps_c), flags,
+                                  C.byref(n)))
+        return n.value
+
+    def profile(self, enable):
+        _chk(load().mr_profile(self.h, int(enable)))
+
+    def profile_read(self):
+        """{kernel name: (total ms, launches)} of the recorded launches."""
+        out = {}
+        for kid in range(NUM_KERNELS):
+            t, n, name = C.c_double(), C.c_int(), C.c_char_p()
+            _chk(load().mr_profile_read(self.h, kid, C.byref(t), C.byref(n), C.byref(name)))
+            if n.value:
+                out[name.value.decode()] = (t.value, n.value)
+        return out
+
+    def launch_count(self):
+        n = C.c_longlong()
+        _chk(load().mr_launch_count(self.h, C.byref(n)))
+        return n.value
+
+    def mass(self, fid):
+        m = C.c_double()
+        _chk(load().mr_mass(self.h, fid, C.byref(m)))
+        return m.value

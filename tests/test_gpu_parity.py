@@ -1,0 +1,191 @@
+"""GPU path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances: FP64 ghost fill / criterion inputs are bit-exact (same
+operation order, no fused multiply-add on either side); FP64 stencils and
+RK3 steps within 1e-12 relative to the field maximum; FP32 within 1e-5 of the
+field maximum (rounding of ~1e2 FP32 operations per point per stage).
+"""
+import numpy as np
+import pytest
+
+from paper_2112_07537_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+WAV = [(2, 0), (2, 2), (4, 0), (4, 2), (6, 0), (6, 2)]
+
+
+@pytest.fixture(scope="module")
+def mr():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2112_07537_gb300 import build, mrgb
+    build.build()
+    mrgb.load()
+    return mrgb
+
+
+def _sorted_by_oracle_keys(O, lev, anc, kl):
+    keys = np.array([O.morton_key(l, *a, kl) for l, a in zip(lev, anc)], dtype=np.uint64)
+    order = np.argsort(keys, kind="stable")
+    return lev[order], anc[order], keys[order]
+
+
+def _three_level(nb):
+    nt, tl = (4, 4, 4), 0.25
+    lev, anc = I.uniform_leaves(nt, 0)
+    lev, anc = I.refine_leaves(lev, anc, np.all((anc >= 1) & (anc <= 2), axis=1))
+    lev, anc = I.refine_leaves(lev, anc, (lev == 1) & np.all(anc == 3, axis=1))
+    lev, anc = I.balance(nt, lev, anc)
+    return nt, tl, lev, anc
+
+
+def _grid(mr, O, nt, tl, nb, N, Nt, lev, anc, prec, lmax, nfields=1, cap=None):
+    g = mr.Grid(nt, tl, nb, 0, lmax, N, Nt, lev, anc, precision=prec, nfields=nfields, capacity=cap)
+    glev, ganc, gkeys = g.leaves()
+    olev, oanc, okeys = _sorted_by_oracle_keys(O, lev, anc, lmax)
+    # S0: the device's Morton order and keys equal the oracle's, bit for bit
+    assert np.array_equal(glev, olev) and np.array_equal(ganc, oanc)
+    assert np.array_equal(gkeys, okeys)
+    og = O.Grid(nt, tl, nb, N, Nt, 0, lmax, glev, ganc)
+    return g, og
+
+
+@pytest.mark.parametrize("N,Nt", WAV)
+def test_ghost_fill_fp64_bitexact(mr, oracle_mod, N, Nt):
+    O = oracle_mod
+    nb = 16 if N < 6 else 24
+    nt, tl, lev, anc = _three_level(nb)
+    g, og = _grid(mr, O, nt, tl, nb, N, Nt, lev, anc, mr.F64, 2)
+    rng = np.random.default_rng(100 + N + Nt)
+    phi = rng.normal(size=(og.nleaf, nb, nb, nb))
+    import torch
+    for G in sorted({3, O.adapt_shell(N, Nt)}):
+        g.field_copy_in(0, phi)
+        W = nb + 2 * G
+        pad = torch.empty((og.nleaf, W, W, W), dtype=torch.float64, device="cuda")
+        g.ghost_fill(0, G, pad)
+        g.sync()
+        ref_pad, ref_sub = O.ghost_fill(og, phi, G)
+        assert np.array_equal(pad.cpu().numpy(), ref_pad), np.abs(pad.cpu().numpy() - ref_pad).max()
+        assert np.array_equal(g.field_copy_out(0), ref_sub)
+
+
+@pytest.mark.parametrize("N,Nt", [(4, 0), (4, 2), (6, 2)])
+def test_ghost_fill64_of_fp32_field_bitexact(mr, oracle_mod, N, Nt):
+    """The adaptation path: FP64 ghosts from an FP32 field equal the oracle's
+    ghosts of the same (upcast) values."""
+    O = oracle_mod
+    nb = 16 if N < 6 else 24
+    nt, tl, lev, anc = _three_level(nb)
+    g, og = _grid(mr, O, nt, tl, nb, N, Nt, lev, anc, mr.F32, 2)
+    rng = np.random.default_rng(7)
+    phi = rng.normal(size=(og.nleaf, nb, nb, nb)).astype(np.float32)
+    g.field_copy_in(0, phi)
+    G = O.adapt_shell(N, Nt)
+    import torch
+    W = nb + 2 * G
+    pad = torch.empty((og.nleaf, W, W, W), dtype=torch.float64, device="cuda")
+    g.ghost_fill64(0, G, pad)
+    g.sync()
+    ref_pad, ref_sub = O.ghost_fill(og, phi.astype(np.float64), G)
+    assert np.array_equal(pad.cpu().numpy(), ref_pad)
+    assert np.array_equal(g.field_copy_out(0), ref_sub.astype(np.float32))
+
+
+@pytest.mark.parametrize("N,Nt", [(2, 0), (4, 2), (6, 2)])
+def test_ghost_fill_fp32_tolerance(mr, oracle_mod, N, Nt):
+    O = oracle_mod
+    nb = 16 if N < 6 else 24
+    nt, tl, lev, anc = _three_level(nb)
+    g, og = _grid(mr, O, nt, tl, nb, N, Nt, lev, anc, mr.F32, 2)
+    xyz = I.point_coords(nt, tl, nb, og.lev, og.anc)
+    phi = I.fourier_front(xyz, seed=3, kmax=4, width=0.05).astype(np.float32)
+    g.field_copy_in(0, phi)
+    import torch
+    W = nb + 6
+    pad = torch.empty((og.nleaf, W, W, W), dtype=torch.float32, device="cuda")
+    g.ghost_fill(0, 3, pad)
+    g.sync()
+    ref_pad, _ = O.ghost_fill(og, phi.astype(np.float64), 3)
+    scale = np.abs(ref_pad).max()
+    assert np.abs(pad.cpu().numpy() - ref_pad).max() <= 1e-6 * scale
+
+
+@pytest.mark.parametrize("scheme", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_rhs_parity(mr, oracle_mod, scheme, prec):
+    O = oracle_mod
+    nt, tl, nb = (2, 2, 2), 0.5, 16
+    lev, anc = I.tree_config1()
+    g, og = _grid(mr, O, nt, tl, nb, 4, 0, lev, anc, prec, 1, nfields=2)
+    xyz = I.point_coords(nt, tl, nb, og.lev, og.anc)
+    phi = I.gaussian_images(xyz, (0.45, 0.55, 0.5), 0.1, nimg=1)
+    if prec == 0:
+        phi = phi.astype(np.float32)
+    g.field_copy_in(0, phi)
+    u = (1.0, -0.5, 0.25)
+    g.rhs_advect(0, u, 1, scheme)
+    got = g.field_copy_out(1).astype(np.float64)
+    pad, _ = O.ghost_fill(og, phi.astype(np.float64), 3)
+    ref = O.rhs(og, pad, 3, scheme, u)
+    tol = 1e-12 if prec == 1 else 2e-5
+    assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
+
+
+def test_rk_stage_elementwise(mr, oracle_mod):
+    nt, tl, nb = (2, 2, 2), 0.5, 16
+    lev, anc = I.tree_config1()
+    g = mr.Grid(nt, tl, nb, 0, 1, 4, 0, lev, anc, precision=mr.F64, nfields=4)
+    rng = np.random.default_rng(5)
+    a, b, c = (rng.normal(size=(g.nleaf, nb, nb, nb)) for _ in range(3))
+    for fid, x in enumerate((a, b, c)):
+        g.field_copy_in(fid, x)
+    for stage, ref in ((0, b + 0.1 * c), (1, 0.75 * a + 0.25 * (b + 0.1 * c)),
+                       (2, a / 3 + 2.0 / 3 * (b + 0.1 * c))):
+        g.rk_stage(stage, 0.1, 0, 1, 2, 3)
+        assert np.allclose(g.field_copy_out(3), ref, rtol=1e-14, atol=1e-14)
+
+
+@pytest.mark.parametrize("prec,scheme", [(1, 2), (1, 1), (0, 2), (0, 1)])
+def test_config1_ten_steps(mr, oracle_mod, prec, scheme):
+    """Tiny configuration: 2x2x2 trees, one refined (15 leaves of 16^3), 4.0
+    wavelet, Gaussian sigma=0.1 at the centre, u=(1,1,1), RK3, CFL 0.5,
+    10 steps, fixed tree: GPU vs oracle after every step."""
+    O = oracle_mod
+    nt, tl, nb = (2, 2, 2), 0.5, 16
+    lev, anc = I.tree_config1()
+    g, og = _grid(mr, O, nt, tl, nb, 4, 0, lev, anc, prec, 1)
+    xyz = I.point_coords(nt, tl, nb, og.lev, og.anc)
+    phi = I.gaussian(xyz, (0.5, 0.5, 0.5), 0.1)
+    if prec == 0:
+        phi = phi.astype(np.float32)
+    g.field_copy_in(0, phi)
+    u = (1.0, 1.0, 1.0)
+    dt = O.dt_cfl(og, 0.5, u)
+    ref = phi.astype(np.float64)
+    m0 = O.moments(og, ref)[0]
+    for _ in range(10):
+        g.step(0, dt, u, scheme)
+        ref = O.rk3_step(og, ref, dt, scheme, u)
+    got = g.field_copy_out(0).astype(np.float64)
+    err = np.abs(got - ref).max() / np.abs(ref).max()
+    assert err <= (1e-12 if prec == 1 else 1e-5), err
+    # FP64 mass on the device matches the oracle quadrature of the same field
+    assert g.mass(0) == pytest.approx(O.moments(og, got)[0], rel=1e-12)
+    assert abs(O.moments(og, ref)[0] - m0) < 1e-3 * abs(m0)
+
+
+def test_invalid_trees_are_rejected(mr):
+    nt = (1, 1, 1)
+    lev, anc = I.uniform_leaves(nt, 1)
+    # refine one leaf twice -> 2-level jump next to level-1 leaves
+    lev, anc = I.refine_leaves(lev, anc, np.arange(len(lev)) == 0)
+    lev, anc = I.refine_leaves(lev, anc, np.arange(len(lev)) == 0)
+    with pytest.raises(mr.MRError) as e:
+        mr.Grid(nt, 1.0, 16, 0, 3, 4, 0, lev, anc)
+    assert e.value.code == -6
+    lev2, anc2 = I.uniform_leaves(nt, 1)
+    with pytest.raises(mr.MRError):  # a missing leaf leaves a hole
+        mr.Grid(nt, 1.0, 16, 0, 3, 4, 0, lev2[1:], anc2[1:])
