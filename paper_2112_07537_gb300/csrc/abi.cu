@@ -128,8 +128,8 @@ static int layout(const mr_grid_desc *d, Layout *L, int *shell_rk, int *shell_ad
       8 * cap * 4,                               // newsrc
       64 * 4,                                    // counter
       64 * 8,                                    // dscratch
-      cap * 4,                                   // cmask
-      0};
+      cap * 8,                                   // cmask + new-band masks
+      cap * 4};                                  // hasD
   size_t o = 0;
   for (int i = 0; i < 24; ++i) {
     L->off[i] = o;
@@ -251,6 +251,7 @@ int mr_grid_create(const mr_grid_desc *desc, void *workspace, size_t workspace_b
   g->counter = (int *)(w + L.off[20]);
   g->dscratch = (double *)(w + L.off[21]);
   g->cmask = (int *)(w + L.off[22]);
+  g->hasD = (int *)(w + L.off[23]);
   g->shell_rk = srk;
   g->shell_ad = sad;
   g->map_cells = mc;
@@ -379,10 +380,11 @@ int mr_ghost_fill(mr_grid *g, int fid, int G, void *padded) {
   if (!fid_ok(g, fid)) return MR_ERR_INVALID;
   void *P;
   int Gi;
+  bool is64;
   void *f = field_ptr(g, fid);
-  int e = launch_ghost(g, f, f, G, false, &P, &Gi);
+  int e = launch_ghost(g, f, f, G, false, &P, &Gi, &is64);
   if (e) return e;
-  if (padded) e = launch_crop(g, P, Gi, padded, G, false);
+  if (padded) e = launch_crop(g, P, Gi, padded, G, is64);
   return e;
 }
 

@@ -1,18 +1,637 @@
 // adapt.cu -- block criterion and grid adaptation (Alg. SM3) on the device.
+//
+// One iteration: FP64 ghost fill with the adaptation shell -> per-leaf max
+// |detail| (criterion) -> status -> policy (Jacobi iteration to the least
+// fixed point) -> new leaves in Morton order (scan + emit) -> owner map of
+// the new tree -> per field: ghost fill, refinement / coarsening / copy into
+// the second pool, update step next to newly coarsened leaves.
 #include "mr_internal.cuh"
 
 namespace mr {
 
-int launch_criterion(mr_grid *g, const double *P64, int Gi, double *maxdet) {
-  (void)g, (void)P64, (void)Gi, (void)maxdet;
-  set_error("criterion not built yet");
+enum { KIND_COPY = 0, KIND_CHILD = 1, KIND_PARENT = 2 };
+enum { ST_COARSER = -1, ST_SAME = 0, ST_FINER = 1 };
+
+// ------------------------------------------------------------- criterion
+// Per leaf: max |gamma| over [-ext_f, nb-1+ext_b]^3 (points with an odd
+// coordinate), gamma = 1D filters applied x, then y, then z (G^a on odd, H^a
+// on even coordinates).  The z-planes of the y-pass results live in a ring of
+// 2*hmax+1 shared-memory planes, so each pass is computed once.
+template <int N, int NT>
+__global__ void __launch_bounds__(256) k_criterion(Tree t, const double *__restrict__ P, int Gi,
+                                                   double *__restrict__ maxdet) {
+  using W = Wav<N, NT>;
+  constexpr int hm = W::hmax;
+  const int b = blockIdx.x, nb = t.nb, Wd = nb + 2 * Gi;
+  const int r0 = -W::ext_f, r1 = nb - 1 + W::ext_b, nR = r1 - r0 + 1, nA = nR + 2 * hm;
+  const int lo = -Gi, hi = nb - 1 + Gi;  // stored padded range
+  extern __shared__ double sm[];
+  double *ring = sm;
+  double *A = sm + (size_t)(2 * hm + 1) * nR * nR;
+  const double *Pb = P + (size_t)b * Wd * Wd * Wd;
+  auto pidx = [&](int i, int j, int k) {
+    return (size_t)(i + Gi) + Wd * ((size_t)(j + Gi) + (size_t)Wd * (k + Gi));
+  };
+  double mx = 0.0;
+  for (int kk = r0 - hm; kk <= r1 + hm; ++kk) {
+    const int slot = (kk - (r0 - hm)) % (2 * hm + 1);
+    const bool kin = kk >= lo && kk <= hi;
+    // x pass into A (rows j = r0-hm .. r1+hm)
+    for (int idx = threadIdx.x; idx < nR * nA; idx += blockDim.x) {
+      const int i = r0 + idx % nR, jj = r0 - hm + idx / nR;
+      double s = 0.0;
+      if (kin && jj >= lo && jj <= hi) {
+        const bool od = i & 1;
+        const int hw = od ? W::hwG : W::hwH;
+        for (int tx = -hw; tx <= hw; ++tx) {
+          const double w = od ? W::G(tx) : W::H(tx);
+          if (w == 0.0) continue;
+          s = radd(s, rmul(w, Pb[pidx(i + tx, jj, kk)]));
+        }
+      }
+      A[idx] = s;
+    }
+    __syncthreads();
+    // y pass into ring plane kk
+    for (int idx = threadIdx.x; idx < nR * nR; idx += blockDim.x) {
+      const int ii = idx % nR, j = r0 + idx / nR;
+      const bool od = j & 1;
+      const int hw = od ? W::hwG : W::hwH;
+      double s = 0.0;
+      for (int ty = -hw; ty <= hw; ++ty) {
+        const double w = od ? W::G(ty) : W::H(ty);
+        if (w == 0.0) continue;
+        s = radd(s, rmul(w, A[ii + nR * (j + ty - (r0 - hm))]));
+      }
+      ring[(size_t)slot * nR * nR + idx] = s;
+    }
+    __syncthreads();
+    // z pass for output plane k = kk - hm
+    const int k = kk - hm;
+    if (k >= r0) {
+      const bool odk = k & 1;
+      const int hw = odk ? W::hwG : W::hwH;
+      for (int idx = threadIdx.x; idx < nR * nR; idx += blockDim.x) {
+        const int i = r0 + idx % nR, j = r0 + idx / nR;
+        if (!((i | j | k) & 1)) continue;
+        double s = 0.0;
+        for (int tz = -hw; tz <= hw; ++tz) {
+          const double w = odk ? W::G(tz) : W::H(tz);
+          if (w == 0.0) continue;
+          const int sl = (k + tz - (r0 - hm)) % (2 * hm + 1);
+          s = radd(s, rmul(w, ring[(size_t)sl * nR * nR + idx]));
+        }
+        mx = fmax(mx, fabs(s));
+      }
+    }
+    __syncthreads();
+  }
+  // block max
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  __shared__ double red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (threadIdx.x == 0) maxdet[b] = v;
+  }
+}
+
+template <int N, int NT>
+static size_t crit_smem(int nb) {
+  using W = Wav<N, NT>;
+  const int nR = nb + W::ext_f + W::ext_b, hm = W::hmax;
+  return sizeof(double) * ((size_t)(2 * hm + 1) * nR * nR + (size_t)nR * (nR + 2 * hm));
+}
+
+template <int N, int NT>
+static int criterion_impl(mr_grid *g, const double *P, int Gi, double *maxdet) {
+  const size_t sm = crit_smem<N, NT>(g->desc.nb);
+  if (sm > 227 * 1024) return MR_ERR_UNSUPPORTED;
+  if (check_cuda(cudaFuncSetAttribute(k_criterion<N, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sm),
+                 "criterion smem"))
+    return MR_ERR_CUDA;
+  Tree t = tree_view(g);
+  MR_LAUNCH(g, MRK_CRITERION, k_criterion<N, NT><<<g->nleaf, 256, sm, g->stream>>>(t, P, Gi, maxdet));
+  return check_cuda(cudaGetLastError(), "k_criterion") ? MR_ERR_CUDA : MR_OK;
+}
+
+int launch_criterion(mr_grid *g, const double *P, int Gi, double *maxdet) {
+  const int N = g->desc.wav_N, Nt = g->desc.wav_Nt;
+#define MR_CCASE(n_, nt_) \
+  if (N == n_ && Nt == nt_) return criterion_impl<n_, nt_>(g, P, Gi, maxdet);
+  MR_CCASE(2, 0) MR_CCASE(2, 2) MR_CCASE(4, 0) MR_CCASE(4, 2) MR_CCASE(6, 0) MR_CCASE(6, 2)
+#undef MR_CCASE
   return MR_ERR_UNSUPPORTED;
 }
 
-int adapt_iteration(mr_grid *g, int crit_fid, double er, double ec, int flags, int *nch) {
-  (void)g, (void)crit_fid, (void)er, (void)ec, (void)flags, (void)nch;
-  set_error("adaptation not built yet");
+// --------------------------------------------------------- status, policy
+__global__ void k_status(int n, const double *maxdet, double er, double ec, int flags, const int *lev,
+                         const int *refined, int lmin, int lmax, int8_t *st) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n) return;
+  const double m = maxdet[b];
+  int s = m >= er ? ST_FINER : (m <= ec ? ST_COARSER : ST_SAME);
+  if (s == ST_FINER && !(flags & MR_ADAPT_REFINE)) s = ST_SAME;
+  if (s == ST_COARSER && !(flags & MR_ADAPT_COARSEN)) s = ST_SAME;
+  const int L = lev[b];
+  if (s == ST_FINER && L >= lmax) s = ST_SAME;
+  if (s == ST_COARSER && (L <= lmin || L == 0 || refined[b])) s = ST_SAME;
+  st[b] = (int8_t)s;
+}
+
+// One Jacobi sweep of the policy rules (monotone: statuses only rise, so the
+// sweeps converge to the same least fixed point as any other order).
+__global__ void k_policy(Tree t, const int8_t *__restrict__ sin, int8_t *__restrict__ sout, int *changed) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= t.nleaf) return;
+  const int L = __ldg(t.lev + b), nb = t.nb;
+  const int s = sin[b];
+  int ns = s;
+  const bool fin = L < t.M;
+  const int Ls = fin ? L + 1 : L, span = fin ? 2 * nb : nb;
+  int base[3];
+  for (int d = 0; d < 3; ++d) base[d] = __ldg(t.anc + 3 * b + d) * span;
+  bool raise = false, cancel = false;
+  for (int m = 0; m < 27; ++m) {
+    if (m == 13) continue;
+    const int dd[3] = {m % 3 - 1, (m / 3) % 3 - 1, m / 9 - 1};
+    const int c0 = dd[0] ? 1 : 2, c1 = dd[1] ? 1 : 2, c2 = dd[2] ? 1 : 2;
+    for (int cz = 0; cz < c2; ++cz)
+      for (int cy = 0; cy < c1; ++cy)
+        for (int cx = 0; cx < c0; ++cx) {
+          const int cc[3] = {cx, cy, cz};
+          int g[3];
+          for (int d = 0; d < 3; ++d)
+            g[d] = dd[d] < 0 ? base[d] - 1 : dd[d] > 0 ? base[d] + span : base[d] + cc[d] * (span / 2);
+          const int o = owner(t, Ls, g[0], g[1], g[2]);
+          if (o == b) continue;
+          const int Lo = __ldg(t.lev + o), so = sin[o];
+          if (Lo > L && so == ST_FINER) raise = true;
+          if (Lo > L || (Lo == L && so == ST_FINER)) cancel = true;
+        }
+  }
+  if (s != ST_FINER && raise) ns = ST_FINER;
+  if (ns == ST_COARSER) {
+    if (cancel) ns = ST_SAME;
+    for (int c = 0; c < 8 && ns == ST_COARSER; ++c) {
+      int a[3];
+      for (int d = 0; d < 3; ++d) a[d] = (__ldg(t.anc + 3 * b + d) & ~1) + ((c >> d) & 1);
+      const int o = owner(t, L, a[0] * nb, a[1] * nb, a[2] * nb);
+      const bool leaf = __ldg(t.lev + o) == L && __ldg(t.anc + 3 * o) == a[0] &&
+                        __ldg(t.anc + 3 * o + 1) == a[1] && __ldg(t.anc + 3 * o + 2) == a[2];
+      if (!leaf || sin[o] != ST_COARSER) ns = ST_SAME;
+    }
+  }
+  sout[b] = (int8_t)ns;
+  if (ns != s) atomicAdd(changed, 1);
+}
+
+// ------------------------------------------------------------ new tree
+__global__ void k_count(int n, const int8_t *st, const int *anc, int *cnt, int *changed) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n) return;
+  const int s = st[b];
+  int c = 1;
+  if (s == ST_FINER) c = 8;
+  if (s == ST_COARSER) c = ((anc[3 * b] | anc[3 * b + 1] | anc[3 * b + 2]) & 1) ? 0 : 1;
+  cnt[b] = c;
+  if (s != ST_SAME) atomicAdd(changed, 1);
+}
+
+// exclusive scan of cnt[0..n) in place, total in cnt[n]; one CTA of 1024
+__global__ void __launch_bounds__(1024) k_scan(int *cnt, int n) {
+  __shared__ int part[1024];
+  const int chunk = (n + 1023) / 1024;
+  const int beg = threadIdx.x * chunk, end = min(n, beg + chunk);
+  int s = 0;
+  for (int i = beg; i < end; ++i) s += cnt[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    int v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int run = part[threadIdx.x] - s;
+  for (int i = beg; i < end; ++i) {
+    const int c = cnt[i];
+    cnt[i] = run;
+    run += c;
+  }
+  if (threadIdx.x == 1023) cnt[n] = part[1023];
+}
+
+__device__ unsigned long long morton_key_dev(int lev, int ax, int ay, int az, int M) {
+  const unsigned long long x = (unsigned long long)ax << (M - lev), y = (unsigned long long)ay << (M - lev),
+                           z = (unsigned long long)az << (M - lev);
+  unsigned long long key = 0;
+  for (int bit = 0; bit < 19; ++bit) {
+    key |= ((x >> bit) & 1ULL) << (3 * bit);
+    key |= ((y >> bit) & 1ULL) << (3 * bit + 1);
+    key |= ((z >> bit) & 1ULL) << (3 * bit + 2);
+  }
+  return (key << 5) | (unsigned long long)lev;
+}
+
+__global__ void k_emit(int n, int M, const int8_t *st, const int *pos, const int *lev, const int *anc,
+                       const int *refined, int *nlev, int *nanc, unsigned long long *nkey, int *nref,
+                       int *src) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n) return;
+  const int s = st[b], p = pos[b], L = lev[b];
+  const int a0 = anc[3 * b], a1 = anc[3 * b + 1], a2 = anc[3 * b + 2];
+  if (s == ST_FINER) {
+    for (int c = 0; c < 8; ++c) {
+      const int q = p + c;
+      const int x = 2 * a0 + (c & 1), y = 2 * a1 + ((c >> 1) & 1), z = 2 * a2 + (c >> 2);
+      nlev[q] = L + 1;
+      nanc[3 * q] = x, nanc[3 * q + 1] = y, nanc[3 * q + 2] = z;
+      nkey[q] = morton_key_dev(L + 1, x, y, z, M);
+      nref[q] = 1;
+      src[2 * q] = KIND_CHILD;
+      src[2 * q + 1] = (b << 3) | c;
+    }
+  } else if (s == ST_COARSER) {
+    if ((a0 | a1 | a2) & 1) return;
+    nlev[p] = L - 1;
+    nanc[3 * p] = a0 / 2, nanc[3 * p + 1] = a1 / 2, nanc[3 * p + 2] = a2 / 2;
+    nkey[p] = morton_key_dev(L - 1, a0 / 2, a1 / 2, a2 / 2, M);
+    nref[p] = 0;
+    src[2 * p] = KIND_PARENT;
+    src[2 * p + 1] = b;
+  } else {
+    nlev[p] = L;
+    nanc[3 * p] = a0, nanc[3 * p + 1] = a1, nanc[3 * p + 2] = a2;
+    nkey[p] = morton_key_dev(L, a0, a1, a2, M);
+    nref[p] = refined[b];
+    src[2 * p] = KIND_COPY;
+    src[2 * p + 1] = b;
+  }
+}
+
+// ------------------------------------------------------ interpolation
+// New leaf values: copy, zero-detail refinement of the parent's padded block
+// (J^s / K^s), or tensor H^a coarsening of the 8 children's padded blocks.
+template <typename TO, int N, int NT>
+__global__ void __launch_bounds__(256) k_interp(Tree to, const int *__restrict__ src,
+                                                const double *__restrict__ P, int Gi,
+                                                const TO *__restrict__ fold, TO *__restrict__ fnew) {
+  using W = Wav<N, NT>;
+  const int q = blockIdx.x, nb = to.nb, Wd = nb + 2 * Gi;
+  const size_t nb3 = (size_t)nb * nb * nb, np = (size_t)Wd * Wd * Wd;
+  const int kind = src[2 * q], s = src[2 * q + 1];
+  TO *out = fnew + (size_t)q * nb3;
+  auto pidx = [&](int i, int j, int k) {
+    return (size_t)(i + Gi) + Wd * ((size_t)(j + Gi) + (size_t)Wd * (k + Gi));
+  };
+  if (kind == KIND_COPY) {
+    for (int p = threadIdx.x; p < (int)nb3; p += blockDim.x) out[p] = fold[(size_t)s * nb3 + p];
+  } else if (kind == KIND_CHILD) {
+    const int par = s >> 3, ch = s & 7;
+    const double *Pp = P + (size_t)par * np;
+    for (int p = threadIdx.x; p < (int)nb3; p += blockDim.x) {
+      const int i = p % nb, j = (p / nb) % nb, k = p / (nb * nb);
+      const int f[3] = {(ch & 1) * nb + i, ((ch >> 1) & 1) * nb + j, ((ch >> 2) & 1) * nb + k};
+      const bool od[3] = {(bool)(f[0] & 1), (bool)(f[1] & 1), (bool)(f[2] & 1)};
+      const int h[3] = {od[0] ? W::hwK : W::hwJ, od[1] ? W::hwK : W::hwJ, od[2] ? W::hwK : W::hwJ};
+      double acc = 0.0;
+      for (int oz = -h[2]; oz <= h[2]; ++oz) {
+        if ((f[2] + oz) & 1) continue;
+        const double wz = od[2] ? W::K(oz) : W::J(oz);
+        for (int oy = -h[1]; oy <= h[1]; ++oy) {
+          if ((f[1] + oy) & 1) continue;
+          const double wy = od[1] ? W::K(oy) : W::J(oy);
+          for (int ox = -h[0]; ox <= h[0]; ++ox) {
+            if ((f[0] + ox) & 1) continue;
+            const double wx = od[0] ? W::K(ox) : W::J(ox);
+            const double wgt = rmul(rmul(wx, wy), wz);
+            if (wgt == 0.0) continue;
+            acc = radd(acc, rmul(wgt, Pp[pidx((f[0] + ox) / 2, (f[1] + oy) / 2, (f[2] + oz) / 2)]));
+          }
+        }
+      }
+      out[p] = TO(acc);
+    }
+  } else {
+    // children of the new parent in the old tree (level L = parent level + 1)
+    __shared__ int chs[8];
+    const int L = __ldg(to.lev + s);
+    if (threadIdx.x < 8) {
+      const int c = threadIdx.x;
+      int a[3];
+      for (int d = 0; d < 3; ++d) a[d] = __ldg(to.anc + 3 * s + d) + ((c >> d) & 1);
+      chs[c] = owner(to, L, a[0] * nb, a[1] * nb, a[2] * nb);
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < (int)nb3; p += blockDim.x) {
+      const int i = p % nb, j = (p / nb) % nb, k = p / (nb * nb);
+      const int f[3] = {2 * i, 2 * j, 2 * k};
+      int ch = 0, loc[3];
+      for (int d = 0; d < 3; ++d) {
+        const int cd = f[d] >= nb;
+        ch |= cd << d;
+        loc[d] = f[d] - cd * nb;
+      }
+      const double *Pc = P + (size_t)chs[ch] * np;
+      double acc = 0.0;
+      for (int tz = -W::hwH; tz <= W::hwH; ++tz)
+        for (int ty = -W::hwH; ty <= W::hwH; ++ty)
+          for (int tx = -W::hwH; tx <= W::hwH; ++tx) {
+            const double wgt = rmul(rmul(W::H(tx), W::H(ty)), W::H(tz));
+            if (wgt == 0.0) continue;
+            acc = radd(acc, rmul(wgt, Pc[pidx(loc[0] + tx, loc[1] + ty, loc[2] + tz)]));
+          }
+      out[p] = TO(acc);
+    }
+  }
+}
+
+// ------------------------------------------------------------- update
+__device__ __forceinline__ bool in_band_dev(int mask, int i, int j, int k, int nb, int ef, int eb) {
+  for (int m = 0; m < 27; ++m) {
+    if (!((mask >> m) & 1)) continue;
+    const int d0 = m % 3 - 1, d1 = (m / 3) % 3 - 1, d2 = m / 9 - 1;
+    if ((d0 < 0 ? i < eb : d0 > 0 ? i >= nb - ef : true) && (d1 < 0 ? j < eb : d1 > 0 ? j >= nb - ef : true) &&
+        (d2 < 0 ? k < eb : d2 > 0 ? k >= nb - ef : true))
+      return true;
+  }
+  return false;
+}
+
+// Directions of newly coarsened neighbours (one level coarser) of unchanged
+// new leaves; 0 for other leaves.
+__global__ void k_newmask(Tree tn, const int *src, int *nmask) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= tn.nleaf) return;
+  int mask = 0;
+  if (src[2 * q] == KIND_COPY) {
+    const int L = __ldg(tn.lev + q), nb = tn.nb;
+    for (int m = 0; m < 27; ++m) {
+      if (m == 13) continue;
+      const int dd[3] = {m % 3 - 1, (m / 3) % 3 - 1, m / 9 - 1};
+      int g[3];
+      for (int d = 0; d < 3; ++d) g[d] = __ldg(tn.anc + 3 * q + d) * nb + (dd[d] < 0 ? -1 : dd[d] > 0 ? nb : 0);
+      const int o = owner(tn, L, g[0], g[1], g[2]);
+      if (__ldg(tn.lev + o) == L - 1 && src[2 * o] == KIND_PARENT) mask |= 1 << m;
+    }
+  }
+  nmask[q] = mask;
+}
+
+// gamma over the extended region of every unchanged leaf F for the details
+// the coarsening discarded (in newly coarsened leaves, or in the new bands of
+// F or of its unchanged same-level neighbours), 0 elsewhere.  Q is indexed by
+// F's old slot in the padded layout.
+template <int N, int NT>
+__global__ void __launch_bounds__(256) k_update_gamma(Tree tn, const int *__restrict__ src,
+                                                      const int *__restrict__ nmask,
+                                                      const double *__restrict__ P, int Gi,
+                                                      double *__restrict__ Q, int *hasD) {
+  using W = Wav<N, NT>;
+  const int q = blockIdx.x;
+  if (src[2 * q] != KIND_COPY) return;
+  const int s = src[2 * q + 1], L = __ldg(tn.lev + q), nb = tn.nb, Wd = nb + 2 * Gi;
+  const int ef = W::ext_f, eb = W::ext_b, E = nb + ef + eb;
+  const size_t np = (size_t)Wd * Wd * Wd;
+  const double *Pb = P + (size_t)s * np;
+  double *Qb = Q + (size_t)s * np;
+  auto pidx = [&](int i, int j, int k) {
+    return (size_t)(i + Gi) + Wd * ((size_t)(j + Gi) + (size_t)Wd * (k + Gi));
+  };
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  const int a[3] = {__ldg(tn.anc + 3 * q) * nb, __ldg(tn.anc + 3 * q + 1) * nb, __ldg(tn.anc + 3 * q + 2) * nb};
+  for (int p = threadIdx.x; p < E * E * E; p += blockDim.x) {
+    const int i = p % E - ef, j = (p / E) % E - ef, k = p / (E * E) - ef;
+    double gam = 0.0;
+    if ((i | j | k) & 1) {
+      const int o = owner(tn, L, a[0] + i, a[1] + j, a[2] + k);
+      const int Lo = __ldg(tn.lev + o), ko = src[2 * o];
+      bool inD = false;
+      if (Lo == L - 1 && ko == KIND_PARENT) {
+        inD = true;
+      } else if (Lo == L && ko == KIND_COPY) {
+        const int mk = nmask[o];
+        if (mk) {
+          int loc[3];
+          const int gg[3] = {a[0] + i, a[1] + j, a[2] + k};
+          for (int d = 0; d < 3; ++d) loc[d] = pwrap(gg[d] - __ldg(tn.anc + 3 * o + d) * nb, npts(tn, L, d));
+          inD = in_band_dev(mk, loc[0], loc[1], loc[2], nb, ef, eb);
+        }
+      }
+      if (inD) {
+        any = 1;
+        // detail, x then y then z (same order as the criterion)
+        const bool ox = i & 1, oy = j & 1, oz = k & 1;
+        const int hx = ox ? W::hwG : W::hwH, hy = oy ? W::hwG : W::hwH, hz = oz ? W::hwG : W::hwH;
+        double bz = 0.0;
+        for (int tz = -hz; tz <= hz; ++tz) {
+          const double wz = oz ? W::G(tz) : W::H(tz);
+          if (wz == 0.0) continue;
+          double by = 0.0;
+          for (int ty = -hy; ty <= hy; ++ty) {
+            const double wy = oy ? W::G(ty) : W::H(ty);
+            if (wy == 0.0) continue;
+            double bx = 0.0;
+            for (int tx = -hx; tx <= hx; ++tx) {
+              const double wx = ox ? W::G(tx) : W::H(tx);
+              if (wx == 0.0) continue;
+              bx = radd(bx, rmul(wx, Pb[pidx(i + tx, j + ty, k + tz)]));
+            }
+            by = radd(by, rmul(wy, bx));
+          }
+          bz = radd(bz, rmul(wz, by));
+        }
+        gam = bz;
+      }
+    }
+    Qb[pidx(i, j, k)] = gam;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) hasD[q] = any;
+}
+
+// subtract the synthesis (J^s / K^s tensor taps) of the discarded details
+template <typename TO, int N, int NT>
+__global__ void __launch_bounds__(256) k_update_apply(Tree tn, const int *__restrict__ src,
+                                                      const int *__restrict__ hasD,
+                                                      const double *__restrict__ Q, int Gi,
+                                                      TO *__restrict__ fnew) {
+  using W = Wav<N, NT>;
+  const int q = blockIdx.x;
+  if (src[2 * q] != KIND_COPY || !hasD[q]) return;
+  const int s = src[2 * q + 1], nb = tn.nb, Wd = nb + 2 * Gi;
+  const int ef = W::ext_f, eb = W::ext_b;
+  const double *Qb = Q + (size_t)s * Wd * Wd * Wd;
+  TO *v = fnew + (size_t)q * nb * nb * nb;
+  auto pidx = [&](int i, int j, int k) {
+    return (size_t)(i + Gi) + Wd * ((size_t)(j + Gi) + (size_t)Wd * (k + Gi));
+  };
+  for (int p = threadIdx.x; p < nb * nb * nb; p += blockDim.x) {
+    const int i = p % nb, j = (p / nb) % nb, k = p / (nb * nb);
+    const bool od[3] = {(bool)(i & 1), (bool)(j & 1), (bool)(k & 1)};
+    const int h[3] = {od[0] ? W::hwK : W::hwJ, od[1] ? W::hwK : W::hwJ, od[2] ? W::hwK : W::hwJ};
+    double acc = 0.0;
+    for (int oz = -h[2]; oz <= h[2]; ++oz) {
+      const int nz = k + oz;
+      if (nz < -ef || nz >= nb + eb) continue;
+      const double wz = od[2] ? W::K(oz) : W::J(oz);
+      for (int oy = -h[1]; oy <= h[1]; ++oy) {
+        const int ny = j + oy;
+        if (ny < -ef || ny >= nb + eb) continue;
+        const double wy = od[1] ? W::K(oy) : W::J(oy);
+        for (int ox = -h[0]; ox <= h[0]; ++ox) {
+          const int nx = i + ox;
+          if (nx < -ef || nx >= nb + eb) continue;
+          const double g = Qb[pidx(nx, ny, nz)];
+          if (g == 0.0) continue;
+          const double wx = od[0] ? W::K(ox) : W::J(ox);
+          const double wgt = rmul(rmul(wx, wy), wz);
+          if (wgt == 0.0) continue;
+          acc = radd(acc, rmul(wgt, g));
+        }
+      }
+    }
+    if (acc != 0.0) v[p] = TO(radd((double)v[p], -acc));
+  }
+}
+
+// ------------------------------------------------------------- driver
+static Tree next_view(const mr_grid *g, int nleaf) {
+  Tree t = tree_view(g);
+  const int nx = g->cur ^ 1;
+  t.lev = g->lev[nx];
+  t.anc = g->anc[nx];
+  t.map = g->maps[nx];
+  t.nleaf = nleaf;
+  return t;
+}
+
+template <typename TO, int N, int NT>
+static int interp_update(mr_grid *g, const Tree &to, const Tree &tn, const double *P, int Gi, int fid,
+                         int *nmask, int *hasD) {
+  const int *src = g->newsrc;
+  MR_LAUNCH(g, MRK_INTERP, k_interp<TO, N, NT><<<tn.nleaf, 256, 0, g->stream>>>(
+                               to, src, P, Gi, (const TO *)field_ptr(g, fid), (TO *)next_field_ptr(g, fid)));
+  MR_LAUNCH(g, MRK_UPDATE, k_update_gamma<N, NT><<<tn.nleaf, 256, 0, g->stream>>>(tn, src, nmask, P, Gi,
+                                                                                 g->padQ64, hasD));
+  MR_LAUNCH(g, MRK_UPDATE, k_update_apply<TO, N, NT><<<tn.nleaf, 256, 0, g->stream>>>(
+                               tn, src, hasD, g->padQ64, Gi, (TO *)next_field_ptr(g, fid)));
+  return check_cuda(cudaGetLastError(), "interp/update") ? MR_ERR_CUDA : MR_OK;
+}
+
+template <typename TO>
+static int interp_dispatch(mr_grid *g, const Tree &to, const Tree &tn, const double *P, int Gi, int fid,
+                           int *nmask, int *hasD) {
+  const int N = g->desc.wav_N, Nt = g->desc.wav_Nt;
+#define MR_ICASE(n_, nt_) \
+  if (N == n_ && Nt == nt_) return interp_update<TO, n_, nt_>(g, to, tn, P, Gi, fid, nmask, hasD);
+  MR_ICASE(2, 0) MR_ICASE(2, 2) MR_ICASE(4, 0) MR_ICASE(4, 2) MR_ICASE(6, 0) MR_ICASE(6, 2)
+#undef MR_ICASE
   return MR_ERR_UNSUPPORTED;
+}
+
+static int read_ints(mr_grid *g, const int *dev, int *host, int n) {
+  if (check_cuda(cudaMemcpyAsync(host, dev, sizeof(int) * n, cudaMemcpyDeviceToHost, g->stream), "readback"))
+    return MR_ERR_CUDA;
+  return check_cuda(cudaStreamSynchronize(g->stream), "readback sync") ? MR_ERR_CUDA : MR_OK;
+}
+
+int adapt_iteration(mr_grid *g, int crit, double er, double ec, int flags, int *nch) {
+  *nch = 0;
+  const int n = g->nleaf, G = adapt_shell(g->desc.wav_N, g->desc.wav_Nt);
+  cudaStream_t st = g->stream;
+  void *Pv;
+  int Gi;
+  // 1-2: ghosts of the criterion field, block criterion
+  int e = launch_ghost(g, field_ptr(g, crit), field_ptr(g, crit), G, true, &Pv, &Gi);
+  if (e) return e;
+  const double *P = (const double *)Pv;
+  e = launch_criterion(g, P, Gi, g->maxdet);
+  if (e) return e;
+  // 3-4: status and policy
+  Tree t = tree_view(g);
+  const int tb = 128, nblk = (n + tb - 1) / tb;
+  MR_LAUNCH(g, MRK_STATUS, k_status<<<nblk, tb, 0, st>>>(n, g->maxdet, er, ec, flags, g->lev[g->cur], g->refined,
+                                                         g->desc.lmin, g->desc.lmax, g->status));
+  int8_t *sa = g->status, *sb = (int8_t *)g->newsrc;
+  int it = 0;
+  for (;; ++it) {
+    if (it > 256) {
+      set_error("policy did not reach a fixed point within 256 sweeps");
+      return MR_ERR_TIMEOUT;
+    }
+    if (check_cuda(cudaMemsetAsync(g->counter, 0, sizeof(int), st), "memset")) return MR_ERR_CUDA;
+    MR_LAUNCH(g, MRK_POLICY, k_policy<<<nblk, tb, 0, st>>>(t, sa, sb, g->counter));
+    int changed;
+    e = read_ints(g, g->counter, &changed, 1);
+    if (e) return e;
+    int8_t *tmp = sa;
+    sa = sb, sb = tmp;
+    if (!changed) break;
+  }
+  if (sa != g->status &&
+      check_cuda(cudaMemcpyAsync(g->status, sa, n, cudaMemcpyDeviceToDevice, st), "status copy"))
+    return MR_ERR_CUDA;
+  // 5: new tree
+  if (check_cuda(cudaMemsetAsync(g->counter, 0, sizeof(int), st), "memset")) return MR_ERR_CUDA;
+  MR_LAUNCH(g, MRK_SCAN, k_count<<<nblk, tb, 0, st>>>(n, g->status, g->anc[g->cur], g->scan, g->counter));
+  MR_LAUNCH(g, MRK_SCAN, k_scan<<<1, 1024, 0, st>>>(g->scan, n));
+  int hc[2];
+  e = read_ints(g, g->counter, &hc[0], 1);
+  if (!e) e = read_ints(g, g->scan + n, &hc[1], 1);
+  if (e) return e;
+  const int changed = hc[0], nn = hc[1];
+  if (check_cuda(cudaGetLastError(), "policy")) return MR_ERR_CUDA;
+  if (changed == 0) return MR_OK;
+  if (nn > g->desc.capacity) {
+    set_error("adaptation exceeds the leaf capacity");
+    return MR_ERR_NOMEM;
+  }
+  const int nx = g->cur ^ 1;
+  MR_LAUNCH(g, MRK_EMIT, k_emit<<<nblk, tb, 0, st>>>(n, g->M, g->status, g->scan, g->lev[g->cur],
+                                                     g->anc[g->cur], g->refined, g->lev[nx], g->anc[nx],
+                                                     g->keys[nx], g->refined2, g->newsrc));
+  // owner map of the new tree
+  Tree tn = next_view(g, nn);
+  {
+    const int saved_cur = g->cur, saved_n = g->nleaf;
+    g->cur = nx, g->nleaf = nn;
+    e = build_map(g);
+    g->cur = saved_cur, g->nleaf = saved_n;
+    if (e) return e;
+  }
+  int *nmask = g->cmask + g->desc.capacity;  // second half of the mask buffer
+  int *hasD = g->hasD;
+  MR_LAUNCH(g, MRK_UPDATE, k_newmask<<<(nn + tb - 1) / tb, tb, 0, st>>>(tn, g->newsrc, nmask));
+  // 6-9: every field: ghosts (criterion field first: P is current), interpolate, update
+  const bool f32 = g->desc.precision == MR_F32;
+  for (int pass = 0; pass < g->desc.nfields; ++pass) {
+    const int fid = pass == 0 ? crit : (pass <= crit ? pass - 1 : pass);
+    if (pass > 0) {
+      e = launch_ghost(g, field_ptr(g, fid), field_ptr(g, fid), G, true, &Pv, &Gi);
+      if (e) return e;
+      P = (const double *)Pv;
+    }
+    e = f32 ? interp_dispatch<float>(g, t, tn, P, Gi, fid, nmask, hasD)
+            : interp_dispatch<double>(g, t, tn, P, Gi, fid, nmask, hasD);
+    if (e) return e;
+  }
+  // swap to the new tree and pool
+  g->cur = nx;
+  g->map = g->maps[nx];
+  g->pool_cur ^= 1;
+  g->nleaf = nn;
+  int *tmp = g->refined;
+  g->refined = g->refined2;
+  g->refined2 = tmp;
+  *nch = changed;
+  return check_cuda(cudaGetLastError(), "adapt") ? MR_ERR_CUDA : MR_OK;
 }
 
 }  // namespace mr

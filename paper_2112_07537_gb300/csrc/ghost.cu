@@ -293,14 +293,17 @@ static int ghost_dispatch(mr_grid *g, const TI *phi_in, TI *phi_out, int G, TP *
 // Ghost fill of phi_in with requested shell G.  fp64: padded buffers in FP64
 // (the adaptation path), else in the field's element type.  On return *P is
 // the padded buffer (internal shell *Gi).
-int launch_ghost(mr_grid *g, const void *phi_in, void *phi_out, int G, bool fp64, void **P, int *Gi) {
+int launch_ghost(mr_grid *g, const void *phi_in, void *phi_out, int G, bool fp64, void **P, int *Gi,
+                 bool *p_is64) {
   const int nb = g->desc.nb;
   if (G < 1 || G > MR_MAX_SHELL) return MR_ERR_INVALID;
   if (G > nb / 2) return MR_ERR_BALANCE;
   const int gi = internal_shell(g->desc.wav_N, g->desc.wav_Nt, G, nb);
-  const int cap = fp64 ? g->shell_ad : g->shell_rk;
-  if (gi > cap) return MR_ERR_UNSUPPORTED;
+  // shells wider than the stencil buffers go through the (wider) FP64 buffers
+  if (gi > g->shell_rk) fp64 = true;
+  if (gi > g->shell_ad) return MR_ERR_UNSUPPORTED;
   *Gi = gi;
+  if (p_is64) *p_is64 = fp64 || g->desc.precision == MR_F64;
   const bool f32 = g->desc.precision == MR_F32;
   if (fp64) {
     *P = g->padP64;

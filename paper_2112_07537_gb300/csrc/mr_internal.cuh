@@ -164,7 +164,8 @@ struct mr_grid {
   int *newsrc;            // 8*capacity: source mapping of new leaves
   int *counter;           // device words: [0] changed count, [1] error bits, [2..] scratch
   double *dscratch;       // reduction scratch
-  int *cmask;             // per-leaf coarse-direction masks (ghost fill)
+  int *cmask;             // per-leaf coarse-direction masks (ghost fill), then new-band masks
+  int *hasD;              // per new leaf: the update step has discarded details
   // launch registry: counts every kernel launch; with profiling on, brackets
   // each launch with CUDA events on the grid's stream
   long long launches[32];
@@ -200,7 +201,7 @@ void *next_field_ptr(mr_grid *g, int fid);
 
 // ghost.cu
 int launch_ghost(mr_grid *g, const void *phi_in, void *phi_out, int G, bool fp64, void **P,
-                 int *Gi);
+                 int *Gi, bool *p_is64 = nullptr);
 int launch_crop(mr_grid *g, const void *P, int Gi, void *out, int G, bool fp64_src);
 int launch_crop64(mr_grid *g, const double *P, int Gi, double *out, int G);
 int adapt_shell(int N, int Nt);

@@ -1,0 +1,121 @@
+"""Device criterion and adaptation vs the FP64 oracle, through the C ABI.
+
+Integer results (trees, Morton keys, statuses through the trees they
+produce) must be bit-exact.  The FP64 criterion is bit-exact (same evaluation
+order, no fused multiply-add); FP64 adaptation fields are compared at 1e-13
+relative; FP32 grids are compared against the oracle run on the same FP32
+snapshot (upcast), with FP64 ghosts on both sides, so the refinement and
+coarsening decisions must agree exactly.
+"""
+import numpy as np
+import pytest
+
+from paper_2112_07537_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mr():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2112_07537_gb300 import build, mrgb
+    build.build()
+    return mrgb
+
+
+def _tree():
+    nt, tl = (4, 4, 4), 0.25
+    lev, anc = I.uniform_leaves(nt, 0)
+    lev, anc = I.refine_leaves(lev, anc, np.all((anc >= 1) & (anc <= 2), axis=1))
+    lev, anc = I.refine_leaves(lev, anc, (lev == 1) & np.all(anc == 3, axis=1))
+    lev, anc = I.balance(nt, lev, anc)
+    return nt, tl, lev, anc
+
+
+def _setup(mr, O, N, Nt, prec, lmax=3, cap=4000):
+    nt, tl, lev, anc = _tree()
+    nb = 16 if N < 6 else 24
+    g = mr.Grid(nt, tl, nb, 0, lmax, N, Nt, lev, anc, precision=prec, capacity=cap)
+    glev, ganc, _ = g.leaves()
+    og = O.Grid(nt, tl, nb, N, Nt, 0, lmax, glev, ganc)
+    xyz = I.point_coords(nt, tl, nb, glev, ganc)
+    phi = I.gaussian(xyz, (0.52, 0.5, 0.47), 0.06) + 0.3 * I.gaussian(xyz, (0.2, 0.8, 0.3), 0.1)
+    if prec == mr.F32:
+        phi = phi.astype(np.float32)
+    g.field_copy_in(0, phi)
+    return g, og, phi.astype(np.float64)
+
+
+@pytest.mark.parametrize("N,Nt", [(2, 0), (4, 0), (4, 2), (6, 2)])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_criterion_bitexact(mr, oracle_mod, N, Nt, prec):
+    import torch
+    O = oracle_mod
+    g, og, phi = _setup(mr, O, N, Nt, prec)
+    md = torch.empty(og.nleaf, dtype=torch.float64, device="cuda")
+    g.criterion(0, md)
+    g.sync()
+    ref = O.block_maxdet(og, phi)
+    assert np.array_equal(md.cpu().numpy(), ref)
+
+
+def _eps(ref):
+    s = np.sort(ref)
+    return float(s[int(0.8 * len(s))]), float(s[int(0.45 * len(s))])
+
+
+@pytest.mark.parametrize("N,Nt", [(2, 0), (4, 0), (4, 2), (2, 2)])
+def test_adapt_iteration_fp64_matches_oracle(mr, oracle_mod, N, Nt):
+    O = oracle_mod
+    g, og, phi = _setup(mr, O, N, Nt, mr.F64)
+    er, ec = _eps(O.block_maxdet(og, phi))
+    nch = g.adapt_iter(0, er, ec)
+    og2, ophi, _, onch, _, st = O.adapt_iter(og, phi, er, ec)
+    assert nch == onch and nch > 0
+    assert (st == 1).any() and (st == -1).any()
+    glev, ganc, gkeys = g.leaves()
+    okeys = np.array([O.morton_key(l, *a, og.lmax) for l, a in zip(og2.lev, og2.anc)], np.uint64)
+    assert np.array_equal(glev, og2.lev) and np.array_equal(ganc, og2.anc)
+    assert np.array_equal(gkeys, okeys) and np.all(np.diff(gkeys.astype(np.float64)) > 0)
+    got = g.field_copy_out(0)
+    assert np.abs(got - ophi).max() <= 1e-13 * np.abs(ophi).max()
+
+
+@pytest.mark.parametrize("N,Nt", [(4, 2), (6, 2)])
+def test_adapt_to_convergence_fp32_flags_exact(mr, oracle_mod, N, Nt):
+    """Full Alg. SM3 loop on an FP32 grid: each iteration the oracle runs on
+    the device's FP32 snapshot; statuses (through the trees) match exactly."""
+    O = oracle_mod
+    g, og, phi = _setup(mr, O, N, Nt, mr.F32)
+    er, ec = _eps(O.block_maxdet(og, phi))
+    refined = None
+    for it in range(12):
+        lev, anc, _ = g.leaves()
+        cur = og.with_leaves(lev, anc)
+        snap = g.field_copy_out(0).astype(np.float64)
+        og2, ophi, refined_o, onch, _, _ = O.adapt_iter(cur, snap, er, ec, refined)
+        nch = g.adapt_iter(0, er, ec) if it else g.adapt_iter(0, er, ec)
+        assert nch == onch
+        lev2, anc2, _ = g.leaves()
+        assert np.array_equal(lev2, og2.lev) and np.array_equal(anc2, og2.anc)
+        got = g.field_copy_out(0).astype(np.float64)
+        assert np.abs(got - ophi).max() <= 2e-6 * max(1.0, np.abs(ophi).max())
+        refined = refined_o
+        if nch == 0:
+            break
+    assert it > 0
+
+
+def test_mr_adapt_loop_fp64(mr, oracle_mod):
+    O = oracle_mod
+    g, og, phi = _setup(mr, O, 4, 2, mr.F64)
+    er, ec = _eps(O.block_maxdet(og, phi))
+    total = g.adapt(0, er, ec)
+    og2, ophi, iters = O.adapt(og, phi, er, ec)
+    lev, anc, _ = g.leaves()
+    assert total > 0
+    assert np.array_equal(lev, og2.lev) and np.array_equal(anc, og2.anc)
+    got = g.field_copy_out(0)
+    assert np.abs(got - ophi).max() <= 1e-13 * np.abs(ophi).max()
