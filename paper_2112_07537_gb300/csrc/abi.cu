@@ -107,7 +107,7 @@ static int layout(const mr_grid_desc *d, Layout *L, int *shell_rk, int *shell_ad
   const size_t nb3 = (size_t)d->nb * d->nb * d->nb, cap = (size_t)d->capacity;
   const int gad = adapt_shell(d->wav_N, d->wav_Nt);
   *shell_rk = internal_shell(d->wav_N, d->wav_Nt, 3, d->nb);
-  *shell_ad = internal_shell(d->wav_N, d->wav_Nt, gad, d->nb);
+  *shell_ad = std::max(internal_shell(d->wav_N, d->wav_Nt, gad, d->nb), *shell_rk);
   const size_t wr = d->nb + 2 * *shell_rk, wa = d->nb + 2 * *shell_ad;
   *M = d->lmax;
   *map_cells = ((size_t)d->ntree[0] << d->lmax) * ((size_t)d->ntree[1] << d->lmax) *
@@ -402,9 +402,16 @@ int mr_ghost_fill64(mr_grid *g, int fid, int G, double *padded) {
 
 int mr_rhs_advect(mr_grid *g, int phi, const double *u, int out, int scheme) {
   if (!fid_ok(g, phi) || !fid_ok(g, out) || !u) return MR_ERR_INVALID;
+  void *f = field_ptr(g, phi);
+  if (g->desc.precision == MR_F32) {
+    int Gi;
+    int e = launch_prep32(g, f, &Gi);
+    if (!e) e = launch_fused(g, f, g->padP, g->padQ, Gi, nullptr, field_ptr(g, out), 0, 0.0, u, scheme, true);
+    if (!e) e = launch_writeback32(g, Gi, f);
+    return e;
+  }
   void *P;
   int Gi;
-  void *f = field_ptr(g, phi);
   int e = launch_ghost(g, f, f, 3, false, &P, &Gi);
   if (e) return e;
   return launch_rhs_stage(g, P, Gi, nullptr, field_ptr(g, out), 0, 0.0, u, scheme, true);
@@ -424,12 +431,21 @@ int mr_step(mr_grid *g, int phi, double dt, const double *u, int scheme) {
   void *y1 = field_ptr(g, g->desc.nfields), *y2 = field_ptr(g, g->desc.nfields + 1);
   void *src[3] = {un, y1, y2};
   void *dst[3] = {y1, y2, un};
+  const bool fused = g->desc.precision == MR_F32;
   for (int s = 0; s < 3; ++s) {
-    void *P;
-    int Gi;
-    int e = launch_ghost(g, src[s], src[s], 3, false, &P, &Gi);
-    if (e) return e;
-    e = launch_rhs_stage(g, P, Gi, un, dst[s], s, dt, u, scheme, false);
+    int Gi, e;
+    if (fused) {
+      // FP32: substitution pre-pass for leaves next to a coarser one, then the
+      // fused ghost-gather + rhs + stage kernel; the stage-0 substitution of
+      // u^n is written back (stages 1 and 2 read u^n pointwise)
+      e = launch_prep32(g, src[s], &Gi);
+      if (!e) e = launch_fused(g, src[s], g->padP, g->padQ, Gi, un, dst[s], s, dt, u, scheme, false);
+      if (!e && s == 0) e = launch_writeback32(g, Gi, un);
+    } else {
+      void *P;
+      e = launch_ghost(g, src[s], src[s], 3, false, &P, &Gi);
+      if (!e) e = launch_rhs_stage(g, P, Gi, un, dst[s], s, dt, u, scheme, false);
+    }
     if (e) return e;
   }
   return MR_OK;

@@ -164,6 +164,191 @@ __global__ void __launch_bounds__(256) k_part1(Tree t, const TI *__restrict__ ph
   }
 }
 
+// ---------------------------------------------------------------------------
+// Part 1 with the coarse-level values staged in shared memory, substitution,
+// and Part 2 pushed to the coarser neighbours.
+//
+// T tile: every level-(L-1) value the zero-detail refinement of the padded
+// cube can read, fetched once (one owner lookup per coarse point instead of
+// one per tap).  Same taps, weights and summation order as refine_point, so
+// the FP64 instantiation stays bit-identical to the direct evaluation.
+// After the substitution, the leaf coarsens (tensor H^a) its padded block at
+// every ghost point (shell Gpush) of each coarser neighbour c that lies in
+// the leaf's region, and writes the value into c's entry of Q: each ghost
+// point of c is owned by exactly one finer leaf, so the writes never collide.
+// ---------------------------------------------------------------------------
+template <int N>
+__host__ __device__ constexpr int tq_lo(int Gi) { return -((Gi + 2) / 2) - (N / 2 - 1); }
+template <int N>
+__host__ __device__ constexpr int tq_hi(int nb, int Gi) { return (nb + Gi - 2) / 2 + N / 2; }
+
+template <typename TI, typename TP, int N, int NT>
+__global__ void __launch_bounds__(256) k_prep(Tree t, const TI *__restrict__ phi, TP *__restrict__ P,
+                                              TP *__restrict__ Q, int Gi, int Gpush, int only_coarse,
+                                              int use_tile, int *cmask_out, int *err) {
+  using W = Wav<N, NT>;
+  const int b = blockIdx.x;
+  const int nb = t.nb, Wd = nb + 2 * Gi;
+  const size_t np = (size_t)Wd * Wd * Wd;
+  const int L = __ldg(t.lev + b);
+  const int ax = __ldg(t.anc + 3 * b) * nb, ay = __ldg(t.anc + 3 * b + 1) * nb,
+            az = __ldg(t.anc + 3 * b + 2) * nb;
+  __shared__ int cmask;
+  __shared__ int cslots[27];
+  __shared__ int ncs;
+  if (threadIdx.x == 0) cmask = 0, ncs = 0;
+  __syncthreads();
+  if (threadIdx.x < 27) {
+    int m = coarse_mask_dir(t, b, threadIdx.x, err);
+    if (m) atomicOr(&cmask, m);
+  }
+  __syncthreads();
+  const int mask = cmask;
+  if (threadIdx.x == 0 && cmask_out) cmask_out[b] = mask;
+  if (only_coarse && !mask) return;
+  extern __shared__ unsigned char smraw[];
+  TP *T = reinterpret_cast<TP *>(smraw);
+  const int qlo = tq_lo<N>(Gi), nq = tq_hi<N>(nb, Gi) - qlo + 1;
+  const bool tile = use_tile && mask;
+  if (tile) {
+    const int cx = ax / 2 + qlo, cy = ay / 2 + qlo, cz = az / 2 + qlo;
+    for (int p = threadIdx.x; p < nq * nq * nq; p += blockDim.x) {
+      const int qx = cx + p % nq, qy = cy + (p / nq) % nq, qz = cz + p / (nq * nq);
+      const int o = owner(t, L - 1, qx, qy, qz);
+      TP v;
+      if (__ldg(t.lev + o) < L - 1) {
+        v = TP(__int_as_float(0x7fc00000));  // never read by a valid refinement
+      } else {
+        const int Lo = __ldg(t.lev + o);
+        const int lx = local_index(t, o, Lo, L - 1, qx, 0), ly = local_index(t, o, Lo, L - 1, qy, 1),
+                  lz = local_index(t, o, Lo, L - 1, qz, 2);
+        v = TP(ld(phi + (size_t)o * nb * nb * nb + lx + nb * (ly + nb * lz)));
+      }
+      T[p] = v;
+    }
+    __syncthreads();
+  }
+  TP *Pb = P + (size_t)b * np;
+  const TI *phib = phi + (size_t)b * nb * nb * nb;
+  for (size_t p = threadIdx.x; p < np; p += blockDim.x) {
+    const int i = (int)(p % Wd) - Gi, j = (int)((p / Wd) % Wd) - Gi, k = (int)(p / ((size_t)Wd * Wd)) - Gi;
+    TP v;
+    if (i >= 0 && i < nb && j >= 0 && j < nb && k >= 0 && k < nb) {
+      v = TP(ld(phib + i + nb * (j + nb * k)));
+    } else {
+      const int gx = ax + i, gy = ay + j, gz = az + k;
+      const int o = owner(t, L, gx, gy, gz);
+      const int Lo = __ldg(t.lev + o);
+      if (Lo >= L) {
+        v = TP(leaf_value(t, phi, o, L, gx, gy, gz, err));
+      } else if (Lo == L - 1) {
+        if (tile) {
+          // refine_point with T from shared memory (local coarse index g/2)
+          const bool odx = i & 1, ody = j & 1, odz = k & 1;
+          const int hx = odx ? W::hwK : W::hwJ, hy = ody ? W::hwK : W::hwJ, hz = odz ? W::hwK : W::hwJ;
+          TP s = TP(0);
+          for (int oz = -hz; oz <= hz; ++oz) {
+            if ((k + oz) & 1) continue;
+            const TP wz = TP(odz ? W::K(oz) : W::J(oz));
+            for (int oy = -hy; oy <= hy; ++oy) {
+              if ((j + oy) & 1) continue;
+              const TP wy = TP(ody ? W::K(oy) : W::J(oy));
+              for (int ox = -hx; ox <= hx; ++ox) {
+                if ((i + ox) & 1) continue;
+                const TP wx = TP(odx ? W::K(ox) : W::J(ox));
+                const TP wgt = rmul(rmul(wx, wy), wz);
+                if (wgt == TP(0)) continue;
+                const int qx = (i + ox) / 2 - qlo, qy = (j + oy) / 2 - qlo, qz = (k + oz) / 2 - qlo;
+                s = radd(s, rmul(wgt, T[qx + nq * (qy + nq * qz)]));
+              }
+            }
+          }
+          if (s != s) atomicOr(err, 2);
+          v = s;
+        } else {
+          v = refine_point<TI, TP, N, NT>(t, phi, L, gx, gy, gz, err);
+        }
+      } else {
+        atomicOr(err, 8);
+        v = TP(0);
+      }
+    }
+    Pb[p] = v;
+  }
+  __syncthreads();
+  if (!mask) return;
+  // substitution, degree by degree
+  for (int deg = 1; deg <= 3; ++deg) {
+    for (int p = threadIdx.x; p < nb * nb * nb; p += blockDim.x) {
+      const int i = p % nb, j = (p / nb) % nb, k = p / (nb * nb);
+      const int o0 = i & 1, o1 = j & 1, o2 = k & 1;
+      if (o0 + o1 + o2 != deg) continue;
+      if (!in_band(mask, i, j, k, nb, W::ext_f, W::ext_b)) continue;
+      const int hx = o0 ? W::hwG : 0, hy = o1 ? W::hwG : 0, hz = o2 ? W::hwG : 0;
+      TP s = TP(0);
+      for (int tz = -hz; tz <= hz; ++tz)
+        for (int ty = -hy; ty <= hy; ++ty)
+          for (int tx = -hx; tx <= hx; ++tx) {
+            if (!tx && !ty && !tz) continue;
+            const TP wgt = rmul(rmul(TP(o0 ? W::G(tx) : 1.0), TP(o1 ? W::G(ty) : 1.0)),
+                                TP(o2 ? W::G(tz) : 1.0));
+            if (wgt == TP(0)) continue;
+            s = radd(s, rmul(wgt, Pb[(i + tx + Gi) + Wd * ((j + ty + Gi) + (size_t)Wd * (k + tz + Gi))]));
+          }
+      Pb[(i + Gi) + Wd * ((j + Gi) + (size_t)Wd * (k + Gi))] = -s;
+    }
+    __syncthreads();
+  }
+  // distinct coarser neighbours
+  if (threadIdx.x == 0) {
+    for (int m = 0; m < 27; ++m) {
+      if (!((mask >> m) & 1)) continue;
+      const int dd[3] = {m % 3 - 1, (m / 3) % 3 - 1, m / 9 - 1};
+      const int o = owner(t, L, ax + (dd[0] < 0 ? -1 : dd[0] > 0 ? nb : 0),
+                          ay + (dd[1] < 0 ? -1 : dd[1] > 0 ? nb : 0), az + (dd[2] < 0 ? -1 : dd[2] > 0 ? nb : 0));
+      bool seen = false;
+      for (int q = 0; q < ncs; ++q) seen |= cslots[q] == o;
+      if (!seen) cslots[ncs++] = o;
+    }
+  }
+  __syncthreads();
+  // push: ghost points of each coarser neighbour c inside this leaf's region
+  const int hb = nb / 2;
+  const int Wg = nb + 2 * Gi;
+  for (int ci = 0; ci < ncs; ++ci) {
+    const int c = cslots[ci];
+    const int Lc = L - 1;
+    int ac[3];
+    for (int d = 0; d < 3; ++d) ac[d] = __ldg(t.anc + 3 * c + d) * nb;
+    for (int p = threadIdx.x; p < hb * hb * hb; p += blockDim.x) {
+      // coarse point inside this leaf (level Lc index)
+      const int G[3] = {ax / 2 + p % hb, ay / 2 + (p / hb) % hb, az / 2 + p / (hb * hb)};
+      int lc[3];
+      bool in = true, inside = true;
+      for (int d = 0; d < 3; ++d) {
+        const int Pn = npts(t, Lc, d);
+        int off = pwrap(G[d] - ac[d], Pn);
+        if (off >= Pn / 2) off -= Pn;
+        lc[d] = off;
+        in &= off >= -Gpush && off < nb + Gpush;
+        inside &= off >= 0 && off < nb;
+      }
+      if (!in || inside) continue;
+      // fine index in this leaf of the coincident point: 2G - a*nb
+      const int fl[3] = {2 * G[0] - ax, 2 * G[1] - ay, 2 * G[2] - az};
+      TP s = TP(0);
+      for (int tz = -W::hwH; tz <= W::hwH; ++tz)
+        for (int ty = -W::hwH; ty <= W::hwH; ++ty)
+          for (int tx = -W::hwH; tx <= W::hwH; ++tx) {
+            const TP wgt = rmul(rmul(TP(W::H(tx)), TP(W::H(ty))), TP(W::H(tz)));
+            if (wgt == TP(0)) continue;
+            s = radd(s, rmul(wgt, Pb[(fl[0] + tx + Gi) + Wd * ((fl[1] + ty + Gi) + (size_t)Wd * (fl[2] + tz + Gi))]));
+          }
+      Q[(size_t)c * np + (lc[0] + Gi) + Wg * ((lc[1] + Gi) + (size_t)Wg * (lc[2] + Gi))] = s;
+    }
+  }
+}
+
 // Part 2: ghost points (shell G) owned by a finer leaf F <- tensor H^a of
 // F's padded block, nearest periodic image.  Writes Q only.
 template <typename TP, int N, int NT>
@@ -280,11 +465,34 @@ static int ghost_impl(mr_grid *g, const TI *phi_in, TI *phi_out, int G, TP *P, T
   return MR_OK;
 }
 
+template <typename TI, typename TP, int N, int NT>
+static int ghost_impl(mr_grid *g, const TI *phi_in, TI *phi_out, int G, TP *P, TP *Q, int Gi, int only_coarse) {
+  Tree t = tree_view(g);
+  const int n = g->nleaf, nb = g->desc.nb;
+  int *err = g->counter + 1;
+  const int nq = tq_hi<N>(nb, Gi) - tq_lo<N>(Gi) + 1;
+  const size_t smT = sizeof(TP) * (size_t)nq * nq * nq;
+  const int use_tile = smT <= 200 * 1024;
+  const size_t sm = use_tile ? smT : 0;
+  if (sm > 48 * 1024 &&
+      check_cuda(cudaFuncSetAttribute(k_prep<TI, TP, N, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
+                 "k_prep smem"))
+    return MR_ERR_CUDA;
+  MR_LAUNCH(g, MRK_PART1, k_prep<TI, TP, N, NT><<<n, 256, sm, g->stream>>>(t, phi_in, P, Q, Gi, G, only_coarse,
+                                                                           use_tile, g->cmask, err));
+  if (check_cuda(cudaGetLastError(), "k_prep")) return MR_ERR_CUDA;
+  if (only_coarse) return MR_OK;
+  MR_LAUNCH(g, MRK_MERGE, k_merge<TI, TP><<<n, 256, 0, g->stream>>>(t, P, Q, Gi, G, g->cmask, phi_out));
+  if (check_cuda(cudaGetLastError(), "k_merge")) return MR_ERR_CUDA;
+  return MR_OK;
+}
+
 template <typename TI, typename TP>
-static int ghost_dispatch(mr_grid *g, const TI *phi_in, TI *phi_out, int G, TP *P, TP *Q, int Gi) {
+static int ghost_dispatch(mr_grid *g, const TI *phi_in, TI *phi_out, int G, TP *P, TP *Q, int Gi,
+                          int only_coarse = 0) {
   const int N = g->desc.wav_N, Nt = g->desc.wav_Nt;
 #define MR_GCASE(n_, nt_) \
-  if (N == n_ && Nt == nt_) return ghost_impl<TI, TP, n_, nt_>(g, phi_in, phi_out, G, P, Q, Gi);
+  if (N == n_ && Nt == nt_) return ghost_impl<TI, TP, n_, nt_>(g, phi_in, phi_out, G, P, Q, Gi, only_coarse);
   MR_GCASE(2, 0) MR_GCASE(2, 2) MR_GCASE(4, 0) MR_GCASE(4, 2) MR_GCASE(6, 0) MR_GCASE(6, 2)
 #undef MR_GCASE
   return MR_ERR_UNSUPPORTED;
@@ -301,7 +509,7 @@ int launch_ghost(mr_grid *g, const void *phi_in, void *phi_out, int G, bool fp64
   const int gi = internal_shell(g->desc.wav_N, g->desc.wav_Nt, G, nb);
   // shells wider than the stencil buffers go through the (wider) FP64 buffers
   if (gi > g->shell_rk) fp64 = true;
-  if (gi > g->shell_ad) return MR_ERR_UNSUPPORTED;
+  if (fp64 && gi > g->shell_ad) return MR_ERR_UNSUPPORTED;
   *Gi = gi;
   if (p_is64) *p_is64 = fp64 || g->desc.precision == MR_F64;
   const bool f32 = g->desc.precision == MR_F32;
@@ -319,6 +527,35 @@ int launch_ghost(mr_grid *g, const void *phi_in, void *phi_out, int G, bool fp64
                                         (float *)g->padP, (float *)g->padQ, gi);
   return ghost_dispatch<double, double>(g, (const double *)phi_in, (double *)phi_out, G,
                                         (double *)g->padP, (double *)g->padQ, gi);
+}
+
+// substituted band of leaves with a coarser neighbour -> field
+template <typename TO, typename TP>
+__global__ void __launch_bounds__(256) k_writeback(int nb, const TP *__restrict__ P, int Gi, const int *__restrict__ cmask,
+                                                   TO *__restrict__ phi) {
+  const int b = blockIdx.x;
+  if (!cmask[b]) return;
+  const int Wd = nb + 2 * Gi;
+  const size_t np = (size_t)Wd * Wd * Wd;
+  for (int p = threadIdx.x; p < nb * nb * nb; p += blockDim.x) {
+    const int i = p % nb, j = (p / nb) % nb, k = p / (nb * nb);
+    if (!((i | j | k) & 1)) continue;
+    phi[(size_t)b * nb * nb * nb + p] = TO(P[(size_t)b * np + (i + Gi) + Wd * ((j + Gi) + (size_t)Wd * (k + Gi))]);
+  }
+}
+
+// Pre-pass of the fused FP32 stage: leaves with a coarser neighbour build
+// their padded block (substituted) and push Part-2 values (shell 3).
+int launch_prep32(mr_grid *g, const void *phi, int *Gi) {
+  const int gi = internal_shell(g->desc.wav_N, g->desc.wav_Nt, 3, g->desc.nb);
+  *Gi = gi;
+  return ghost_dispatch<float, float>(g, (const float *)phi, nullptr, 3, (float *)g->padP, (float *)g->padQ, gi, 1);
+}
+
+int launch_writeback32(mr_grid *g, int Gi, void *phi) {
+  MR_LAUNCH(g, MRK_MERGE, k_writeback<float, float><<<g->nleaf, 256, 0, g->stream>>>(
+                              g->desc.nb, (const float *)g->padP, Gi, g->cmask, (float *)phi));
+  return check_cuda(cudaGetLastError(), "k_writeback") ? MR_ERR_CUDA : MR_OK;
 }
 
 int launch_crop64(mr_grid *g, const double *P, int Gi, double *out, int G) {

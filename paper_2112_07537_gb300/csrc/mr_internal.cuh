@@ -204,6 +204,10 @@ int launch_ghost(mr_grid *g, const void *phi_in, void *phi_out, int G, bool fp64
                  int *Gi, bool *p_is64 = nullptr);
 int launch_crop(mr_grid *g, const void *P, int Gi, void *out, int G, bool fp64_src);
 int launch_crop64(mr_grid *g, const double *P, int Gi, double *out, int G);
+int launch_prep32(mr_grid *g, const void *phi, int *Gi);
+int launch_writeback32(mr_grid *g, int Gi, void *phi);
+int launch_fused(mr_grid *g, const void *phi, const void *P, const void *Q, int Gi, const void *u, void *out,
+                 int stage, double dt, const double *uc, int scheme, bool rhs_only);
 int adapt_shell(int N, int Nt);
 // stencil.cu
 int launch_rhs_stage(mr_grid *g, const void *P, int Gi, const void *u, void *out, int stage,

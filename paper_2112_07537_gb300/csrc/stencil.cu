@@ -97,6 +97,172 @@ __global__ void __launch_bounds__(256) k_rhs_stage(Tree t, const T *__restrict__
   }
 }
 
+__device__ __forceinline__ int floordiv2(int a) { return a >= 0 ? a / 2 : -((-a + 1) / 2); }
+
+// ---------------------------------------------------------------------------
+// Fused FP32 stage: one CTA per leaf.  Shared memory holds the block and the
+// six face slabs (3 deep) that the 1D WENO/CONS stencils read:
+//   interior  <- field (or the substituted block written by k_prep);
+//   same-level face  <- copy of the neighbour's field;
+//   coarser face     <- zero-detail refinement (J^s/K^s) of a coarse tile
+//                       staged per face (one owner lookup per coarse point);
+//   finer face       <- the Part-2 coarsening pushed by the finer leaves
+//                       (lifted wavelets) or the coincident value (N.0).
+// Then rhs and the RK3 stage combination, written to out.
+// ---------------------------------------------------------------------------
+template <int N, int NT, int SCHEME>
+__global__ void __launch_bounds__(512) k_fused(Tree t, const float *__restrict__ phi, const float *__restrict__ P,
+                                               const float *__restrict__ Q, int Gi, const int *__restrict__ cmask,
+                                               const float *u, float *out, int stage, float dt, float ux, float uy,
+                                               float uz, int rhs_only, int *err) {
+  using W = Wav<N, NT>;
+  constexpr int GS = 3;
+  const int b = blockIdx.x, nb = t.nb, Ws = nb + 2 * GS, Wd = nb + 2 * Gi;
+  const size_t np = (size_t)Wd * Wd * Wd, nb3 = (size_t)nb * nb * nb;
+  const int L = __ldg(t.lev + b);
+  const int a[3] = {__ldg(t.anc + 3 * b) * nb, __ldg(t.anc + 3 * b + 1) * nb, __ldg(t.anc + 3 * b + 2) * nb};
+  extern __shared__ float sm[];
+  float *tile = sm;
+  float *Tt = sm + (size_t)Ws * Ws * Ws;
+  auto tix = [&](int i, int j, int k) { return (i + GS) + Ws * ((j + GS) + Ws * (k + GS)); };
+  const int mask = cmask[b];
+  // interior
+  if (mask) {
+    const float *Pb = P + (size_t)b * np;
+    for (int p = threadIdx.x; p < (int)nb3; p += blockDim.x) {
+      const int i = p % nb, j = (p / nb) % nb, k = p / (nb * nb);
+      tile[tix(i, j, k)] = Pb[(i + Gi) + Wd * ((j + Gi) + (size_t)Wd * (k + Gi))];
+    }
+  } else {
+    const float4 *src = reinterpret_cast<const float4 *>(phi + (size_t)b * nb3);
+    const int nq = nb / 4;
+    for (int p = threadIdx.x; p < (int)nb3 / 4; p += blockDim.x) {
+      const float4 v = __ldg(src + p);
+      const int i = (p % nq) * 4, j = (p / nq) % nb, k = p / (nq * nb);
+      float *d = tile + tix(i, j, k);
+      d[0] = v.x, d[1] = v.y, d[2] = v.z, d[3] = v.w;
+    }
+  }
+  // faces
+  for (int f = 0; f < 6; ++f) {
+    const int ax = f >> 1, sg = (f & 1) ? 1 : -1;
+    int g0[3] = {a[0], a[1], a[2]};
+    g0[ax] += sg < 0 ? -1 : nb;
+    const int o = owner(t, L, g0[0], g0[1], g0[2]);
+    const int Lo = __ldg(t.lev + o);
+    // slab index ranges (block-local, level L)
+    int lo[3] = {0, 0, 0}, ext[3] = {nb, nb, nb};
+    lo[ax] = sg < 0 ? -GS : nb;
+    ext[ax] = GS;
+    const int cnt = ext[0] * ext[1] * ext[2];
+    if (Lo == L) {
+      const float *po = phi + (size_t)o * nb3;
+      for (int p = threadIdx.x; p < cnt; p += blockDim.x) {
+        int c[3] = {lo[0] + p % ext[0], lo[1] + (p / ext[0]) % ext[1], lo[2] + p / (ext[0] * ext[1])};
+        int l[3] = {c[0], c[1], c[2]};
+        l[ax] = sg < 0 ? c[ax] + nb : c[ax] - nb;
+        tile[tix(c[0], c[1], c[2])] = __ldg(po + l[0] + nb * (l[1] + nb * l[2]));
+      }
+    } else if (Lo > L) {
+      for (int p = threadIdx.x; p < cnt; p += blockDim.x) {
+        const int c[3] = {lo[0] + p % ext[0], lo[1] + (p / ext[0]) % ext[1], lo[2] + p / (ext[0] * ext[1])};
+        float v;
+        if (NT == 0) {
+          const int gx = a[0] + c[0], gy = a[1] + c[1], gz = a[2] + c[2];
+          const int of = owner(t, L, gx, gy, gz);
+          const int Lf = __ldg(t.lev + of);
+          const int lx = local_index(t, of, Lf, L, gx, 0), ly = local_index(t, of, Lf, L, gy, 1),
+                    lz = local_index(t, of, Lf, L, gz, 2);
+          v = __ldg(phi + (size_t)of * nb3 + lx + nb * (ly + nb * lz));
+        } else {
+          v = Q[(size_t)b * np + (c[0] + Gi) + Wd * ((c[1] + Gi) + (size_t)Wd * (c[2] + Gi))];
+        }
+        tile[tix(c[0], c[1], c[2])] = v;
+      }
+    } else {
+      // coarse tile for this face
+      int q0[3], nqd[3];
+      for (int d = 0; d < 3; ++d) {
+        const int l0 = lo[d], l1 = lo[d] + ext[d] - 1;
+        q0[d] = floordiv2(l0 - 1) - (N / 2 - 1);
+        nqd[d] = floordiv2(l1 - 1) + N / 2 - q0[d] + 1;
+      }
+      const int nqt = nqd[0] * nqd[1] * nqd[2];
+      __syncthreads();  // Tt reuse across faces
+      for (int p = threadIdx.x; p < nqt; p += blockDim.x) {
+        const int qx = a[0] / 2 + q0[0] + p % nqd[0], qy = a[1] / 2 + q0[1] + (p / nqd[0]) % nqd[1],
+                  qz = a[2] / 2 + q0[2] + p / (nqd[0] * nqd[1]);
+        const int oc = owner(t, L - 1, qx, qy, qz);
+        const int Lc = __ldg(t.lev + oc);
+        float v = __int_as_float(0x7fc00000);
+        if (Lc >= L - 1) {
+          const int lx = local_index(t, oc, Lc, L - 1, qx, 0), ly = local_index(t, oc, Lc, L - 1, qy, 1),
+                    lz = local_index(t, oc, Lc, L - 1, qz, 2);
+          v = __ldg(phi + (size_t)oc * nb3 + lx + nb * (ly + nb * lz));
+        }
+        Tt[p] = v;
+      }
+      __syncthreads();
+      for (int p = threadIdx.x; p < cnt; p += blockDim.x) {
+        const int c[3] = {lo[0] + p % ext[0], lo[1] + (p / ext[0]) % ext[1], lo[2] + p / (ext[0] * ext[1])};
+        const bool od[3] = {(bool)(c[0] & 1), (bool)(c[1] & 1), (bool)(c[2] & 1)};
+        const int h[3] = {od[0] ? W::hwK : W::hwJ, od[1] ? W::hwK : W::hwJ, od[2] ? W::hwK : W::hwJ};
+        float s = 0.f;
+        for (int oz = -h[2]; oz <= h[2]; ++oz) {
+          if ((c[2] + oz) & 1) continue;
+          const float wz = (float)(od[2] ? W::K(oz) : W::J(oz));
+          for (int oy = -h[1]; oy <= h[1]; ++oy) {
+            if ((c[1] + oy) & 1) continue;
+            const float wy = (float)(od[1] ? W::K(oy) : W::J(oy));
+            for (int ox = -h[0]; ox <= h[0]; ++ox) {
+              if ((c[0] + ox) & 1) continue;
+              const float w = (float)(od[0] ? W::K(ox) : W::J(ox)) * wy * wz;
+              if (w == 0.f) continue;
+              const int tx = floordiv2(c[0] + ox) - q0[0], ty = floordiv2(c[1] + oy) - q0[1],
+                        tz = floordiv2(c[2] + oz) - q0[2];
+              s = fmaf(w, Tt[tx + nqd[0] * (ty + nqd[1] * tz)], s);
+            }
+          }
+        }
+        if (s != s) atomicOr(err, 2);
+        tile[tix(c[0], c[1], c[2])] = s;
+      }
+    }
+  }
+  __syncthreads();
+  // rhs + stage
+  const float uc[3] = {ux, uy, uz};
+  const int stride[3] = {1, Ws, Ws * Ws};
+  const float h = (float)(t.tree_len / ((double)nb * (double)(1 << L)));
+  const float invh = 1.0f / h;
+  for (int p = threadIdx.x; p < (int)nb3; p += blockDim.x) {
+    const int i = p % nb, j = (p / nb) % nb, k = p / (nb * nb);
+    const int cidx = tix(i, j, k);
+    float acc = 0.f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (uc[d] == 0.f) continue;
+      float fv[7];
+#pragma unroll
+      for (int m = 0; m < 7; ++m) fv[m] = uc[d] * tile[cidx + (m - 3) * stride[d]];
+      const bool left = uc[d] >= 0.f;
+      acc += iface_flux<float, SCHEME>(fv + 1, left) - iface_flux<float, SCHEME>(fv, left);
+    }
+    const float r = -acc * invh;
+    const size_t q = (size_t)b * nb3 + p;
+    if (rhs_only) {
+      out[q] = r;
+    } else {
+      const float v = tile[cidx] + dt * r;
+      float o;
+      if (stage == 0) o = v;
+      else if (stage == 1) o = 0.75f * u[q] + 0.25f * v;
+      else o = (1.0f / 3) * u[q] + (2.0f / 3) * v;
+      out[q] = o;
+    }
+  }
+}
+
 template <typename T>
 static int rhs_dispatch(mr_grid *g, const T *P, int Gi, const T *u, T *out, int stage, double dt,
                         const double *uc, int scheme, bool rhs_only) {
@@ -134,6 +300,43 @@ __global__ void k_rk_combine(size_t n, int stage, T dt, const T *u, const T *y, 
     else o = T(1.0 / 3) * u[q] + T(2.0 / 3) * v;
     out[q] = o;
   }
+}
+
+template <int N, int NT>
+static int fused_impl(mr_grid *g, const float *phi, const float *P, const float *Q, int Gi, const float *u,
+                      float *out, int stage, double dt, const double *uc, int scheme, bool rhs_only) {
+  Tree t = tree_view(g);
+  const int nb = g->desc.nb, Ws = nb + 6;
+  const size_t sm = sizeof(float) * ((size_t)Ws * Ws * Ws + (size_t)(N + 1) * (nb / 2 + N) * (nb / 2 + N));
+  const float ux = (float)uc[0], uy = (float)uc[1], uz = (float)uc[2];
+#define MR_FL(S)                                                                                          \
+  do {                                                                                                    \
+    if (check_cuda(cudaFuncSetAttribute(k_fused<N, NT, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                        (int)sm),                                                         \
+                   "fused smem"))                                                                         \
+      return MR_ERR_CUDA;                                                                                 \
+    MR_LAUNCH(g, MRK_RHS, k_fused<N, NT, S><<<g->nleaf, 512, sm, g->stream>>>(                            \
+                              t, phi, P, Q, Gi, g->cmask, u, out, stage, (float)dt, ux, uy, uz, rhs_only, \
+                              g->counter + 1));                                                           \
+  } while (0)
+  if (scheme == MR_CONS3) MR_FL(MR_CONS3);
+  else if (scheme == MR_CONS5) MR_FL(MR_CONS5);
+  else if (scheme == MR_WENOZ5) MR_FL(MR_WENOZ5);
+  else return MR_ERR_INVALID;
+#undef MR_FL
+  return check_cuda(cudaGetLastError(), "k_fused") ? MR_ERR_CUDA : MR_OK;
+}
+
+int launch_fused(mr_grid *g, const void *phi, const void *P, const void *Q, int Gi, const void *u, void *out,
+                 int stage, double dt, const double *uc, int scheme, bool rhs_only) {
+  const int N = g->desc.wav_N, Nt = g->desc.wav_Nt;
+  const float *a = (const float *)phi, *p = (const float *)P, *q = (const float *)Q, *uu = (const float *)u;
+  float *o = (float *)out;
+#define MR_FCASE(n_, nt_) \
+  if (N == n_ && Nt == nt_) return fused_impl<n_, nt_>(g, a, p, q, Gi, uu, o, stage, dt, uc, scheme, rhs_only);
+  MR_FCASE(2, 0) MR_FCASE(2, 2) MR_FCASE(4, 0) MR_FCASE(4, 2) MR_FCASE(6, 0) MR_FCASE(6, 2)
+#undef MR_FCASE
+  return MR_ERR_UNSUPPORTED;
 }
 
 int launch_rk_combine(mr_grid *g, int stage, double dt, const void *u, const void *y, const void *r,
