@@ -296,24 +296,9 @@ __global__ void __launch_bounds__(256) k_interp(Tree to, const int *__restrict__
     for (int p = threadIdx.x; p < (int)nb3; p += blockDim.x) {
       const int i = p % nb, j = (p / nb) % nb, k = p / (nb * nb);
       const int f[3] = {(ch & 1) * nb + i, ((ch >> 1) & 1) * nb + j, ((ch >> 2) & 1) * nb + k};
-      const bool od[3] = {(bool)(f[0] & 1), (bool)(f[1] & 1), (bool)(f[2] & 1)};
-      const int h[3] = {od[0] ? W::hwK : W::hwJ, od[1] ? W::hwK : W::hwJ, od[2] ? W::hwK : W::hwJ};
-      double acc = 0.0;
-      for (int oz = -h[2]; oz <= h[2]; ++oz) {
-        if ((f[2] + oz) & 1) continue;
-        const double wz = od[2] ? W::K(oz) : W::J(oz);
-        for (int oy = -h[1]; oy <= h[1]; ++oy) {
-          if ((f[1] + oy) & 1) continue;
-          const double wy = od[1] ? W::K(oy) : W::J(oy);
-          for (int ox = -h[0]; ox <= h[0]; ++ox) {
-            if ((f[0] + ox) & 1) continue;
-            const double wx = od[0] ? W::K(ox) : W::J(ox);
-            const double wgt = rmul(rmul(wx, wy), wz);
-            if (wgt == 0.0) continue;
-            acc = radd(acc, rmul(wgt, Pp[pidx((f[0] + ox) / 2, (f[1] + oy) / 2, (f[2] + oz) / 2)]));
-          }
-        }
-      }
+      const double acc = refine_dispatch<N, NT, double>(f[0] & 1, f[1] & 1, f[2] & 1, [&](int ox, int oy, int oz) {
+        return Pp[pidx((f[0] + ox) / 2, (f[1] + oy) / 2, (f[2] + oz) / 2)];
+      });
       out[p] = TO(acc);
     }
   } else {
@@ -337,14 +322,9 @@ __global__ void __launch_bounds__(256) k_interp(Tree to, const int *__restrict__
         loc[d] = f[d] - cd * nb;
       }
       const double *Pc = P + (size_t)chs[ch] * np;
-      double acc = 0.0;
-      for (int tz = -W::hwH; tz <= W::hwH; ++tz)
-        for (int ty = -W::hwH; ty <= W::hwH; ++ty)
-          for (int tx = -W::hwH; tx <= W::hwH; ++tx) {
-            const double wgt = rmul(rmul(W::H(tx), W::H(ty)), W::H(tz));
-            if (wgt == 0.0) continue;
-            acc = radd(acc, rmul(wgt, Pc[pidx(loc[0] + tx, loc[1] + ty, loc[2] + tz)]));
-          }
+      const double acc = coarsen_sum<N, NT, double>([&](int tx, int ty, int tz) {
+        return Pc[pidx(loc[0] + tx, loc[1] + ty, loc[2] + tz)];
+      });
       out[p] = TO(acc);
     }
   }

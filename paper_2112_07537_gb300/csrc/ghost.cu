@@ -1,13 +1,13 @@
 // ghost.cu -- ghost-point reconstruction on the device (Alg. SM1 / SM2).
 //
 // Three kernels, one CTA per leaf:
-//   part1: padded block = interior + same-level copies + zero-detail
+//   prep:  padded block = interior + same-level copies + zero-detail
 //          refinement of the coarse-level values where a coarser leaf owns
 //          the point + the coincident value where a finer leaf owns it; then
 //          the degree-ordered substitution of the band next to coarser
-//          leaves (Sec. 2.2.4, eqs 2.27-2.29) on the padded block;
-//   part2: points owned by a finer leaf F <- tensor H^a of F's padded block
-//          (written to a side buffer, so every read sees the part1 state);
+//          leaves (Sec. 2.2.4, eqs 2.27-2.29) on the padded block; then the
+//          tensor H^a coarsening of the block at every ghost point of a
+//          coarser neighbour that it owns, pushed to a side buffer (Part 2);
 //   merge: side buffer -> padded block; substituted interior -> field.
 // The wavelet arithmetic uses explicitly rounded multiply/add in the same
 // order as a plain nested-loop evaluation, so the FP64 instantiation is
@@ -42,33 +42,15 @@ __device__ __forceinline__ double leaf_value(const Tree &t, const TI *phi, int o
 // (J^s on even, K^s on odd coordinates; taps landing on details skipped).
 template <typename TI, typename TP, int N, int NT>
 __device__ TP refine_point(const Tree &t, const TI *phi, int L, int gx, int gy, int gz, int *err) {
-  using W = Wav<N, NT>;
-  const bool odx = gx & 1, ody = gy & 1, odz = gz & 1;
-  const int hx = odx ? W::hwK : W::hwJ, hy = ody ? W::hwK : W::hwJ, hz = odz ? W::hwK : W::hwJ;
-  TP s = TP(0);
-  for (int oz = -hz; oz <= hz; ++oz) {
-    if ((gz + oz) & 1) continue;
-    const TP wz = TP(odz ? W::K(oz) : W::J(oz));
-    for (int oy = -hy; oy <= hy; ++oy) {
-      if ((gy + oy) & 1) continue;
-      const TP wy = TP(ody ? W::K(oy) : W::J(oy));
-      for (int ox = -hx; ox <= hx; ++ox) {
-        if ((gx + ox) & 1) continue;
-        const TP wx = TP(odx ? W::K(ox) : W::J(ox));
-        const TP wgt = rmul(rmul(wx, wy), wz);
-        if (wgt == TP(0)) continue;
-        const int qx = (gx + ox) / 2, qy = (gy + oy) / 2, qz = (gz + oz) / 2;
-        const int o = owner(t, L - 1, qx, qy, qz);
-        if (__ldg(t.lev + o) < L - 1) {
-          atomicOr(err, 2);
-          continue;
-        }
-        const TP v = TP(leaf_value(t, phi, o, L - 1, qx, qy, qz, err));
-        s = radd(s, rmul(wgt, v));
-      }
+  return refine_dispatch<N, NT, TP>(gx & 1, gy & 1, gz & 1, [&](int ox, int oy, int oz) -> TP {
+    const int qx = (gx + ox) / 2, qy = (gy + oy) / 2, qz = (gz + oz) / 2;
+    const int o = owner(t, L - 1, qx, qy, qz);
+    if (__ldg(t.lev + o) < L - 1) {
+      atomicOr(err, 2);
+      return TP(0);
     }
-  }
-  return s;
+    return TP(leaf_value(t, phi, o, L - 1, qx, qy, qz, err));
+  });
 }
 
 __device__ __forceinline__ bool in_band(int mask, int i, int j, int k, int nb, int ef, int eb) {
@@ -95,73 +77,6 @@ __device__ int coarse_mask_dir(const Tree &t, int b, int m, int *err) {
   const int Lo = __ldg(t.lev + o);
   if (Lo < L - 1 || Lo > L + 1) atomicOr(err, 4);
   return Lo < L ? (1 << m) : 0;
-}
-
-template <typename TI, typename TP, int N, int NT>
-__global__ void __launch_bounds__(256) k_part1(Tree t, const TI *__restrict__ phi, TP *__restrict__ P,
-                                               int Gi, int *cmask_out, int *err) {
-  using W = Wav<N, NT>;
-  const int b = blockIdx.x;
-  const int nb = t.nb, Wd = nb + 2 * Gi;
-  const size_t np = (size_t)Wd * Wd * Wd;
-  const int L = __ldg(t.lev + b);
-  const int ax = __ldg(t.anc + 3 * b) * nb, ay = __ldg(t.anc + 3 * b + 1) * nb,
-            az = __ldg(t.anc + 3 * b + 2) * nb;
-  __shared__ int cmask;
-  if (threadIdx.x == 0) cmask = 0;
-  __syncthreads();
-  if (threadIdx.x < 27) {
-    int m = coarse_mask_dir(t, b, threadIdx.x, err);
-    if (m) atomicOr(&cmask, m);
-  }
-  TP *Pb = P + (size_t)b * np;
-  const TI *phib = phi + (size_t)b * nb * nb * nb;
-  for (size_t p = threadIdx.x; p < np; p += blockDim.x) {
-    const int i = (int)(p % Wd) - Gi, j = (int)((p / Wd) % Wd) - Gi, k = (int)(p / ((size_t)Wd * Wd)) - Gi;
-    TP v;
-    if (i >= 0 && i < nb && j >= 0 && j < nb && k >= 0 && k < nb) {
-      v = TP(ld(phib + i + nb * (j + nb * k)));
-    } else {
-      const int gx = ax + i, gy = ay + j, gz = az + k;
-      const int o = owner(t, L, gx, gy, gz);
-      const int Lo = __ldg(t.lev + o);
-      if (Lo >= L) {
-        v = TP(leaf_value(t, phi, o, L, gx, gy, gz, err));
-      } else if (Lo == L - 1) {
-        v = refine_point<TI, TP, N, NT>(t, phi, L, gx, gy, gz, err);
-      } else {
-        atomicOr(err, 8);
-        v = TP(0);
-      }
-    }
-    Pb[p] = v;
-  }
-  __syncthreads();
-  const int mask = cmask;
-  if (threadIdx.x == 0 && cmask_out) cmask_out[b] = mask;
-  if (!mask) return;
-  // substitution, degree by degree (points of one degree never read each other)
-  for (int deg = 1; deg <= 3; ++deg) {
-    for (int p = threadIdx.x; p < nb * nb * nb; p += blockDim.x) {
-      const int i = p % nb, j = (p / nb) % nb, k = p / (nb * nb);
-      const int o0 = i & 1, o1 = j & 1, o2 = k & 1;
-      if (o0 + o1 + o2 != deg) continue;
-      if (!in_band(mask, i, j, k, nb, W::ext_f, W::ext_b)) continue;
-      const int hx = o0 ? W::hwG : 0, hy = o1 ? W::hwG : 0, hz = o2 ? W::hwG : 0;
-      TP s = TP(0);
-      for (int tz = -hz; tz <= hz; ++tz)
-        for (int ty = -hy; ty <= hy; ++ty)
-          for (int tx = -hx; tx <= hx; ++tx) {
-            if (!tx && !ty && !tz) continue;
-            const TP wgt = rmul(rmul(TP(o0 ? W::G(tx) : 1.0), TP(o1 ? W::G(ty) : 1.0)),
-                                TP(o2 ? W::G(tz) : 1.0));
-            if (wgt == TP(0)) continue;
-            s = radd(s, rmul(wgt, Pb[(i + tx + Gi) + Wd * ((j + ty + Gi) + (size_t)Wd * (k + tz + Gi))]));
-          }
-      Pb[(i + Gi) + Wd * ((j + Gi) + (size_t)Wd * (k + Gi))] = -s;
-    }
-    __syncthreads();
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -244,25 +159,10 @@ __global__ void __launch_bounds__(256) k_prep(Tree t, const TI *__restrict__ phi
       } else if (Lo == L - 1) {
         if (tile) {
           // refine_point with T from shared memory (local coarse index g/2)
-          const bool odx = i & 1, ody = j & 1, odz = k & 1;
-          const int hx = odx ? W::hwK : W::hwJ, hy = ody ? W::hwK : W::hwJ, hz = odz ? W::hwK : W::hwJ;
-          TP s = TP(0);
-          for (int oz = -hz; oz <= hz; ++oz) {
-            if ((k + oz) & 1) continue;
-            const TP wz = TP(odz ? W::K(oz) : W::J(oz));
-            for (int oy = -hy; oy <= hy; ++oy) {
-              if ((j + oy) & 1) continue;
-              const TP wy = TP(ody ? W::K(oy) : W::J(oy));
-              for (int ox = -hx; ox <= hx; ++ox) {
-                if ((i + ox) & 1) continue;
-                const TP wx = TP(odx ? W::K(ox) : W::J(ox));
-                const TP wgt = rmul(rmul(wx, wy), wz);
-                if (wgt == TP(0)) continue;
-                const int qx = (i + ox) / 2 - qlo, qy = (j + oy) / 2 - qlo, qz = (k + oz) / 2 - qlo;
-                s = radd(s, rmul(wgt, T[qx + nq * (qy + nq * qz)]));
-              }
-            }
-          }
+          const TP s = refine_dispatch<N, NT, TP>(i & 1, j & 1, k & 1, [&](int ox, int oy, int oz) -> TP {
+            const int qx = (i + ox) / 2 - qlo, qy = (j + oy) / 2 - qlo, qz = (k + oz) / 2 - qlo;
+            return T[qx + nq * (qy + nq * qz)];
+          });
           if (s != s) atomicOr(err, 2);
           v = s;
         } else {
@@ -284,18 +184,10 @@ __global__ void __launch_bounds__(256) k_prep(Tree t, const TI *__restrict__ phi
       const int o0 = i & 1, o1 = j & 1, o2 = k & 1;
       if (o0 + o1 + o2 != deg) continue;
       if (!in_band(mask, i, j, k, nb, W::ext_f, W::ext_b)) continue;
-      const int hx = o0 ? W::hwG : 0, hy = o1 ? W::hwG : 0, hz = o2 ? W::hwG : 0;
-      TP s = TP(0);
-      for (int tz = -hz; tz <= hz; ++tz)
-        for (int ty = -hy; ty <= hy; ++ty)
-          for (int tx = -hx; tx <= hx; ++tx) {
-            if (!tx && !ty && !tz) continue;
-            const TP wgt = rmul(rmul(TP(o0 ? W::G(tx) : 1.0), TP(o1 ? W::G(ty) : 1.0)),
-                                TP(o2 ? W::G(tz) : 1.0));
-            if (wgt == TP(0)) continue;
-            s = radd(s, rmul(wgt, Pb[(i + tx + Gi) + Wd * ((j + ty + Gi) + (size_t)Wd * (k + tz + Gi))]));
-          }
-      Pb[(i + Gi) + Wd * ((j + Gi) + (size_t)Wd * (k + Gi))] = -s;
+      Pb[(i + Gi) + Wd * ((j + Gi) + (size_t)Wd * (k + Gi))] =
+          subst_dispatch<N, NT, TP>(o0, o1, o2, [&](int tx, int ty, int tz) -> TP {
+            return Pb[(i + tx + Gi) + Wd * ((j + ty + Gi) + (size_t)Wd * (k + tz + Gi))];
+          });
     }
     __syncthreads();
   }
@@ -336,65 +228,11 @@ __global__ void __launch_bounds__(256) k_prep(Tree t, const TI *__restrict__ phi
       if (!in || inside) continue;
       // fine index in this leaf of the coincident point: 2G - a*nb
       const int fl[3] = {2 * G[0] - ax, 2 * G[1] - ay, 2 * G[2] - az};
-      TP s = TP(0);
-      for (int tz = -W::hwH; tz <= W::hwH; ++tz)
-        for (int ty = -W::hwH; ty <= W::hwH; ++ty)
-          for (int tx = -W::hwH; tx <= W::hwH; ++tx) {
-            const TP wgt = rmul(rmul(TP(W::H(tx)), TP(W::H(ty))), TP(W::H(tz)));
-            if (wgt == TP(0)) continue;
-            s = radd(s, rmul(wgt, Pb[(fl[0] + tx + Gi) + Wd * ((fl[1] + ty + Gi) + (size_t)Wd * (fl[2] + tz + Gi))]));
-          }
+      const TP s = coarsen_sum<N, NT, TP>([&](int tx, int ty, int tz) -> TP {
+        return Pb[(fl[0] + tx + Gi) + Wd * ((fl[1] + ty + Gi) + (size_t)Wd * (fl[2] + tz + Gi))];
+      });
       Q[(size_t)c * np + (lc[0] + Gi) + Wg * ((lc[1] + Gi) + (size_t)Wg * (lc[2] + Gi))] = s;
     }
-  }
-}
-
-// Part 2: ghost points (shell G) owned by a finer leaf F <- tensor H^a of
-// F's padded block, nearest periodic image.  Writes Q only.
-template <typename TP, int N, int NT>
-__global__ void __launch_bounds__(256) k_part2(Tree t, const TP *__restrict__ P, TP *__restrict__ Q,
-                                               int Gi, int G, int *err) {
-  using W = Wav<N, NT>;
-  const int b = blockIdx.x;
-  const int nb = t.nb, Wd = nb + 2 * Gi, Wg = nb + 2 * G;
-  const size_t np = (size_t)Wd * Wd * Wd;
-  const int L = __ldg(t.lev + b);
-  const int a[3] = {__ldg(t.anc + 3 * b) * nb, __ldg(t.anc + 3 * b + 1) * nb, __ldg(t.anc + 3 * b + 2) * nb};
-  for (int p = threadIdx.x; p < Wg * Wg * Wg; p += blockDim.x) {
-    const int i = p % Wg - G, j = (p / Wg) % Wg - G, k = p / (Wg * Wg) - G;
-    if (i >= 0 && i < nb && j >= 0 && j < nb && k >= 0 && k < nb) continue;
-    const int g[3] = {a[0] + i, a[1] + j, a[2] + k};
-    const int F = owner(t, L, g[0], g[1], g[2]);
-    const int LF = __ldg(t.lev + F);
-    if (LF <= L) continue;
-    if (LF > L + 1) {
-      atomicOr(err, 16);
-      continue;
-    }
-    int fl[3];
-    for (int d = 0; d < 3; ++d) {
-      const int Pn = npts(t, L + 1, d);
-      int off = pwrap(2 * g[d] - __ldg(t.anc + 3 * F + d) * nb, Pn);
-      if (off >= Pn / 2) off -= Pn;
-      fl[d] = off;
-    }
-    const TP *PF = P + (size_t)F * np;
-    TP s = TP(0);
-    bool bad = false;
-    for (int tz = -W::hwH; tz <= W::hwH; ++tz)
-      for (int ty = -W::hwH; ty <= W::hwH; ++ty)
-        for (int tx = -W::hwH; tx <= W::hwH; ++tx) {
-          const TP wgt = rmul(rmul(TP(W::H(tx)), TP(W::H(ty))), TP(W::H(tz)));
-          if (wgt == TP(0)) continue;
-          const int qx = fl[0] + tx, qy = fl[1] + ty, qz = fl[2] + tz;
-          if (qx < -Gi || qx >= nb + Gi || qy < -Gi || qy >= nb + Gi || qz < -Gi || qz >= nb + Gi) {
-            bad = true;
-            continue;
-          }
-          s = radd(s, rmul(wgt, PF[(qx + Gi) + Wd * ((qy + Gi) + (size_t)Wd * (qz + Gi))]));
-        }
-    if (bad) atomicOr(err, 32);
-    Q[(size_t)b * np + (i + Gi) + Wd * ((j + Gi) + (size_t)Wd * (k + Gi))] = s;
   }
 }
 
@@ -448,21 +286,6 @@ static int internal_shell(int N, int Nt, int G, int nb) {
   if (hwG > gi) gi = hwG;
   if (2 * G + hwH - nb > gi) gi = 2 * G + hwH - nb;
   return gi;
-}
-
-template <typename TI, typename TP, int N, int NT>
-static int ghost_impl(mr_grid *g, const TI *phi_in, TI *phi_out, int G, TP *P, TP *Q, int Gi) {
-  Tree t = tree_view(g);
-  const int n = g->nleaf;
-  int *err = g->counter + 1;
-  int *cm = g->cmask;
-  MR_LAUNCH(g, MRK_PART1, k_part1<TI, TP, N, NT><<<n, 256, 0, g->stream>>>(t, phi_in, P, Gi, cm, err));
-  if (check_cuda(cudaGetLastError(), "k_part1")) return MR_ERR_CUDA;
-  MR_LAUNCH(g, MRK_PART2, k_part2<TP, N, NT><<<n, 256, 0, g->stream>>>(t, P, Q, Gi, G, err));
-  if (check_cuda(cudaGetLastError(), "k_part2")) return MR_ERR_CUDA;
-  MR_LAUNCH(g, MRK_MERGE, k_merge<TI, TP><<<n, 256, 0, g->stream>>>(t, P, Q, Gi, G, cm, phi_out));
-  if (check_cuda(cudaGetLastError(), "k_merge")) return MR_ERR_CUDA;
-  return MR_OK;
 }
 
 template <typename TI, typename TP, int N, int NT>

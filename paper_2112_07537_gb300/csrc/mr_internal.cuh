@@ -74,6 +74,115 @@ __device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a,
 __device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
 
 // ---------------------------------------------------------------------------
+// Tensor sums with the parity of the output point fixed at compile time, so
+// every loop bound is a constant and zero taps disappear when unrolled.  The
+// terms are visited in ascending offset order, z outermost, x innermost, and
+// each weight is (wx*wy)*wz: the order of a plain nested-loop evaluation.
+// ---------------------------------------------------------------------------
+
+// zero-detail refinement (J^s / K^s, taps landing on coarse points only):
+// sum_o w(o) * T((c+o)/2); val(qx, qy, qz) returns the coarse value at the
+// coarse offsets relative to floor(c/2) ... passed as (c+o)/2 - c/2 style:
+// the callback receives the three fine offsets o.
+template <int N, int NT, bool OX, bool OY, bool OZ, typename TP, typename F>
+__device__ __forceinline__ TP refine_sum(F val) {
+  using W = Wav<N, NT>;
+  constexpr int hx = OX ? W::hwK : W::hwJ, hy = OY ? W::hwK : W::hwJ, hz = OZ ? W::hwK : W::hwJ;
+  TP s = TP(0);
+#pragma unroll
+  for (int oz = -hz; oz <= hz; ++oz) {
+    if (((oz & 1) != 0) != OZ) continue;  // c+oz must be even
+    const TP wz = TP(OZ ? W::K(oz) : W::J(oz));
+#pragma unroll
+    for (int oy = -hy; oy <= hy; ++oy) {
+      if (((oy & 1) != 0) != OY) continue;
+      const TP wy = TP(OY ? W::K(oy) : W::J(oy));
+#pragma unroll
+      for (int ox = -hx; ox <= hx; ++ox) {
+        if (((ox & 1) != 0) != OX) continue;
+        const TP wgt = rmul(rmul(TP(OX ? W::K(ox) : W::J(ox)), wy), wz);
+        if (wgt == TP(0)) continue;
+        s = radd(s, rmul(wgt, val(ox, oy, oz)));
+      }
+    }
+  }
+  return s;
+}
+
+template <int N, int NT, typename TP, typename F>
+__device__ __forceinline__ TP refine_dispatch(bool ox, bool oy, bool oz, F val) {
+  switch ((int)ox | ((int)oy << 1) | ((int)oz << 2)) {
+    case 0: return refine_sum<N, NT, false, false, false, TP>(val);
+    case 1: return refine_sum<N, NT, true, false, false, TP>(val);
+    case 2: return refine_sum<N, NT, false, true, false, TP>(val);
+    case 3: return refine_sum<N, NT, true, true, false, TP>(val);
+    case 4: return refine_sum<N, NT, false, false, true, TP>(val);
+    case 5: return refine_sum<N, NT, true, false, true, TP>(val);
+    case 6: return refine_sum<N, NT, false, true, true, TP>(val);
+    default: return refine_sum<N, NT, true, true, true, TP>(val);
+  }
+}
+
+// tensor H^a: sum over nonzero (tx, ty, tz) of H(tx)H(ty)H(tz) val(tx,ty,tz)
+template <int N, int NT, typename TP, typename F>
+__device__ __forceinline__ TP coarsen_sum(F val) {
+  using W = Wav<N, NT>;
+  TP s = TP(0);
+#pragma unroll
+  for (int tz = -W::hwH; tz <= W::hwH; ++tz) {
+    if (W::H(tz) == 0.0) continue;
+#pragma unroll
+    for (int ty = -W::hwH; ty <= W::hwH; ++ty) {
+      if (W::H(ty) == 0.0) continue;
+#pragma unroll
+      for (int tx = -W::hwH; tx <= W::hwH; ++tx) {
+        if (W::H(tx) == 0.0) continue;
+        const TP wgt = rmul(rmul(TP(W::H(tx)), TP(W::H(ty))), TP(W::H(tz)));
+        s = radd(s, rmul(wgt, val(tx, ty, tz)));
+      }
+    }
+  }
+  return s;
+}
+
+// substitution: -sum over t != 0 (t only along odd dims) of prod G^a
+template <int N, int NT, bool OX, bool OY, bool OZ, typename TP, typename F>
+__device__ __forceinline__ TP subst_sum(F val) {
+  using W = Wav<N, NT>;
+  constexpr int hx = OX ? W::hwG : 0, hy = OY ? W::hwG : 0, hz = OZ ? W::hwG : 0;
+  TP s = TP(0);
+#pragma unroll
+  for (int tz = -hz; tz <= hz; ++tz) {
+    if (OZ && W::G(tz) == 0.0) continue;
+#pragma unroll
+    for (int ty = -hy; ty <= hy; ++ty) {
+      if (OY && W::G(ty) == 0.0) continue;
+#pragma unroll
+      for (int tx = -hx; tx <= hx; ++tx) {
+        if (OX && W::G(tx) == 0.0) continue;
+        if (!tx && !ty && !tz) continue;
+        const TP wgt = rmul(rmul(TP(OX ? W::G(tx) : 1.0), TP(OY ? W::G(ty) : 1.0)), TP(OZ ? W::G(tz) : 1.0));
+        s = radd(s, rmul(wgt, val(tx, ty, tz)));
+      }
+    }
+  }
+  return -s;
+}
+
+template <int N, int NT, typename TP, typename F>
+__device__ __forceinline__ TP subst_dispatch(bool ox, bool oy, bool oz, F val) {
+  switch ((int)ox | ((int)oy << 1) | ((int)oz << 2)) {
+    case 1: return subst_sum<N, NT, true, false, false, TP>(val);
+    case 2: return subst_sum<N, NT, false, true, false, TP>(val);
+    case 3: return subst_sum<N, NT, true, true, false, TP>(val);
+    case 4: return subst_sum<N, NT, false, false, true, TP>(val);
+    case 5: return subst_sum<N, NT, true, false, true, TP>(val);
+    case 6: return subst_sum<N, NT, false, true, true, TP>(val);
+    default: return subst_sum<N, NT, true, true, true, TP>(val);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Device view of the octree: leaves in Morton order (slot = rank) and a dense
 // owner map at level M (the grid's lmax): map[cell] = slot of the leaf whose
 // region contains that level-M block cell.

@@ -14,6 +14,12 @@ struct WenoC {
   static constexpr double rcap = 1e15;
 };
 
+// FP32 divisions of the WENO-Z weights use the 2-ulp fast divide (their
+// operands stay far inside the normal range: beta + eps >= 1e-30, and the
+// weight sum is >= gamma_min); FP64 divides exactly.
+__device__ __forceinline__ float wdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double wdiv(double a, double b) { return a / b; }
+
 // Interface flux F_{i+1/2} from f[0..5] = f_{i-2..i+3} (Tables SM3 / SM4).
 template <typename T, int SCHEME>
 __device__ __forceinline__ T iface_flux(const T *f, bool left) {
@@ -48,12 +54,12 @@ __device__ __forceinline__ T iface_flux(const T *f, bool left) {
   const T b2 = T(0.25) * t2 * t2 + T(13.0 / 12) * u2 * u2;
   const T tau = fabs(b0 - b2);
   const T eps = T(WenoC<T>::eps), cap = T(WenoC<T>::rcap);
-  T r0 = tau / (b0 + eps), r1 = tau / (b1 + eps), r2 = tau / (b2 + eps);
+  T r0 = wdiv(tau, b0 + eps), r1 = wdiv(tau, b1 + eps), r2 = wdiv(tau, b2 + eps);
   r0 = r0 > cap ? cap : r0;
   r1 = r1 > cap ? cap : r1;
   r2 = r2 > cap ? cap : r2;
   const T a0 = g0 * (T(1) + r0 * r0), a1 = g1 * (T(1) + r1 * r1), a2 = g2 * (T(1) + r2 * r2);
-  return (a0 * s0 + a1 * s1 + a2 * s2) / (a0 + a1 + a2);
+  return wdiv(a0 * s0 + a1 * s1 + a2 * s2, a0 + a1 + a2);
 }
 
 // One CTA per leaf: rhs from the padded block P (shell Gi >= 3), then the RK
@@ -205,25 +211,11 @@ __global__ void __launch_bounds__(512) k_fused(Tree t, const float *__restrict__
       __syncthreads();
       for (int p = threadIdx.x; p < cnt; p += blockDim.x) {
         const int c[3] = {lo[0] + p % ext[0], lo[1] + (p / ext[0]) % ext[1], lo[2] + p / (ext[0] * ext[1])};
-        const bool od[3] = {(bool)(c[0] & 1), (bool)(c[1] & 1), (bool)(c[2] & 1)};
-        const int h[3] = {od[0] ? W::hwK : W::hwJ, od[1] ? W::hwK : W::hwJ, od[2] ? W::hwK : W::hwJ};
-        float s = 0.f;
-        for (int oz = -h[2]; oz <= h[2]; ++oz) {
-          if ((c[2] + oz) & 1) continue;
-          const float wz = (float)(od[2] ? W::K(oz) : W::J(oz));
-          for (int oy = -h[1]; oy <= h[1]; ++oy) {
-            if ((c[1] + oy) & 1) continue;
-            const float wy = (float)(od[1] ? W::K(oy) : W::J(oy));
-            for (int ox = -h[0]; ox <= h[0]; ++ox) {
-              if ((c[0] + ox) & 1) continue;
-              const float w = (float)(od[0] ? W::K(ox) : W::J(ox)) * wy * wz;
-              if (w == 0.f) continue;
-              const int tx = floordiv2(c[0] + ox) - q0[0], ty = floordiv2(c[1] + oy) - q0[1],
-                        tz = floordiv2(c[2] + oz) - q0[2];
-              s = fmaf(w, Tt[tx + nqd[0] * (ty + nqd[1] * tz)], s);
-            }
-          }
-        }
+        const float s = refine_dispatch<N, NT, float>(c[0] & 1, c[1] & 1, c[2] & 1, [&](int ox, int oy, int oz) -> float {
+          const int tx = floordiv2(c[0] + ox) - q0[0], ty = floordiv2(c[1] + oy) - q0[1],
+                    tz = floordiv2(c[2] + oz) - q0[2];
+          return Tt[tx + nqd[0] * (ty + nqd[1] * tz)];
+        });
         if (s != s) atomicOr(err, 2);
         tile[tix(c[0], c[1], c[2])] = s;
       }
