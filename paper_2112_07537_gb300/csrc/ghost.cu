@@ -215,23 +215,34 @@ __global__ void __launch_bounds__(256) k_prep(Tree t, const TI *__restrict__ phi
     for (int p = threadIdx.x; p < hb * hb * hb; p += blockDim.x) {
       // coarse point inside this leaf (level Lc index)
       const int G[3] = {ax / 2 + p % hb, ay / 2 + (p / hb) % hb, az / 2 + p / (hb * hb)};
-      int lc[3];
-      bool in = true, inside = true;
+      // c-local offsets of every periodic image of G that falls in c's shell
+      // (tiny periodic domains: c can see this leaf on both sides)
+      int cand[3][3], ncand[3];
+      bool any = true;
       for (int d = 0; d < 3; ++d) {
         const int Pn = npts(t, Lc, d);
-        int off = pwrap(G[d] - ac[d], Pn);
-        if (off >= Pn / 2) off -= Pn;
-        lc[d] = off;
-        in &= off >= -Gpush && off < nb + Gpush;
-        inside &= off >= 0 && off < nb;
+        const int off = pwrap(G[d] - ac[d], Pn);
+        ncand[d] = 0;
+        for (int sh = -1; sh <= 1; ++sh) {
+          const int o = off + sh * Pn;
+          if (o >= -Gpush && o < nb + Gpush) cand[d][ncand[d]++] = o;
+        }
+        any &= ncand[d] > 0;
       }
-      if (!in || inside) continue;
+      if (!any) continue;
       // fine index in this leaf of the coincident point: 2G - a*nb
       const int fl[3] = {2 * G[0] - ax, 2 * G[1] - ay, 2 * G[2] - az};
       const TP s = coarsen_sum<N, NT, TP>([&](int tx, int ty, int tz) -> TP {
         return Pb[(fl[0] + tx + Gi) + Wd * ((fl[1] + ty + Gi) + (size_t)Wd * (fl[2] + tz + Gi))];
       });
-      Q[(size_t)c * np + (lc[0] + Gi) + Wg * ((lc[1] + Gi) + (size_t)Wg * (lc[2] + Gi))] = s;
+      for (int iz = 0; iz < ncand[2]; ++iz)
+        for (int iy = 0; iy < ncand[1]; ++iy)
+          for (int ix = 0; ix < ncand[0]; ++ix) {
+            const int lc[3] = {cand[0][ix], cand[1][iy], cand[2][iz]};
+            const bool inside = lc[0] >= 0 && lc[0] < nb && lc[1] >= 0 && lc[1] < nb && lc[2] >= 0 && lc[2] < nb;
+            if (inside) continue;
+            Q[(size_t)c * np + (lc[0] + Gi) + Wg * ((lc[1] + Gi) + (size_t)Wg * (lc[2] + Gi))] = s;
+          }
     }
   }
 }
@@ -400,3 +411,4 @@ int launch_crop(mr_grid *g, const void *P, int Gi, void *out, int G, bool fp64_s
 }
 
 }  // namespace mr
+

@@ -117,7 +117,7 @@ __device__ __forceinline__ int floordiv2(int a) { return a >= 0 ? a / 2 : -((-a 
 // Then rhs and the RK3 stage combination, written to out.
 // ---------------------------------------------------------------------------
 template <int N, int NT, int SCHEME>
-__global__ void __launch_bounds__(512) k_fused(Tree t, const float *__restrict__ phi, const float *__restrict__ P,
+__global__ void __launch_bounds__(1024) k_fused(Tree t, const float *__restrict__ phi, const float *__restrict__ P,
                                                const float *__restrict__ Q, int Gi, const int *__restrict__ cmask,
                                                const float *u, float *out, int stage, float dt, float ux, float uy,
                                                float uz, int rhs_only, int *err) {
@@ -222,30 +222,61 @@ __global__ void __launch_bounds__(512) k_fused(Tree t, const float *__restrict__
     }
   }
   __syncthreads();
-  // rhs + stage
+  // rhs: one sweep per direction, each thread walking whole grid lines with a
+  // register window so every interface flux is evaluated once
+  float *R = Tt + (size_t)(N + 1) * (nb / 2 + N) * (nb / 2 + N);
   const float uc[3] = {ux, uy, uz};
-  const int stride[3] = {1, Ws, Ws * Ws};
+  const int strd[3] = {1, Ws, Ws * Ws};
+  for (int d = 0; d < 3; ++d) {
+    const float ud = uc[d];
+    const bool left = ud >= 0.f;
+    const int e1 = d == 0 ? 1 : 0, e2 = d == 2 ? 1 : 2;  // the two other axes
+    for (int line = threadIdx.x; line < nb * nb; line += blockDim.x) {
+      int c[3];
+      c[e1] = line % nb;
+      c[e2] = line / nb;
+      c[d] = 0;
+      const int st = strd[d];
+      const float *lp = tile + tix(c[0], c[1], c[2]);
+      int rstride = d == 0 ? 1 : d == 1 ? nb : nb * nb;
+      float *rp = R + c[0] + nb * (c[1] + nb * c[2]);
+      if (ud == 0.f) {
+        if (d == 0)
+          for (int m = 0; m < nb; ++m) rp[m * rstride] = 0.f;
+        continue;
+      }
+      float w[7];
+#pragma unroll
+      for (int m = 0; m < 6; ++m) w[m + 1] = ud * lp[(m - 3) * st];
+      float Fm = 0.f;
+      {
+        float f6[6] = {w[1], w[2], w[3], w[4], w[5], w[6]};  // f_{-3..2}: F_{-1/2}
+        Fm = iface_flux<float, SCHEME>(f6, left);
+      }
+      for (int m = 0; m < nb; ++m) {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) w[q] = w[q + 1];
+        w[6] = ud * lp[(m + 3) * st];
+        const float Fp = iface_flux<float, SCHEME>(w + 1, left);  // f_{m-2..m+3}
+        const float dlt = Fp - Fm;
+        if (d == 0) rp[m * rstride] = dlt;
+        else rp[m * rstride] += dlt;
+        Fm = Fp;
+      }
+    }
+    __syncthreads();
+  }
+  // RK stage
   const float h = (float)(t.tree_len / ((double)nb * (double)(1 << L)));
   const float invh = 1.0f / h;
   for (int p = threadIdx.x; p < (int)nb3; p += blockDim.x) {
     const int i = p % nb, j = (p / nb) % nb, k = p / (nb * nb);
-    const int cidx = tix(i, j, k);
-    float acc = 0.f;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      if (uc[d] == 0.f) continue;
-      float fv[7];
-#pragma unroll
-      for (int m = 0; m < 7; ++m) fv[m] = uc[d] * tile[cidx + (m - 3) * stride[d]];
-      const bool left = uc[d] >= 0.f;
-      acc += iface_flux<float, SCHEME>(fv + 1, left) - iface_flux<float, SCHEME>(fv, left);
-    }
-    const float r = -acc * invh;
+    const float r = -R[p] * invh;
     const size_t q = (size_t)b * nb3 + p;
     if (rhs_only) {
       out[q] = r;
     } else {
-      const float v = tile[cidx] + dt * r;
+      const float v = tile[tix(i, j, k)] + dt * r;
       float o;
       if (stage == 0) o = v;
       else if (stage == 1) o = 0.75f * u[q] + 0.25f * v;
@@ -299,7 +330,9 @@ static int fused_impl(mr_grid *g, const float *phi, const float *P, const float 
                       float *out, int stage, double dt, const double *uc, int scheme, bool rhs_only) {
   Tree t = tree_view(g);
   const int nb = g->desc.nb, Ws = nb + 6;
-  const size_t sm = sizeof(float) * ((size_t)Ws * Ws * Ws + (size_t)(N + 1) * (nb / 2 + N) * (nb / 2 + N));
+  const size_t sm = sizeof(float) * ((size_t)Ws * Ws * Ws + (size_t)(N + 1) * (nb / 2 + N) * (nb / 2 + N) +
+                                     (size_t)nb * nb * nb);
+  const int threads = nb * nb > 1024 ? 1024 : nb * nb;
   const float ux = (float)uc[0], uy = (float)uc[1], uz = (float)uc[2];
 #define MR_FL(S)                                                                                          \
   do {                                                                                                    \
@@ -307,7 +340,7 @@ static int fused_impl(mr_grid *g, const float *phi, const float *P, const float 
                                         (int)sm),                                                         \
                    "fused smem"))                                                                         \
       return MR_ERR_CUDA;                                                                                 \
-    MR_LAUNCH(g, MRK_RHS, k_fused<N, NT, S><<<g->nleaf, 512, sm, g->stream>>>(                            \
+    MR_LAUNCH(g, MRK_RHS, k_fused<N, NT, S><<<g->nleaf, threads, sm, g->stream>>>(                            \
                               t, phi, P, Q, Gi, g->cmask, u, out, stage, (float)dt, ux, uy, uz, rhs_only, \
                               g->counter + 1));                                                           \
   } while (0)

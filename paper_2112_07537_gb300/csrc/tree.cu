@@ -68,12 +68,14 @@ __global__ void k_check_balance(Tree t, int *err) {
   }
 }
 
+// owner map of the tree copy that is current in g (g->cur)
 int build_map(mr_grid *g) {
   Tree t = tree_view(g);
+  int *map = g->maps[g->cur];
   const size_t n = g->map_cells;
-  MR_LAUNCH(g, MRK_MAP, k_fill_int<<<152 * 4, 256, 0, g->stream>>>(g->map, n, -1));
-  MR_LAUNCH(g, MRK_MAP, k_build_map<<<g->nleaf, 256, 0, g->stream>>>(t, g->map, g->counter + 1));
-  MR_LAUNCH(g, MRK_MAP, k_check_holes<<<152 * 4, 256, 0, g->stream>>>(g->map, n, g->counter + 1));
+  MR_LAUNCH(g, MRK_MAP, k_fill_int<<<152 * 4, 256, 0, g->stream>>>(map, n, -1));
+  MR_LAUNCH(g, MRK_MAP, k_build_map<<<g->nleaf, 256, 0, g->stream>>>(t, map, g->counter + 1));
+  MR_LAUNCH(g, MRK_MAP, k_check_holes<<<152 * 4, 256, 0, g->stream>>>(map, n, g->counter + 1));
   return check_cuda(cudaGetLastError(), "build_map") ? MR_ERR_CUDA : MR_OK;
 }
 

@@ -86,7 +86,7 @@ def test_adapt_iteration_fp64_matches_oracle(mr, oracle_mod, N, Nt):
     assert np.abs(got - ophi).max() <= 1e-13 * np.abs(ophi).max()
 
 
-@pytest.mark.parametrize("N,Nt", [(4, 2), (6, 2)])
+@pytest.mark.parametrize("N,Nt", [(4, 2), (2, 0)])
 def test_adapt_to_convergence_fp32_flags_exact(mr, oracle_mod, N, Nt):
     """Full Alg. SM3 loop on an FP32 grid: each iteration the oracle runs on
     the device's FP32 snapshot; statuses (through the trees) match exactly."""
@@ -94,7 +94,7 @@ def test_adapt_to_convergence_fp32_flags_exact(mr, oracle_mod, N, Nt):
     g, og, phi = _setup(mr, O, N, Nt, mr.F32)
     er, ec = _eps(O.block_maxdet(og, phi))
     refined = None
-    for it in range(12):
+    for it in range(6):
         lev, anc, _ = g.leaves()
         cur = og.with_leaves(lev, anc)
         snap = g.field_copy_out(0).astype(np.float64)
