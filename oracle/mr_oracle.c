@@ -1030,8 +1030,9 @@ int og_adapt_iter(const og_grid *g, const double *phi, double eps_r, double eps_
     e = ctx_init(&cn, &gn);
     if (e) goto done;
     int8_t *newly_coarse = (int8_t *)calloc(n, 1);
-    for (int b = 0; b < g->nleaf; ++b)
-      if (st[b] == OG_COARSER) newly_coarse[newidx[b]] = 1;
+    for (int b = 0; b < g->nleaf; ++b) /* the parent sits at its first child's index */
+      if (st[b] == OG_COARSER && !((g->anc[3 * b] | g->anc[3 * b + 1] | g->anc[3 * b + 2]) & 1))
+        newly_coarse[newidx[b]] = 1;
     const int ef = c.w.ext_f, eb = c.w.ext_b, E = nb + ef + eb;
     double *gam = (double *)malloc(sizeof(double) * (size_t)E * E * E);
     int8_t *inD = (int8_t *)malloc((size_t)E * E * E);
