@@ -34,12 +34,15 @@ from paper_2112_07537_gb300 import inputs as I  # noqa: E402
 
 METRIC = "point-stage updates/s (ghost fill + RHS + RK3 stage)"
 UNIT = "PSU/s"
-RADII = (0.35, 0.25, 0.17, 0.11, 0.06)  # nested refinement balls, levels 3->8
+# nested refinement balls around the blob centre, level 3 -> 3 + len(radii)
+WORKLOADS = {"large": (0.35, 0.25, 0.17, 0.11, 0.06),   # 42 400 leaves, 586 M points
+             "medium": (0.35, 0.25, 0.17),              # 11 768 leaves, 163 M points
+             "small": (0.3, 0.2)}
 U = (1.0, 0.5, 0.25)
 
 
-def workload_tree():
-    return I.tree_sphere((1, 1, 1), 1.0, 3, RADII, centre=(0.5, 0.5, 0.5))
+def workload_tree(name="large"):
+    return I.tree_sphere((1, 1, 1), 1.0, 3, WORKLOADS[name], centre=(0.5, 0.5, 0.5))
 
 
 def clocks_sampler(stop, out):
@@ -126,6 +129,7 @@ def main():
     ap.add_argument("--scheme", default="wenoz5", choices=["wenoz5", "cons5", "cons3"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -145,12 +149,13 @@ def main():
     W = max(3, args.warmup)
     prec = mrgb.F32 if args.precision == "f32" else mrgb.F64
     scheme = {"wenoz5": mrgb.WENOZ5, "cons5": mrgb.CONS5, "cons3": mrgb.CONS3}[args.scheme]
-    lev, anc = workload_tree()
+    lev, anc = workload_tree(args.workload)
+    radii = WORKLOADS[args.workload]
     nb = 24
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        g = mrgb.Grid((1, 1, 1), 1.0, nb, 3, 8, 6, 2, lev, anc, precision=prec, nfields=1,
-                      stream=stream)
+        g = mrgb.Grid((1, 1, 1), 1.0, nb, 3, int(lev.max()), 6, 2, lev, anc, precision=prec,
+                      nfields=1, stream=stream, fixed_tree=True)
         g.field_set(0, mrgb.INIT_GAUSSIAN, [0.5, 0.5, 0.5, 0.08, 1.0])
     n = g.nleaf
     pts = n * nb ** 3
@@ -213,8 +218,9 @@ def main():
         "metric": METRIC, "value": psu, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": W, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-        "config": {"workload": "large single grid, fixed tree: 1 tree, 24^3 blocks, levels 3-8 "
-                               f"(nested balls r={RADII}), {n} leaves, {pts} points; 6.2 lifted "
+        "config": {"workload": f"{args.workload} single grid, fixed tree: 1 tree, 24^3 blocks, "
+                               f"levels 3-{int(lev.max())} (nested balls r={radii}), {n} leaves, "
+                               f"{pts} points; 6.2 lifted "
                                f"wavelet ghosts; {args.scheme} + RK3; u={U}; CFL 0.5",
                    "leaves": n, "points": pts, "l2": "inputs larger than L2 (no flush)",
                    "scheme": args.scheme, "precision": args.precision},

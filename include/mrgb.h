@@ -78,7 +78,12 @@ typedef struct {
   int nfields;      /* user fields held in the block pool (>= 1)           */
   int capacity;     /* maximum number of leaves                            */
   void *stream;     /* cudaStream_t the grid enqueues on (NULL: legacy)    */
+  int flags;        /* MR_GRID_FIXED_TREE: no adaptation buffers (smaller
+                       workspace); mr_adapt*, mr_criterion and
+                       mr_ghost_fill64 then return MR_ERR_UNSUPPORTED      */
 } mr_grid_desc;
+
+#define MR_GRID_FIXED_TREE 1
 
 typedef struct {
   int nleaf;

@@ -105,6 +105,7 @@ static int layout(const mr_grid_desc *d, Layout *L, int *shell_rk, int *shell_ad
     if (d->ntree[k] < 1 || d->ntree[k] > 64) return MR_ERR_INVALID;
   const size_t es = d->precision == MR_F32 ? 4 : 8;
   const size_t nb3 = (size_t)d->nb * d->nb * d->nb, cap = (size_t)d->capacity;
+  const bool fixed = d->flags & MR_GRID_FIXED_TREE;
   const int gad = adapt_shell(d->wav_N, d->wav_Nt);
   *shell_rk = internal_shell(d->wav_N, d->wav_Nt, 3, d->nb);
   *shell_ad = std::max(internal_shell(d->wav_N, d->wav_Nt, gad, d->nb), *shell_rk);
@@ -118,9 +119,9 @@ static int layout(const mr_grid_desc *d, Layout *L, int *shell_rk, int *shell_ad
       cap * 8, cap * 8,                          // keys[2]
       *map_cells * 4, *map_cells * 4,            // maps[2]
       (size_t)(d->nfields + 2) * cap * nb3 * es, // pool 0
-      (size_t)(d->nfields + 2) * cap * nb3 * es, // pool 1
-      cap * wr * wr * wr * es, cap * wr * wr * wr * es,  // padP, padQ
-      cap * wa * wa * wa * 8, cap * wa * wa * wa * 8,    // padP64, padQ64
+      fixed ? 0 : (size_t)(d->nfields + 2) * cap * nb3 * es,  // pool 1
+      cap * wr * wr * wr * es, cap * wr * wr * wr * es,       // padP, padQ
+      fixed ? 0 : cap * wa * wa * wa * 8, fixed ? 0 : cap * wa * wa * wa * 8,  // padP64, padQ64
       cap * 8,                                   // maxdet
       cap,                                       // status
       cap * 4, cap * 4,                          // refined[2]
@@ -388,9 +389,18 @@ int mr_ghost_fill(mr_grid *g, int fid, int G, void *padded) {
   return e;
 }
 
+static int adapt_ok(mr_grid *g) {
+  if (g->desc.flags & MR_GRID_FIXED_TREE) {
+    set_error("grid created with MR_GRID_FIXED_TREE: no adaptation buffers");
+    return 0;
+  }
+  return 1;
+}
+
 // FP64 ghost fill (the adaptation path) into a double padded buffer.
 int mr_ghost_fill64(mr_grid *g, int fid, int G, double *padded) {
   if (!fid_ok(g, fid)) return MR_ERR_INVALID;
+  if (!adapt_ok(g)) return MR_ERR_UNSUPPORTED;
   void *P;
   int Gi;
   void *f = field_ptr(g, fid);
@@ -453,6 +463,7 @@ int mr_step(mr_grid *g, int phi, double dt, const double *u, int scheme) {
 
 int mr_criterion(mr_grid *g, int fid, double *maxdet) {
   if (!fid_ok(g, fid) || !maxdet) return MR_ERR_INVALID;
+  if (!adapt_ok(g)) return MR_ERR_UNSUPPORTED;
   void *P;
   int Gi;
   void *f = field_ptr(g, fid);
@@ -463,6 +474,7 @@ int mr_criterion(mr_grid *g, int fid, double *maxdet) {
 
 int mr_adapt_iter(mr_grid *g, int crit, double er, double ec, int flags, int *nch) {
   if (!fid_ok(g, crit)) return MR_ERR_INVALID;
+  if (!adapt_ok(g)) return MR_ERR_UNSUPPORTED;
   int n = 0;
   int e = adapt_iteration(g, crit, er, ec, flags, &n);
   if (nch) *nch = n;
@@ -471,6 +483,7 @@ int mr_adapt_iter(mr_grid *g, int crit, double er, double ec, int flags, int *nc
 
 int mr_adapt(mr_grid *g, int crit, double er, double ec, int flags, int *nch) {
   if (!fid_ok(g, crit)) return MR_ERR_INVALID;
+  if (!adapt_ok(g)) return MR_ERR_UNSUPPORTED;
   int total = 0;
   cudaMemsetAsync(g->refined, 0, 4 * (size_t)g->desc.capacity, g->stream);
   for (int it = 0; it < 64; ++it) {

@@ -343,7 +343,7 @@ int launch_ghost(mr_grid *g, const void *phi_in, void *phi_out, int G, bool fp64
   const int gi = internal_shell(g->desc.wav_N, g->desc.wav_Nt, G, nb);
   // shells wider than the stencil buffers go through the (wider) FP64 buffers
   if (gi > g->shell_rk) fp64 = true;
-  if (fp64 && gi > g->shell_ad) return MR_ERR_UNSUPPORTED;
+  if (fp64 && (gi > g->shell_ad || (g->desc.flags & MR_GRID_FIXED_TREE))) return MR_ERR_UNSUPPORTED;
   *Gi = gi;
   if (p_is64) *p_is64 = fp64 || g->desc.precision == MR_F64;
   const bool f32 = g->desc.precision == MR_F32;

@@ -20,6 +20,7 @@ F32, F64 = 0, 1
 CONS3, CONS5, WENOZ5 = 0, 1, 2
 INIT_GAUSSIAN, INIT_TANH_SPHERE, INIT_TAYLOR_GREEN = 0, 1, 2
 ADAPT_REFINE, ADAPT_COARSEN = 1, 2
+GRID_FIXED_TREE = 1
 NUM_KERNELS = 18
 
 # every entry point include/mrgb.h declares
@@ -40,7 +41,7 @@ class Desc(C.Structure):
     _fields_ = [("ntree", C.c_int * 3), ("tree_len", C.c_double), ("nb", C.c_int),
                 ("lmin", C.c_int), ("lmax", C.c_int), ("wav_N", C.c_int), ("wav_Nt", C.c_int),
                 ("precision", C.c_int), ("nfields", C.c_int), ("capacity", C.c_int),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("flags", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -114,7 +115,7 @@ class Grid:
     """A periodic forest of octrees of nb^3 blocks on one GPU (mr_grid)."""
 
     def __init__(self, ntree, tree_len, nb, lmin, lmax, N, Nt, lev, anc, precision=F32,
-                 nfields=1, capacity=None, device="cuda", stream=None):
+                 nfields=1, capacity=None, device="cuda", stream=None, fixed_tree=False):
         import torch
         L = load()
         lev = np.ascontiguousarray(lev, np.int32)
@@ -129,6 +130,7 @@ class Grid:
         d.tree_len, d.nb, d.lmin, d.lmax = float(tree_len), nb, lmin, lmax
         d.wav_N, d.wav_Nt, d.precision, d.nfields, d.capacity = N, Nt, precision, nfields, cap
         d.stream = s.cuda_stream
+        d.flags = 1 if fixed_tree else 0
         self.desc = d
         nbytes = C.c_size_t()
         _chk(L.mr_workspace_size(C.byref(d), C.byref(nbytes)))

@@ -76,7 +76,7 @@ def test_adapt_iteration_fp64_matches_oracle(mr, oracle_mod, N, Nt):
     og2, ophi, _, onch, _, st = O.adapt_iter(og, phi, er, ec)
     assert nch == onch and nch > 0
     assert (st == 1).any()
-    if Nt == 2:  # the blob is narrow enough for the lifted wavelets to coarsen
+    if Nt == 2 and N >= 4:  # narrow enough for the higher-order lifted wavelets to coarsen
         assert (st == -1).any()
     glev, ganc, gkeys = g.leaves()
     okeys = np.array([O.morton_key(l, *a, og.lmax) for l, a in zip(og2.lev, og2.anc)], np.uint64)
