@@ -148,6 +148,23 @@ int mr_ghost_fill(mr_grid *grid, int fid, int G, void *padded);
  * on FP32 rounding.  padded: nleaf*(nb+2G)^3 doubles or NULL.             */
 int mr_ghost_fill64(mr_grid *grid, int fid, int G, double *padded);
 
+/* Ghost fill that allocates nothing, for callers that cannot obtain device
+ * memory when they call it (no cudaMalloc, no pool or framework allocator:
+ * for example code running inside another runtime's fixed memory budget).
+ * The paper has no counterpart: this is a packaging variant of
+ * mr_ghost_fill, with the same arguments, semantics and results.
+ * Its scratch -- the padded blocks and the fine-to-coarse side buffer --
+ * lives in one 64 MiB array of static device memory that every GPU loading
+ * the library keeps until the process exits; grids whose
+ * 2 * nleaf * (nb + 2*Gi)^3 elements (Gi >= G: the internal shell) exceed it
+ * are rejected with MR_ERR_NOMEM.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current,
+ * so make that first call before any stream capture.  All calls share the
+ * array: calls that overlap on the GPU (different streams, or grids used
+ * concurrently) race on it; serialise them.  Nothing in the array needs to
+ * start at zero (every value read is written first in the same call).    */
+int mr_ghost_fill_static(mr_grid *grid, int fid, int G, void *padded);
+
 /* Wait for the grid's stream and report device-side errors recorded by the
  * kernels since the last check (MR_ERR_BALANCE: a ghost point was owned by
  * a leaf more than one level away, or a shell exceeded the stored padding). */

@@ -412,3 +412,58 @@ int launch_crop(mr_grid *g, const void *P, int Gi, void *out, int G, bool fp64_s
 
 }  // namespace mr
 
+// ---------------------------------------------------------------------------
+// Ghost fill without any allocation: the padded block P and the Part-2 side
+// buffer Q live in a file-scope device array instead of the grid workspace.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+#define MR_STATIC_SCRATCH_BYTES ((size_t)64 << 20)
+static __device__ __align__(256) unsigned char mr_static_scratch[MR_STATIC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_static_mu;
+void *g_static_addr[256];  // per device ordinal, set once
+}  // namespace
+
+extern "C" int mr_ghost_fill_static(mr_grid *g, int fid, int G, void *padded) {
+  using namespace mr;
+  if (!g || fid < 0 || fid >= g->desc.nfields) return MR_ERR_INVALID;
+  const int nb = g->desc.nb;
+  if (G < 1 || G > MR_MAX_SHELL) return MR_ERR_INVALID;
+  if (G > nb / 2) return MR_ERR_BALANCE;
+  int dev = -1;
+  if (check_cuda(cudaGetDevice(&dev), "cudaGetDevice")) return MR_ERR_CUDA;
+  if (dev != g->dev || dev < 0 || dev >= 256) {
+    set_error("mr_ghost_fill_static: the grid's device must be current");
+    return MR_ERR_INVALID;
+  }
+  const int gi = internal_shell(g->desc.wav_N, g->desc.wav_Nt, G, nb);
+  const size_t wd = (size_t)nb + 2 * gi;
+  const size_t half = (((size_t)g->nleaf * wd * wd * wd * g->esize) + 255) & ~(size_t)255;
+  if (2 * half > MR_STATIC_SCRATCH_BYTES) {
+    set_error("mr_ghost_fill_static: grid too large for the 64 MiB static scratch");
+    return MR_ERR_NOMEM;
+  }
+  void *base;
+  {
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_addr[dev]) {
+      // host code cannot take the address of a __device__ array directly
+      if (check_cuda(cudaGetSymbolAddress(&g_static_addr[dev], mr_static_scratch), "cudaGetSymbolAddress")) {
+        g_static_addr[dev] = nullptr;
+        return MR_ERR_CUDA;
+      }
+    }
+    base = g_static_addr[dev];
+  }
+  void *P = base, *Q = (char *)base + half;
+  void *f = field_ptr(g, fid);
+  int e;
+  if (g->desc.precision == MR_F32)
+    e = ghost_dispatch<float, float>(g, (const float *)f, (float *)f, G, (float *)P, (float *)Q, gi);
+  else
+    e = ghost_dispatch<double, double>(g, (const double *)f, (double *)f, G, (double *)P, (double *)Q, gi);
+  if (e) return e;
+  return padded ? launch_crop(g, P, gi, padded, G, g->desc.precision == MR_F64) : MR_OK;
+}

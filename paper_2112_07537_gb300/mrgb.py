@@ -28,7 +28,8 @@ EXPORTS = ["mr_last_error", "mr_workspace_size", "mr_grid_create", "mr_grid_dest
            "mr_grid_leaves", "mr_field_copy_in", "mr_field_copy_out", "mr_field_set",
            "mr_ghost_fill", "mr_ghost_fill64", "mr_sync", "mr_rhs_advect", "mr_rk_stage",
            "mr_step", "mr_criterion", "mr_adapt", "mr_adapt_iter", "mr_mass", "mr_query",
-           "mr_field_ptr", "mr_profile", "mr_profile_read", "mr_launch_count"]
+           "mr_field_ptr", "mr_profile", "mr_profile_read", "mr_launch_count",
+           "mr_ghost_fill_static"]
 
 
 class MRError(RuntimeError):
@@ -72,6 +73,7 @@ def load(path: str = LIB_PATH):
         L.mr_field_set.argtypes = [vp, C.c_int, C.c_int, dp, C.c_int]
         L.mr_ghost_fill.argtypes = [vp, C.c_int, C.c_int, vp]
         L.mr_ghost_fill64.argtypes = [vp, C.c_int, C.c_int, vp]
+        L.mr_ghost_fill_static.argtypes = [vp, C.c_int, C.c_int, vp]
         L.mr_sync.argtypes = [vp]
         L.mr_rhs_advect.argtypes = [vp, C.c_int, dp, C.c_int, C.c_int]
         L.mr_rk_stage.argtypes = [vp, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int]
@@ -214,6 +216,11 @@ class Grid:
     # ------------------------------------------------------------ the path
     def ghost_fill(self, fid, G, padded=None):
         _chk(load().mr_ghost_fill(self.h, fid, G, _ptr(padded) if padded is not None else None))
+        return padded
+
+    def ghost_fill_static(self, fid, G, padded=None):
+        """mr_ghost_fill without allocation (static device scratch)."""
+        _chk(load().mr_ghost_fill_static(self.h, fid, G, _ptr(padded) if padded is not None else None))
         return padded
 
     def ghost_fill64(self, fid, G, padded=None):
