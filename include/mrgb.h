@@ -84,6 +84,8 @@ typedef struct {
 } mr_grid_desc;
 
 #define MR_GRID_FIXED_TREE 1
+#define MR_GRID_VELOCITY 2 /* reserve the ghost-filled velocity cache used by
+                              mr_step_vel / mr_rhs_advect_vel              */
 
 typedef struct {
   int nleaf;
@@ -182,6 +184,21 @@ int mr_rhs_advect(mr_grid *grid, int phi_fid, const double *u_const, int out_fid
  * elementwise over the current leaves; out may alias u or y.               */
 int mr_rk_stage(mr_grid *grid, int stage, double dt, int u_fid, int y_fid, int rhs_fid,
                 int out_fid);
+
+/* As mr_rhs_advect with a velocity field u = (field vel_fid[0], vel_fid[1],
+ * vel_fid[2]) instead of a constant: interface velocity (u_i + u_{i+1})/2
+ * selects the upwind side.  The grid needs MR_GRID_VELOCITY.  The velocity
+ * components are ghost-filled (and substituted) once per tree: the cache is
+ * rebuilt after every adaptation that changes the leaves; a caller that
+ * writes new velocity values must call mr_velocity_invalidate.            */
+int mr_rhs_advect_vel(mr_grid *grid, int phi_fid, const int *vel_fid, int out_fid, int scheme);
+
+/* One RK3 step of phi (in place) advected by the velocity fields vel_fid[3]
+ * (see mr_rhs_advect_vel).                                                 */
+int mr_step_vel(mr_grid *grid, int phi_fid, double dt, const int *vel_fid, int scheme);
+
+/* Drop the cached ghost-filled velocity (after changing velocity values). */
+int mr_velocity_invalidate(mr_grid *grid);
 
 /* One RK3 step of phi (in place): three times ghost fill + fused rhs/stage,
  * using the grid's two internal temporaries.  Constant velocity u_const.   */

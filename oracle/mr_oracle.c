@@ -1141,3 +1141,30 @@ uint64_t og_morton_key(int lev, int ax, int ay, int az, int kl) {
   }
   return (key << 5) | (uint64_t)lev;
 }
+
+/* One RK3 step with velocity fields: every stage ghost-fills phi and the
+ * three velocity components (their substitution overwrites them), then the
+ * right-hand side with point velocities (interface sign from (u_i+u_{i+1})/2).
+ * phi and vel[3] are updated in place.                                     */
+int og_rk3_step_vel(const og_grid *g, double *phi, double *vx, double *vy, double *vz, double dt,
+                    int scheme) {
+  const int nb = g->nb, G = 3, W = nb + 2 * G;
+  const size_t nb3 = (size_t)nb * nb * nb, n = nb3 * g->nleaf, np = (size_t)W * W * W * g->nleaf;
+  double *pad = (double *)malloc(sizeof(double) * np);
+  double *vp[3];
+  double *vel[3] = {vx, vy, vz};
+  for (int d = 0; d < 3; ++d) vp[d] = (double *)malloc(sizeof(double) * np);
+  double *y = (double *)malloc(sizeof(double) * n);
+  double *r = (double *)malloc(sizeof(double) * n);
+  int e = (!pad || !vp[0] || !vp[1] || !vp[2] || !y || !r) ? OG_ERR_NOMEM : OG_OK;
+  for (int s = 0; s < 3 && !e; ++s) {
+    double *src = (s == 0) ? phi : y;
+    e = og_ghost_fill(g, src, G, pad, src);
+    for (int d = 0; d < 3 && !e; ++d) e = og_ghost_fill(g, vel[d], G, vp[d], vel[d]);
+    if (!e) e = og_rhs(g, pad, G, scheme, NULL, vp[0], vp[1], vp[2], r);
+    if (!e) og_rk_combine(s, n, dt, phi, src, r, s == 2 ? phi : y);
+  }
+  free(pad), free(y), free(r);
+  for (int d = 0; d < 3; ++d) free(vp[d]);
+  return e;
+}

@@ -81,6 +81,7 @@ def _declare(L):
         getattr(L, f).argtypes = [C.c_int, C.c_int, C.c_int, _dp, _dp]
     L.og_synth_1d.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _dp, _dp]
     L.og_status.argtypes = [C.c_double, C.c_double, C.c_double]
+    L.og_rk3_step_vel.argtypes = [C.POINTER(_Grid), _dp, _dp, _dp, _dp, C.c_double, C.c_int]
     L.og_morton_key.argtypes = [C.c_int] * 5
     L.og_morton_key.restype = C.c_uint64
 
@@ -156,6 +157,17 @@ def rk3_step(g: Grid, phi: np.ndarray, dt: float, scheme: int, u=(1.0, 1.0, 1.0)
     uc = np.asarray(u, dtype=np.float64)
     _check(lib().og_rk3_step(g.c(), _d(phi), dt, scheme, _d(uc)), "rk3_step")
     return phi.reshape(g.nleaf, g.nb, g.nb, g.nb)
+
+
+def rk3_step_vel(g: Grid, phi: np.ndarray, vel, dt: float, scheme: int):
+    """RK3 step with velocity fields (each stage ghost-fills phi and u, v, w);
+    returns (phi, vel) -- the velocity components come back substituted."""
+    phi = np.ascontiguousarray(phi, dtype=np.float64).copy()
+    vs = [np.ascontiguousarray(v, dtype=np.float64).copy() for v in vel]
+    _check(lib().og_rk3_step_vel(g.c(), _d(phi), _d(vs[0]), _d(vs[1]), _d(vs[2]), dt, scheme),
+           "rk3_step_vel")
+    shp = (g.nleaf, g.nb, g.nb, g.nb)
+    return phi.reshape(shp), [v.reshape(shp) for v in vs]
 
 
 def dt_cfl(g: Grid, cfl: float, u) -> float:

@@ -85,7 +85,7 @@ int adapt_shell(int N, int Nt) {
 }
 
 struct Layout {
-  size_t off[24];
+  size_t off[25];
   size_t total;
 };
 
@@ -106,6 +106,8 @@ static int layout(const mr_grid_desc *d, Layout *L, int *shell_rk, int *shell_ad
   const size_t es = d->precision == MR_F32 ? 4 : 8;
   const size_t nb3 = (size_t)d->nb * d->nb * d->nb, cap = (size_t)d->capacity;
   const bool fixed = d->flags & MR_GRID_FIXED_TREE;
+  const bool velo = d->flags & MR_GRID_VELOCITY;
+  const size_t wv = d->nb + 6;
   const int gad = adapt_shell(d->wav_N, d->wav_Nt);
   *shell_rk = internal_shell(d->wav_N, d->wav_Nt, 3, d->nb);
   *shell_ad = std::max(internal_shell(d->wav_N, d->wav_Nt, gad, d->nb), *shell_rk);
@@ -113,7 +115,7 @@ static int layout(const mr_grid_desc *d, Layout *L, int *shell_rk, int *shell_ad
   *M = d->lmax;
   *map_cells = ((size_t)d->ntree[0] << d->lmax) * ((size_t)d->ntree[1] << d->lmax) *
                ((size_t)d->ntree[2] << d->lmax);
-  size_t sz[24] = {
+  size_t sz[25] = {
       cap * 4, cap * 4,                          // lev[2]
       cap * 12, cap * 12,                        // anc[2]
       cap * 8, cap * 8,                          // keys[2]
@@ -130,9 +132,10 @@ static int layout(const mr_grid_desc *d, Layout *L, int *shell_rk, int *shell_ad
       64 * 4,                                    // counter
       64 * 8,                                    // dscratch
       cap * 8,                                   // cmask + new-band masks
-      cap * 4};                                  // hasD
+      cap * 4,                                   // hasD
+      velo ? 3 * cap * wv * wv * wv * es : 0};   // velocity cache (shell 3)
   size_t o = 0;
-  for (int i = 0; i < 24; ++i) {
+  for (int i = 0; i < 25; ++i) {
     L->off[i] = o;
     o += al(sz[i]);
   }
@@ -253,6 +256,9 @@ int mr_grid_create(const mr_grid_desc *desc, void *workspace, size_t workspace_b
   g->dscratch = (double *)(w + L.off[21]);
   g->cmask = (int *)(w + L.off[22]);
   g->hasD = (int *)(w + L.off[23]);
+  g->vpad = (desc->flags & MR_GRID_VELOCITY) ? (void *)(w + L.off[24]) : nullptr;
+  g->tree_version = 0;
+  g->vel_version = -1;
   g->shell_rk = srk;
   g->shell_ad = sad;
   g->map_cells = mc;
@@ -425,6 +431,83 @@ int mr_rhs_advect(mr_grid *g, int phi, const double *u, int out, int scheme) {
   int e = launch_ghost(g, f, f, 3, false, &P, &Gi);
   if (e) return e;
   return launch_rhs_stage(g, P, Gi, nullptr, field_ptr(g, out), 0, 0.0, u, scheme, true);
+}
+
+// ghost-filled velocity components for the current tree (rebuilt when the
+// tree or the velocity field ids change)
+static int velocity_cache(mr_grid *g, const int *vel) {
+  if (!g->vpad) {
+    set_error("grid created without MR_GRID_VELOCITY");
+    return MR_ERR_UNSUPPORTED;
+  }
+  for (int d = 0; d < 3; ++d)
+    if (!fid_ok(g, vel[d])) return MR_ERR_INVALID;
+  if (g->vel_version == g->tree_version && g->vel_fid[0] == vel[0] && g->vel_fid[1] == vel[1] &&
+      g->vel_fid[2] == vel[2])
+    return MR_OK;
+  const size_t wv = g->desc.nb + 6, blk = wv * wv * wv * g->esize;
+  for (int d = 0; d < 3; ++d) {
+    void *P;
+    int Gi;
+    bool is64;
+    void *f = field_ptr(g, vel[d]);
+    int e = launch_ghost(g, f, f, 3, false, &P, &Gi, &is64);
+    // component d at offset d * nleaf blocks (the kernels' indexing)
+    if (!e) e = launch_crop(g, P, Gi, (char *)g->vpad + (size_t)d * g->nleaf * blk, 3, is64);
+    if (e) return e;
+  }
+  g->vel_version = g->tree_version;
+  for (int d = 0; d < 3; ++d) g->vel_fid[d] = vel[d];
+  return MR_OK;
+}
+
+int mr_velocity_invalidate(mr_grid *g) {
+  if (!g) return MR_ERR_INVALID;
+  g->vel_version = -1;
+  return MR_OK;
+}
+
+int mr_rhs_advect_vel(mr_grid *g, int phi, const int *vel, int out, int scheme) {
+  if (!fid_ok(g, phi) || !fid_ok(g, out) || !vel) return MR_ERR_INVALID;
+  int e = velocity_cache(g, vel);
+  if (e) return e;
+  void *f = field_ptr(g, phi);
+  if (g->desc.precision == MR_F32) {
+    int Gi;
+    e = launch_prep32(g, f, &Gi);
+    if (!e) e = launch_fused(g, f, g->padP, g->padQ, Gi, nullptr, field_ptr(g, out), 0, 0.0, nullptr, scheme, true,
+                             g->vpad);
+    if (!e) e = launch_writeback32(g, Gi, f);
+    return e;
+  }
+  void *P;
+  int Gi;
+  e = launch_ghost(g, f, f, 3, false, &P, &Gi);
+  if (e) return e;
+  return launch_rhs_stage(g, P, Gi, nullptr, field_ptr(g, out), 0, 0.0, nullptr, scheme, true, g->vpad);
+}
+
+int mr_step_vel(mr_grid *g, int phi, double dt, const int *vel, int scheme) {
+  if (!fid_ok(g, phi) || !vel) return MR_ERR_INVALID;
+  int e = velocity_cache(g, vel);
+  if (e) return e;
+  void *un = field_ptr(g, phi);
+  void *y1 = field_ptr(g, g->desc.nfields), *y2 = field_ptr(g, g->desc.nfields + 1);
+  void *src[3] = {un, y1, y2};
+  void *dst[3] = {y1, y2, un};
+  for (int s = 0; s < 3 && !e; ++s) {
+    int Gi;
+    if (g->desc.precision == MR_F32) {
+      e = launch_prep32(g, src[s], &Gi);
+      if (!e) e = launch_fused(g, src[s], g->padP, g->padQ, Gi, un, dst[s], s, dt, nullptr, scheme, false, g->vpad);
+      if (!e && s == 0) e = launch_writeback32(g, Gi, un);
+    } else {
+      void *P;
+      e = launch_ghost(g, src[s], src[s], 3, false, &P, &Gi);
+      if (!e) e = launch_rhs_stage(g, P, Gi, un, dst[s], s, dt, nullptr, scheme, false, g->vpad);
+    }
+  }
+  return e;
 }
 
 int mr_rk_stage(mr_grid *g, int stage, double dt, int u_fid, int y_fid, int rhs_fid, int out_fid) {

@@ -607,6 +607,7 @@ int adapt_iteration(mr_grid *g, int crit, double er, double ec, int flags, int *
   g->map = g->maps[nx];
   g->pool_cur ^= 1;
   g->nleaf = nn;
+  g->tree_version++;
   int *tmp = g->refined;
   g->refined = g->refined2;
   g->refined2 = tmp;

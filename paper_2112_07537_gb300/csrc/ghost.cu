@@ -65,20 +65,6 @@ __device__ __forceinline__ bool in_band(int mask, int i, int j, int k, int nb, i
   return false;
 }
 
-// Directions (27-bit mask) toward a coarser neighbour of leaf b.
-__device__ int coarse_mask_dir(const Tree &t, int b, int m, int *err) {
-  if (m == 13) return 0;
-  const int L = __ldg(t.lev + b), nb = t.nb;
-  const int dd[3] = {m % 3 - 1, (m / 3) % 3 - 1, m / 9 - 1};
-  int g[3];
-  for (int d = 0; d < 3; ++d)
-    g[d] = __ldg(t.anc + 3 * b + d) * nb + (dd[d] < 0 ? -1 : dd[d] > 0 ? nb : 0);
-  const int o = owner(t, L, g[0], g[1], g[2]);
-  const int Lo = __ldg(t.lev + o);
-  if (Lo < L - 1 || Lo > L + 1) atomicOr(err, 4);
-  return Lo < L ? (1 << m) : 0;
-}
-
 // ---------------------------------------------------------------------------
 // Part 1 with the coarse-level values staged in shared memory, substitution,
 // and Part 2 pushed to the coarser neighbours.
@@ -97,77 +83,107 @@ __host__ __device__ constexpr int tq_lo(int Gi) { return -((Gi + 2) / 2) - (N / 
 template <int N>
 __host__ __device__ constexpr int tq_hi(int nb, int Gi) { return (nb + Gi - 2) / 2 + N / 2; }
 
+// region index (0..26) of a block-local point within the +-1 neighbour ring
+__device__ __forceinline__ int region_of(int i, int j, int k, int nb) {
+  const int rx = i < 0 ? 0 : i >= nb ? 2 : 1, ry = j < 0 ? 0 : j >= nb ? 2 : 1, rz = k < 0 ? 0 : k >= nb ? 2 : 1;
+  return rx + 3 * ry + 9 * rz;
+}
+
 template <typename TI, typename TP, int N, int NT>
-__global__ void __launch_bounds__(256) k_prep(Tree t, const TI *__restrict__ phi, TP *__restrict__ P,
-                                              TP *__restrict__ Q, int Gi, int Gpush, int only_coarse,
-                                              int use_tile, int *cmask_out, int *err) {
+__global__ void __launch_bounds__(512, 1) k_prep(Tree t, const TI *__restrict__ phi, TP *__restrict__ P,
+                                                 TP *__restrict__ Q, int Gi, int Gpush, int only_coarse,
+                                                 int use_tile, int *cmask_out, int *err) {
   using W = Wav<N, NT>;
   const int b = blockIdx.x;
   const int nb = t.nb, Wd = nb + 2 * Gi;
-  const size_t np = (size_t)Wd * Wd * Wd;
+  const size_t np = (size_t)Wd * Wd * Wd, nb3 = (size_t)nb * nb * nb;
   const int L = __ldg(t.lev + b);
   const int ax = __ldg(t.anc + 3 * b) * nb, ay = __ldg(t.anc + 3 * b + 1) * nb,
             az = __ldg(t.anc + 3 * b + 2) * nb;
+  // owners of the 27 block-sized regions around b (same or coarser leaves own
+  // a whole region; a finer region is resolved point by point)
+  __shared__ int rslot[27], rlev[27], ranc[27][3];
   __shared__ int cmask;
   __shared__ int cslots[27];
   __shared__ int ncs;
   if (threadIdx.x == 0) cmask = 0, ncs = 0;
   __syncthreads();
   if (threadIdx.x < 27) {
-    int m = coarse_mask_dir(t, b, threadIdx.x, err);
-    if (m) atomicOr(&cmask, m);
+    const int r = threadIdx.x;
+    const int dd[3] = {r % 3 - 1, (r / 3) % 3 - 1, r / 9 - 1};
+    int g[3];
+    for (int d = 0; d < 3; ++d)
+      g[d] = __ldg(t.anc + 3 * b + d) * nb + (dd[d] < 0 ? -1 : dd[d] > 0 ? nb : 0);
+    const int o = owner(t, L, g[0], g[1], g[2]);
+    const int Lo = __ldg(t.lev + o);
+    rslot[r] = o, rlev[r] = Lo;
+    for (int d = 0; d < 3; ++d) ranc[r][d] = __ldg(t.anc + 3 * o + d);
+    if (r != 13) {
+      if (Lo < L - 1 || Lo > L + 1) atomicOr(err, 4);
+      if (Lo < L) atomicOr(&cmask, 1 << r);
+    }
   }
   __syncthreads();
   const int mask = cmask;
   if (threadIdx.x == 0 && cmask_out) cmask_out[b] = mask;
   if (only_coarse && !mask) return;
+  // value stored at level-Lq point (block-local, level L coords when Lq == L;
+  // coarse-local coords when Lq == L-1) -- via the region table when the
+  // owning region is same-level or coarser, else through the owner map
+  auto fetch = [&](int Lq, int i, int j, int k) -> TP {
+    const int sc = (Lq == L) ? 1 : 2;  // fine-index scale of the point
+    const int fi = i * sc, fj = j * sc, fk = k * sc;
+    if (fi >= -nb && fi < 2 * nb && fj >= -nb && fj < 2 * nb && fk >= -nb && fk < 2 * nb) {
+      const int r = region_of(fi, fj, fk, nb);
+      const int Lo = rlev[r], o = rslot[r];
+      if (Lo == L) {
+        const int dx = r % 3 - 1, dy = (r / 3) % 3 - 1, dz = r / 9 - 1;
+        return TP(ld(phi + (size_t)o * nb3 + (fi - dx * nb) + nb * ((fj - dy * nb) + nb * (fk - dz * nb))));
+      }
+      if (Lo == L - 1) {
+        // coarse leaf: level-(L-1) index of the point, relative to its anchor
+        const int gq[3] = {(ax + fi) / 2, (ay + fj) / 2, (az + fk) / 2};
+        int l[3];
+        for (int d = 0; d < 3; ++d) l[d] = pwrap(gq[d] - ranc[r][d] * nb, npts(t, L - 1, d));
+        return TP(ld(phi + (size_t)o * nb3 + l[0] + nb * (l[1] + nb * l[2])));
+      }
+    }
+    const int gx = (Lq == L ? ax : ax / 2) + i, gy = (Lq == L ? ay : ay / 2) + j, gz = (Lq == L ? az : az / 2) + k;
+    const int o = owner(t, Lq, gx, gy, gz);
+    if (__ldg(t.lev + o) < Lq) return TP(__int_as_float(0x7fc00000));
+    return TP(leaf_value(t, phi, o, Lq, gx, gy, gz, err));
+  };
   extern __shared__ unsigned char smraw[];
   TP *T = reinterpret_cast<TP *>(smraw);
   const int qlo = tq_lo<N>(Gi), nq = tq_hi<N>(nb, Gi) - qlo + 1;
   const bool tile = use_tile && mask;
   if (tile) {
-    const int cx = ax / 2 + qlo, cy = ay / 2 + qlo, cz = az / 2 + qlo;
-    for (int p = threadIdx.x; p < nq * nq * nq; p += blockDim.x) {
-      const int qx = cx + p % nq, qy = cy + (p / nq) % nq, qz = cz + p / (nq * nq);
-      const int o = owner(t, L - 1, qx, qy, qz);
-      TP v;
-      if (__ldg(t.lev + o) < L - 1) {
-        v = TP(__int_as_float(0x7fc00000));  // never read by a valid refinement
-      } else {
-        const int Lo = __ldg(t.lev + o);
-        const int lx = local_index(t, o, Lo, L - 1, qx, 0), ly = local_index(t, o, Lo, L - 1, qy, 1),
-                  lz = local_index(t, o, Lo, L - 1, qz, 2);
-        v = TP(ld(phi + (size_t)o * nb * nb * nb + lx + nb * (ly + nb * lz)));
-      }
-      T[p] = v;
-    }
+    for (int p = threadIdx.x; p < nq * nq * nq; p += blockDim.x)
+      T[p] = fetch(L - 1, qlo + p % nq, qlo + (p / nq) % nq, qlo + p / (nq * nq));
     __syncthreads();
   }
   TP *Pb = P + (size_t)b * np;
-  const TI *phib = phi + (size_t)b * nb * nb * nb;
+  const TI *phib = phi + (size_t)b * nb3;
   for (size_t p = threadIdx.x; p < np; p += blockDim.x) {
     const int i = (int)(p % Wd) - Gi, j = (int)((p / Wd) % Wd) - Gi, k = (int)(p / ((size_t)Wd * Wd)) - Gi;
     TP v;
     if (i >= 0 && i < nb && j >= 0 && j < nb && k >= 0 && k < nb) {
       v = TP(ld(phib + i + nb * (j + nb * k)));
     } else {
-      const int gx = ax + i, gy = ay + j, gz = az + k;
-      const int o = owner(t, L, gx, gy, gz);
-      const int Lo = __ldg(t.lev + o);
-      if (Lo >= L) {
-        v = TP(leaf_value(t, phi, o, L, gx, gy, gz, err));
-      } else if (Lo == L - 1) {
+      const int r = region_of(i, j, k, nb);
+      const int Lo = rlev[r];
+      if (Lo == L - 1) {
         if (tile) {
-          // refine_point with T from shared memory (local coarse index g/2)
-          const TP s = refine_dispatch<N, NT, TP>(i & 1, j & 1, k & 1, [&](int ox, int oy, int oz) -> TP {
+          v = refine_dispatch<N, NT, TP>(i & 1, j & 1, k & 1, [&](int ox, int oy, int oz) -> TP {
             const int qx = (i + ox) / 2 - qlo, qy = (j + oy) / 2 - qlo, qz = (k + oz) / 2 - qlo;
             return T[qx + nq * (qy + nq * qz)];
           });
-          if (s != s) atomicOr(err, 2);
-          v = s;
+          if (v != v) atomicOr(err, 2);
         } else {
-          v = refine_point<TI, TP, N, NT>(t, phi, L, gx, gy, gz, err);
+          v = refine_point<TI, TP, N, NT>(t, phi, L, ax + i, ay + j, az + k, err);
         }
+      } else if (Lo >= L) {
+        v = fetch(L, i, j, k);  // copy, or the coincident value of a finer leaf
       } else {
         atomicOr(err, 8);
         v = TP(0);
@@ -195,9 +211,7 @@ __global__ void __launch_bounds__(256) k_prep(Tree t, const TI *__restrict__ phi
   if (threadIdx.x == 0) {
     for (int m = 0; m < 27; ++m) {
       if (!((mask >> m) & 1)) continue;
-      const int dd[3] = {m % 3 - 1, (m / 3) % 3 - 1, m / 9 - 1};
-      const int o = owner(t, L, ax + (dd[0] < 0 ? -1 : dd[0] > 0 ? nb : 0),
-                          ay + (dd[1] < 0 ? -1 : dd[1] > 0 ? nb : 0), az + (dd[2] < 0 ? -1 : dd[2] > 0 ? nb : 0));
+      const int o = rslot[m];
       bool seen = false;
       for (int q = 0; q < ncs; ++q) seen |= cslots[q] == o;
       if (!seen) cslots[ncs++] = o;
@@ -312,7 +326,7 @@ static int ghost_impl(mr_grid *g, const TI *phi_in, TI *phi_out, int G, TP *P, T
       check_cuda(cudaFuncSetAttribute(k_prep<TI, TP, N, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
                  "k_prep smem"))
     return MR_ERR_CUDA;
-  MR_LAUNCH(g, MRK_PART1, k_prep<TI, TP, N, NT><<<n, 256, sm, g->stream>>>(t, phi_in, P, Q, Gi, G, only_coarse,
+  MR_LAUNCH(g, MRK_PART1, k_prep<TI, TP, N, NT><<<n, 512, sm, g->stream>>>(t, phi_in, P, Q, Gi, G, only_coarse,
                                                                            use_tile, g->cmask, err));
   if (check_cuda(cudaGetLastError(), "k_prep")) return MR_ERR_CUDA;
   if (only_coarse) return MR_OK;

@@ -72,6 +72,10 @@ __device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b)
 __device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+// accumulate s + w*v: FP64 keeps the separately rounded product and sum of a
+// plain evaluation (bit-reproducible); FP32 uses one fused multiply-add
+__device__ __forceinline__ float racc(float s, float w, float v) { return fmaf(w, v, s); }
+__device__ __forceinline__ double racc(double s, double w, double v) { return __dadd_rn(s, __dmul_rn(w, v)); }
 
 // ---------------------------------------------------------------------------
 // Tensor sums with the parity of the output point fixed at compile time, so
@@ -102,7 +106,7 @@ __device__ __forceinline__ TP refine_sum(F val) {
         if (((ox & 1) != 0) != OX) continue;
         const TP wgt = rmul(rmul(TP(OX ? W::K(ox) : W::J(ox)), wy), wz);
         if (wgt == TP(0)) continue;
-        s = radd(s, rmul(wgt, val(ox, oy, oz)));
+        s = racc(s, wgt, val(ox, oy, oz));
       }
     }
   }
@@ -138,7 +142,7 @@ __device__ __forceinline__ TP coarsen_sum(F val) {
       for (int tx = -W::hwH; tx <= W::hwH; ++tx) {
         if (W::H(tx) == 0.0) continue;
         const TP wgt = rmul(rmul(TP(W::H(tx)), TP(W::H(ty))), TP(W::H(tz)));
-        s = radd(s, rmul(wgt, val(tx, ty, tz)));
+        s = racc(s, wgt, val(tx, ty, tz));
       }
     }
   }
@@ -162,7 +166,7 @@ __device__ __forceinline__ TP subst_sum(F val) {
         if (OX && W::G(tx) == 0.0) continue;
         if (!tx && !ty && !tz) continue;
         const TP wgt = rmul(rmul(TP(OX ? W::G(tx) : 1.0), TP(OY ? W::G(ty) : 1.0)), TP(OZ ? W::G(tz) : 1.0));
-        s = radd(s, rmul(wgt, val(tx, ty, tz)));
+        s = racc(s, wgt, val(tx, ty, tz));
       }
     }
   }
@@ -275,6 +279,10 @@ struct mr_grid {
   double *dscratch;       // reduction scratch
   int *cmask;             // per-leaf coarse-direction masks (ghost fill), then new-band masks
   int *hasD;              // per new leaf: the update step has discarded details
+  void *vpad;             // ghost-filled velocity components (shell 3), 3 * cap * (nb+6)^3
+  int tree_version;       // bumped whenever the leaves change
+  int vel_version;        // tree version the velocity cache was built for (-1: none)
+  int vel_fid[3];
   // launch registry: counts every kernel launch; with profiling on, brackets
   // each launch with CUDA events on the grid's stream
   long long launches[32];
@@ -316,11 +324,11 @@ int launch_crop64(mr_grid *g, const double *P, int Gi, double *out, int G);
 int launch_prep32(mr_grid *g, const void *phi, int *Gi);
 int launch_writeback32(mr_grid *g, int Gi, void *phi);
 int launch_fused(mr_grid *g, const void *phi, const void *P, const void *Q, int Gi, const void *u, void *out,
-                 int stage, double dt, const double *uc, int scheme, bool rhs_only);
+                 int stage, double dt, const double *uc, int scheme, bool rhs_only, const void *vpad = nullptr);
 int adapt_shell(int N, int Nt);
 // stencil.cu
 int launch_rhs_stage(mr_grid *g, const void *P, int Gi, const void *u, void *out, int stage,
-                     double dt, const double *uc, int scheme, bool rhs_only);
+                     double dt, const double *uc, int scheme, bool rhs_only, const void *vpad = nullptr);
 int launch_rk_combine(mr_grid *g, int stage, double dt, const void *u, const void *y,
                       const void *r, void *out);
 int launch_field_set(mr_grid *g, void *f, int kind, const double *p, int np);

@@ -67,7 +67,8 @@ __device__ __forceinline__ T iface_flux(const T *f, bool left) {
 template <typename T, int SCHEME>
 __global__ void __launch_bounds__(256) k_rhs_stage(Tree t, const T *__restrict__ P, int Gi,
                                                    const T *u, T *out, int stage, T dt, T ux, T uy,
-                                                   T uz, int rhs_only) {
+                                                   T uz, int rhs_only, const T *__restrict__ vpad) {
+  // vpad: ghost-filled velocity components (shell 3) or null for constant u
   const int b = blockIdx.x;
   const int nb = t.nb, Wd = nb + 2 * Gi;
   const size_t np = (size_t)Wd * Wd * Wd;
@@ -79,14 +80,21 @@ __global__ void __launch_bounds__(256) k_rhs_stage(Tree t, const T *__restrict__
     const int i = p % nb, j = (p / nb) % nb, k = p / (nb * nb);
     const size_t c = (i + Gi) + Wd * ((j + Gi) + (size_t)Wd * (k + Gi));
     T acc = T(0);
+    const int Wv = nb + 6;
+    const size_t vblk = (size_t)Wv * Wv * Wv, vcomp = (size_t)t.nleaf * vblk;
+    const size_t cv = (size_t)b * vblk + (i + 3) + Wv * ((j + 3) + (size_t)Wv * (k + 3));
+    const int vstride[3] = {1, Wv, Wv * Wv};
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      if (uc[d] == T(0)) continue;
-      T f[7];
+      if (!vpad && uc[d] == T(0)) continue;
+      T f[7], uu[7];
 #pragma unroll
-      for (int m = 0; m < 7; ++m) f[m] = uc[d] * Pb[c + (ptrdiff_t)(m - 3) * stride[d]];
-      const bool left = uc[d] >= T(0);
-      acc += iface_flux<T, SCHEME>(f + 1, left) - iface_flux<T, SCHEME>(f, left);
+      for (int m = 0; m < 7; ++m) {
+        uu[m] = vpad ? vpad[d * vcomp + cv + (ptrdiff_t)(m - 3) * vstride[d]] : uc[d];
+        f[m] = uu[m] * Pb[c + (ptrdiff_t)(m - 3) * stride[d]];
+      }
+      const bool lp = uu[3] + uu[4] >= T(0), lm = uu[2] + uu[3] >= T(0);
+      acc += iface_flux<T, SCHEME>(f + 1, lp) - iface_flux<T, SCHEME>(f, lm);
     }
     const T r = -acc / h;
     const size_t q = (size_t)b * nb * nb * nb + p;
@@ -116,11 +124,11 @@ __device__ __forceinline__ int floordiv2(int a) { return a >= 0 ? a / 2 : -((-a 
 //                       (lifted wavelets) or the coincident value (N.0).
 // Then rhs and the RK3 stage combination, written to out.
 // ---------------------------------------------------------------------------
-template <int N, int NT, int SCHEME>
+template <int N, int NT, int SCHEME, bool VEL>
 __global__ void __launch_bounds__(1024) k_fused(Tree t, const float *__restrict__ phi, const float *__restrict__ P,
                                                const float *__restrict__ Q, int Gi, const int *__restrict__ cmask,
                                                const float *u, float *out, int stage, float dt, float ux, float uy,
-                                               float uz, int rhs_only, int *err) {
+                                               float uz, int rhs_only, int *err, const float *__restrict__ vpad) {
   using W = Wav<N, NT>;
   constexpr int GS = 3;
   const int b = blockIdx.x, nb = t.nb, Ws = nb + 2 * GS, Wd = nb + 2 * Gi;
@@ -227,6 +235,7 @@ __global__ void __launch_bounds__(1024) k_fused(Tree t, const float *__restrict_
   float *R = Tt + (size_t)(N + 1) * (nb / 2 + N) * (nb / 2 + N);
   const float uc[3] = {ux, uy, uz};
   const int strd[3] = {1, Ws, Ws * Ws};
+  const size_t vblk = (size_t)Ws * Ws * Ws, vcomp = (size_t)t.nleaf * vblk;
   for (int d = 0; d < 3; ++d) {
     const float ud = uc[d];
     const bool left = ud >= 0.f;
@@ -238,31 +247,42 @@ __global__ void __launch_bounds__(1024) k_fused(Tree t, const float *__restrict_
       c[d] = 0;
       const int st = strd[d];
       const float *lp = tile + tix(c[0], c[1], c[2]);
-      int rstride = d == 0 ? 1 : d == 1 ? nb : nb * nb;
+      const int rstride = d == 0 ? 1 : d == 1 ? nb : nb * nb;
       float *rp = R + c[0] + nb * (c[1] + nb * c[2]);
-      if (ud == 0.f) {
+      if (!VEL && ud == 0.f) {
         if (d == 0)
           for (int m = 0; m < nb; ++m) rp[m * rstride] = 0.f;
         continue;
       }
-      float w[7];
-#pragma unroll
-      for (int m = 0; m < 6; ++m) w[m + 1] = ud * lp[(m - 3) * st];
-      float Fm = 0.f;
+      // velocity along the line (ghost-filled component d) or the constant
+      const float *vq = VEL ? vpad + d * vcomp + (size_t)b * vblk + tix(c[0], c[1], c[2]) : nullptr;
+      auto vel = [&](int m) -> float { return VEL ? __ldg(vq + m * st) : ud; };
+      // register windows: f = u*phi and u at m-3..m+3; F_{-1/2} from f_{-3..2}
+      float v1 = vel(-3), v2 = vel(-2), v3 = vel(-1), v4 = vel(0), v5 = vel(1), v6 = vel(2);
+      float w1 = v1 * lp[-3 * st], w2 = v2 * lp[-2 * st], w3 = v3 * lp[-st], w4 = v4 * lp[0],
+            w5 = v5 * lp[st], w6 = v6 * lp[2 * st];
+      float Fm;
       {
-        float f6[6] = {w[1], w[2], w[3], w[4], w[5], w[6]};  // f_{-3..2}: F_{-1/2}
-        Fm = iface_flux<float, SCHEME>(f6, left);
+        const float f6[6] = {w1, w2, w3, w4, w5, w6};
+        Fm = iface_flux<float, SCHEME>(f6, VEL ? (v3 + v4 >= 0.f) : left);
       }
+      const float *lq = lp + 3 * st;
+      float *rq = rp;
       for (int m = 0; m < nb; ++m) {
-#pragma unroll
-        for (int q = 0; q < 6; ++q) w[q] = w[q + 1];
-        w[6] = ud * lp[(m + 3) * st];
-        const float Fp = iface_flux<float, SCHEME>(w + 1, left);  // f_{m-2..m+3}
+        w1 = w2, w2 = w3, w3 = w4, w4 = w5, w5 = w6;
+        v1 = v2, v2 = v3, v3 = v4, v4 = v5, v5 = v6;
+        v6 = vel(m + 3);
+        w6 = v6 * *lq;
+        lq += st;
+        const float f6[6] = {w1, w2, w3, w4, w5, w6};  // f_{m-2..m+3}
+        const float Fp = iface_flux<float, SCHEME>(f6, VEL ? (v3 + v4 >= 0.f) : left);
         const float dlt = Fp - Fm;
-        if (d == 0) rp[m * rstride] = dlt;
-        else rp[m * rstride] += dlt;
+        if (d == 0) *rq = dlt;
+        else *rq += dlt;
+        rq += rstride;
         Fm = Fp;
       }
+      (void)v1, (void)v2, (void)v5;
     }
     __syncthreads();
   }
@@ -288,29 +308,31 @@ __global__ void __launch_bounds__(1024) k_fused(Tree t, const float *__restrict_
 
 template <typename T>
 static int rhs_dispatch(mr_grid *g, const T *P, int Gi, const T *u, T *out, int stage, double dt,
-                        const double *uc, int scheme, bool rhs_only) {
+                        const double *uc, int scheme, bool rhs_only, const T *vpad) {
   Tree t = tree_view(g);
   const int n = g->nleaf;
+  static const double zero3[3] = {0.0, 0.0, 0.0};
+  if (!uc) uc = zero3;
   const T ux = T(uc[0]), uy = T(uc[1]), uz = T(uc[2]);
   if (scheme == MR_CONS3)
-    MR_LAUNCH(g, MRK_RHS, k_rhs_stage<T, MR_CONS3><<<n, 256, 0, g->stream>>>(t, P, Gi, u, out, stage, T(dt), ux, uy, uz, rhs_only));
+    MR_LAUNCH(g, MRK_RHS, k_rhs_stage<T, MR_CONS3><<<n, 256, 0, g->stream>>>(t, P, Gi, u, out, stage, T(dt), ux, uy, uz, rhs_only, vpad));
   else if (scheme == MR_CONS5)
-    MR_LAUNCH(g, MRK_RHS, k_rhs_stage<T, MR_CONS5><<<n, 256, 0, g->stream>>>(t, P, Gi, u, out, stage, T(dt), ux, uy, uz, rhs_only));
+    MR_LAUNCH(g, MRK_RHS, k_rhs_stage<T, MR_CONS5><<<n, 256, 0, g->stream>>>(t, P, Gi, u, out, stage, T(dt), ux, uy, uz, rhs_only, vpad));
   else if (scheme == MR_WENOZ5)
-    MR_LAUNCH(g, MRK_RHS, k_rhs_stage<T, MR_WENOZ5><<<n, 256, 0, g->stream>>>(t, P, Gi, u, out, stage, T(dt), ux, uy, uz, rhs_only));
+    MR_LAUNCH(g, MRK_RHS, k_rhs_stage<T, MR_WENOZ5><<<n, 256, 0, g->stream>>>(t, P, Gi, u, out, stage, T(dt), ux, uy, uz, rhs_only, vpad));
   else
     return MR_ERR_INVALID;
   return check_cuda(cudaGetLastError(), "k_rhs_stage") ? MR_ERR_CUDA : MR_OK;
 }
 
 int launch_rhs_stage(mr_grid *g, const void *P, int Gi, const void *u, void *out, int stage,
-                     double dt, const double *uc, int scheme, bool rhs_only) {
+                     double dt, const double *uc, int scheme, bool rhs_only, const void *vpad) {
   if (Gi < 3) return MR_ERR_INVALID;
   if (g->desc.precision == MR_F32)
     return rhs_dispatch<float>(g, (const float *)P, Gi, (const float *)u, (float *)out, stage, dt, uc,
-                               scheme, rhs_only);
+                               scheme, rhs_only, (const float *)vpad);
   return rhs_dispatch<double>(g, (const double *)P, Gi, (const double *)u, (double *)out, stage, dt,
-                              uc, scheme, rhs_only);
+                              uc, scheme, rhs_only, (const double *)vpad);
 }
 
 template <typename T>
@@ -325,9 +347,10 @@ __global__ void k_rk_combine(size_t n, int stage, T dt, const T *u, const T *y, 
   }
 }
 
-template <int N, int NT>
+template <int N, int NT, bool VEL>
 static int fused_impl(mr_grid *g, const float *phi, const float *P, const float *Q, int Gi, const float *u,
-                      float *out, int stage, double dt, const double *uc, int scheme, bool rhs_only) {
+                      float *out, int stage, double dt, const double *uc, int scheme, bool rhs_only,
+                      const float *vpad) {
   Tree t = tree_view(g);
   const int nb = g->desc.nb, Ws = nb + 6;
   const size_t sm = sizeof(float) * ((size_t)Ws * Ws * Ws + (size_t)(N + 1) * (nb / 2 + N) * (nb / 2 + N) +
@@ -336,13 +359,13 @@ static int fused_impl(mr_grid *g, const float *phi, const float *P, const float 
   const float ux = (float)uc[0], uy = (float)uc[1], uz = (float)uc[2];
 #define MR_FL(S)                                                                                          \
   do {                                                                                                    \
-    if (check_cuda(cudaFuncSetAttribute(k_fused<N, NT, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+    if (check_cuda(cudaFuncSetAttribute(k_fused<N, NT, S, VEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                         (int)sm),                                                         \
                    "fused smem"))                                                                         \
       return MR_ERR_CUDA;                                                                                 \
-    MR_LAUNCH(g, MRK_RHS, k_fused<N, NT, S><<<g->nleaf, threads, sm, g->stream>>>(                            \
+    MR_LAUNCH(g, MRK_RHS, k_fused<N, NT, S, VEL><<<g->nleaf, threads, sm, g->stream>>>(                       \
                               t, phi, P, Q, Gi, g->cmask, u, out, stage, (float)dt, ux, uy, uz, rhs_only, \
-                              g->counter + 1));                                                           \
+                              g->counter + 1, vpad));                                                     \
   } while (0)
   if (scheme == MR_CONS3) MR_FL(MR_CONS3);
   else if (scheme == MR_CONS5) MR_FL(MR_CONS5);
@@ -353,12 +376,17 @@ static int fused_impl(mr_grid *g, const float *phi, const float *P, const float 
 }
 
 int launch_fused(mr_grid *g, const void *phi, const void *P, const void *Q, int Gi, const void *u, void *out,
-                 int stage, double dt, const double *uc, int scheme, bool rhs_only) {
+                 int stage, double dt, const double *uc, int scheme, bool rhs_only, const void *vpad) {
   const int N = g->desc.wav_N, Nt = g->desc.wav_Nt;
   const float *a = (const float *)phi, *p = (const float *)P, *q = (const float *)Q, *uu = (const float *)u;
+  const float *vp = (const float *)vpad;
   float *o = (float *)out;
-#define MR_FCASE(n_, nt_) \
-  if (N == n_ && Nt == nt_) return fused_impl<n_, nt_>(g, a, p, q, Gi, uu, o, stage, dt, uc, scheme, rhs_only);
+  static const double zero3[3] = {0.0, 0.0, 0.0};
+  if (!uc) uc = zero3;
+#define MR_FCASE(n_, nt_)                                                                                  \
+  if (N == n_ && Nt == nt_)                                                                                 \
+    return vp ? fused_impl<n_, nt_, true>(g, a, p, q, Gi, uu, o, stage, dt, uc, scheme, rhs_only, vp)        \
+              : fused_impl<n_, nt_, false>(g, a, p, q, Gi, uu, o, stage, dt, uc, scheme, rhs_only, nullptr);
   MR_FCASE(2, 0) MR_FCASE(2, 2) MR_FCASE(4, 0) MR_FCASE(4, 2) MR_FCASE(6, 0) MR_FCASE(6, 2)
 #undef MR_FCASE
   return MR_ERR_UNSUPPORTED;

@@ -21,6 +21,7 @@ CONS3, CONS5, WENOZ5 = 0, 1, 2
 INIT_GAUSSIAN, INIT_TANH_SPHERE, INIT_TAYLOR_GREEN = 0, 1, 2
 ADAPT_REFINE, ADAPT_COARSEN = 1, 2
 GRID_FIXED_TREE = 1
+GRID_VELOCITY = 2
 NUM_KERNELS = 18
 
 # every entry point include/mrgb.h declares
@@ -29,7 +30,7 @@ EXPORTS = ["mr_last_error", "mr_workspace_size", "mr_grid_create", "mr_grid_dest
            "mr_ghost_fill", "mr_ghost_fill64", "mr_sync", "mr_rhs_advect", "mr_rk_stage",
            "mr_step", "mr_criterion", "mr_adapt", "mr_adapt_iter", "mr_mass", "mr_query",
            "mr_field_ptr", "mr_profile", "mr_profile_read", "mr_launch_count",
-           "mr_ghost_fill_static"]
+           "mr_ghost_fill_static", "mr_rhs_advect_vel", "mr_step_vel", "mr_velocity_invalidate"]
 
 
 class MRError(RuntimeError):
@@ -74,6 +75,9 @@ def load(path: str = LIB_PATH):
         L.mr_ghost_fill.argtypes = [vp, C.c_int, C.c_int, vp]
         L.mr_ghost_fill64.argtypes = [vp, C.c_int, C.c_int, vp]
         L.mr_ghost_fill_static.argtypes = [vp, C.c_int, C.c_int, vp]
+        L.mr_rhs_advect_vel.argtypes = [vp, C.c_int, ip, C.c_int, C.c_int]
+        L.mr_step_vel.argtypes = [vp, C.c_int, C.c_double, ip, C.c_int]
+        L.mr_velocity_invalidate.argtypes = [vp]
         L.mr_sync.argtypes = [vp]
         L.mr_rhs_advect.argtypes = [vp, C.c_int, dp, C.c_int, C.c_int]
         L.mr_rk_stage.argtypes = [vp, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int]
@@ -117,7 +121,8 @@ class Grid:
     """A periodic forest of octrees of nb^3 blocks on one GPU (mr_grid)."""
 
     def __init__(self, ntree, tree_len, nb, lmin, lmax, N, Nt, lev, anc, precision=F32,
-                 nfields=1, capacity=None, device="cuda", stream=None, fixed_tree=False):
+                 nfields=1, capacity=None, device="cuda", stream=None, fixed_tree=False,
+                 velocity=False):
         import torch
         L = load()
         lev = np.ascontiguousarray(lev, np.int32)
@@ -132,7 +137,7 @@ class Grid:
         d.tree_len, d.nb, d.lmin, d.lmax = float(tree_len), nb, lmin, lmax
         d.wav_N, d.wav_Nt, d.precision, d.nfields, d.capacity = N, Nt, precision, nfields, cap
         d.stream = s.cuda_stream
-        d.flags = 1 if fixed_tree else 0
+        d.flags = (GRID_FIXED_TREE if fixed_tree else 0) | (GRID_VELOCITY if velocity else 0)
         self.desc = d
         nbytes = C.c_size_t()
         _chk(L.mr_workspace_size(C.byref(d), C.byref(nbytes)))
@@ -229,6 +234,17 @@ class Grid:
 
     def rhs_advect(self, phi_fid, u, out_fid, scheme):
         _chk(load().mr_rhs_advect(self.h, phi_fid, _u3(u), out_fid, scheme))
+
+    def rhs_advect_vel(self, phi_fid, vel_fids, out_fid, scheme):
+        v = (C.c_int32 * 3)(*vel_fids)
+        _chk(load().mr_rhs_advect_vel(self.h, phi_fid, v, out_fid, scheme))
+
+    def step_vel(self, phi_fid, dt, vel_fids, scheme):
+        v = (C.c_int32 * 3)(*vel_fids)
+        _chk(load().mr_step_vel(self.h, phi_fid, float(dt), v, scheme))
+
+    def velocity_invalidate(self):
+        _chk(load().mr_velocity_invalidate(self.h))
 
     def rk_stage(self, stage, dt, u_fid, y_fid, rhs_fid, out_fid):
         _chk(load().mr_rk_stage(self.h, stage, float(dt), u_fid, y_fid, rhs_fid, out_fid))
