@@ -62,6 +62,7 @@ extern "C" {
 #define MR_INIT_GAUSSIAN 0    /* params: cx cy cz sigma amp; nearest image  */
 #define MR_INIT_TANH_SPHERE 1 /* params: cx cy cz radius width             */
 #define MR_INIT_TAYLOR_GREEN 2 /* params: component(0,1,2) scale phase    */
+#define MR_INIT_GAUSSIAN_SUM 3 /* params: n, then n x (cx cy cz sigma amp), n <= 12 */
 
 /* adaptation flags */
 #define MR_ADAPT_REFINE 1
@@ -188,7 +189,9 @@ int mr_rk_stage(mr_grid *grid, int stage, double dt, int u_fid, int y_fid, int r
 /* As mr_rhs_advect with a velocity field u = (field vel_fid[0], vel_fid[1],
  * vel_fid[2]) instead of a constant: interface velocity (u_i + u_{i+1})/2
  * selects the upwind side.  The grid needs MR_GRID_VELOCITY.  The velocity
- * components are ghost-filled (and substituted) once per tree: the cache is
+ * components are substituted and ghost-filled once per tree (the velocity
+ * does not change in time, and substitution is idempotent, so these equal
+ * the ghosts of a fill at every stage): the cache is
  * rebuilt after every adaptation that changes the leaves; a caller that
  * writes new velocity values must call mr_velocity_invalidate.            */
 int mr_rhs_advect_vel(mr_grid *grid, int phi_fid, const int *vel_fid, int out_fid, int scheme);

@@ -379,7 +379,8 @@ int mr_field_ptr(mr_grid *g, int fid, void **ptr) {
 }
 
 int mr_field_set(mr_grid *g, int fid, int kind, const double *params, int np) {
-  if (!fid_ok(g, fid) || !params || np < 1 || kind < 0 || kind > 2) return MR_ERR_INVALID;
+  if (!fid_ok(g, fid) || !params || np < 1 || np > 64 || kind < 0 || kind > 3) return MR_ERR_INVALID;
+  if (kind == MR_INIT_GAUSSIAN_SUM && (params[0] < 0 || 1 + 5 * (int)params[0] > np)) return MR_ERR_INVALID;
   return launch_field_set(g, field_ptr(g, fid), kind, params, np);
 }
 
@@ -451,7 +452,11 @@ static int velocity_cache(mr_grid *g, const int *vel) {
     int Gi;
     bool is64;
     void *f = field_ptr(g, vel[d]);
+    // the first fill substitutes the component in place; substitution is
+    // idempotent, so the second fill yields the ghosts every later stage
+    // would compute
     int e = launch_ghost(g, f, f, 3, false, &P, &Gi, &is64);
+    if (!e) e = launch_ghost(g, f, f, 3, false, &P, &Gi, &is64);
     // component d at offset d * nleaf blocks (the kernels' indexing)
     if (!e) e = launch_crop(g, P, Gi, (char *)g->vpad + (size_t)d * g->nleaf * blk, 3, is64);
     if (e) return e;

@@ -408,7 +408,7 @@ int launch_rk_combine(mr_grid *g, int stage, double dt, const void *u, const voi
 
 // ---------------------------------------------------------------- analytic
 struct InitParams {
-  double p[8];
+  double p[64];
 };
 
 __device__ __forceinline__ double pdelta(double x, double c, double ext) {
@@ -441,6 +441,17 @@ __global__ void k_field_set(Tree t, T *f, int kind, InitParams ip) {
         r2 += dd * dd;
       }
       v = 0.5 * (1.0 - tanh((sqrt(r2) - ip.p[3]) / ip.p[4]));
+    } else if (kind == MR_INIT_GAUSSIAN_SUM) {
+      const int ng = (int)ip.p[0];
+      for (int q = 0; q < ng; ++q) {
+        const double *c = ip.p + 1 + 5 * q;
+        double r2 = 0.0;
+        for (int d = 0; d < 3; ++d) {
+          const double dd = pdelta(x[d], c[d], ext[d]);
+          r2 += dd * dd;
+        }
+        v += c[4] * exp(-r2 / (c[3] * c[3]));
+      }
     } else if (kind == MR_INIT_TAYLOR_GREEN) {
       const double w = 2.0 * M_PI, s = ip.p[1], ph = ip.p[2];
       const int comp = (int)ip.p[0];
@@ -454,7 +465,7 @@ __global__ void k_field_set(Tree t, T *f, int kind, InitParams ip) {
 
 int launch_field_set(mr_grid *g, void *f, int kind, const double *p, int np) {
   InitParams ip{};
-  for (int i = 0; i < np && i < 8; ++i) ip.p[i] = p[i];
+  for (int i = 0; i < np && i < 64; ++i) ip.p[i] = p[i];
   Tree t = tree_view(g);
   if (g->desc.precision == MR_F32)
     MR_LAUNCH(g, MRK_FIELDSET, k_field_set<float><<<g->nleaf, 256, 0, g->stream>>>(t, (float *)f, kind, ip));

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libmrgb.so")
 MR_OK = 0
 F32, F64 = 0, 1
 CONS3, CONS5, WENOZ5 = 0, 1, 2
-INIT_GAUSSIAN, INIT_TANH_SPHERE, INIT_TAYLOR_GREEN = 0, 1, 2
+INIT_GAUSSIAN, INIT_TANH_SPHERE, INIT_TAYLOR_GREEN, INIT_GAUSSIAN_SUM = 0, 1, 2, 3
 ADAPT_REFINE, ADAPT_COARSEN = 1, 2
 GRID_FIXED_TREE = 1
 GRID_VELOCITY = 2

@@ -190,3 +190,57 @@ def test_invalid_trees_are_rejected(mr):
     lev2, anc2 = I.uniform_leaves(nt, 1)
     with pytest.raises(mr.MRError):  # a missing leaf leaves a hole
         mr.Grid(nt, 1.0, 16, 0, 3, 4, 0, lev2[1:], anc2[1:])
+
+
+def _tg(xyz, comp, s=1.0, ph=0.3):
+    """Taylor-Green-like divergence-free velocity component (comp 0, 1, 2)."""
+    w = 2 * np.pi
+    x, y, z = xyz
+    if comp == 0:
+        return s * np.sin(w * x + ph) * np.cos(w * y) * np.cos(w * z)
+    if comp == 1:
+        return -s * np.cos(w * x + ph) * np.sin(w * y) * np.cos(w * z)
+    return np.zeros_like(x)
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("scheme", [1, 2])
+def test_velocity_field_rhs_and_steps(mr, oracle_mod, prec, scheme):
+    """Advection by grid velocity fields (u, v, w ghost-filled like phi,
+    interface velocity (u_i + u_{i+1})/2 picks the upwind side): rhs and
+    three RK3 steps against the oracle, which ghost-fills the velocity every
+    stage (the device caches it per tree)."""
+    O = oracle_mod
+    nt, tl, nb = (2, 2, 2), 0.5, 16
+    lev, anc = I.tree_config1()
+    g = mr.Grid(nt, tl, nb, 0, 1, 6, 2, lev, anc, precision=prec, nfields=5, velocity=True)
+    glev, ganc, _ = g.leaves()
+    og = O.Grid(nt, tl, nb, 6, 2, 0, 1, glev, ganc)
+    xyz = I.point_coords(nt, tl, nb, glev, ganc)
+    phi = I.gaussian_images(xyz, (0.45, 0.5, 0.55), 0.1, nimg=1)
+    vel = [_tg(xyz, d) for d in range(3)]
+    cast = (lambda a: a.astype(np.float32)) if prec == 0 else (lambda a: a)
+    g.field_copy_in(0, cast(phi))
+    for d in range(3):
+        g.field_copy_in(1 + d, cast(vel[d]))
+    phi64 = cast(phi).astype(np.float64)
+    # the device substitutes the velocity once per tree (idempotent); start
+    # the oracle from the substituted velocity too
+    vel64 = [O.ghost_fill(og, cast(v).astype(np.float64), 3)[1] for v in vel]
+    # rhs
+    g.rhs_advect_vel(0, (1, 2, 3), 4, scheme)
+    got = g.field_copy_out(4).astype(np.float64)
+    pad, _ = O.ghost_fill(og, phi64, 3)
+    vp = [O.ghost_fill(og, v, 3)[0] for v in vel64]
+    ref = O.rhs(og, pad, 3, scheme, vel=vp)
+    tol = 1e-12 if prec == 1 else 2e-5
+    assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
+    # steps (fresh copies: the rhs call substituted phi in place on both sides)
+    g.field_copy_in(0, cast(phi))
+    ref, vref = phi64, vel64
+    dt = 0.5 * (0.5 / (nb * 2)) / 2.0
+    for _ in range(3):
+        g.step_vel(0, dt, (1, 2, 3), scheme)
+        ref, vref = O.rk3_step_vel(og, ref, vref, dt, scheme)
+    err = np.abs(g.field_copy_out(0).astype(np.float64) - ref).max() / np.abs(ref).max()
+    assert err <= (1e-12 if prec == 1 else 1e-5), err
