@@ -1,19 +1,25 @@
 """Benchmark: grid-point stage updates per second (PSU/s) of the multilevel
-stencil step (ghost reconstruction + advection RHS + RK3-TVD stage) and the
-HBM-roofline fraction of its dominant kernel, on one GB300.
+stencil step (ghost reconstruction + advection RHS + RK3-TVD stage, with grid
+adaptation) and the HBM-roofline fraction of its dominant kernel, on one GB300.
 
-Default workload ("large single grid"): one periodic tree, 24^3 blocks at
-levels 3-8 refined in nested balls around a seeded Gaussian blob (~40k
-leaves, ~0.55 G points), 6.2 lifted wavelet, FP32 storage and arithmetic,
-WENO-Z5 flux, RK3, constant velocity (1, 0.5, 0.25), fixed tree.  Inputs are
-larger than L2 (no flush needed).  One step = 3 stages over every point.
+Default workload ("large single grid"): one periodic tree of 24^3 blocks,
+levels 3-8; FP32 scalar (sum of 48 seeded sharp Gaussians) advected by three
+FP32 velocity fields (seeded divergence-free Taylor-Green-like field);
+6.2 lifted wavelet, eps_refine = 1e-5, eps_coarsen = 1e-7; WENO-Z5 + RK3,
+CFL 0.5; adaptation every 2 steps inside the timed region.  The initial grid
+is built by alternating analytic sampling and refinement from a uniform
+level-3 grid, then one full adaptation (all untimed).  Fields are far larger
+than L2 (no flush needed).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision f32|f64]
-                  [--scheme wenoz5|cons5|cons3] [--impl ours|reference]
+                  [--scheme wenoz5|cons5|cons3] [--workload large|fixed-*]
+                  [--impl ours|reference]
 
---impl reference times the FP64 CPU oracle (the plain reference
-implementation of the same path) on the host cores, on a bounded sample of
-the same workload, and prints the same metric.
+fixed-large / fixed-medium / fixed-small: the stencil step alone (no
+adaptation, constant velocity) on fixed nested-ball trees, used for kernel
+profiling.  --impl reference times the FP64 CPU oracle (the plain restatement
+of the same path) on the host cores on a bounded sample and prints the same
+metric.
 """
 from __future__ import annotations
 
@@ -35,14 +41,48 @@ from paper_2112_07537_gb300 import inputs as I  # noqa: E402
 METRIC = "point-stage updates/s (ghost fill + RHS + RK3 stage)"
 UNIT = "PSU/s"
 # nested refinement balls around the blob centre, level 3 -> 3 + len(radii)
-WORKLOADS = {"large": (0.35, 0.25, 0.17, 0.11, 0.06),   # 42 400 leaves, 586 M points
-             "medium": (0.35, 0.25, 0.17),              # 11 768 leaves, 163 M points
-             "small": (0.3, 0.2)}
+WORKLOADS = {"fixed-large": (0.35, 0.25, 0.17, 0.11, 0.06),   # 42 400 leaves, 586 M points
+             "fixed-medium": (0.35, 0.25, 0.17),              # 11 768 leaves, 163 M points
+             "fixed-small": (0.3, 0.2)}                       # 3 424 leaves, 47 M points
+GAUSS = dict(seed=5, n=48, smin=0.0015, smax=0.006)  # large single grid scalar
+EPS_R, EPS_C, CFL, ADAPT_EVERY = 1e-5, 1e-7, 0.5, 2
 U = (1.0, 0.5, 0.25)
 
 
-def workload_tree(name="large"):
+def workload_tree(name="fixed-large"):
     return I.tree_sphere((1, 1, 1), 1.0, 3, WORKLOADS[name], centre=(0.5, 0.5, 0.5))
+
+
+def gauss_params(seed, n, smin, smax):
+    """n seeded Gaussians: centres U[0.15, 0.85]^3, sigma U[smin, smax], amp 1."""
+    rng = np.random.default_rng(seed)
+    p = [n]
+    for _ in range(n):
+        c = rng.uniform(0.15, 0.85, 3)
+        p += [*c, rng.uniform(smin, smax), 1.0]
+    return p
+
+
+TG = (1.0, 0.3)  # Taylor-Green scale and phase (seeded constants of the velocity field)
+
+
+def init_large(mrgb, stream, prec, cap):
+    """Initial adapted grid (untimed): uniform level 3, then alternate analytic
+    sampling and refinement until no block refines, sample again, and run
+    one full adaptation."""
+    lev, anc = I.uniform_leaves((1, 1, 1), 3)
+    g = mrgb.Grid((1, 1, 1), 1.0, 24, 3, 8, 6, 2, lev, anc, precision=prec, nfields=4,
+                  capacity=cap, stream=stream, velocity=True)
+    p = gauss_params(**GAUSS)
+    for _ in range(12):
+        g.field_set(0, mrgb.INIT_GAUSSIAN_SUM, p)
+        if g.adapt_iter(0, EPS_R, EPS_C, flags=mrgb.ADAPT_REFINE) == 0:
+            break
+    g.field_set(0, mrgb.INIT_GAUSSIAN_SUM, p)
+    for d in range(3):
+        g.field_set(1 + d, mrgb.INIT_TAYLOR_GREEN, [d, TG[0], TG[1]])
+    g.adapt(0, EPS_R, EPS_C)
+    return g
 
 
 def clocks_sampler(stop, out):
@@ -82,26 +122,33 @@ def peaks():
 
 
 def cpu_baseline(budget_s=15.0):
-    """The FP64 oracle (single-threaded C) on a bounded sample of the workload:
-    the 2x2x2-tree two-level grid (15 leaves of 16^3) with the workload's
-    scheme, as many RK3 steps as fit the time budget."""
+    """The FP64 oracle (single-threaded C) on a bounded sample of the
+    workload: the two-level 15-leaf grid of 16^3 blocks (2x2x2 trees, one
+    refined), 6.2 ghosts, scalar + Taylor-Green-like velocity fields (all four
+    ghost-filled every stage), WENO-Z5 + RK3, as many steps as fit the
+    budget."""
     sys.path.insert(0, os.path.join(ROOT, "oracle"))
     import oracle as O
     nt, tl, nb = (2, 2, 2), 0.5, 16
     lev, anc = I.tree_config1()
     og = O.Grid(nt, tl, nb, 6, 2, 0, 1, lev, anc)
-    phi = I.gaussian(I.point_coords(nt, tl, nb, lev, anc), (0.5, 0.5, 0.5), 0.1)
-    dt = O.dt_cfl(og, 0.5, U)
+    xyz = I.point_coords(nt, tl, nb, lev, anc)
+    phi = I.gaussian(xyz, (0.5, 0.5, 0.5), 0.1)
+    w = 2 * np.pi
+    vel = [TG[0] * np.sin(w * xyz[0] + TG[1]) * np.cos(w * xyz[1]) * np.cos(w * xyz[2]),
+           -TG[0] * np.cos(w * xyz[0] + TG[1]) * np.sin(w * xyz[1]) * np.cos(w * xyz[2]),
+           np.zeros_like(xyz[0])]
+    dt = CFL * (tl / (nb * 2)) / (2 * TG[0])
     t0 = time.perf_counter()
     steps = 0
     while time.perf_counter() - t0 < budget_s or steps == 0:
-        phi = O.rk3_step(og, phi, dt, O.WENOZ5, U)
+        phi, vel = O.rk3_step_vel(og, phi, vel, dt, O.WENOZ5)
         steps += 1
     el = time.perf_counter() - t0
     pts = og.nleaf * nb ** 3
     return {"value": pts * 3 * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} RK3 steps (WENO-Z5, 6.2 ghosts) of the 15-leaf 16^3 two-level "
-                      f"grid, {pts} points, {el:.1f} s, single thread"}
+            "sample": f"{steps} RK3 steps (WENO-Z5, 6.2 ghosts, velocity fields) of the 15-leaf "
+                      f"16^3 two-level grid, {pts} points, {el:.1f} s, single thread"}
 
 
 def run_reference(args):
@@ -129,7 +176,8 @@ def main():
     ap.add_argument("--scheme", default="wenoz5", choices=["wenoz5", "cons5", "cons3"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="large", choices=["large"] + sorted(WORKLOADS))
+    ap.add_argument("--capacity", type=int, default=60000)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -149,21 +197,38 @@ def main():
     W = max(3, args.warmup)
     prec = mrgb.F32 if args.precision == "f32" else mrgb.F64
     scheme = {"wenoz5": mrgb.WENOZ5, "cons5": mrgb.CONS5, "cons3": mrgb.CONS3}[args.scheme]
-    lev, anc = workload_tree(args.workload)
-    radii = WORKLOADS[args.workload]
     nb = 24
+    adaptive = args.workload == "large"
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        g = mrgb.Grid((1, 1, 1), 1.0, nb, 3, int(lev.max()), 6, 2, lev, anc, precision=prec,
-                      nfields=1, stream=stream, fixed_tree=True)
-        g.field_set(0, mrgb.INIT_GAUSSIAN, [0.5, 0.5, 0.5, 0.08, 1.0])
-    n = g.nleaf
-    pts = n * nb ** 3
-    hmin = 1.0 / (nb * 2 ** int(lev.max()))
-    dt = 0.5 * hmin / sum(abs(u) for u in U)
+        if adaptive:
+            g = init_large(mrgb, stream, prec, args.capacity)
+            lmax = 8
+            umax = 2.0 * TG[0]  # |u| + |v| <= 2 s for the Taylor-Green-like field
+        else:
+            lev, anc = workload_tree(args.workload)
+            lmax = int(lev.max())
+            g = mrgb.Grid((1, 1, 1), 1.0, nb, 3, lmax, 6, 2, lev, anc, precision=prec,
+                          nfields=1, stream=stream, fixed_tree=True)
+            g.field_set(0, mrgb.INIT_GAUSSIAN, [0.5, 0.5, 0.5, 0.08, 1.0])
+            umax = sum(abs(u) for u in U)
+    dt = CFL * (1.0 / (nb * 2 ** lmax)) / umax
+    stats0 = g.query()
 
-    for _ in range(W):
-        g.step(0, dt, U, scheme)
+    def one_step(i):
+        """One RK3 step (+ adaptation every ADAPT_EVERY steps); returns the
+        point-stage updates it performed."""
+        pts = g.nleaf * nb ** 3
+        if adaptive:
+            g.step_vel(0, dt, (1, 2, 3), scheme)
+            if (i + 1) % ADAPT_EVERY == 0:
+                g.adapt(0, EPS_R, EPS_C)
+        else:
+            g.step(0, dt, U, scheme)
+        return 3 * pts
+
+    for i in range(W):
+        one_step(i)
     stream.synchronize()
 
     samples, stop = [], threading.Event()
@@ -175,9 +240,10 @@ def main():
     l0 = g.launch_count()
     g.profile(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    psu_count = 0
     e0.record(stream)
-    for _ in range(args.steps):
-        g.step(0, dt, U, scheme)
+    for i in range(args.steps):
+        psu_count += one_step(i)
     e1.record(stream)
     e1.synchronize()
     g.profile(False)
@@ -191,50 +257,73 @@ def main():
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
+    stats1 = g.query()
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers: each step copies
+    # the scalar in from pinned host memory and reads it back
     es = 4 if prec == mrgb.F32 else 8
-    host = torch.empty((n, nb, nb, nb), dtype=g.dtype, pin_memory=True)
-    g.field_copy_out(0, host.numpy())
-    ke = max(2, min(args.steps, 5))
+    host = torch.empty((args.capacity if adaptive else g.nleaf) * nb ** 3, dtype=g.dtype,
+                       pin_memory=True)
+    ke = max(2, min(args.steps, 4))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(ke):
-        g.field_copy_in(0, host.numpy())
-        g.step(0, dt, U, scheme)
-        g.field_copy_out(0, host.numpy())
+    e2e_psu, h2d, d2h = 0, 0, 0
+    for i in range(ke):
+        n = g.nleaf * nb ** 3
+        g.field_copy_out(0, host[:n].numpy())  # establishes the host copy
+        g.field_copy_in(0, host[:n].numpy())
+        h2d += n * es
+        e2e_psu += one_step(i)
+        n = g.nleaf * nb ** 3
+        g.field_copy_out(0, host[:n].numpy())
+        d2h += n * es
     e2e_s = time.perf_counter() - t0
 
-    psu = world * pts * 3 * args.steps / (ms / 1e3)
+    psu = world * psu_count / (ms / 1e3)
     hbm, src = peaks()
-    # dominant kernel of the step
     name, (tot, cnt) = max(prof.items(), key=lambda kv: kv[1][0])
-    bpp = {"f32": 4, "f64": 8}[args.precision]
-    alg_bytes = {"rhs_stage": pts * bpp * 32.0 / 3 / 4,  # 8 B stage 1, 12 B stages 2-3 (FP32)
-                 "ghost_part1": pts * bpp * 2.0, "ghost_part2": 0.0, "ghost_merge": 0.0}
-    per_launch = alg_bytes.get(name, pts * bpp * 2.0)
-    achieved = per_launch / (tot / cnt / 1e3) / 1e9
+    bpp = 4 if prec == mrgb.F32 else 8
+    mean_pts = psu_count / (3 * args.steps)
+    # algorithmic bytes per point-stage of the fused stage: phi read, RK
+    # output written, u^n read in stages 1-2 (2/3 on average), plus the three
+    # velocity components when the velocity is a field
+    per_pt = bpp * (1 + 1 + 2.0 / 3 + (3 if adaptive else 0))
+    alg = {"rhs_stage": mean_pts * per_pt}
+    per_launch = alg.get(name, None)
+    achieved = per_launch / (tot / cnt / 1e3) / 1e9 if per_launch else None
+    workload = ("large single grid, adaptive: 1 tree, 24^3 blocks, levels 3-8, "
+                f"{stats0.nleaf}->{stats1.nleaf} leaves; FP32 scalar (48 seeded Gaussians, sigma "
+                f"{GAUSS['smin']}-{GAUSS['smax']}) + 3 velocity fields (Taylor-Green-like, scale "
+                f"{TG[0]}, phase {TG[1]}); 6.2 lifted wavelet, eps_r {EPS_R}, eps_c {EPS_C}; "
+                f"{args.scheme} + RK3, CFL {CFL}; adapt every {ADAPT_EVERY} steps"
+                if adaptive else
+                f"{args.workload} single grid, fixed tree, stencil step only: 1 tree, 24^3 blocks, "
+                f"levels 3-{lmax} (nested balls r={WORKLOADS[args.workload]}), {g.nleaf} leaves; "
+                f"6.2 lifted wavelet ghosts; {args.scheme} + RK3; u={U}; CFL {CFL}")
+    shares = {k: v[0] / sum(x[0] for x in prof.values()) for k, v in prof.items()}
     line = {
         "metric": METRIC, "value": psu, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": W, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-        "config": {"workload": f"{args.workload} single grid, fixed tree: 1 tree, 24^3 blocks, "
-                               f"levels 3-{int(lev.max())} (nested balls r={radii}), {n} leaves, "
-                               f"{pts} points; 6.2 lifted "
-                               f"wavelet ghosts; {args.scheme} + RK3; u={U}; CFL 0.5",
-                   "leaves": n, "points": pts, "l2": "inputs larger than L2 (no flush)",
+        "config": {"workload": workload, "leaves": [stats0.nleaf, stats1.nleaf],
+                   "mean_points": mean_pts, "l2": "fields larger than L2 (no flush)",
                    "scheme": args.scheme, "precision": args.precision},
-        "roofline": {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm,
-                     "unit": "GB/s", "frac": achieved / hbm, "peak_source": src,
-                     "traffic": None,
-                     "alg_bytes_per_launch": per_launch},
-        "kernels": {k: {"ms_total": v[0], "launches": v[1], "share": v[0] / sum(x[0] for x in prof.values())}
-                    for k, v in prof.items()},
+        "roofline": {"bound": "hbm", "kernel": name if per_launch else "rhs_stage",
+                     "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm if achieved else None, "peak_source": src,
+                     "traffic": None, "alg_bytes_per_launch": per_launch,
+                     "alg_bytes_per_point_stage": per_pt},
+        "kernels": {k: {"ms_total": v[0], "launches": v[1], "share": shares[k]} for k, v in prof.items()},
         "gpu_launches": launches,
-        "e2e": {"value": pts * 3 * ke / e2e_s, "unit": UNIT,
-                "h2d_bytes_per_step": pts * es, "d2h_bytes_per_step": pts * es},
+        "e2e": {"value": e2e_psu / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d // ke,
+                "d2h_bytes_per_step": d2h // ke},
         "clocks": summarize_clocks(samples),
     }
+    if "rhs_stage" in prof:
+        t_rhs, n_rhs = prof["rhs_stage"]
+        a_rhs = mean_pts * per_pt / (t_rhs / n_rhs / 1e3) / 1e9
+        line["roofline_stage_kernel"] = {"kernel": "rhs_stage", "achieved": a_rhs, "peak": hbm,
+                                         "unit": "GB/s", "frac": a_rhs / hbm}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:

@@ -62,7 +62,7 @@ extern "C" {
 #define MR_INIT_GAUSSIAN 0    /* params: cx cy cz sigma amp; nearest image  */
 #define MR_INIT_TANH_SPHERE 1 /* params: cx cy cz radius width             */
 #define MR_INIT_TAYLOR_GREEN 2 /* params: component(0,1,2) scale phase    */
-#define MR_INIT_GAUSSIAN_SUM 3 /* params: n, then n x (cx cy cz sigma amp), n <= 12 */
+#define MR_INIT_GAUSSIAN_SUM 3 /* params: n, then n x (cx cy cz sigma amp), n <= 51 */
 
 /* adaptation flags */
 #define MR_ADAPT_REFINE 1

@@ -1168,3 +1168,24 @@ int og_rk3_step_vel(const og_grid *g, double *phi, double *vx, double *vy, doubl
   for (int d = 0; d < 3; ++d) free(vp[d]);
   return e;
 }
+
+/* One RK3 step with the velocity's padded blocks held fixed (vx/vy/vz are
+ * padded arrays with shell 3, computed once for the tree): the per-tree
+ * velocity ghosts the GPU path uses.  phi is updated in place.             */
+int og_rk3_step_velpad(const og_grid *g, double *phi, const double *vpx, const double *vpy,
+                       const double *vpz, double dt, int scheme) {
+  const int nb = g->nb, G = 3, W = nb + 2 * G;
+  const size_t nb3 = (size_t)nb * nb * nb, n = nb3 * g->nleaf, np = (size_t)W * W * W * g->nleaf;
+  double *pad = (double *)malloc(sizeof(double) * np);
+  double *y = (double *)malloc(sizeof(double) * n);
+  double *r = (double *)malloc(sizeof(double) * n);
+  int e = (!pad || !y || !r) ? OG_ERR_NOMEM : OG_OK;
+  for (int s = 0; s < 3 && !e; ++s) {
+    double *src = (s == 0) ? phi : y;
+    e = og_ghost_fill(g, src, G, pad, src);
+    if (!e) e = og_rhs(g, pad, G, scheme, NULL, vpx, vpy, vpz, r);
+    if (!e) og_rk_combine(s, n, dt, phi, src, r, s == 2 ? phi : y);
+  }
+  free(pad), free(y), free(r);
+  return e;
+}

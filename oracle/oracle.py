@@ -82,6 +82,7 @@ def _declare(L):
     L.og_synth_1d.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _dp, _dp]
     L.og_status.argtypes = [C.c_double, C.c_double, C.c_double]
     L.og_rk3_step_vel.argtypes = [C.POINTER(_Grid), _dp, _dp, _dp, _dp, C.c_double, C.c_int]
+    L.og_rk3_step_velpad.argtypes = [C.POINTER(_Grid), _dp, _dp, _dp, _dp, C.c_double, C.c_int]
     L.og_morton_key.argtypes = [C.c_int] * 5
     L.og_morton_key.restype = C.c_uint64
 
@@ -168,6 +169,15 @@ def rk3_step_vel(g: Grid, phi: np.ndarray, vel, dt: float, scheme: int):
            "rk3_step_vel")
     shp = (g.nleaf, g.nb, g.nb, g.nb)
     return phi.reshape(shp), [v.reshape(shp) for v in vs]
+
+
+def rk3_step_velpad(g: Grid, phi: np.ndarray, vpads, dt: float, scheme: int):
+    """RK3 step with the velocity's padded blocks (shell 3) held fixed."""
+    phi = np.ascontiguousarray(phi, dtype=np.float64).copy()
+    vp = [np.ascontiguousarray(v, dtype=np.float64) for v in vpads]
+    _check(lib().og_rk3_step_velpad(g.c(), _d(phi), _d(vp[0]), _d(vp[1]), _d(vp[2]), dt, scheme),
+           "rk3_step_velpad")
+    return phi.reshape(g.nleaf, g.nb, g.nb, g.nb)
 
 
 def dt_cfl(g: Grid, cfl: float, u) -> float:

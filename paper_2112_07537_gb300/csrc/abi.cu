@@ -379,7 +379,7 @@ int mr_field_ptr(mr_grid *g, int fid, void **ptr) {
 }
 
 int mr_field_set(mr_grid *g, int fid, int kind, const double *params, int np) {
-  if (!fid_ok(g, fid) || !params || np < 1 || np > 64 || kind < 0 || kind > 3) return MR_ERR_INVALID;
+  if (!fid_ok(g, fid) || !params || np < 1 || np > 256 || kind < 0 || kind > 3) return MR_ERR_INVALID;
   if (kind == MR_INIT_GAUSSIAN_SUM && (params[0] < 0 || 1 + 5 * (int)params[0] > np)) return MR_ERR_INVALID;
   return launch_field_set(g, field_ptr(g, fid), kind, params, np);
 }

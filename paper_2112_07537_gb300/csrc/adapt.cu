@@ -481,6 +481,64 @@ __global__ void __launch_bounds__(256) k_update_apply(Tree tn, const int *__rest
   }
 }
 
+// ------------------------------------------------- fields needing ghosts
+// Leaves touching b across a face, edge or corner (one probe per adjacent
+// level-(L+1) cell; finer neighbours are at most one level finer).
+template <typename F>
+__device__ __forceinline__ void for_each_nbr(const Tree &t, int b, F f) {
+  const int L = __ldg(t.lev + b), nb = t.nb;
+  const bool fin = L < t.M;
+  const int Ls = fin ? L + 1 : L, span = fin ? 2 * nb : nb;
+  int base[3];
+  for (int d = 0; d < 3; ++d) base[d] = __ldg(t.anc + 3 * b + d) * span;
+  for (int m = 0; m < 27; ++m) {
+    if (m == 13) continue;
+    const int dd[3] = {m % 3 - 1, (m / 3) % 3 - 1, m / 9 - 1};
+    const int c0 = dd[0] ? 1 : 2, c1 = dd[1] ? 1 : 2, c2 = dd[2] ? 1 : 2;
+    for (int cz = 0; cz < c2; ++cz)
+      for (int cy = 0; cy < c1; ++cy)
+        for (int cx = 0; cx < c0; ++cx) {
+          const int cc[3] = {cx, cy, cz};
+          int g[3];
+          for (int d = 0; d < 3; ++d)
+            g[d] = dd[d] < 0 ? base[d] - 1 : dd[d] > 0 ? base[d] + span : base[d] + cc[d] * (span / 2);
+          const int o = owner(t, Ls, g[0], g[1], g[2]);
+          if (o != b) f(o);
+        }
+  }
+}
+
+// ring 1: a neighbour changes level
+__global__ void k_need1(Tree t, const int8_t *st, int *nb1) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= t.nleaf) return;
+  int any = 0;
+  for_each_nbr(t, b, [&](int o) { any |= st[o] != ST_SAME; });
+  nb1[b] = any;
+}
+
+// ring 2: the leaf changes, or a neighbour does, or a neighbour's neighbour
+// (whose new substitution band can lie within this leaf's update reach)
+__global__ void k_need2(Tree t, const int8_t *st, const int *nb1, int *need) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= t.nleaf) return;
+  int any = st[b] != ST_SAME || nb1[b];
+  if (!any) for_each_nbr(t, b, [&](int o) { any |= nb1[o]; });
+  need[b] = any;
+}
+
+// finer neighbours of needed leaves push the fine-to-coarse ghost values the
+// needed leaves read; leaves next to a coarser leaf substitute their band
+// (the adaptation's ghost fill overwrites every field)
+__global__ void k_need3(Tree t, const int *need, int *need2) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= t.nleaf) return;
+  const int L = __ldg(t.lev + b);
+  int any = need[b];
+  if (!any) for_each_nbr(t, b, [&](int o) { any |= (__ldg(t.lev + o) < L); });
+  need2[b] = any;
+}
+
 // ------------------------------------------------------------- driver
 static Tree next_view(const mr_grid *g, int nleaf) {
   Tree t = tree_view(g);
@@ -588,13 +646,19 @@ int adapt_iteration(mr_grid *g, int crit, double er, double ec, int flags, int *
   }
   int *nmask = g->cmask + g->desc.capacity;  // second half of the mask buffer
   int *hasD = g->hasD;
+  // leaves whose ghosts the other fields need (statuses are final; maxdet and
+  // scan are free from here on)
+  int *nb1 = reinterpret_cast<int *>(g->maxdet), *need2 = nb1 + g->desc.capacity, *need = g->scan;
+  MR_LAUNCH(g, MRK_MISC, k_need1<<<nblk, tb, 0, st>>>(t, g->status, nb1));
+  MR_LAUNCH(g, MRK_MISC, k_need2<<<nblk, tb, 0, st>>>(t, g->status, nb1, need));
+  MR_LAUNCH(g, MRK_MISC, k_need3<<<nblk, tb, 0, st>>>(t, need, need2));
   MR_LAUNCH(g, MRK_UPDATE, k_newmask<<<(nn + tb - 1) / tb, tb, 0, st>>>(tn, g->newsrc, nmask));
   // 6-9: every field: ghosts (criterion field first: P is current), interpolate, update
   const bool f32 = g->desc.precision == MR_F32;
   for (int pass = 0; pass < g->desc.nfields; ++pass) {
     const int fid = pass == 0 ? crit : (pass <= crit ? pass - 1 : pass);
     if (pass > 0) {
-      e = launch_ghost(g, field_ptr(g, fid), field_ptr(g, fid), G, true, &Pv, &Gi);
+      e = launch_ghost(g, field_ptr(g, fid), field_ptr(g, fid), G, true, &Pv, &Gi, nullptr, need2);
       if (e) return e;
       P = (const double *)Pv;
     }

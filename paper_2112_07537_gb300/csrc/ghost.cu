@@ -92,9 +92,11 @@ __device__ __forceinline__ int region_of(int i, int j, int k, int nb) {
 template <typename TI, typename TP, int N, int NT>
 __global__ void __launch_bounds__(512, 1) k_prep(Tree t, const TI *__restrict__ phi, TP *__restrict__ P,
                                                  TP *__restrict__ Q, int Gi, int Gpush, int only_coarse,
-                                                 int use_tile, int *cmask_out, int *err) {
+                                                 int use_tile, int *cmask_out, int *err,
+                                                 const int *__restrict__ need) {
   using W = Wav<N, NT>;
   const int b = blockIdx.x;
+  if (need && !need[b]) return;
   const int nb = t.nb, Wd = nb + 2 * Gi;
   const size_t np = (size_t)Wd * Wd * Wd, nb3 = (size_t)nb * nb * nb;
   const int L = __ldg(t.lev + b);
@@ -261,24 +263,41 @@ __global__ void __launch_bounds__(512, 1) k_prep(Tree t, const TI *__restrict__ 
   }
 }
 
-// Merge the part-2 values into P and write the substituted interior back to
-// the field of leaves that have a coarser neighbour.
+// Merge the part-2 values into P (only the neighbour regions owned by finer
+// leaves hold them) and write the substituted interior back to the field of
+// leaves that have a coarser neighbour.
 template <typename TO, typename TP>
 __global__ void __launch_bounds__(256) k_merge(Tree t, TP *__restrict__ P, const TP *__restrict__ Q,
                                                int Gi, int G, const int *__restrict__ cmask,
-                                               TO *__restrict__ phi_out) {
+                                               TO *__restrict__ phi_out, const int *__restrict__ need) {
   const int b = blockIdx.x;
-  const int nb = t.nb, Wd = nb + 2 * Gi, Wg = nb + 2 * G;
+  if (need && !need[b]) return;
+  const int nb = t.nb, Wd = nb + 2 * Gi;
   const size_t np = (size_t)Wd * Wd * Wd;
   const int L = __ldg(t.lev + b);
-  const int a[3] = {__ldg(t.anc + 3 * b) * nb, __ldg(t.anc + 3 * b + 1) * nb, __ldg(t.anc + 3 * b + 2) * nb};
-  for (int p = threadIdx.x; p < Wg * Wg * Wg; p += blockDim.x) {
-    const int i = p % Wg - G, j = (p / Wg) % Wg - G, k = p / (Wg * Wg) - G;
-    if (i >= 0 && i < nb && j >= 0 && j < nb && k >= 0 && k < nb) continue;
-    const int F = owner(t, L, a[0] + i, a[1] + j, a[2] + k);
-    if (__ldg(t.lev + F) != L + 1) continue;
-    const size_t q = (size_t)b * np + (i + Gi) + Wd * ((j + Gi) + (size_t)Wd * (k + Gi));
-    P[q] = Q[q];
+  __shared__ int rfin[27];
+  if (threadIdx.x < 27) {
+    const int r = threadIdx.x;
+    const int dd[3] = {r % 3 - 1, (r / 3) % 3 - 1, r / 9 - 1};
+    int g[3];
+    for (int d = 0; d < 3; ++d) g[d] = __ldg(t.anc + 3 * b + d) * nb + (dd[d] < 0 ? -1 : dd[d] > 0 ? nb : 0);
+    rfin[r] = r != 13 && __ldg(t.lev + owner(t, L, g[0], g[1], g[2])) > L;
+  }
+  __syncthreads();
+  for (int r = 0; r < 27; ++r) {
+    if (!rfin[r]) continue;
+    const int dd[3] = {r % 3 - 1, (r / 3) % 3 - 1, r / 9 - 1};
+    int lo[3], ext[3];
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = dd[d] < 0 ? -G : dd[d] > 0 ? nb : 0;
+      ext[d] = dd[d] ? G : nb;
+    }
+    const int cnt = ext[0] * ext[1] * ext[2];
+    for (int p = threadIdx.x; p < cnt; p += blockDim.x) {
+      const int i = lo[0] + p % ext[0], j = lo[1] + (p / ext[0]) % ext[1], k = lo[2] + p / (ext[0] * ext[1]);
+      const size_t q = (size_t)b * np + (i + Gi) + Wd * ((j + Gi) + (size_t)Wd * (k + Gi));
+      P[q] = Q[q];
+    }
   }
   if (phi_out && cmask[b]) {
     for (int p = threadIdx.x; p < nb * nb * nb; p += blockDim.x) {
@@ -314,7 +333,8 @@ static int internal_shell(int N, int Nt, int G, int nb) {
 }
 
 template <typename TI, typename TP, int N, int NT>
-static int ghost_impl(mr_grid *g, const TI *phi_in, TI *phi_out, int G, TP *P, TP *Q, int Gi, int only_coarse) {
+static int ghost_impl(mr_grid *g, const TI *phi_in, TI *phi_out, int G, TP *P, TP *Q, int Gi, int only_coarse,
+                      const int *need) {
   Tree t = tree_view(g);
   const int n = g->nleaf, nb = g->desc.nb;
   int *err = g->counter + 1;
@@ -327,20 +347,20 @@ static int ghost_impl(mr_grid *g, const TI *phi_in, TI *phi_out, int G, TP *P, T
                  "k_prep smem"))
     return MR_ERR_CUDA;
   MR_LAUNCH(g, MRK_PART1, k_prep<TI, TP, N, NT><<<n, 512, sm, g->stream>>>(t, phi_in, P, Q, Gi, G, only_coarse,
-                                                                           use_tile, g->cmask, err));
+                                                                           use_tile, g->cmask, err, need));
   if (check_cuda(cudaGetLastError(), "k_prep")) return MR_ERR_CUDA;
   if (only_coarse) return MR_OK;
-  MR_LAUNCH(g, MRK_MERGE, k_merge<TI, TP><<<n, 256, 0, g->stream>>>(t, P, Q, Gi, G, g->cmask, phi_out));
+  MR_LAUNCH(g, MRK_MERGE, k_merge<TI, TP><<<n, 256, 0, g->stream>>>(t, P, Q, Gi, G, g->cmask, phi_out, need));
   if (check_cuda(cudaGetLastError(), "k_merge")) return MR_ERR_CUDA;
   return MR_OK;
 }
 
 template <typename TI, typename TP>
 static int ghost_dispatch(mr_grid *g, const TI *phi_in, TI *phi_out, int G, TP *P, TP *Q, int Gi,
-                          int only_coarse = 0) {
+                          int only_coarse = 0, const int *need = nullptr) {
   const int N = g->desc.wav_N, Nt = g->desc.wav_Nt;
 #define MR_GCASE(n_, nt_) \
-  if (N == n_ && Nt == nt_) return ghost_impl<TI, TP, n_, nt_>(g, phi_in, phi_out, G, P, Q, Gi, only_coarse);
+  if (N == n_ && Nt == nt_) return ghost_impl<TI, TP, n_, nt_>(g, phi_in, phi_out, G, P, Q, Gi, only_coarse, need);
   MR_GCASE(2, 0) MR_GCASE(2, 2) MR_GCASE(4, 0) MR_GCASE(4, 2) MR_GCASE(6, 0) MR_GCASE(6, 2)
 #undef MR_GCASE
   return MR_ERR_UNSUPPORTED;
@@ -350,7 +370,7 @@ static int ghost_dispatch(mr_grid *g, const TI *phi_in, TI *phi_out, int G, TP *
 // (the adaptation path), else in the field's element type.  On return *P is
 // the padded buffer (internal shell *Gi).
 int launch_ghost(mr_grid *g, const void *phi_in, void *phi_out, int G, bool fp64, void **P, int *Gi,
-                 bool *p_is64) {
+                 bool *p_is64, const int *need) {
   const int nb = g->desc.nb;
   if (G < 1 || G > MR_MAX_SHELL) return MR_ERR_INVALID;
   if (G > nb / 2) return MR_ERR_BALANCE;
@@ -365,16 +385,16 @@ int launch_ghost(mr_grid *g, const void *phi_in, void *phi_out, int G, bool fp64
     *P = g->padP64;
     if (f32)
       return ghost_dispatch<float, double>(g, (const float *)phi_in, (float *)phi_out, G, g->padP64,
-                                           g->padQ64, gi);
+                                           g->padQ64, gi, 0, need);
     return ghost_dispatch<double, double>(g, (const double *)phi_in, (double *)phi_out, G, g->padP64,
-                                          g->padQ64, gi);
+                                          g->padQ64, gi, 0, need);
   }
   *P = g->padP;
   if (f32)
     return ghost_dispatch<float, float>(g, (const float *)phi_in, (float *)phi_out, G,
-                                        (float *)g->padP, (float *)g->padQ, gi);
+                                        (float *)g->padP, (float *)g->padQ, gi, 0, need);
   return ghost_dispatch<double, double>(g, (const double *)phi_in, (double *)phi_out, G,
-                                        (double *)g->padP, (double *)g->padQ, gi);
+                                        (double *)g->padP, (double *)g->padQ, gi, 0, need);
 }
 
 // substituted band of leaves with a coarser neighbour -> field

@@ -318,7 +318,7 @@ void *next_field_ptr(mr_grid *g, int fid);
 
 // ghost.cu
 int launch_ghost(mr_grid *g, const void *phi_in, void *phi_out, int G, bool fp64, void **P,
-                 int *Gi, bool *p_is64 = nullptr);
+                 int *Gi, bool *p_is64 = nullptr, const int *need = nullptr);
 int launch_crop(mr_grid *g, const void *P, int Gi, void *out, int G, bool fp64_src);
 int launch_crop64(mr_grid *g, const double *P, int Gi, double *out, int G);
 int launch_prep32(mr_grid *g, const void *phi, int *Gi);

@@ -408,7 +408,7 @@ int launch_rk_combine(mr_grid *g, int stage, double dt, const void *u, const voi
 
 // ---------------------------------------------------------------- analytic
 struct InitParams {
-  double p[64];
+  double p[256];
 };
 
 __device__ __forceinline__ double pdelta(double x, double c, double ext) {
@@ -465,7 +465,7 @@ __global__ void k_field_set(Tree t, T *f, int kind, InitParams ip) {
 
 int launch_field_set(mr_grid *g, void *f, int kind, const double *p, int np) {
   InitParams ip{};
-  for (int i = 0; i < np && i < 64; ++i) ip.p[i] = p[i];
+  for (int i = 0; i < np && i < 256; ++i) ip.p[i] = p[i];
   Tree t = tree_view(g);
   if (g->desc.precision == MR_F32)
     MR_LAUNCH(g, MRK_FIELDSET, k_field_set<float><<<g->nleaf, 256, 0, g->stream>>>(t, (float *)f, kind, ip));
