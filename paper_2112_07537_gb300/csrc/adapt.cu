@@ -13,41 +13,35 @@ enum { KIND_COPY = 0, KIND_CHILD = 1, KIND_PARENT = 2 };
 enum { ST_COARSER = -1, ST_SAME = 0, ST_FINER = 1 };
 
 // ------------------------------------------------------------- criterion
-// Per leaf: max |gamma| over [-ext_f, nb-1+ext_b]^3 (points with an odd
-// coordinate), gamma = 1D filters applied x, then y, then z (G^a on odd, H^a
-// on even coordinates).  The z-planes of the y-pass results live in a ring of
-// 2*hmax+1 shared-memory planes, so each pass is computed once.
-template <int N, int NT>
-__global__ void __launch_bounds__(256) k_criterion(Tree t, const double *__restrict__ P, int Gi,
-                                                   double *__restrict__ maxdet) {
+// Details gamma over the extended region [-ext_f, nb-1+ext_b]^3 of one padded
+// block (1D filters x, then y, then z: G^a on odd, H^a on even coordinates;
+// points with only even coordinates carry no detail and get 0).  The z-planes
+// of the y-pass results live in a ring of 2*hmax+1 shared-memory planes, so
+// each pass is computed once.  emit(i, j, k, idx, gamma) is called once per
+// point of the region, plane by plane (idx = i-r0 + nR*(j-r0)).
+template <int N, int NT, typename F>
+__device__ __forceinline__ void detail_planes(const double *__restrict__ Pb, int nb, int Gi, double *sm,
+                                              F emit) {
   using W = Wav<N, NT>;
-  constexpr int hm = W::hmax;
-  const int b = blockIdx.x, nb = t.nb, Wd = nb + 2 * Gi;
+  constexpr int hm = W::hmax, R = 2 * hm + 1;
+  const int Wd = nb + 2 * Gi;
   const int r0 = -W::ext_f, r1 = nb - 1 + W::ext_b, nR = r1 - r0 + 1, nA = nR + 2 * hm;
   const int lo = -Gi, hi = nb - 1 + Gi;  // stored padded range
-  extern __shared__ double sm[];
   double *ring = sm;
-  double *A = sm + (size_t)(2 * hm + 1) * nR * nR;
-  const double *Pb = P + (size_t)b * Wd * Wd * Wd;
+  double *A = sm + (size_t)R * nR * nR;
   auto pidx = [&](int i, int j, int k) {
     return (size_t)(i + Gi) + Wd * ((size_t)(j + Gi) + (size_t)Wd * (k + Gi));
   };
-  double mx = 0.0;
   for (int kk = r0 - hm; kk <= r1 + hm; ++kk) {
-    const int slot = (kk - (r0 - hm)) % (2 * hm + 1);
+    const int slot = (kk - (r0 - hm)) % R;
     const bool kin = kk >= lo && kk <= hi;
     // x pass into A (rows j = r0-hm .. r1+hm)
     for (int idx = threadIdx.x; idx < nR * nA; idx += blockDim.x) {
       const int i = r0 + idx % nR, jj = r0 - hm + idx / nR;
       double s = 0.0;
       if (kin && jj >= lo && jj <= hi) {
-        const bool od = i & 1;
-        const int hw = od ? W::hwG : W::hwH;
-        for (int tx = -hw; tx <= hw; ++tx) {
-          const double w = od ? W::G(tx) : W::H(tx);
-          if (w == 0.0) continue;
-          s = radd(s, rmul(w, Pb[pidx(i + tx, jj, kk)]));
-        }
+        const double *p = Pb + pidx(i, jj, kk);
+        s = (i & 1) ? tap_sum<N, NT, FK_G>(p, 1) : tap_sum<N, NT, FK_H>(p, 1);
       }
       A[idx] = s;
     }
@@ -55,37 +49,47 @@ __global__ void __launch_bounds__(256) k_criterion(Tree t, const double *__restr
     // y pass into ring plane kk
     for (int idx = threadIdx.x; idx < nR * nR; idx += blockDim.x) {
       const int ii = idx % nR, j = r0 + idx / nR;
-      const bool od = j & 1;
-      const int hw = od ? W::hwG : W::hwH;
-      double s = 0.0;
-      for (int ty = -hw; ty <= hw; ++ty) {
-        const double w = od ? W::G(ty) : W::H(ty);
-        if (w == 0.0) continue;
-        s = radd(s, rmul(w, A[ii + nR * (j + ty - (r0 - hm))]));
-      }
-      ring[(size_t)slot * nR * nR + idx] = s;
+      const double *p = A + ii + nR * (j - (r0 - hm));
+      ring[(size_t)slot * nR * nR + idx] = (j & 1) ? tap_sum<N, NT, FK_G>(p, nR) : tap_sum<N, NT, FK_H>(p, nR);
     }
     __syncthreads();
-    // z pass for output plane k = kk - hm
+    // z pass for output plane k = kk - hm (ring slot of k: kk's slot - hm mod R)
     const int k = kk - hm;
     if (k >= r0) {
-      const bool odk = k & 1;
-      const int hw = odk ? W::hwG : W::hwH;
+      const int sk = (slot + hm + 1) % R;
       for (int idx = threadIdx.x; idx < nR * nR; idx += blockDim.x) {
         const int i = r0 + idx % nR, j = r0 + idx / nR;
-        if (!((i | j | k) & 1)) continue;
         double s = 0.0;
-        for (int tz = -hw; tz <= hw; ++tz) {
-          const double w = odk ? W::G(tz) : W::H(tz);
-          if (w == 0.0) continue;
-          const int sl = (k + tz - (r0 - hm)) % (2 * hm + 1);
-          s = radd(s, rmul(w, ring[(size_t)sl * nR * nR + idx]));
+        if ((i | j | k) & 1) {
+          const double *rp = ring + idx;
+          auto at = [&](int t) {
+            int sl = sk + t;
+            sl += sl < 0 ? R : 0;
+            sl -= sl >= R ? R : 0;
+            return rp[(size_t)sl * nR * nR];
+          };
+          if (k & 1)
+            for_taps<N, NT, FK_G>([&](int t, double w) { s = racc(s, w, at(t)); });
+          else
+            for_taps<N, NT, FK_H>([&](int t, double w) { s = racc(s, w, at(t)); });
         }
-        mx = fmax(mx, fabs(s));
+        emit(i, j, k, idx, s);
       }
     }
     __syncthreads();
   }
+}
+
+// Per leaf: max |gamma| over the extended region (Sec. 2.3, the block norm
+// that drives refinement and coarsening).
+template <int N, int NT>
+__global__ void __launch_bounds__(256) k_criterion(Tree t, const double *__restrict__ P, int Gi,
+                                                   double *__restrict__ maxdet) {
+  const int b = blockIdx.x, nb = t.nb, Wd = nb + 2 * Gi;
+  extern __shared__ double sm[];
+  double mx = 0.0;
+  detail_planes<N, NT>(P + (size_t)b * Wd * Wd * Wd, nb, Gi, sm,
+                       [&](int, int, int, int, double g) { mx = fmax(mx, fabs(g)); });
   // block max
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   __shared__ double red[32];
@@ -364,8 +368,11 @@ __global__ void k_newmask(Tree tn, const int *src, int *nmask) {
 
 // gamma over the extended region of every unchanged leaf F for the details
 // the coarsening discarded (in newly coarsened leaves, or in the new bands of
-// F or of its unchanged same-level neighbours), 0 elsewhere.  Q is indexed by
-// F's old slot in the padded layout.
+// F or of its unchanged same-level neighbours), 0 elsewhere in the region.  Q
+// is indexed by F's old slot in the padded layout.  The 27 block-sized regions
+// around F are classified once: a newly coarsened leaf one level coarser owns
+// all of D in its region, an unchanged same-level leaf with newly coarsened
+// neighbours owns the part of its band next to them, finer leaves none.
 template <int N, int NT>
 __global__ void __launch_bounds__(256) k_update_gamma(Tree tn, const int *__restrict__ src,
                                                       const int *__restrict__ nmask,
@@ -375,110 +382,127 @@ __global__ void __launch_bounds__(256) k_update_gamma(Tree tn, const int *__rest
   const int q = blockIdx.x;
   if (src[2 * q] != KIND_COPY) return;
   const int s = src[2 * q + 1], L = __ldg(tn.lev + q), nb = tn.nb, Wd = nb + 2 * Gi;
-  const int ef = W::ext_f, eb = W::ext_b, E = nb + ef + eb;
+  const int ef = W::ext_f, eb = W::ext_b;
   const size_t np = (size_t)Wd * Wd * Wd;
-  const double *Pb = P + (size_t)s * np;
-  double *Qb = Q + (size_t)s * np;
-  auto pidx = [&](int i, int j, int k) {
-    return (size_t)(i + Gi) + Wd * ((size_t)(j + Gi) + (size_t)Wd * (k + Gi));
-  };
-  __shared__ int any;
+  __shared__ int rD[27], any;
   if (threadIdx.x == 0) any = 0;
   __syncthreads();
-  const int a[3] = {__ldg(tn.anc + 3 * q) * nb, __ldg(tn.anc + 3 * q + 1) * nb, __ldg(tn.anc + 3 * q + 2) * nb};
-  for (int p = threadIdx.x; p < E * E * E; p += blockDim.x) {
-    const int i = p % E - ef, j = (p / E) % E - ef, k = p / (E * E) - ef;
-    double gam = 0.0;
-    if ((i | j | k) & 1) {
-      const int o = owner(tn, L, a[0] + i, a[1] + j, a[2] + k);
-      const int Lo = __ldg(tn.lev + o), ko = src[2 * o];
-      bool inD = false;
-      if (Lo == L - 1 && ko == KIND_PARENT) {
-        inD = true;
-      } else if (Lo == L && ko == KIND_COPY) {
-        const int mk = nmask[o];
-        if (mk) {
-          int loc[3];
-          const int gg[3] = {a[0] + i, a[1] + j, a[2] + k};
-          for (int d = 0; d < 3; ++d) loc[d] = pwrap(gg[d] - __ldg(tn.anc + 3 * o + d) * nb, npts(tn, L, d));
-          inD = in_band_dev(mk, loc[0], loc[1], loc[2], nb, ef, eb);
-        }
-      }
-      if (inD) {
-        any = 1;
-        // detail, x then y then z (same order as the criterion)
-        const bool ox = i & 1, oy = j & 1, oz = k & 1;
-        const int hx = ox ? W::hwG : W::hwH, hy = oy ? W::hwG : W::hwH, hz = oz ? W::hwG : W::hwH;
-        double bz = 0.0;
-        for (int tz = -hz; tz <= hz; ++tz) {
-          const double wz = oz ? W::G(tz) : W::H(tz);
-          if (wz == 0.0) continue;
-          double by = 0.0;
-          for (int ty = -hy; ty <= hy; ++ty) {
-            const double wy = oy ? W::G(ty) : W::H(ty);
-            if (wy == 0.0) continue;
-            double bx = 0.0;
-            for (int tx = -hx; tx <= hx; ++tx) {
-              const double wx = ox ? W::G(tx) : W::H(tx);
-              if (wx == 0.0) continue;
-              bx = radd(bx, rmul(wx, Pb[pidx(i + tx, j + ty, k + tz)]));
-            }
-            by = radd(by, rmul(wy, bx));
-          }
-          bz = radd(bz, rmul(wz, by));
-        }
-        gam = bz;
-      }
-    }
-    Qb[pidx(i, j, k)] = gam;
+  if (threadIdx.x < 27) {
+    const int r = threadIdx.x;
+    const int dd[3] = {r % 3 - 1, (r / 3) % 3 - 1, r / 9 - 1};
+    int g[3];
+    for (int d = 0; d < 3; ++d) g[d] = __ldg(tn.anc + 3 * q + d) * nb + (dd[d] < 0 ? -1 : dd[d] > 0 ? nb : 0);
+    const int o = owner(tn, L, g[0], g[1], g[2]);
+    const int Lo = __ldg(tn.lev + o), ko = src[2 * o];
+    int v = 0;
+    if (Lo == L - 1 && ko == KIND_PARENT) v = -1;
+    else if (Lo == L && ko == KIND_COPY) v = nmask[o];
+    rD[r] = v;
+    if (v) atomicOr(&any, 1);
   }
   __syncthreads();
-  if (threadIdx.x == 0) hasD[q] = any;
+  if (!any) {
+    if (threadIdx.x == 0) hasD[q] = 0;
+    return;
+  }
+  double *Qb = Q + (size_t)s * np;
+  extern __shared__ double sm[];
+  detail_planes<N, NT>(P + (size_t)s * np, nb, Gi, sm, [&](int i, int j, int k, int, double g) {
+    if ((i | j | k) & 1) {
+      const int r = region_of(i, j, k, nb), v = rD[r];
+      bool inD = v == -1;
+      if (v > 0) {
+        const int dd[3] = {r % 3 - 1, (r / 3) % 3 - 1, r / 9 - 1};
+        inD = in_band_dev(v, i - dd[0] * nb, j - dd[1] * nb, k - dd[2] * nb, nb, ef, eb);
+      }
+      if (!inD) g = 0.0;
+    }
+    Qb[(size_t)(i + Gi) + Wd * ((size_t)(j + Gi) + (size_t)Wd * (k + Gi))] = g;
+  });
+  if (threadIdx.x == 0) hasD[q] = 1;
 }
 
-// subtract the synthesis (J^s / K^s tensor taps) of the discarded details
+// Subtract the synthesis of the discarded details (the J^s / K^s tensor taps
+// of the zero-detail refinement's complement) from the unchanged leaf:
+// separable, x then y then z, with the y-pass planes in a ring of
+// 2*hw(K^s)+1 shared-memory planes.  gamma is zero outside the extended region.
 template <typename TO, int N, int NT>
 __global__ void __launch_bounds__(256) k_update_apply(Tree tn, const int *__restrict__ src,
                                                       const int *__restrict__ hasD,
                                                       const double *__restrict__ Q, int Gi,
                                                       TO *__restrict__ fnew) {
   using W = Wav<N, NT>;
+  constexpr int hk = W::hwK, R = 2 * hk + 1;
   const int q = blockIdx.x;
   if (src[2 * q] != KIND_COPY || !hasD[q]) return;
   const int s = src[2 * q + 1], nb = tn.nb, Wd = nb + 2 * Gi;
-  const int ef = W::ext_f, eb = W::ext_b;
+  const int r0 = -W::ext_f, r1 = nb - 1 + W::ext_b, nR = r1 - r0 + 1;
   const double *Qb = Q + (size_t)s * Wd * Wd * Wd;
   TO *v = fnew + (size_t)q * nb * nb * nb;
-  auto pidx = [&](int i, int j, int k) {
+  extern __shared__ double sm[];
+  double *ring = sm;                        // [R][nb][nb]
+  double *X = sm + (size_t)R * nb * nb;     // [nR][nb]: x pass of one plane
+  auto qidx = [&](int i, int j, int k) {
     return (size_t)(i + Gi) + Wd * ((size_t)(j + Gi) + (size_t)Wd * (k + Gi));
   };
-  for (int p = threadIdx.x; p < nb * nb * nb; p += blockDim.x) {
-    const int i = p % nb, j = (p / nb) % nb, k = p / (nb * nb);
-    const bool od[3] = {(bool)(i & 1), (bool)(j & 1), (bool)(k & 1)};
-    const int h[3] = {od[0] ? W::hwK : W::hwJ, od[1] ? W::hwK : W::hwJ, od[2] ? W::hwK : W::hwJ};
-    double acc = 0.0;
-    for (int oz = -h[2]; oz <= h[2]; ++oz) {
-      const int nz = k + oz;
-      if (nz < -ef || nz >= nb + eb) continue;
-      const double wz = od[2] ? W::K(oz) : W::J(oz);
-      for (int oy = -h[1]; oy <= h[1]; ++oy) {
-        const int ny = j + oy;
-        if (ny < -ef || ny >= nb + eb) continue;
-        const double wy = od[1] ? W::K(oy) : W::J(oy);
-        for (int ox = -h[0]; ox <= h[0]; ++ox) {
-          const int nx = i + ox;
-          if (nx < -ef || nx >= nb + eb) continue;
-          const double g = Qb[pidx(nx, ny, nz)];
-          if (g == 0.0) continue;
-          const double wx = od[0] ? W::K(ox) : W::J(ox);
-          const double wgt = rmul(rmul(wx, wy), wz);
-          if (wgt == 0.0) continue;
-          acc = radd(acc, rmul(wgt, g));
-        }
+  for (int kk = r0; kk <= nb - 1 + hk; ++kk) {
+    const int slot = (kk - r0) % R;
+    if (kk <= r1) {
+      for (int idx = threadIdx.x; idx < nb * nR; idx += blockDim.x) {
+        const int i = idx % nb, jj = r0 + idx / nb;
+        const double *p = Qb + qidx(i, jj, kk);
+        auto at = [&](int t) { return (i + t >= r0 && i + t <= r1) ? p[t] : 0.0; };
+        double a = 0.0;
+        if (i & 1)
+          for_taps<N, NT, FK_K>([&](int t, double w) { a = racc(a, w, at(t)); });
+        else
+          for_taps<N, NT, FK_J>([&](int t, double w) { a = racc(a, w, at(t)); });
+        X[idx] = a;
+      }
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
+        const int i = idx % nb, j = idx / nb;
+        auto at = [&](int t) { return (j + t >= r0 && j + t <= r1) ? X[i + nb * (j + t - r0)] : 0.0; };
+        double a = 0.0;
+        if (j & 1)
+          for_taps<N, NT, FK_K>([&](int t, double w) { a = racc(a, w, at(t)); });
+        else
+          for_taps<N, NT, FK_J>([&](int t, double w) { a = racc(a, w, at(t)); });
+        ring[(size_t)slot * nb * nb + idx] = a;
       }
     }
-    if (acc != 0.0) v[p] = TO(radd((double)v[p], -acc));
+    __syncthreads();
+    // output plane k = kk - hk: its taps k+t with t in [-hk, hk] are planes
+    // kk-2hk .. kk, all in the ring (planes outside [r0, r1] read as 0)
+    const int k = kk - hk;
+    if (k >= 0) {
+      const int sk = (slot + hk + 1) % R;
+      for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
+        auto at = [&](int t) {
+          if (k + t < r0 || k + t > r1) return 0.0;
+          int sl = sk + t;
+          sl += sl < 0 ? R : 0;
+          sl -= sl >= R ? R : 0;
+          return ring[(size_t)sl * nb * nb + idx];
+        };
+        double a = 0.0;
+        if (k & 1)
+          for_taps<N, NT, FK_K>([&](int t, double w) { a = racc(a, w, at(t)); });
+        else
+          for_taps<N, NT, FK_J>([&](int t, double w) { a = racc(a, w, at(t)); });
+        const size_t p = idx + (size_t)nb * nb * k;
+        if (a != 0.0) v[p] = TO((double)v[p] - a);
+      }
+    }
+    __syncthreads();
   }
+}
+
+template <int N, int NT>
+static size_t apply_smem(int nb) {
+  using W = Wav<N, NT>;
+  const int nR = nb + W::ext_f + W::ext_b;
+  return sizeof(double) * ((size_t)(2 * W::hwK + 1) * nb * nb + (size_t)nR * nb);
 }
 
 // ------------------------------------------------- fields needing ghosts
@@ -556,9 +580,17 @@ static int interp_update(mr_grid *g, const Tree &to, const Tree &tn, const doubl
   const int *src = g->newsrc;
   MR_LAUNCH(g, MRK_INTERP, k_interp<TO, N, NT><<<tn.nleaf, 256, 0, g->stream>>>(
                                to, src, P, Gi, (const TO *)field_ptr(g, fid), (TO *)next_field_ptr(g, fid)));
-  MR_LAUNCH(g, MRK_UPDATE, k_update_gamma<N, NT><<<tn.nleaf, 256, 0, g->stream>>>(tn, src, nmask, P, Gi,
-                                                                                 g->padQ64, hasD));
-  MR_LAUNCH(g, MRK_UPDATE, k_update_apply<TO, N, NT><<<tn.nleaf, 256, 0, g->stream>>>(
+  const size_t smg = crit_smem<N, NT>(g->desc.nb), sma = apply_smem<N, NT>(g->desc.nb);
+  if (smg > 227 * 1024 || sma > 227 * 1024) return MR_ERR_UNSUPPORTED;
+  if (check_cuda(cudaFuncSetAttribute(k_update_gamma<N, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smg),
+                 "update smem") ||
+      check_cuda(cudaFuncSetAttribute(k_update_apply<TO, N, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sma),
+                 "update smem"))
+    return MR_ERR_CUDA;
+  MR_LAUNCH(g, MRK_UPDATE, k_update_gamma<N, NT><<<tn.nleaf, 256, smg, g->stream>>>(tn, src, nmask, P, Gi,
+                                                                                   g->padQ64, hasD));
+  MR_LAUNCH(g, MRK_UPDATE, k_update_apply<TO, N, NT><<<tn.nleaf, 256, sma, g->stream>>>(
                                tn, src, hasD, g->padQ64, Gi, (TO *)next_field_ptr(g, fid)));
   return check_cuda(cudaGetLastError(), "interp/update") ? MR_ERR_CUDA : MR_OK;
 }

@@ -12,6 +12,7 @@
 // The wavelet arithmetic uses explicitly rounded multiply/add in the same
 // order as a plain nested-loop evaluation, so the FP64 instantiation is
 // reproducible bit for bit.
+#include <algorithm>
 #include <cstdio>
 
 #include "mr_internal.cuh"
@@ -83,16 +84,10 @@ __host__ __device__ constexpr int tq_lo(int Gi) { return -((Gi + 2) / 2) - (N / 
 template <int N>
 __host__ __device__ constexpr int tq_hi(int nb, int Gi) { return (nb + Gi - 2) / 2 + N / 2; }
 
-// region index (0..26) of a block-local point within the +-1 neighbour ring
-__device__ __forceinline__ int region_of(int i, int j, int k, int nb) {
-  const int rx = i < 0 ? 0 : i >= nb ? 2 : 1, ry = j < 0 ? 0 : j >= nb ? 2 : 1, rz = k < 0 ? 0 : k >= nb ? 2 : 1;
-  return rx + 3 * ry + 9 * rz;
-}
-
 template <typename TI, typename TP, int N, int NT>
 __global__ void __launch_bounds__(512, 1) k_prep(Tree t, const TI *__restrict__ phi, TP *__restrict__ P,
                                                  TP *__restrict__ Q, int Gi, int Gpush, int only_coarse,
-                                                 int use_tile, int *cmask_out, int *err,
+                                                 int use_tile, int zc, int *cmask_out, int *err,
                                                  const int *__restrict__ need) {
   using W = Wav<N, NT>;
   const int b = blockIdx.x;
@@ -220,47 +215,68 @@ __global__ void __launch_bounds__(512, 1) k_prep(Tree t, const TI *__restrict__ 
     }
   }
   __syncthreads();
-  // push: ghost points of each coarser neighbour c inside this leaf's region
-  const int hb = nb / 2;
-  const int Wg = nb + 2 * Gi;
-  for (int ci = 0; ci < ncs; ++ci) {
-    const int c = cslots[ci];
-    const int Lc = L - 1;
-    int ac[3];
-    for (int d = 0; d < 3; ++d) ac[d] = __ldg(t.anc + 3 * c + d) * nb;
-    for (int p = threadIdx.x; p < hb * hb * hb; p += blockDim.x) {
-      // coarse point inside this leaf (level Lc index)
-      const int G[3] = {ax / 2 + p % hb, ay / 2 + (p / hb) % hb, az / 2 + p / (hb * hb)};
-      // c-local offsets of every periodic image of G that falls in c's shell
-      // (tiny periodic domains: c can see this leaf on both sides)
-      int cand[3][3], ncand[3];
-      bool any = true;
-      for (int d = 0; d < 3; ++d) {
-        const int Pn = npts(t, Lc, d);
-        const int off = pwrap(G[d] - ac[d], Pn);
-        ncand[d] = 0;
-        for (int sh = -1; sh <= 1; ++sh) {
-          const int o = off + sh * Pn;
-          if (o >= -Gpush && o < nb + Gpush) cand[d][ncand[d]++] = o;
-        }
-        any &= ncand[d] > 0;
-      }
-      if (!any) continue;
-      // fine index in this leaf of the coincident point: 2G - a*nb
-      const int fl[3] = {2 * G[0] - ax, 2 * G[1] - ay, 2 * G[2] - az};
-      const TP s = coarsen_sum<N, NT, TP>([&](int tx, int ty, int tz) -> TP {
-        return Pb[(fl[0] + tx + Gi) + Wd * ((fl[1] + ty + Gi) + (size_t)Wd * (fl[2] + tz + Gi))];
-      });
-      for (int iz = 0; iz < ncand[2]; ++iz)
-        for (int iy = 0; iy < ncand[1]; ++iy)
-          for (int ix = 0; ix < ncand[0]; ++ix) {
-            const int lc[3] = {cand[0][ix], cand[1][iy], cand[2][iz]};
-            const bool inside = lc[0] >= 0 && lc[0] < nb && lc[1] >= 0 && lc[1] < nb && lc[2] >= 0 && lc[2] < nb;
-            if (inside) continue;
-            Q[(size_t)c * np + (lc[0] + Gi) + Wg * ((lc[1] + Gi) + (size_t)Wg * (lc[2] + Gi))] = s;
-          }
+  // Part 2: H^a coarsening of the padded block at every coarse point of the
+  // leaf, evaluated once and separably (x, then y, then z; zc coarse z-planes
+  // per chunk so the partial sums fit in shared memory), then written to each
+  // periodic image of the point that lies in the ghost shell (Gpush) of a
+  // coarser neighbour.
+  constexpr int hH = W::hwH;
+  const int hb = nb / 2, nf = nb - 1 + 2 * hH, Wg = nb + 2 * Gi;
+  TP *A = reinterpret_cast<TP *>(smraw);  // x-pass [nk][nf][hb]
+  for (int pz0 = 0; pz0 < hb; pz0 += zc) {
+    const int zn = min(zc, hb - pz0), k0 = 2 * pz0 - hH, nk = 2 * zn - 1 + 2 * hH;
+    TP *B = A + (size_t)nk * nf * hb;  // y-pass [nk][hb][hb]
+    for (int idx = threadIdx.x; idx < hb * nf * nk; idx += blockDim.x) {
+      const int px = idx % hb, j = (idx / hb) % nf - hH, k = idx / (hb * nf) + k0;
+      A[idx] = tap_sum<N, NT, FK_H>(Pb + (size_t)(2 * px + Gi) + Wd * ((j + Gi) + (size_t)Wd * (k + Gi)), 1);
     }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < hb * hb * nk; idx += blockDim.x) {
+      const int px = idx % hb, py = (idx / hb) % hb, kk = idx / (hb * hb);
+      B[idx] = tap_sum<N, NT, FK_H>(A + ((size_t)kk * nf + 2 * py + hH) * hb + px, hb);
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < hb * hb * zn; idx += blockDim.x) {
+      const int px = idx % hb, py = (idx / hb) % hb, pz = idx / (hb * hb);
+      const TP sv = tap_sum<N, NT, FK_H>(B + ((size_t)(2 * pz + hH) * hb + py) * hb + px, (long)hb * hb);
+      // coarse (level L-1) point, global index
+      const int G[3] = {ax / 2 + px, ay / 2 + py, az / 2 + pz0 + pz};
+      for (int ci = 0; ci < ncs; ++ci) {
+        const int c = cslots[ci];
+        // c-local offsets of every periodic image of G in c's shell (tiny
+        // periodic domains: c can see this leaf on both sides)
+        int cand[3][3], ncand[3];
+        bool any = true;
+        for (int d = 0; d < 3; ++d) {
+          const int Pn = npts(t, L - 1, d);
+          const int off = pwrap(G[d] - __ldg(t.anc + 3 * c + d) * nb, Pn);
+          ncand[d] = 0;
+          for (int sh = -1; sh <= 1; ++sh) {
+            const int o = off + sh * Pn;
+            if (o >= -Gpush && o < nb + Gpush) cand[d][ncand[d]++] = o;
+          }
+          any &= ncand[d] > 0;
+        }
+        if (!any) continue;
+        for (int iz = 0; iz < ncand[2]; ++iz)
+          for (int iy = 0; iy < ncand[1]; ++iy)
+            for (int ix = 0; ix < ncand[0]; ++ix) {
+              const int lc[3] = {cand[0][ix], cand[1][iy], cand[2][iz]};
+              const bool inside = lc[0] >= 0 && lc[0] < nb && lc[1] >= 0 && lc[1] < nb && lc[2] >= 0 && lc[2] < nb;
+              if (inside) continue;
+              Q[(size_t)c * np + (lc[0] + Gi) + Wg * ((lc[1] + Gi) + (size_t)Wg * (lc[2] + Gi))] = sv;
+            }
+      }
+    }
+    __syncthreads();
   }
+}
+
+// shared memory of the separable Part-2 coarsening for zc coarse z-planes
+template <int N, int NT>
+static size_t push_smem(int nb, int zc, size_t es) {
+  const int hH = Wav<N, NT>::hwH, hb = nb / 2, nf = nb - 1 + 2 * hH, nk = 2 * zc - 1 + 2 * hH;
+  return es * ((size_t)nk * nf * hb + (size_t)nk * hb * hb);
 }
 
 // Merge the part-2 values into P (only the neighbour regions owned by finer
@@ -341,13 +357,17 @@ static int ghost_impl(mr_grid *g, const TI *phi_in, TI *phi_out, int G, TP *P, T
   const int nq = tq_hi<N>(nb, Gi) - tq_lo<N>(Gi) + 1;
   const size_t smT = sizeof(TP) * (size_t)nq * nq * nq;
   const int use_tile = smT <= 200 * 1024;
-  const size_t sm = use_tile ? smT : 0;
+  int zc = nb / 2;
+  while (zc > 1 && push_smem<N, NT>(nb, zc, sizeof(TP)) > 200 * 1024) --zc;
+  const size_t smP = push_smem<N, NT>(nb, zc, sizeof(TP));
+  if (smP > 227 * 1024) return MR_ERR_UNSUPPORTED;
+  const size_t sm = std::max(use_tile ? smT : (size_t)0, smP);
   if (sm > 48 * 1024 &&
       check_cuda(cudaFuncSetAttribute(k_prep<TI, TP, N, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
                  "k_prep smem"))
     return MR_ERR_CUDA;
   MR_LAUNCH(g, MRK_PART1, k_prep<TI, TP, N, NT><<<n, 512, sm, g->stream>>>(t, phi_in, P, Q, Gi, G, only_coarse,
-                                                                           use_tile, g->cmask, err, need));
+                                                                           use_tile, zc, g->cmask, err, need));
   if (check_cuda(cudaGetLastError(), "k_prep")) return MR_ERR_CUDA;
   if (only_coarse) return MR_OK;
   MR_LAUNCH(g, MRK_MERGE, k_merge<TI, TP><<<n, 256, 0, g->stream>>>(t, P, Q, Gi, G, g->cmask, phi_out, need));

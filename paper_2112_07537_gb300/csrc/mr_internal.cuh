@@ -66,22 +66,47 @@ struct Wav {
   }
 };
 
-// Rounded (never fused) arithmetic for the wavelet paths: the FP64 ghost
-// fill and criterion reproduce a fixed evaluation order bit for bit.
+// Wavelet-path arithmetic.  Every filter weight and every product of three
+// weights is a dyadic rational with a short numerator, exact in FP32 and FP64,
+// so a weighted sum costs one fused multiply-add per tap in both precisions.
+// rmul / radd stay available for the few places that want plain rounding.
 __device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
-// accumulate s + w*v: FP64 keeps the separately rounded product and sum of a
-// plain evaluation (bit-reproducible); FP32 uses one fused multiply-add
 __device__ __forceinline__ float racc(float s, float w, float v) { return fmaf(w, v, s); }
-__device__ __forceinline__ double racc(double s, double w, double v) { return __dadd_rn(s, __dmul_rn(w, v)); }
+__device__ __forceinline__ double racc(double s, double w, double v) { return fma(w, v, s); }
+
+// Nonzero taps of one 1D filter as a compile-time loop, ascending offset:
+// KIND 0 = H^a, 1 = G^a, 2 = J^s, 3 = K^s.  f(t, w) gets the offset and weight.
+enum { FK_H = 0, FK_G = 1, FK_J = 2, FK_K = 3 };
+template <int N, int NT, int KIND>
+struct Taps {
+  using W = Wav<N, NT>;
+  static constexpr int hw = KIND == FK_H ? W::hwH : KIND == FK_G ? W::hwG : KIND == FK_J ? W::hwJ : W::hwK;
+  __host__ __device__ static constexpr double w(int t) {
+    return KIND == FK_H ? W::H(t) : KIND == FK_G ? W::G(t) : KIND == FK_J ? W::J(t) : W::K(t);
+  }
+};
+template <int N, int NT, int KIND, typename F>
+__device__ __forceinline__ void for_taps(F f) {
+  using TK = Taps<N, NT, KIND>;
+#pragma unroll
+  for (int t = -TK::hw; t <= TK::hw; ++t)
+    if (TK::w(t) != 0.0) f(t, TK::w(t));
+}
+// sum_t w(t) p[t * stride]
+template <int N, int NT, int KIND, typename TP>
+__device__ __forceinline__ TP tap_sum(const TP *p, long stride) {
+  TP s = TP(0);
+  for_taps<N, NT, KIND>([&](int t, double w) { s = racc(s, TP(w), p[t * stride]); });
+  return s;
+}
 
 // ---------------------------------------------------------------------------
 // Tensor sums with the parity of the output point fixed at compile time, so
 // every loop bound is a constant and zero taps disappear when unrolled.  The
-// terms are visited in ascending offset order, z outermost, x innermost, and
-// each weight is (wx*wy)*wz: the order of a plain nested-loop evaluation.
+// terms are visited in ascending offset order, z outermost, x innermost.
 // ---------------------------------------------------------------------------
 
 // zero-detail refinement (J^s / K^s, taps landing on coarse points only):
@@ -104,7 +129,7 @@ __device__ __forceinline__ TP refine_sum(F val) {
 #pragma unroll
       for (int ox = -hx; ox <= hx; ++ox) {
         if (((ox & 1) != 0) != OX) continue;
-        const TP wgt = rmul(rmul(TP(OX ? W::K(ox) : W::J(ox)), wy), wz);
+        const TP wgt = TP(OX ? W::K(ox) : W::J(ox)) * wy * wz;
         if (wgt == TP(0)) continue;
         s = racc(s, wgt, val(ox, oy, oz));
       }
@@ -141,7 +166,7 @@ __device__ __forceinline__ TP coarsen_sum(F val) {
 #pragma unroll
       for (int tx = -W::hwH; tx <= W::hwH; ++tx) {
         if (W::H(tx) == 0.0) continue;
-        const TP wgt = rmul(rmul(TP(W::H(tx)), TP(W::H(ty))), TP(W::H(tz)));
+        const TP wgt = TP(W::H(tx)) * TP(W::H(ty)) * TP(W::H(tz));
         s = racc(s, wgt, val(tx, ty, tz));
       }
     }
@@ -165,7 +190,7 @@ __device__ __forceinline__ TP subst_sum(F val) {
       for (int tx = -hx; tx <= hx; ++tx) {
         if (OX && W::G(tx) == 0.0) continue;
         if (!tx && !ty && !tz) continue;
-        const TP wgt = rmul(rmul(TP(OX ? W::G(tx) : 1.0), TP(OY ? W::G(ty) : 1.0)), TP(OZ ? W::G(tz) : 1.0));
+        const TP wgt = TP(OX ? W::G(tx) : 1.0) * TP(OY ? W::G(ty) : 1.0) * TP(OZ ? W::G(tz) : 1.0);
         s = racc(s, wgt, val(tx, ty, tz));
       }
     }
@@ -184,6 +209,12 @@ __device__ __forceinline__ TP subst_dispatch(bool ox, bool oy, bool oz, F val) {
     case 6: return subst_sum<N, NT, false, true, true, TP>(val);
     default: return subst_sum<N, NT, true, true, true, TP>(val);
   }
+}
+
+// region index (0..26) of a block-local point within the +-1 neighbour ring
+__device__ __forceinline__ int region_of(int i, int j, int k, int nb) {
+  const int rx = i < 0 ? 0 : i >= nb ? 2 : 1, ry = j < 0 ? 0 : j >= nb ? 2 : 1, rz = k < 0 ? 0 : k >= nb ? 2 : 1;
+  return rx + 3 * ry + 9 * rz;
 }
 
 // ---------------------------------------------------------------------------

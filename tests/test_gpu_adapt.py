@@ -1,11 +1,13 @@
 """Device criterion and adaptation vs the FP64 oracle, through the C ABI.
 
 Integer results (trees, Morton keys, statuses through the trees they
-produce) must be bit-exact.  The FP64 criterion is bit-exact (same evaluation
-order, no fused multiply-add); FP64 adaptation fields are compared at 1e-13
-relative; FP32 grids are compared against the oracle run on the same FP32
-snapshot (upcast), with FP64 ghosts on both sides, so the refinement and
-coarsening decisions must agree exactly.
+produce) must be bit-exact.  The FP64 block norms agree within 1e-12 of the
+field maximum (fused multiply-adds and separable sums on the device; the
+same bound as the ghost fill), and the seeded fields keep every block norm
+farther than that from both thresholds, so the decisions are unique and must
+agree exactly.  FP64 adaptation fields are compared at 1e-12 relative; FP32
+grids are compared against the oracle run on the same FP32 snapshot
+(upcast), with FP64 ghosts on both sides.
 """
 import numpy as np
 import pytest
@@ -52,7 +54,7 @@ def _setup(mr, O, N, Nt, prec, lmax=3, cap=12000):
 
 @pytest.mark.parametrize("N,Nt", [(2, 0), (4, 0), (4, 2), (6, 2)])
 @pytest.mark.parametrize("prec", [0, 1])
-def test_criterion_bitexact(mr, oracle_mod, N, Nt, prec):
+def test_criterion_matches_oracle(mr, oracle_mod, N, Nt, prec):
     import torch
     O = oracle_mod
     g, og, phi = _setup(mr, O, N, Nt, prec)
@@ -60,18 +62,31 @@ def test_criterion_bitexact(mr, oracle_mod, N, Nt, prec):
     g.criterion(0, md)
     g.sync()
     ref = O.block_maxdet(og, phi)
-    assert np.array_equal(md.cpu().numpy(), ref)
+    assert np.abs(md.cpu().numpy() - ref).max() <= TOL * np.abs(phi).max()
 
 
-def _eps(ref):
-    return 1e-3, 1e-7
+TOL = 1e-12
+
+
+def _eps(ref, phi=None):
+    er, ec = 1e-3, 1e-7
+    if phi is not None:
+        _no_near_ties(ref, er, ec, phi)
+    return er, ec
+
+
+def _no_near_ties(maxdet, er, ec, phi):
+    """Every block norm is farther than the FP64 tolerance from both
+    thresholds, so the refine / coarsen decision of each block is unique."""
+    tol = TOL * np.abs(phi).max()
+    assert np.all(np.abs(maxdet - er) > tol) and np.all(np.abs(maxdet - ec) > tol)
 
 
 @pytest.mark.parametrize("N,Nt", [(2, 0), (4, 0), (4, 2), (2, 2)])
 def test_adapt_iteration_fp64_matches_oracle(mr, oracle_mod, N, Nt):
     O = oracle_mod
     g, og, phi = _setup(mr, O, N, Nt, mr.F64)
-    er, ec = _eps(O.block_maxdet(og, phi))
+    er, ec = _eps(O.block_maxdet(og, phi), phi)
     nch = g.adapt_iter(0, er, ec)
     og2, ophi, _, onch, _, st = O.adapt_iter(og, phi, er, ec)
     assert nch == onch and nch > 0
@@ -83,7 +98,7 @@ def test_adapt_iteration_fp64_matches_oracle(mr, oracle_mod, N, Nt):
     assert np.array_equal(glev, og2.lev) and np.array_equal(ganc, og2.anc)
     assert np.array_equal(gkeys, okeys) and np.all(np.diff(gkeys.astype(np.float64)) > 0)
     got = g.field_copy_out(0)
-    assert np.abs(got - ophi).max() <= 1e-13 * np.abs(ophi).max()
+    assert np.abs(got - ophi).max() <= TOL * np.abs(ophi).max()
 
 
 @pytest.mark.parametrize("N,Nt", [(4, 2), (2, 0)])
@@ -98,6 +113,7 @@ def test_adapt_to_convergence_fp32_flags_exact(mr, oracle_mod, N, Nt):
         lev, anc, _ = g.leaves()
         cur = og.with_leaves(lev, anc)
         snap = g.field_copy_out(0).astype(np.float64)
+        _no_near_ties(O.block_maxdet(cur, snap), er, ec, snap)
         og2, ophi, refined_o, onch, _, _ = O.adapt_iter(cur, snap, er, ec, refined)
         nch = g.adapt_iter(0, er, ec)
         assert nch == onch
@@ -121,4 +137,4 @@ def test_mr_adapt_loop_fp64(mr, oracle_mod):
     assert total > 0
     assert np.array_equal(lev, og2.lev) and np.array_equal(anc, og2.anc)
     got = g.field_copy_out(0)
-    assert np.abs(got - ophi).max() <= 1e-13 * np.abs(ophi).max()
+    assert np.abs(got - ophi).max() <= TOL * np.abs(ophi).max()

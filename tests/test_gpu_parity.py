@@ -1,9 +1,12 @@
 """GPU path vs the FP64 oracle, element by element, through the C ABI.
 
-Tolerances: FP64 ghost fill / criterion inputs are bit-exact (same
-operation order, no fused multiply-add on either side); FP64 stencils and
-RK3 steps within 1e-12 relative to the field maximum; FP32 within 1e-5 of the
-field maximum (rounding of ~1e2 FP32 operations per point per stage).
+Tolerances: FP64 ghost fill within 1e-12 of the field maximum (the device
+sums with fused multiply-adds and evaluates the Part-2 coarsening
+separably; a sum of n <= 729 terms with weights of absolute sum <= 14 in 3D
+errs by at most n * 2^-53 * 14 * max|phi| ~ 1e-12 * max|phi|, typically
+1e-15); FP64 stencils and RK3 steps within 1e-12 relative to the field
+maximum; FP32 within 1e-5 of the field maximum (rounding of ~1e2 FP32
+operations per point per stage).
 """
 import numpy as np
 import pytest
@@ -13,6 +16,7 @@ from paper_2112_07537_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 WAV = [(2, 0), (2, 2), (4, 0), (4, 2), (6, 0), (6, 2)]
+FP64_GHOST_TOL = 1e-12
 
 
 @pytest.fixture(scope="module")
@@ -53,7 +57,7 @@ def _grid(mr, O, nt, tl, nb, N, Nt, lev, anc, prec, lmax, nfields=1, cap=None):
 
 
 @pytest.mark.parametrize("N,Nt", WAV)
-def test_ghost_fill_fp64_bitexact(mr, oracle_mod, N, Nt):
+def test_ghost_fill_fp64(mr, oracle_mod, N, Nt):
     O = oracle_mod
     nb = 16 if N < 6 else 24
     nt, tl, lev, anc = _three_level(nb)
@@ -68,12 +72,14 @@ def test_ghost_fill_fp64_bitexact(mr, oracle_mod, N, Nt):
         g.ghost_fill(0, G, pad)
         g.sync()
         ref_pad, ref_sub = O.ghost_fill(og, phi, G)
-        assert np.array_equal(pad.cpu().numpy(), ref_pad), np.abs(pad.cpu().numpy() - ref_pad).max()
-        assert np.array_equal(g.field_copy_out(0), ref_sub)
+        tol = FP64_GHOST_TOL * np.abs(phi).max()
+        err = np.abs(pad.cpu().numpy() - ref_pad).max()
+        assert err <= tol, (G, err)
+        assert np.abs(g.field_copy_out(0) - ref_sub).max() <= tol
 
 
 @pytest.mark.parametrize("N,Nt", [(4, 0), (4, 2), (6, 2)])
-def test_ghost_fill64_of_fp32_field_bitexact(mr, oracle_mod, N, Nt):
+def test_ghost_fill64_of_fp32_field(mr, oracle_mod, N, Nt):
     """The adaptation path: FP64 ghosts from an FP32 field equal the oracle's
     ghosts of the same (upcast) values."""
     O = oracle_mod
@@ -90,8 +96,11 @@ def test_ghost_fill64_of_fp32_field_bitexact(mr, oracle_mod, N, Nt):
     g.ghost_fill64(0, G, pad)
     g.sync()
     ref_pad, ref_sub = O.ghost_fill(og, phi.astype(np.float64), G)
-    assert np.array_equal(pad.cpu().numpy(), ref_pad)
-    assert np.array_equal(g.field_copy_out(0), ref_sub.astype(np.float32))
+    tol = FP64_GHOST_TOL * np.abs(phi).max()
+    assert np.abs(pad.cpu().numpy() - ref_pad).max() <= tol
+    # the substituted interior is stored back in FP32: one rounding
+    got = g.field_copy_out(0).astype(np.float64)
+    assert np.abs(got - ref_sub).max() <= 2.0 ** -24 * np.abs(ref_sub).max() + tol
 
 
 @pytest.mark.parametrize("N,Nt", [(2, 0), (4, 2), (6, 2)])
