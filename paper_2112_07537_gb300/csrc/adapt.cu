@@ -27,6 +27,7 @@ __device__ __forceinline__ void detail_planes(const double *__restrict__ Pb, int
   const int Wd = nb + 2 * Gi;
   const int r0 = -W::ext_f, r1 = nb - 1 + W::ext_b, nR = r1 - r0 + 1, nA = nR + 2 * hm;
   const int lo = -Gi, hi = nb - 1 + Gi;  // stored padded range
+  const int nodd = par_count(r0, r1 + 1, 1);
   double *ring = sm;
   double *A = sm + (size_t)R * nR * nR;
   auto pidx = [&](int i, int j, int k) {
@@ -35,15 +36,18 @@ __device__ __forceinline__ void detail_planes(const double *__restrict__ Pb, int
   for (int kk = r0 - hm; kk <= r1 + hm; ++kk) {
     const int slot = (kk - (r0 - hm)) % R;
     const bool kin = kk >= lo && kk <= hi;
-    // x pass into A (rows j = r0-hm .. r1+hm)
+    // x pass into A (rows j = r0-hm .. r1+hm); the odd columns (G^a) are
+    // enumerated before the even ones (H^a) so a warp runs one filter
     for (int idx = threadIdx.x; idx < nR * nA; idx += blockDim.x) {
-      const int i = r0 + idx % nR, jj = r0 - hm + idx / nR;
+      const bool od = idx < nodd * nA;
+      const int q = od ? idx : idx - nodd * nA, nc = od ? nodd : nR - nodd;
+      const int i = par_first(r0, od) + 2 * (q % nc), jj = r0 - hm + q / nc;
       double s = 0.0;
       if (kin && jj >= lo && jj <= hi) {
         const double *p = Pb + pidx(i, jj, kk);
-        s = (i & 1) ? tap_sum<N, NT, FK_G>(p, 1) : tap_sum<N, NT, FK_H>(p, 1);
+        s = od ? tap_sum<N, NT, FK_G>(p, 1) : tap_sum<N, NT, FK_H>(p, 1);
       }
-      A[idx] = s;
+      A[(i - r0) + nR * (jj - (r0 - hm))] = s;
     }
     __syncthreads();
     // y pass into ring plane kk
@@ -83,22 +87,22 @@ __device__ __forceinline__ void detail_planes(const double *__restrict__ Pb, int
 // Per leaf: max |gamma| over the extended region (Sec. 2.3, the block norm
 // that drives refinement and coarsening).
 template <int N, int NT>
-__global__ void __launch_bounds__(256) k_criterion(Tree t, const double *__restrict__ P, int Gi,
+__global__ void __launch_bounds__(512) k_criterion(Tree t, const double *__restrict__ P, int Gi,
                                                    double *__restrict__ maxdet) {
   const int b = blockIdx.x, nb = t.nb, Wd = nb + 2 * Gi;
   extern __shared__ double sm[];
-  double mx = 0.0;
+  unsigned long long mx = 0;  // max |gamma| as an integer key (integer pipe)
   detail_planes<N, NT>(P + (size_t)b * Wd * Wd * Wd, nb, Gi, sm,
-                       [&](int, int, int, int, double g) { mx = fmax(mx, fabs(g)); });
+                       [&](int, int, int, int, double g) { mx = max(mx, abs_key(g)); });
   // block max
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  __shared__ unsigned long long red[32];
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
   __syncthreads();
   if (threadIdx.x < 32) {
-    double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (threadIdx.x == 0) maxdet[b] = v;
+    unsigned long long v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0ULL;
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (threadIdx.x == 0) maxdet[b] = __longlong_as_double((long long)v);
   }
 }
 
@@ -118,7 +122,7 @@ static int criterion_impl(mr_grid *g, const double *P, int Gi, double *maxdet) {
                  "criterion smem"))
     return MR_ERR_CUDA;
   Tree t = tree_view(g);
-  MR_LAUNCH(g, MRK_CRITERION, k_criterion<N, NT><<<g->nleaf, 256, sm, g->stream>>>(t, P, Gi, maxdet));
+  MR_LAUNCH(g, MRK_CRITERION, k_criterion<N, NT><<<g->nleaf, 512, sm, g->stream>>>(t, P, Gi, maxdet));
   return check_cuda(cudaGetLastError(), "k_criterion") ? MR_ERR_CUDA : MR_OK;
 }
 
@@ -448,16 +452,20 @@ __global__ void __launch_bounds__(256) k_update_apply(Tree tn, const int *__rest
   for (int kk = r0; kk <= nb - 1 + hk; ++kk) {
     const int slot = (kk - r0) % R;
     if (kk <= r1) {
+      // odd columns (K^s) first, then even ones (J^s): one filter per warp
+      const int hn = nb / 2;
       for (int idx = threadIdx.x; idx < nb * nR; idx += blockDim.x) {
-        const int i = idx % nb, jj = r0 + idx / nb;
+        const bool od = idx < hn * nR;
+        const int q = od ? idx : idx - hn * nR;
+        const int i = 2 * (q % hn) + od, jj = r0 + q / hn;
         const double *p = Qb + qidx(i, jj, kk);
         auto at = [&](int t) { return (i + t >= r0 && i + t <= r1) ? p[t] : 0.0; };
         double a = 0.0;
-        if (i & 1)
+        if (od)
           for_taps<N, NT, FK_K>([&](int t, double w) { a = racc(a, w, at(t)); });
         else
           for_taps<N, NT, FK_J>([&](int t, double w) { a = racc(a, w, at(t)); });
-        X[idx] = a;
+        X[i + nb * (jj - r0)] = a;
       }
       __syncthreads();
       for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
@@ -491,7 +499,7 @@ __global__ void __launch_bounds__(256) k_update_apply(Tree tn, const int *__rest
         else
           for_taps<N, NT, FK_J>([&](int t, double w) { a = racc(a, w, at(t)); });
         const size_t p = idx + (size_t)nb * nb * k;
-        if (a != 0.0) v[p] = TO((double)v[p] - a);
+        if (abs_key(a)) v[p] = TO(Cvt<double>::f(v[p]) - a);
       }
     }
     __syncthreads();

@@ -25,8 +25,8 @@ __device__ __forceinline__ T ld(const T *p) { return __ldg(p); }
 // Value stored by leaf o (level Lo >= L or a coarse grid point) at level-L
 // point g; flags a balance error through *err when g is not on o's grid.
 template <typename TI>
-__device__ __forceinline__ double leaf_value(const Tree &t, const TI *phi, int o, int L, int gx,
-                                             int gy, int gz, int *err) {
+__device__ __forceinline__ TI leaf_value(const Tree &t, const TI *phi, int o, int L, int gx,
+                                         int gy, int gz, int *err) {
   const int Lo = __ldg(t.lev + o);
   const int lx = local_index(t, o, Lo, L, gx, 0);
   const int ly = local_index(t, o, Lo, L, gy, 1);
@@ -34,9 +34,9 @@ __device__ __forceinline__ double leaf_value(const Tree &t, const TI *phi, int o
   const int nb = t.nb;
   if (lx < 0 || ly < 0 || lz < 0 || lx >= nb || ly >= nb || lz >= nb) {
     atomicOr(err, 1);
-    return 0.0;
+    return TI(0);
   }
-  return (double)ld(phi + (size_t)o * nb * nb * nb + lx + nb * (ly + nb * lz));
+  return ld(phi + (size_t)o * nb * nb * nb + lx + nb * (ly + nb * lz));
 }
 
 // Zero-detail refinement at level-L point g from the level-(L-1) values
@@ -50,20 +50,8 @@ __device__ TP refine_point(const Tree &t, const TI *phi, int L, int gx, int gy, 
       atomicOr(err, 2);
       return TP(0);
     }
-    return TP(leaf_value(t, phi, o, L - 1, qx, qy, qz, err));
+    return Cvt<TP>::f(leaf_value(t, phi, o, L - 1, qx, qy, qz, err));
   });
-}
-
-__device__ __forceinline__ bool in_band(int mask, int i, int j, int k, int nb, int ef, int eb) {
-  for (int m = 0; m < 27; ++m) {
-    if (!((mask >> m) & 1)) continue;
-    const int d0 = m % 3 - 1, d1 = (m / 3) % 3 - 1, d2 = m / 9 - 1;
-    bool ok = (d0 < 0 ? i < eb : d0 > 0 ? i >= nb - ef : true) &&
-              (d1 < 0 ? j < eb : d1 > 0 ? j >= nb - ef : true) &&
-              (d2 < 0 ? k < eb : d2 > 0 ? k >= nb - ef : true);
-    if (ok) return true;
-  }
-  return false;
 }
 
 // ---------------------------------------------------------------------------
@@ -135,75 +123,140 @@ __global__ void __launch_bounds__(512, 1) k_prep(Tree t, const TI *__restrict__ 
       const int Lo = rlev[r], o = rslot[r];
       if (Lo == L) {
         const int dx = r % 3 - 1, dy = (r / 3) % 3 - 1, dz = r / 9 - 1;
-        return TP(ld(phi + (size_t)o * nb3 + (fi - dx * nb) + nb * ((fj - dy * nb) + nb * (fk - dz * nb))));
+        return Cvt<TP>::f(ld(phi + (size_t)o * nb3 + (fi - dx * nb) + nb * ((fj - dy * nb) + nb * (fk - dz * nb))));
       }
       if (Lo == L - 1) {
         // coarse leaf: level-(L-1) index of the point, relative to its anchor
         const int gq[3] = {(ax + fi) / 2, (ay + fj) / 2, (az + fk) / 2};
         int l[3];
         for (int d = 0; d < 3; ++d) l[d] = pwrap(gq[d] - ranc[r][d] * nb, npts(t, L - 1, d));
-        return TP(ld(phi + (size_t)o * nb3 + l[0] + nb * (l[1] + nb * l[2])));
+        return Cvt<TP>::f(ld(phi + (size_t)o * nb3 + l[0] + nb * (l[1] + nb * l[2])));
       }
     }
     const int gx = (Lq == L ? ax : ax / 2) + i, gy = (Lq == L ? ay : ay / 2) + j, gz = (Lq == L ? az : az / 2) + k;
     const int o = owner(t, Lq, gx, gy, gz);
     if (__ldg(t.lev + o) < Lq) return TP(__int_as_float(0x7fc00000));
-    return TP(leaf_value(t, phi, o, Lq, gx, gy, gz, err));
+    return Cvt<TP>::f(leaf_value(t, phi, o, Lq, gx, gy, gz, err));
   };
   extern __shared__ unsigned char smraw[];
   TP *T = reinterpret_cast<TP *>(smraw);
   const int qlo = tq_lo<N>(Gi), nq = tq_hi<N>(nb, Gi) - qlo + 1;
   const bool tile = use_tile && mask;
+  const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  // boxes of the coarser leaves' regions in the padded cube, and the disjoint
+  // cells of the substitution band: per dimension [0, eb), [eb, nb-ef),
+  // [nb-ef, nb); a cell is in the band when a coarser direction covers it
+  __shared__ BoxList rbox, sbox;
+  if (threadIdx.x == 0) {
+    rbox.n = sbox.n = 0;
+    for (int r = 0; r < 27; ++r) {
+      if (!((mask >> r) & 1)) continue;
+      const int dd[3] = {r % 3 - 1, (r / 3) % 3 - 1, r / 9 - 1};
+      for (int d = 0; d < 3; ++d) {
+        rbox.lo[rbox.n][d] = dd[d] < 0 ? -Gi : dd[d] > 0 ? nb : 0;
+        rbox.hi[rbox.n][d] = dd[d] < 0 ? 0 : dd[d] > 0 ? nb + Gi : nb;
+      }
+      ++rbox.n;
+    }
+    const int cut[4] = {0, W::ext_b, nb - W::ext_f, nb};
+    for (int c = 0; c < 27; ++c) {
+      const int cc[3] = {c % 3, (c / 3) % 3, c / 9};
+      bool in = false;
+      for (int m = 0; m < 27 && !in; ++m) {
+        if (!((mask >> m) & 1)) continue;
+        const int dd[3] = {m % 3 - 1, (m / 3) % 3 - 1, m / 9 - 1};
+        bool cov = true;
+        for (int d = 0; d < 3; ++d) cov &= dd[d] == 0 || (dd[d] < 0 && cc[d] == 0) || (dd[d] > 0 && cc[d] == 2);
+        in = cov;
+      }
+      if (!in) continue;
+      for (int d = 0; d < 3; ++d) sbox.lo[sbox.n][d] = cut[cc[d]], sbox.hi[sbox.n][d] = cut[cc[d] + 1];
+      ++sbox.n;
+    }
+  }
   if (tile) {
-    for (int p = threadIdx.x; p < nq * nq * nq; p += blockDim.x)
-      T[p] = fetch(L - 1, qlo + p % nq, qlo + (p / nq) % nq, qlo + p / (nq * nq));
-    __syncthreads();
+    // coarse tile, one row of nq values per warp
+    for (int row = threadIdx.x >> 5; row < nq * nq; row += nwarp) {
+      const int qy = qlo + row % nq, qz = qlo + row / nq;
+      for (int x = lane; x < nq; x += 32) T[x + (size_t)nq * row] = fetch(L - 1, qlo + x, qy, qz);
+    }
   }
   TP *Pb = P + (size_t)b * np;
   const TI *phib = phi + (size_t)b * nb3;
-  for (size_t p = threadIdx.x; p < np; p += blockDim.x) {
-    const int i = (int)(p % Wd) - Gi, j = (int)((p / Wd) % Wd) - Gi, k = (int)(p / ((size_t)Wd * Wd)) - Gi;
-    TP v;
-    if (i >= 0 && i < nb && j >= 0 && j < nb && k >= 0 && k < nb) {
-      v = TP(ld(phib + i + nb * (j + nb * k)));
-    } else {
-      const int r = region_of(i, j, k, nb);
-      const int Lo = rlev[r];
-      if (Lo == L - 1) {
-        if (tile) {
-          v = refine_dispatch<N, NT, TP>(i & 1, j & 1, k & 1, [&](int ox, int oy, int oz) -> TP {
-            const int qx = (i + ox) / 2 - qlo, qy = (j + oy) / 2 - qlo, qz = (k + oz) / 2 - qlo;
-            return T[qx + nq * (qy + nq * qz)];
-          });
-          if (v != v) atomicOr(err, 2);
-        } else {
-          v = refine_point<TI, TP, N, NT>(t, phi, L, ax + i, ay + j, az + k, err);
-        }
-      } else if (Lo >= L) {
-        v = fetch(L, i, j, k);  // copy, or the coincident value of a finer leaf
+  // every padded point outside the coarser leaves' regions (all points when
+  // the tile is off): interior, same-level copy, coincident value of a finer
+  // leaf; one padded row per warp
+  for (int row = threadIdx.x >> 5; row < Wd * Wd; row += nwarp) {
+    const int j = row % Wd - Gi, k = row / Wd - Gi;
+    const int ryz = 3 * (j < 0 ? 0 : j >= nb ? 2 : 1) + 9 * (k < 0 ? 0 : k >= nb ? 2 : 1);
+    TP *prow = Pb + (size_t)row * Wd + Gi;
+    for (int i = lane - Gi; i < nb + Gi; i += 32) {
+      const int r = (i < 0 ? 0 : i >= nb ? 2 : 1) + ryz;
+      TP v;
+      if (r == 13) {
+        v = Cvt<TP>::f(ld(phib + i + nb * (j + nb * k)));
       } else {
-        atomicOr(err, 8);
-        v = TP(0);
+        const int Lo = rlev[r];
+        if (Lo == L - 1) {
+          if (tile) continue;
+          v = refine_point<TI, TP, N, NT>(t, phi, L, ax + i, ay + j, az + k, err);
+        } else if (Lo >= L) {
+          v = fetch(L, i, j, k);  // copy, or the coincident value of a finer leaf
+        } else {
+          atomicOr(err, 8);
+          v = TP(0);
+        }
       }
+      prow[i] = v;
     }
-    Pb[p] = v;
   }
   __syncthreads();
   if (!mask) return;
-  // substitution, degree by degree
-  for (int deg = 1; deg <= 3; ++deg) {
-    for (int p = threadIdx.x; p < nb * nb * nb; p += blockDim.x) {
-      const int i = p % nb, j = (p / nb) % nb, k = p / (nb * nb);
-      const int o0 = i & 1, o1 = j & 1, o2 = k & 1;
-      if (o0 + o1 + o2 != deg) continue;
-      if (!in_band(mask, i, j, k, nb, W::ext_f, W::ext_b)) continue;
-      Pb[(i + Gi) + Wd * ((j + Gi) + (size_t)Wd * (k + Gi))] =
-          subst_dispatch<N, NT, TP>(o0, o1, o2, [&](int tx, int ty, int tz) -> TP {
-            return Pb[(i + tx + Gi) + Wd * ((j + ty + Gi) + (size_t)Wd * (k + tz + Gi))];
-          });
-    }
+  // zero-detail refinement of the coarse regions from the tile, one parity
+  // class at a time (every warp runs one tap sequence)
+  if (tile) {
+    auto refine_cls = [&](auto cls) {
+      constexpr int OX = decltype(cls)::x, OY = decltype(cls)::y, OZ = decltype(cls)::z;
+      for_class_points<OX, OY, OZ>(rbox, [&](int i, int j, int k) {
+        const TP v = refine_sum<N, NT, OX, OY, OZ, TP>([&](int ox, int oy, int oz) -> TP {
+          const int qx = (i + ox) / 2 - qlo, qy = (j + oy) / 2 - qlo, qz = (k + oz) / 2 - qlo;
+          return T[qx + nq * (qy + nq * qz)];
+        });
+        if (nan_bits(v)) atomicOr(err, 2);
+        Pb[(i + Gi) + Wd * ((j + Gi) + (size_t)Wd * (k + Gi))] = v;
+      });
+    };
+    refine_cls(Cls<0, 0, 0>());
+    refine_cls(Cls<1, 0, 0>());
+    refine_cls(Cls<0, 1, 0>());
+    refine_cls(Cls<1, 1, 0>());
+    refine_cls(Cls<0, 0, 1>());
+    refine_cls(Cls<1, 0, 1>());
+    refine_cls(Cls<0, 1, 1>());
+    refine_cls(Cls<1, 1, 1>());
     __syncthreads();
   }
+  // substitution, degree by degree (a point of degree d reads lower degrees
+  // only, so the classes of one degree are independent)
+  auto subst_cls = [&](auto cls) {
+    constexpr int OX = decltype(cls)::x, OY = decltype(cls)::y, OZ = decltype(cls)::z;
+    for_class_points<OX, OY, OZ>(sbox, [&](int i, int j, int k) {
+      TP *c = Pb + (i + Gi) + Wd * ((j + Gi) + (size_t)Wd * (k + Gi));
+      *c = subst_sum<N, NT, OX, OY, OZ, TP>([&](int tx, int ty, int tz) -> TP {
+        return c[tx + Wd * (ty + (long)Wd * tz)];
+      });
+    });
+  };
+  subst_cls(Cls<1, 0, 0>());
+  subst_cls(Cls<0, 1, 0>());
+  subst_cls(Cls<0, 0, 1>());
+  __syncthreads();
+  subst_cls(Cls<1, 1, 0>());
+  subst_cls(Cls<1, 0, 1>());
+  subst_cls(Cls<0, 1, 1>());
+  __syncthreads();
+  subst_cls(Cls<1, 1, 1>());
+  __syncthreads();
   // distinct coarser neighbours
   if (threadIdx.x == 0) {
     for (int m = 0; m < 27; ++m) {

@@ -77,6 +77,40 @@ __device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a,
 __device__ __forceinline__ float racc(float s, float w, float v) { return fmaf(w, v, s); }
 __device__ __forceinline__ double racc(double s, double w, double v) { return fma(w, v, s); }
 
+// float -> double widening on the integer pipe (exact; this part's FP64
+// pipe is narrow and also executes the hardware conversion): zero and normal
+// numbers by moving sign, rebiased exponent (+1023-127) and mantissa;
+// subnormals, infinities and NaN through the hardware conversion.
+__device__ __forceinline__ double widen(float f) {
+  const unsigned u = __float_as_uint(f), e = (u >> 23) & 0xffu;
+  const unsigned long long sgn = (unsigned long long)(u >> 31) << 63;
+  if ((u & 0x7fffffffu) == 0u) return __longlong_as_double((long long)sgn);
+  if (e == 0u || e == 0xffu) return (double)f;
+  return __longlong_as_double(
+      (long long)(sgn | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+// value of the field element type TI in the working precision TP
+template <typename TP>
+struct Cvt;
+template <>
+struct Cvt<double> {
+  static __device__ __forceinline__ double f(float v) { return widen(v); }
+  static __device__ __forceinline__ double f(double v) { return v; }
+};
+template <>
+struct Cvt<float> {
+  static __device__ __forceinline__ float f(float v) { return v; }
+  static __device__ __forceinline__ float f(double v) { return (float)v; }
+};
+__device__ __forceinline__ bool nan_bits(double v) {
+  return (__double_as_longlong(v) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL;
+}
+__device__ __forceinline__ bool nan_bits(float v) { return (__float_as_int(v) & 0x7fffffff) > 0x7f800000; }
+// |v| as an integer key: ordered like |v| for every non-NaN double
+__device__ __forceinline__ unsigned long long abs_key(double v) {
+  return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
+}
+
 // Nonzero taps of one 1D filter as a compile-time loop, ascending offset:
 // KIND 0 = H^a, 1 = G^a, 2 = J^s, 3 = K^s.  f(t, w) gets the offset and weight.
 enum { FK_H = 0, FK_G = 1, FK_J = 2, FK_K = 3 };
@@ -208,6 +242,51 @@ __device__ __forceinline__ TP subst_dispatch(bool ox, bool oy, bool oz, F val) {
     case 5: return subst_sum<N, NT, true, false, true, TP>(val);
     case 6: return subst_sum<N, NT, false, true, true, TP>(val);
     default: return subst_sum<N, NT, true, true, true, TP>(val);
+  }
+}
+
+// Parity class of a point as a type: the tap sums of a class have
+// compile-time bounds, and a warp that runs one class runs one tap sequence.
+template <int X, int Y, int Z>
+struct Cls {
+  static constexpr int x = X, y = Y, z = Z;
+};
+
+// up to 27 disjoint boxes [lo, hi) of block-local points
+struct BoxList {
+  int n;
+  int lo[27][3], hi[27][3];
+};
+
+// first point of parity par at or after lo; number of such points in [lo, hi)
+__device__ __forceinline__ int par_first(int lo, int par) { return lo + ((lo ^ par) & 1); }
+__device__ __forceinline__ int par_count(int lo, int hi, int par) {
+  const int f = par_first(lo, par);
+  return f < hi ? (hi - f + 1) >> 1 : 0;
+}
+
+// f(i, j, k) for every point of parity class (OX, OY, OZ) in the boxes, as
+// one flat index space spread over the CTA (each thread walks the boxes
+// forward, so locating a point's box costs O(1) amortised)
+template <int OX, int OY, int OZ, typename F>
+__device__ __forceinline__ void for_class_points(const BoxList &bl, F f) {
+  auto cnt3 = [&](int e, int &nx, int &ny) {
+    nx = par_count(bl.lo[e][0], bl.hi[e][0], OX);
+    ny = par_count(bl.lo[e][1], bl.hi[e][1], OY);
+    return nx * ny * par_count(bl.lo[e][2], bl.hi[e][2], OZ);
+  };
+  int total = 0, nx, ny;
+  for (int e = 0; e < bl.n; ++e) total += cnt3(e, nx, ny);
+  if (!total) return;
+  int e = 0, base = 0, cnt = cnt3(0, nx, ny);
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    while (idx >= base + cnt) {
+      base += cnt;
+      cnt = cnt3(++e, nx, ny);
+    }
+    const int q = idx - base, qx = q % nx, qy = (q / nx) % ny, qz = q / (nx * ny);
+    f(par_first(bl.lo[e][0], OX) + 2 * qx, par_first(bl.lo[e][1], OY) + 2 * qy,
+      par_first(bl.lo[e][2], OZ) + 2 * qz);
   }
 }
 
