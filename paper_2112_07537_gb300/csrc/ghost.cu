@@ -75,8 +75,8 @@ __host__ __device__ constexpr int tq_hi(int nb, int Gi) { return (nb + Gi - 2) /
 template <typename TI, typename TP, int N, int NT>
 __global__ void __launch_bounds__(512, 1) k_prep(Tree t, const TI *__restrict__ phi, TP *__restrict__ P,
                                                  TP *__restrict__ Q, int Gi, int Gpush, int only_coarse,
-                                                 int use_tile, int zc, int *cmask_out, int *err,
-                                                 const int *__restrict__ need) {
+                                                 int use_tile, int tile_bytes, int zc, int *cmask_out,
+                                                 int *err, const int *__restrict__ need) {
   using W = Wav<N, NT>;
   const int b = blockIdx.x;
   if (need && !need[b]) return;
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(512, 1) k_prep(Tree t, const TI *__restrict__ 
   // value stored at level-Lq point (block-local, level L coords when Lq == L;
   // coarse-local coords when Lq == L-1) -- via the region table when the
   // owning region is same-level or coarser, else through the owner map
-  auto fetch = [&](int Lq, int i, int j, int k) -> TP {
+  auto fetch_raw = [&](int Lq, int i, int j, int k) -> TI {
     const int sc = (Lq == L) ? 1 : 2;  // fine-index scale of the point
     const int fi = i * sc, fj = j * sc, fk = k * sc;
     if (fi >= -nb && fi < 2 * nb && fj >= -nb && fj < 2 * nb && fk >= -nb && fk < 2 * nb) {
@@ -123,23 +123,24 @@ __global__ void __launch_bounds__(512, 1) k_prep(Tree t, const TI *__restrict__ 
       const int Lo = rlev[r], o = rslot[r];
       if (Lo == L) {
         const int dx = r % 3 - 1, dy = (r / 3) % 3 - 1, dz = r / 9 - 1;
-        return Cvt<TP>::f(ld(phi + (size_t)o * nb3 + (fi - dx * nb) + nb * ((fj - dy * nb) + nb * (fk - dz * nb))));
+        return ld(phi + (size_t)o * nb3 + (fi - dx * nb) + nb * ((fj - dy * nb) + nb * (fk - dz * nb)));
       }
       if (Lo == L - 1) {
         // coarse leaf: level-(L-1) index of the point, relative to its anchor
         const int gq[3] = {(ax + fi) / 2, (ay + fj) / 2, (az + fk) / 2};
         int l[3];
         for (int d = 0; d < 3; ++d) l[d] = pwrap(gq[d] - ranc[r][d] * nb, npts(t, L - 1, d));
-        return Cvt<TP>::f(ld(phi + (size_t)o * nb3 + l[0] + nb * (l[1] + nb * l[2])));
+        return ld(phi + (size_t)o * nb3 + l[0] + nb * (l[1] + nb * l[2]));
       }
     }
     const int gx = (Lq == L ? ax : ax / 2) + i, gy = (Lq == L ? ay : ay / 2) + j, gz = (Lq == L ? az : az / 2) + k;
     const int o = owner(t, Lq, gx, gy, gz);
-    if (__ldg(t.lev + o) < Lq) return TP(__int_as_float(0x7fc00000));
-    return Cvt<TP>::f(leaf_value(t, phi, o, Lq, gx, gy, gz, err));
+    if (__ldg(t.lev + o) < Lq) return TI(__int_as_float(0x7fc00000));
+    return leaf_value(t, phi, o, Lq, gx, gy, gz, err);
   };
+  auto fetch = [&](int Lq, int i, int j, int k) -> TP { return Cvt<TP>::f(fetch_raw(Lq, i, j, k)); };
   extern __shared__ unsigned char smraw[];
-  TP *T = reinterpret_cast<TP *>(smraw);
+  TI *T = reinterpret_cast<TI *>(smraw);  // coarse tile, in the field's type
   const int qlo = tq_lo<N>(Gi), nq = tq_hi<N>(nb, Gi) - qlo + 1;
   const bool tile = use_tile && mask;
   const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
@@ -178,7 +179,7 @@ __global__ void __launch_bounds__(512, 1) k_prep(Tree t, const TI *__restrict__ 
     // coarse tile, one row of nq values per warp
     for (int row = threadIdx.x >> 5; row < nq * nq; row += nwarp) {
       const int qy = qlo + row % nq, qz = qlo + row / nq;
-      for (int x = lane; x < nq; x += 32) T[x + (size_t)nq * row] = fetch(L - 1, qlo + x, qy, qz);
+      for (int x = lane; x < nq; x += 32) T[x + (size_t)nq * row] = fetch_raw(L - 1, qlo + x, qy, qz);
     }
   }
   TP *Pb = P + (size_t)b * np;
@@ -212,15 +213,109 @@ __global__ void __launch_bounds__(512, 1) k_prep(Tree t, const TI *__restrict__ 
   }
   __syncthreads();
   if (!mask) return;
-  // zero-detail refinement of the coarse regions from the tile, one parity
-  // class at a time (every warp runs one tap sequence)
-  if (tile) {
+  // zero-detail refinement of the coarse regions from the tile: separably per
+  // region box when the partial sums fit next to the tile (use_tile == 2),
+  // else one parity class at a time (every warp runs one tap sequence)
+  if (tile && use_tile == 2) {
+    TP *U = reinterpret_cast<TP *>(smraw + tile_bytes);
+    constexpr int ko = N - 1;  // widest odd K^s tap
+    const long ts[3] = {1, nq, (long)nq * nq}, ps[3] = {1, Wd, (long)Wd * Wd};
+    for (int e = 0; e < rbox.n; ++e) {
+      int fl[3], fn[3], cl[3], cn[3];
+      bool ok = true;
+      for (int d = 0; d < 3; ++d) {
+        fl[d] = rbox.lo[e][d], fn[d] = rbox.hi[e][d] - fl[d];
+        cl[d] = (fl[d] - ko) >> 1;
+        cn[d] = ((fl[d] + fn[d] - 1 + ko) >> 1) - cl[d] + 1;
+        ok &= cl[d] >= qlo && cl[d] + cn[d] <= qlo + nq;
+      }
+      if (!ok) {  // outside the tile: not a valid shell for this block size
+        if (threadIdx.x == 0) atomicOr(err, 2);
+        continue;
+      }
+      // expansion order: thinnest dimension first, thickest last
+      int a = 0, c = 0;
+      for (int d = 1; d < 3; ++d) {
+        if (fn[d] < fn[a]) a = d;
+        if (fn[d] >= fn[c]) c = d;
+      }
+      if (a == c) c = (a + 2) % 3;
+      const int bd = 3 - a - c;
+      // per-box scalars (the loops below index nothing dynamically)
+      const int nfa = fn[a], nfb = fn[bd], nfc = fn[c], ncb = cn[bd], ncc = cn[c];
+      const int la = fl[a], lb = fl[bd], lc = fl[c], cb = cl[bd], cc = cl[c];
+      const long tsa = ts[a], tsb = ts[bd], tsc = ts[c], psa = ps[a], psb = ps[bd], psc = ps[c];
+      TP *U1 = U, *U2 = U + (size_t)nfa * ncb * ncc;
+      // pass 1: along a, coarse tile -> U1[ia][jb][kc] (odd fine points first)
+      {
+        const int no = par_count(la, la + nfa, 1), ne = nfa - no, m = ncb * ncc;
+        for (int idx = threadIdx.x; idx < nfa * m; idx += blockDim.x) {
+          const bool od = idx < no * m;
+          const int q = od ? idx : idx - no * m, nh = od ? no : ne;
+          const int f = par_first(la, od) + 2 * (q % nh), r = q / nh, jb = r % ncb, kc = r / ncb;
+          const TI *tp = T + (cb + jb - qlo) * tsb + (cc + kc - qlo) * tsc;
+          TP v;
+          if (od) {
+            v = TP(0);
+#pragma unroll
+            for (int t = -ko; t <= ko; t += 2)
+              v = racc(v, TP(Wav<N, NT>::K(t)), Cvt<TP>::f(tp[(((f + t) >> 1) - qlo) * tsa]));
+          } else {
+            v = Cvt<TP>::f(tp[((f >> 1) - qlo) * tsa]);
+          }
+          U1[(f - la) + nfa * (jb + ncb * kc)] = v;
+        }
+      }
+      __syncthreads();
+      // pass 2: along b, U1 -> U2[ia][ib][kc]
+      {
+        const int no = par_count(lb, lb + nfb, 1), ne = nfb - no;
+        for (int idx = threadIdx.x; idx < nfa * nfb * ncc; idx += blockDim.x) {
+          const bool od = idx < nfa * no * ncc;
+          const int q = od ? idx : idx - nfa * no * ncc, nh = od ? no : ne;
+          const int ia = q % nfa, f = par_first(lb, od) + 2 * ((q / nfa) % nh), kc = q / (nfa * nh);
+          const TP *up = U1 + ia + (size_t)nfa * ncb * kc;
+          TP v;
+          if (od) {
+            v = TP(0);
+#pragma unroll
+            for (int t = -ko; t <= ko; t += 2) v = racc(v, TP(Wav<N, NT>::K(t)), up[nfa * (((f + t) >> 1) - cb)]);
+          } else {
+            v = up[nfa * ((f >> 1) - cb)];
+          }
+          U2[ia + nfa * ((f - lb) + nfb * kc)] = v;
+        }
+      }
+      __syncthreads();
+      // pass 3: along c, U2 -> padded block
+      {
+        const int no = par_count(lc, lc + nfc, 1), ne = nfc - no, m = nfa * nfb;
+        for (int idx = threadIdx.x; idx < m * nfc; idx += blockDim.x) {
+          const bool od = idx < m * no;
+          const int q = od ? idx : idx - m * no, nh = od ? no : ne;
+          const int ia = q % nfa, ib = (q / nfa) % nfb, f = par_first(lc, od) + 2 * (q / m);
+          const TP *up = U2 + ia + (size_t)nfa * ib;
+          TP v;
+          if (od) {
+            v = TP(0);
+#pragma unroll
+            for (int t = -ko; t <= ko; t += 2) v = racc(v, TP(Wav<N, NT>::K(t)), up[(size_t)m * (((f + t) >> 1) - cc)]);
+          } else {
+            v = up[(size_t)m * ((f >> 1) - cc)];
+          }
+          if (nan_bits(v)) atomicOr(err, 2);
+          Pb[(la + ia + Gi) * psa + (lb + ib + Gi) * psb + (f + Gi) * psc] = v;
+        }
+      }
+      __syncthreads();
+    }
+  } else if (tile) {
     auto refine_cls = [&](auto cls) {
       constexpr int OX = decltype(cls)::x, OY = decltype(cls)::y, OZ = decltype(cls)::z;
       for_class_points<OX, OY, OZ>(rbox, [&](int i, int j, int k) {
         const TP v = refine_sum<N, NT, OX, OY, OZ, TP>([&](int ox, int oy, int oz) -> TP {
           const int qx = (i + ox) / 2 - qlo, qy = (j + oy) / 2 - qlo, qz = (k + oz) / 2 - qlo;
-          return T[qx + nq * (qy + nq * qz)];
+          return Cvt<TP>::f(T[qx + nq * (qy + nq * qz)]);
         });
         if (nan_bits(v)) atomicOr(err, 2);
         Pb[(i + Gi) + Wd * ((j + Gi) + (size_t)Wd * (k + Gi))] = v;
@@ -325,6 +420,26 @@ __global__ void __launch_bounds__(512, 1) k_prep(Tree t, const TI *__restrict__ 
   }
 }
 
+// partial sums of the separable refinement of the largest coarse-region box
+// (face nb x nb x Gi, edge nb x Gi x Gi, corner Gi^3; thinnest side first)
+static size_t sep_refine_elems(int N, int nb, int Gi) {
+  const int ko = N - 1;
+  auto ncmax = [&](int n) {
+    int m = 0;
+    for (int fl = 0; fl < 2; ++fl) m = std::max(m, ((fl + n - 1 + ko) >> 1) - ((fl - ko) >> 1) + 1);
+    return m;
+  };
+  const int shapes[3][3] = {{Gi, nb, nb}, {Gi, Gi, nb}, {Gi, Gi, Gi}};
+  size_t best = 0;
+  for (auto &sh : shapes) {
+    int f[3] = {sh[0], sh[1], sh[2]};
+    std::sort(f, f + 3);
+    const size_t u1 = (size_t)f[0] * ncmax(f[1]) * ncmax(f[2]), u2 = (size_t)f[0] * f[1] * ncmax(f[2]);
+    best = std::max(best, u1 + u2);
+  }
+  return best;
+}
+
 // shared memory of the separable Part-2 coarsening for zc coarse z-planes
 template <int N, int NT>
 static size_t push_smem(int nb, int zc, size_t es) {
@@ -408,19 +523,24 @@ static int ghost_impl(mr_grid *g, const TI *phi_in, TI *phi_out, int G, TP *P, T
   const int n = g->nleaf, nb = g->desc.nb;
   int *err = g->counter + 1;
   const int nq = tq_hi<N>(nb, Gi) - tq_lo<N>(Gi) + 1;
-  const size_t smT = sizeof(TP) * (size_t)nq * nq * nq;
-  const int use_tile = smT <= 200 * 1024;
+  const size_t smT = (sizeof(TI) * (size_t)nq * nq * nq + 15) & ~(size_t)15;
+  const size_t smU = sizeof(TP) * sep_refine_elems(N, nb, Gi);
+  const size_t budget = 220 * 1024;
+  // 2: coarse tile + separable refinement, 1: tile + per-point tensor sums,
+  // 0: per-point sums through the owner map
+  const int use_tile = smT + smU <= budget ? 2 : smT <= budget ? 1 : 0;
   int zc = nb / 2;
-  while (zc > 1 && push_smem<N, NT>(nb, zc, sizeof(TP)) > 200 * 1024) --zc;
+  while (zc > 1 && push_smem<N, NT>(nb, zc, sizeof(TP)) > budget) --zc;
   const size_t smP = push_smem<N, NT>(nb, zc, sizeof(TP));
   if (smP > 227 * 1024) return MR_ERR_UNSUPPORTED;
-  const size_t sm = std::max(use_tile ? smT : (size_t)0, smP);
+  const size_t sm = std::max(use_tile == 2 ? smT + smU : use_tile ? smT : (size_t)0, smP);
   if (sm > 48 * 1024 &&
       check_cuda(cudaFuncSetAttribute(k_prep<TI, TP, N, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
                  "k_prep smem"))
     return MR_ERR_CUDA;
   MR_LAUNCH(g, MRK_PART1, k_prep<TI, TP, N, NT><<<n, 512, sm, g->stream>>>(t, phi_in, P, Q, Gi, G, only_coarse,
-                                                                           use_tile, zc, g->cmask, err, need));
+                                                                           use_tile, (int)smT, zc, g->cmask, err,
+                                                                           need));
   if (check_cuda(cudaGetLastError(), "k_prep")) return MR_ERR_CUDA;
   if (only_coarse) return MR_OK;
   MR_LAUNCH(g, MRK_MERGE, k_merge<TI, TP><<<n, 256, 0, g->stream>>>(t, P, Q, Gi, G, g->cmask, phi_out, need));
