@@ -14,70 +14,107 @@ enum { ST_COARSER = -1, ST_SAME = 0, ST_FINER = 1 };
 
 // ------------------------------------------------------------- criterion
 // Details gamma over the extended region [-ext_f, nb-1+ext_b]^3 of one padded
-// block (1D filters x, then y, then z: G^a on odd, H^a on even coordinates;
-// points with only even coordinates carry no detail and get 0).  The z-planes
-// of the y-pass results live in a ring of 2*hmax+1 shared-memory planes, so
-// each pass is computed once.  emit(i, j, k, idx, gamma) is called once per
-// point of the region, plane by plane (idx = i-r0 + nR*(j-r0)).
+// block: 1D filters x, then y, then z, G^a on odd and H^a on even
+// coordinates; points with only even coordinates carry no detail and get 0.
+// Each 1D pass uses the lifting form of the pair: the G^a output at an odd
+// point is the point minus the K^s-weighted prediction from its even
+// neighbours (odd taps only), and the H^a output at an even point is the
+// point plus 1/4 of the two neighbouring G^a outputs (N.2; H^a is the
+// identity for N.0) -- the same filters, about half the multiply-adds.
+// The z-planes of the y-pass results live in a ring of 2(N-1)+1 planes and the
+// z-details of the last two odd planes in a second ring.  emit(i, j, k, idx,
+// gamma) is called once per point of the region (idx = i-r0 + nR*(j-r0)).
 template <int N, int NT, typename F>
 __device__ __forceinline__ void detail_planes(const double *__restrict__ Pb, int nb, int Gi, double *sm,
                                               F emit) {
   using W = Wav<N, NT>;
-  constexpr int hm = W::hmax, R = 2 * hm + 1;
+  constexpr int ko = N - 1, R = 2 * ko + 1;
+  constexpr double U = NT ? 0.25 : 0.0;  // lifting update weight
   const int Wd = nb + 2 * Gi;
-  const int r0 = -W::ext_f, r1 = nb - 1 + W::ext_b, nR = r1 - r0 + 1, nA = nR + 2 * hm;
+  const int r0 = -W::ext_f, r1 = nb - 1 + W::ext_b, nR = r1 - r0 + 1, nA = nR + 2 * ko;
   const int lo = -Gi, hi = nb - 1 + Gi;  // stored padded range
-  const int nodd = par_count(r0, r1 + 1, 1);
-  double *ring = sm;
-  double *A = sm + (size_t)R * nR * nR;
-  auto pidx = [&](int i, int j, int k) {
-    return (size_t)(i + Gi) + Wd * ((size_t)(j + Gi) + (size_t)Wd * (k + Gi));
+  const int nodd = par_count(r0, r1 + 1, 1), nev = nR - nodd;
+  const int fo = par_first(r0, 1), fe = par_first(r0, 0);
+  const size_t pl = (size_t)nR * nR;
+  double *ring = sm;             // [R][nR][nR]  y-pass planes
+  double *dz = sm + R * pl;      // [2][nR][nR]  z-details of odd planes
+  double *A = dz + 2 * pl;       // [nA][nR]     x-pass of one plane
+  // G^a output: v[0] - sum_{t odd} K(t) v[t*stride]
+  auto gsum = [](const double *v, long stride) {
+    double s = v[0];
+#pragma unroll
+    for (int t = -ko; t <= ko; t += 2) s = fma(-Wav<N, NT>::K(t), v[t * stride], s);
+    return s;
   };
-  for (int kk = r0 - hm; kk <= r1 + hm; ++kk) {
-    const int slot = (kk - (r0 - hm)) % R;
+  for (int kk = r0 - ko; kk <= r1 + ko + 1; ++kk) {
+    const int slot = (kk - (r0 - ko)) % R;
     const bool kin = kk >= lo && kk <= hi;
-    // x pass into A (rows j = r0-hm .. r1+hm); the odd columns (G^a) are
-    // enumerated before the even ones (H^a) so a warp runs one filter
-    for (int idx = threadIdx.x; idx < nR * nA; idx += blockDim.x) {
-      const bool od = idx < nodd * nA;
-      const int q = od ? idx : idx - nodd * nA, nc = od ? nodd : nR - nodd;
-      const int i = par_first(r0, od) + 2 * (q % nc), jj = r0 - hm + q / nc;
-      double s = 0.0;
-      if (kin && jj >= lo && jj <= hi) {
-        const double *p = Pb + pidx(i, jj, kk);
-        s = od ? tap_sum<N, NT, FK_G>(p, 1) : tap_sum<N, NT, FK_H>(p, 1);
-      }
-      A[(i - r0) + nR * (jj - (r0 - hm))] = s;
+    const double *pk = Pb + (size_t)(kk + Gi) * Wd * Wd;
+    // x pass: odd columns, then even columns (rows jj = r0-ko .. r1+ko)
+    for (int idx = threadIdx.x; idx < nodd * nA; idx += blockDim.x) {
+      const int i = fo + 2 * (idx % nodd), jj = r0 - ko + idx / nodd;
+      const bool in = kin && jj >= lo && jj <= hi;
+      A[(i - r0) + nR * (jj - (r0 - ko))] = in ? gsum(pk + (size_t)(jj + Gi) * Wd + (i + Gi), 1) : 0.0;
     }
     __syncthreads();
-    // y pass into ring plane kk
-    for (int idx = threadIdx.x; idx < nR * nR; idx += blockDim.x) {
-      const int ii = idx % nR, j = r0 + idx / nR;
-      const double *p = A + ii + nR * (j - (r0 - hm));
-      ring[(size_t)slot * nR * nR + idx] = (j & 1) ? tap_sum<N, NT, FK_G>(p, nR) : tap_sum<N, NT, FK_H>(p, nR);
+    for (int idx = threadIdx.x; idx < nev * nA; idx += blockDim.x) {
+      const int i = fe + 2 * (idx % nev), jj = r0 - ko + idx / nev;
+      const bool in = kin && jj >= lo && jj <= hi;
+      double *a = A + (i - r0) + nR * (jj - (r0 - ko));
+      double v = in ? pk[(size_t)(jj + Gi) * Wd + (i + Gi)] : 0.0;
+      if (NT) v = fma(U, a[-1] + a[1], v);
+      *a = v;
     }
     __syncthreads();
-    // z pass for output plane k = kk - hm (ring slot of k: kk's slot - hm mod R)
-    const int k = kk - hm;
-    if (k >= r0) {
-      const int sk = (slot + hm + 1) % R;
-      for (int idx = threadIdx.x; idx < nR * nR; idx += blockDim.x) {
-        const int i = r0 + idx % nR, j = r0 + idx / nR;
-        double s = 0.0;
-        if ((i | j | k) & 1) {
-          const double *rp = ring + idx;
-          auto at = [&](int t) {
-            int sl = sk + t;
+    // y pass into ring plane kk: odd rows, then even rows
+    double *rp = ring + slot * pl;
+    for (int idx = threadIdx.x; idx < nR * nodd; idx += blockDim.x) {
+      const int ii = idx % nR, j = fo + 2 * (idx / nR);
+      rp[ii + nR * (j - r0)] = gsum(A + ii + nR * (j - (r0 - ko)), nR);
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nR * nev; idx += blockDim.x) {
+      const int ii = idx % nR, j = fe + 2 * (idx / nR);
+      double *r = rp + ii + nR * (j - r0);
+      double v = A[ii + nR * (j - (r0 - ko))];
+      if (NT) v = fma(U, r[-(long)nR] + r[nR], v);
+      *r = v;
+    }
+    __syncthreads();
+    // z: odd plane k1 = kk - ko (planes k1-ko .. k1+ko are in the ring), then
+    // the even plane k1 - 1 from its ring plane and the odd planes around it
+    const int k1 = kk - ko;
+    if ((k1 & 1) && k1 >= r0 && k1 <= r1 + 1) {
+      const int s1 = (slot + ko + 1) % R;  // ring slot of plane k1
+      double *d1 = dz + (((k1 - fo) >> 1) & 1) * pl, *d0 = dz + ((((k1 - fo) >> 1) + 1) & 1) * pl;
+      if (k1 <= r1) {
+        for (int idx = threadIdx.x; idx < (int)pl; idx += blockDim.x) {
+          const double *c = ring + idx;
+          double v = c[s1 * pl];
+#pragma unroll
+          for (int t = -ko; t <= ko; t += 2) {
+            int sl = s1 + t;
             sl += sl < 0 ? R : 0;
             sl -= sl >= R ? R : 0;
-            return rp[(size_t)sl * nR * nR];
-          };
-          if (k & 1)
-            for_taps<N, NT, FK_G>([&](int t, double w) { s = racc(s, w, at(t)); });
-          else
-            for_taps<N, NT, FK_H>([&](int t, double w) { s = racc(s, w, at(t)); });
+            v = fma(-Wav<N, NT>::K(t), c[sl * pl], v);
+          }
+          d1[idx] = v;
+          emit(r0 + idx % nR, r0 + idx / nR, k1, idx, v);
         }
-        emit(i, j, k, idx, s);
+      }
+      __syncthreads();
+      const int k0 = k1 - 1;
+      if (k0 >= r0 && k0 <= r1) {
+        const int s0 = s1 == 0 ? R - 1 : s1 - 1;
+        for (int idx = threadIdx.x; idx < (int)pl; idx += blockDim.x) {
+          const int i = r0 + idx % nR, j = r0 + idx / nR;
+          double v = 0.0;
+          if ((i | j) & 1) {
+            v = ring[s0 * pl + idx];
+            if (NT) v = fma(U, d0[idx] + d1[idx], v);
+          }
+          emit(i, j, k0, idx, v);
+        }
       }
     }
     __syncthreads();
@@ -109,8 +146,8 @@ __global__ void __launch_bounds__(512) k_criterion(Tree t, const double *__restr
 template <int N, int NT>
 static size_t crit_smem(int nb) {
   using W = Wav<N, NT>;
-  const int nR = nb + W::ext_f + W::ext_b, hm = W::hmax;
-  return sizeof(double) * ((size_t)(2 * hm + 1) * nR * nR + (size_t)nR * (nR + 2 * hm));
+  const int nR = nb + W::ext_f + W::ext_b, ko = N - 1;
+  return sizeof(double) * ((size_t)(2 * ko + 3) * nR * nR + (size_t)nR * (nR + 2 * ko));
 }
 
 template <int N, int NT>
