@@ -243,6 +243,15 @@ int mr_query(mr_grid *grid, mr_stats *stats);
 int mr_profile(mr_grid *grid, int enable);
 int mr_profile_read(mr_grid *grid, int kid, double *total_ms, int *nlaunch, const char **name);
 int mr_launch_count(mr_grid *grid, long long *n);
+/* Algorithmic bytes of the recorded launches of kernel kid (the roofline
+ * numerator), accumulated on the device while profiling is on.  Defined for
+ * the ghost pre-pass (kid 0): every ghost point of the padded block of each
+ * leaf the launch reconstructs is written once and its source value read
+ * once, (Wd^3 - nb^3) * (source + padded element size) per leaf, Wd the
+ * padded width; leaves a launch skips (need mask, stencil pre-pass of a leaf
+ * without coarser neighbours) count zero.  0 for other kernels.
+ * Synchronises; *bytes (host) receives the sum since the last mr_profile(1). */
+int mr_profile_bytes(mr_grid *grid, int kid, double *bytes);
 
 /* Device pointer of field fid (slot-major layout above). */
 int mr_field_ptr(mr_grid *grid, int fid, void **ptr);

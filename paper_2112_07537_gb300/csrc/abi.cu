@@ -305,8 +305,23 @@ static const char *kernel_names[MRK_COUNT] = {
 
 int mr_profile(mr_grid *g, int enable) {
   if (!g) return MR_ERR_INVALID;
-  if (enable) g->nrec = 0;
+  if (enable) {
+    g->nrec = 0;
+    if (check_cuda(cudaMemsetAsync(g->dscratch + MR_ALG_BYTES_SLOT, 0, sizeof(double) * MRK_COUNT, g->stream),
+                   "profile reset"))
+      return MR_ERR_CUDA;
+  }
   g->profiling = enable ? 1 : 0;
+  return MR_OK;
+}
+
+int mr_profile_bytes(mr_grid *g, int kid, double *bytes) {
+  if (!g || !bytes || kid < 0 || kid >= MRK_COUNT) return MR_ERR_INVALID;
+  if (check_cuda(cudaMemcpyAsync(bytes, g->dscratch + MR_ALG_BYTES_SLOT + kid, sizeof(double),
+                                 cudaMemcpyDeviceToHost, g->stream),
+                 "profile bytes") ||
+      check_cuda(cudaStreamSynchronize(g->stream), "profile bytes sync"))
+    return MR_ERR_CUDA;
   return MR_OK;
 }
 

@@ -505,6 +505,27 @@ __global__ void k_crop(const TP *__restrict__ P, int Gi, TO *__restrict__ out, i
   }
 }
 
+// Profiling only: units a launch processed (leaves whose flag is set, all
+// leaves without flags) times the algorithmic bytes of one unit, added to the
+// kernel's accumulator.
+__global__ void k_units(const int *__restrict__ flags, int n, double bytes_per_unit, double *acc) {
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  int c = 0;
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < n; b += gridDim.x * blockDim.x)
+    c += flags ? (flags[b] != 0) : 1;
+  atomicAdd(&cnt, c);
+  __syncthreads();
+  if (threadIdx.x == 0 && cnt) atomicAdd(acc, cnt * bytes_per_unit);
+}
+
+void count_units(mr_grid *g, int kid, const int *flags, int n, double bytes_per_unit) {
+  if (!g->profiling || n < 1) return;
+  MR_LAUNCH(g, MRK_MISC, k_units<<<(n + 255) / 256, 256, 0, g->stream>>>(flags, n, bytes_per_unit,
+                                                                         g->dscratch + MR_ALG_BYTES_SLOT + kid));
+}
+
 // internal shell: the requested one, the substitution reach, and what the
 // part-2 coarsening of a finer neighbour reads
 static int internal_shell(int N, int Nt, int G, int nb) {
@@ -542,6 +563,11 @@ static int ghost_impl(mr_grid *g, const TI *phi_in, TI *phi_out, int G, TP *P, T
                                                                            use_tile, (int)smT, zc, g->cmask, err,
                                                                            need));
   if (check_cuda(cudaGetLastError(), "k_prep")) return MR_ERR_CUDA;
+  {
+    const double wd = nb + 2.0 * Gi;
+    count_units(g, MRK_PART1, only_coarse ? g->cmask : need, n,
+                (wd * wd * wd - (double)nb * nb * nb) * (double)(sizeof(TI) + sizeof(TP)));
+  }
   if (only_coarse) return MR_OK;
   MR_LAUNCH(g, MRK_MERGE, k_merge<TI, TP><<<n, 256, 0, g->stream>>>(t, P, Q, Gi, G, g->cmask, phi_out, need));
   if (check_cuda(cudaGetLastError(), "k_merge")) return MR_ERR_CUDA;

@@ -403,6 +403,10 @@ struct mr_grid {
   int ev_ready;
 };
 
+// dscratch[MR_ALG_BYTES_SLOT + kid]: algorithmic bytes of kernel kid while
+// profiling (dscratch holds 64 doubles; [0] is the mass reduction)
+#define MR_ALG_BYTES_SLOT 32
+
 // kernel ids of the launch registry
 enum {
   MRK_PART1 = 0, MRK_PART2, MRK_MERGE, MRK_CROP, MRK_RHS, MRK_COMBINE, MRK_FIELDSET, MRK_MASS,
@@ -427,6 +431,7 @@ void *field_ptr(mr_grid *g, int fid);      // fid >= nfields: temporaries
 void *next_field_ptr(mr_grid *g, int fid);
 
 // ghost.cu
+void count_units(mr_grid *g, int kid, const int *flags, int n, double bytes_per_unit);
 int launch_ghost(mr_grid *g, const void *phi_in, void *phi_out, int G, bool fp64, void **P,
                  int *Gi, bool *p_is64 = nullptr, const int *need = nullptr);
 int launch_crop(mr_grid *g, const void *P, int Gi, void *out, int G, bool fp64_src);

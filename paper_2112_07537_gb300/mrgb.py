@@ -29,7 +29,7 @@ EXPORTS = ["mr_last_error", "mr_workspace_size", "mr_grid_create", "mr_grid_dest
            "mr_grid_leaves", "mr_field_copy_in", "mr_field_copy_out", "mr_field_set",
            "mr_ghost_fill", "mr_ghost_fill64", "mr_sync", "mr_rhs_advect", "mr_rk_stage",
            "mr_step", "mr_criterion", "mr_adapt", "mr_adapt_iter", "mr_mass", "mr_query",
-           "mr_field_ptr", "mr_profile", "mr_profile_read", "mr_launch_count",
+           "mr_field_ptr", "mr_profile", "mr_profile_read", "mr_launch_count", "mr_profile_bytes",
            "mr_ghost_fill_static", "mr_rhs_advect_vel", "mr_step_vel", "mr_velocity_invalidate"]
 
 
@@ -91,6 +91,7 @@ def load(path: str = LIB_PATH):
         L.mr_field_ptr.argtypes = [vp, C.c_int, C.POINTER(vp)]
         L.mr_profile.argtypes = [vp, C.c_int]
         L.mr_profile_read.argtypes = [vp, C.c_int, dp, C.POINTER(C.c_int), C.POINTER(C.c_char_p)]
+        L.mr_profile_bytes.argtypes = [vp, C.c_int, dp]
         L.mr_launch_count.argtypes = [vp, C.POINTER(C.c_longlong)]
         _lib = L
     return _lib
@@ -279,6 +280,12 @@ class Grid:
             if n.value:
                 out[name.value.decode()] = (t.value, n.value)
         return out
+
+    def profile_bytes(self, kid=0):
+        """Algorithmic bytes of the recorded launches of kernel id kid."""
+        b = C.c_double()
+        _chk(load().mr_profile_bytes(self.h, kid, C.byref(b)))
+        return b.value
 
     def launch_count(self):
         n = C.c_longlong()

@@ -256,3 +256,26 @@ def test_velocity_field_rhs_and_steps(mr, oracle_mod, prec, scheme):
         ref = O.rk3_step_velpad(og, ref, vpads, dt, scheme)
     err = np.abs(g.field_copy_out(0).astype(np.float64) - ref).max() / np.abs(ref).max()
     assert err <= (1e-12 if prec == 1 else 1e-5), err
+
+
+def test_profile_bytes_of_a_full_ghost_fill(mr, oracle_mod):
+    """The ghost pre-pass's algorithmic bytes (roofline numerator): every
+    ghost point of every leaf's padded block written once and its source
+    value read once."""
+    import torch
+    O = oracle_mod
+    nb, N, Nt, G = 16, 4, 2, 3
+    nt, tl, lev, anc = _three_level(nb)
+    g, og = _grid(mr, O, nt, tl, nb, N, Nt, lev, anc, mr.F32, 2)
+    g.field_copy_in(0, np.zeros((og.nleaf, nb, nb, nb), np.float32))
+    W = nb + 2 * G
+    pad = torch.empty((og.nleaf, W, W, W), dtype=torch.float32, device="cuda")
+    g.profile(True)
+    g.ghost_fill(0, G, pad)
+    g.sync()
+    got = g.profile_bytes(0)
+    g.profile(False)
+    Gi = max(G, N, N - 1, 2 * G + N - nb)  # internal shell of the padded block
+    Wd = nb + 2 * Gi
+    assert got == og.nleaf * (Wd ** 3 - nb ** 3) * (4 + 4)
+    assert g.profile_bytes(5) == 0.0
