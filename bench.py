@@ -45,6 +45,8 @@ WORKLOADS = {"fixed-large": (0.35, 0.25, 0.17, 0.11, 0.06),   # 42 400 leaves, 5
              "fixed-medium": (0.35, 0.25, 0.17),              # 11 768 leaves, 163 M points
              "fixed-small": (0.3, 0.2)}                       # 3 424 leaves, 47 M points
 GAUSS = dict(seed=5, n=48, smin=0.0015, smax=0.006)  # large single grid scalar
+# the same adaptive path on a small grid (for profiler captures of a few GB)
+GAUSS_SMALL = dict(seed=5, n=3, smin=0.0015, smax=0.006)
 EPS_R, EPS_C, CFL, ADAPT_EVERY = 1e-5, 1e-7, 0.5, 2
 U = (1.0, 0.5, 0.25)
 
@@ -66,14 +68,14 @@ def gauss_params(seed, n, smin, smax):
 TG = (1.0, 0.3)  # Taylor-Green scale and phase (seeded constants of the velocity field)
 
 
-def init_large(mrgb, stream, prec, cap):
+def init_large(mrgb, stream, prec, cap, gauss=GAUSS):
     """Initial adapted grid (untimed): uniform level 3, then alternate analytic
     sampling and refinement until no block refines, sample again, and run
     one full adaptation."""
     lev, anc = I.uniform_leaves((1, 1, 1), 3)
     g = mrgb.Grid((1, 1, 1), 1.0, 24, 3, 8, 6, 2, lev, anc, precision=prec, nfields=4,
                   capacity=cap, stream=stream, velocity=True)
-    p = gauss_params(**GAUSS)
+    p = gauss_params(**gauss)
     for _ in range(12):
         g.field_set(0, mrgb.INIT_GAUSSIAN_SUM, p)
         if g.adapt_iter(0, EPS_R, EPS_C, flags=mrgb.ADAPT_REFINE) == 0:
@@ -176,7 +178,7 @@ def main():
     ap.add_argument("--scheme", default="wenoz5", choices=["wenoz5", "cons5", "cons3"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="large", choices=["large"] + sorted(WORKLOADS))
+    ap.add_argument("--workload", default="large", choices=["large", "adaptive-small"] + sorted(WORKLOADS))
     ap.add_argument("--capacity", type=int, default=60000)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -198,11 +200,12 @@ def main():
     prec = mrgb.F32 if args.precision == "f32" else mrgb.F64
     scheme = {"wenoz5": mrgb.WENOZ5, "cons5": mrgb.CONS5, "cons3": mrgb.CONS3}[args.scheme]
     nb = 24
-    adaptive = args.workload == "large"
+    adaptive = args.workload in ("large", "adaptive-small")
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         if adaptive:
-            g = init_large(mrgb, stream, prec, args.capacity)
+            g = init_large(mrgb, stream, prec, args.capacity,
+                           GAUSS if args.workload == "large" else GAUSS_SMALL)
             lmax = 8
             umax = 2.0 * TG[0]  # |u| + |v| <= 2 s for the Taylor-Green-like field
         else:
@@ -238,6 +241,8 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     l0 = g.launch_count()
+    cudart = torch.cuda.cudart()
+    cudart.cudaProfilerStart()  # an attached profiler captures the timed steps only
     g.profile(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     psu_count = 0
@@ -247,6 +252,7 @@ def main():
     e1.record(stream)
     e1.synchronize()
     g.profile(False)
+    cudart.cudaProfilerStop()
     ms = e0.elapsed_time(e1)
     launches = g.launch_count() - l0
     torch.cuda.synchronize()
@@ -296,9 +302,10 @@ def main():
         alg["ghost_part1"] = ghost_bytes / prof["ghost_part1"][1]
     per_launch = alg.get(name, None)
     achieved = per_launch / (tot / cnt / 1e3) / 1e9 if per_launch else None
-    workload = ("large single grid, adaptive: 1 tree, 24^3 blocks, levels 3-8, "
-                f"{stats0.nleaf}->{stats1.nleaf} leaves; FP32 scalar (48 seeded Gaussians, sigma "
-                f"{GAUSS['smin']}-{GAUSS['smax']}) + 3 velocity fields (Taylor-Green-like, scale "
+    gs = GAUSS if args.workload == "large" else GAUSS_SMALL
+    workload = (f"{args.workload} single grid, adaptive: 1 tree, 24^3 blocks, levels 3-8, "
+                f"{stats0.nleaf}->{stats1.nleaf} leaves; FP32 scalar ({gs['n']} seeded Gaussians, sigma "
+                f"{gs['smin']}-{gs['smax']}) + 3 velocity fields (Taylor-Green-like, scale "
                 f"{TG[0]}, phase {TG[1]}); 6.2 lifted wavelet, eps_r {EPS_R}, eps_c {EPS_C}; "
                 f"{args.scheme} + RK3, CFL {CFL}; adapt every {ADAPT_EVERY} steps"
                 if adaptive else
