@@ -65,6 +65,8 @@ def _declare(L):
     L.og_ghost_fill.argtypes = [C.POINTER(_Grid), _dp, C.c_int, _dp, _dp]
     L.og_rhs.argtypes = [C.POINTER(_Grid), _dp, C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp]
     L.og_rk3_step.argtypes = [C.POINTER(_Grid), _dp, C.c_double, C.c_int, _dp]
+    L.og_laplacian.argtypes = [C.POINTER(_Grid), _dp, C.c_int, C.c_int, _dp]
+    L.og_rk3_step_diff.argtypes = [C.POINTER(_Grid), _dp, C.c_double, C.c_int, _dp, C.c_double, C.c_int]
     L.og_dt.argtypes = [C.POINTER(_Grid), C.c_double, _dp]
     L.og_dt.restype = C.c_double
     L.og_moments.argtypes = [C.POINTER(_Grid), _dp, _dp, _dp]
@@ -151,6 +153,22 @@ def rhs(g: Grid, pad: np.ndarray, G: int, scheme: int, u=(1.0, 1.0, 1.0), vel=No
     _check(lib().og_rhs(g.c(), _d(pad), G, scheme, _d(uc), _d(vs[0]), _d(vs[1]), _d(vs[2]),
                         _d(out)), "rhs")
     return out
+
+
+def laplacian(g: Grid, pad: np.ndarray, G: int, order: int):
+    """DIFF-2 / DIFF-4 central Laplacian of a padded field (shell G)."""
+    pad = np.ascontiguousarray(pad, dtype=np.float64)
+    out = np.empty((g.nleaf, g.nb, g.nb, g.nb))
+    _check(lib().og_laplacian(g.c(), _d(pad), G, order, _d(out)), "laplacian")
+    return out
+
+
+def rk3_step_diff(g: Grid, phi: np.ndarray, dt: float, scheme: int, u, nu: float, order: int):
+    """RK3 step of d phi/dt = -div(u phi) + nu Laplacian(phi), constant u."""
+    phi = np.ascontiguousarray(phi, dtype=np.float64).copy()
+    uc = np.asarray(u, dtype=np.float64)
+    _check(lib().og_rk3_step_diff(g.c(), _d(phi), dt, scheme, _d(uc), float(nu), int(order)), "rk3_step_diff")
+    return phi.reshape(g.nleaf, g.nb, g.nb, g.nb)
 
 
 def rk3_step(g: Grid, phi: np.ndarray, dt: float, scheme: int, u=(1.0, 1.0, 1.0)):

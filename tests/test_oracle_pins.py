@@ -444,3 +444,94 @@ def test_rk3_gaussian_translate_converges(oracle_mod):
         ex = I.gaussian_images(xyz, (0.5 + T, 0.5 + T, 0.5 + T), 0.1, nimg=1)
         errs.append(np.abs(phi - ex).max())
     assert errs[1] < errs[0] / 6, errs
+
+
+# ---------------------------------------------------------------- DIFF-2/4
+def _lambda_diff(order, theta, h):
+    """Discrete symbol of the central second difference on exp(i theta j)."""
+    if order == 2:
+        return (2 * np.cos(theta) - 2) / h ** 2
+    return (-2 * np.cos(2 * theta) + 32 * np.cos(theta) - 30) / (12 * h ** 2)
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_laplacian_discrete_symbol(oracle_mod, order):
+    """DIFF-2 / DIFF-4 (Sec. 4.3) on a uniform periodic grid: a Fourier mode
+    sin(2 pi m.x + c) is an eigenvector of the central Laplacian with
+    eigenvalue sum_d lambda(2 pi m_d h) -- a closed form that any wrong
+    coefficient, sign, offset or direction breaks."""
+    O = oracle_mod
+    nt, tl, nb, L = (1, 1, 1), 1.0, 8, 1
+    lev, anc = I.uniform_leaves(nt, L)
+    g = O.Grid(nt, tl, nb, 4, 0, 0, L, lev, anc)
+    X, Y, Z = I.point_coords(nt, tl, nb, lev, anc)
+    h = tl / (nb * 2 ** L)
+    m = (1, 3, 2)
+    f = np.sin(2 * np.pi * (m[0] * X + m[1] * Y + m[2] * Z) + 0.3)
+    pad, _ = O.ghost_fill(g, f, 3)
+    lap = O.laplacian(g, pad, 3, order)
+    lam = sum(_lambda_diff(order, 2 * np.pi * md * h, h) for md in m)
+    assert np.abs(lap - lam * f).max() <= 1e-9 * abs(lam)
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_laplacian_design_order(oracle_mod, order):
+    """The central Laplacians converge at their design order to the exact
+    Laplacian of a smooth periodic field."""
+    O = oracle_mod
+    errs = []
+    for L in (1, 2):
+        nt, tl, nb = (1, 1, 1), 1.0, 8
+        lev, anc = I.uniform_leaves(nt, L)
+        g = O.Grid(nt, tl, nb, 4, 0, 0, L, lev, anc)
+        X, Y, Z = I.point_coords(nt, tl, nb, lev, anc)
+        k = 2 * np.pi
+        f = np.sin(k * X) * np.cos(k * Y) * np.sin(k * Z + 0.3)
+        pad, _ = O.ghost_fill(g, f, 3)
+        errs.append(np.abs(O.laplacian(g, pad, 3, order) - (-3 * k * k) * f).max())
+    assert abs(np.log2(errs[0] / errs[1]) - order) < 0.3, errs
+
+
+@pytest.mark.parametrize("N,order,lo,hi", [(4, 4, 1.5, 2.7), (6, 4, 3.4, 4.9), (4, 2, 1.6, 2.6)])
+def test_two_level_laplacian_order_across_jump(oracle_mod, N, order, lo, hi):
+    """P7 (Sec. 4.3): across face, edge and corner resolution jumps the
+    Laplacian error converges as h^min(k, N - 2): 2nd order with 4.0 ghosts
+    whatever the stencil, 4th order for DIFF-4 with 6.0 ghosts."""
+    O = oracle_mod
+    errs = []
+    for nb in (16, 32):
+        nt, tl = (1, 1, 1), 1.0
+        lev, anc = I.uniform_leaves(nt, 1)
+        lev, anc = I.refine_leaves(lev, anc, np.all(anc == 0, axis=1))
+        g = O.Grid(nt, tl, nb, N, 0, 0, 2, lev, anc)
+        xyz = I.point_coords(nt, tl, nb, lev, anc)
+        c, s = (0.45, 0.45, 0.45), 0.1
+        f = I.gaussian(xyz, c, s)
+        d = [I.periodic_delta(xyz[i], c[i], 1.0) for i in range(3)]
+        r2 = sum(di ** 2 for di in d)
+        ex = (4 * r2 / s ** 4 - 6 / s ** 2) * f  # Laplacian of exp(-r^2/s^2)
+        pad, _ = O.ghost_fill(g, f, 3)
+        errs.append(np.abs(O.laplacian(g, pad, 3, order) - ex).max())
+    p = np.log2(errs[0] / errs[1])
+    assert lo < p < hi, (errs, p)
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_rk3_diffusion_amplification(oracle_mod, order):
+    """Pure diffusion of one Fourier mode on a uniform grid: each RK3-TVD step
+    multiplies it by 1 + z + z^2/2 + z^3/6, z = dt nu lambda (lambda the
+    discrete symbol) -- closed form of the stage combination."""
+    O = oracle_mod
+    nt, tl, nb, L = (1, 1, 1), 1.0, 8, 1
+    lev, anc = I.uniform_leaves(nt, L)
+    g = O.Grid(nt, tl, nb, 4, 0, 0, L, lev, anc)
+    X, Y, Z = I.point_coords(nt, tl, nb, lev, anc)
+    h = tl / (nb * 2 ** L)
+    m = (2, 1, 1)
+    f = np.sin(2 * np.pi * (m[0] * X + m[1] * Y + m[2] * Z) + 0.7)
+    nu, dt = 0.01, 0.2 * h * h / 0.01 / 6
+    lam = sum(_lambda_diff(order, 2 * np.pi * md * h, h) for md in m)
+    z = dt * nu * lam
+    amp = 1 + z + z * z / 2 + z ** 3 / 6
+    out = O.rk3_step_diff(g, f, dt, O.CONS5, (0.0, 0.0, 0.0), nu, order)
+    assert np.abs(out - amp * f).max() <= 1e-12
