@@ -180,6 +180,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="large", choices=["large", "adaptive-small"] + sorted(WORKLOADS))
     ap.add_argument("--capacity", type=int, default=60000)
+    ap.add_argument("--diffusion", type=int, default=0, choices=[0, 2, 4],
+                    help="add nu * DIFF-2/DIFF-4 Laplacian to the stencil step")
+    ap.add_argument("--nu", type=float, default=1e-4)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -216,6 +219,10 @@ def main():
             g.field_set(0, mrgb.INIT_GAUSSIAN, [0.5, 0.5, 0.5, 0.08, 1.0])
             umax = sum(abs(u) for u in U)
     dt = CFL * (1.0 / (nb * 2 ** lmax)) / umax
+    if args.diffusion:
+        g.set_diffusion(args.nu, args.diffusion)
+        hmin = 1.0 / (nb * 2 ** lmax)
+        dt = min(dt, 0.1 * hmin * hmin / args.nu)  # explicit diffusion limit
     stats0 = g.query()
 
     def one_step(i):
@@ -319,7 +326,8 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": {"workload": workload, "leaves": [stats0.nleaf, stats1.nleaf],
                    "mean_points": mean_pts, "l2": "fields larger than L2 (no flush)",
-                   "scheme": args.scheme, "precision": args.precision},
+                   "scheme": args.scheme, "precision": args.precision,
+                   "diffusion": f"DIFF-{args.diffusion}, nu={args.nu}" if args.diffusion else None},
         "roofline": {"bound": "hbm", "kernel": name,
                      "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm if achieved else None, "peak_source": src,

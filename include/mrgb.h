@@ -232,6 +232,19 @@ int mr_mass(mr_grid *grid, int fid, double *mass);
 /* Leaf counts.  Synchronises. */
 int mr_query(mr_grid *grid, mr_stats *stats);
 
+/* Diffusion term of the stencil step: every following mr_rhs_advect,
+ * mr_rhs_advect_vel, mr_step and mr_step_vel adds nu times the central
+ * Laplacian of the same ghost-filled field to the advection right-hand side,
+ *   d phi / dt = -div(u phi) + nu * Laplacian(phi),
+ * order 2: DIFF-2, sum_d (f[i-1] - 2 f[i] + f[i+1]) / h^2;
+ * order 4: DIFF-4, sum_d (-f[i-2] + 16 f[i-1] - 30 f[i] + 16 f[i+1] - f[i+2]) / (12 h^2)
+ * (Sec. 4.3 names second- and fourth-order central Laplacians; h is the
+ * leaf's grid spacing).  order 0 or nu = 0 removes the term (the default).
+ * The time step stays the caller's: explicit diffusion also needs
+ * dt <= c h_min^2 / nu.  Errors: MR_ERR_INVALID for a negative or non-finite
+ * nu or another order.  No device work. */
+int mr_set_diffusion(mr_grid *grid, double nu, int order);
+
 /* Launch registry (the per-operation timers of the library).
  * mr_profile(grid, 1) clears the records and brackets every following kernel
  * launch with CUDA events on the grid's stream (up to 4096 launches);

@@ -2,6 +2,7 @@
 // the initial leaves, owner map, balance check), field transfers and the
 // drivers that chain the ghost, stencil and adaptation kernels.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -259,6 +260,8 @@ int mr_grid_create(const mr_grid_desc *desc, void *workspace, size_t workspace_b
   g->vpad = (desc->flags & MR_GRID_VELOCITY) ? (void *)(w + L.off[24]) : nullptr;
   g->tree_version = 0;
   g->vel_version = -1;
+  g->diff_nu = 0.0;
+  g->diff_order = 0;
   g->shell_rk = srk;
   g->shell_ad = sad;
   g->map_cells = mc;
@@ -302,6 +305,14 @@ static const char *kernel_names[MRK_COUNT] = {
     "ghost_part1", "ghost_part2", "ghost_merge", "ghost_crop", "rhs_stage", "rk_combine",
     "field_set", "mass", "owner_map", "balance_check", "criterion", "status", "policy", "scan",
     "emit", "interpolate", "update", "misc"};
+
+int mr_set_diffusion(mr_grid *g, double nu, int order) {
+  if (!g || !(nu >= 0.0) || !std::isfinite(nu) || (order != 0 && order != 2 && order != 4)) return MR_ERR_INVALID;
+  if (order == 0) nu = 0.0;
+  g->diff_nu = nu;
+  g->diff_order = nu > 0.0 ? order : 0;
+  return MR_OK;
+}
 
 int mr_profile(mr_grid *g, int enable) {
   if (!g) return MR_ERR_INVALID;

@@ -393,6 +393,8 @@ struct mr_grid {
   int tree_version;       // bumped whenever the leaves change
   int vel_version;        // tree version the velocity cache was built for (-1: none)
   int vel_fid[3];
+  double diff_nu;         // diffusion coefficient of the stencil step (0: none)
+  int diff_order;         // 0, 2 (DIFF-2) or 4 (DIFF-4)
   // launch registry: counts every kernel launch; with profiling on, brackets
   // each launch with CUDA events on the grid's stream
   long long launches[32];

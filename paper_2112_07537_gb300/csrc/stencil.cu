@@ -64,10 +64,27 @@ __device__ __forceinline__ T iface_flux(const T *f, bool left) {
 
 // One CTA per leaf: rhs from the padded block P (shell Gi >= 3), then the RK
 // stage combination (or the bare rhs).  u: u^n (stages 1, 2), may alias out.
+// Central Laplacian at *c (Sec. 4.3, DIFF-2 / DIFF-4), unscaled by 1/h^2:
+// sum over the three directions of the 1D second difference along it.
+template <typename T>
+__device__ __forceinline__ T lap_at(const T *c, const int *stride, int diff) {
+  T s = T(0);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int st = stride[d];
+    if (diff == 2)
+      s += (c[-st] + c[st]) - T(2) * c[0];
+    else
+      s += (T(16) * (c[-st] + c[st]) - (c[-2 * st] + c[2 * st]) - T(30) * c[0]) * T(1.0 / 12);
+  }
+  return s;
+}
+
 template <typename T, int SCHEME>
 __global__ void __launch_bounds__(256) k_rhs_stage(Tree t, const T *__restrict__ P, int Gi,
                                                    const T *u, T *out, int stage, T dt, T ux, T uy,
-                                                   T uz, int rhs_only, const T *__restrict__ vpad) {
+                                                   T uz, int rhs_only, const T *__restrict__ vpad, T nu,
+                                                   int diff) {
   // vpad: ghost-filled velocity components (shell 3) or null for constant u
   const int b = blockIdx.x;
   const int nb = t.nb, Wd = nb + 2 * Gi;
@@ -96,7 +113,8 @@ __global__ void __launch_bounds__(256) k_rhs_stage(Tree t, const T *__restrict__
       const bool lp = uu[3] + uu[4] >= T(0), lm = uu[2] + uu[3] >= T(0);
       acc += iface_flux<T, SCHEME>(f + 1, lp) - iface_flux<T, SCHEME>(f, lm);
     }
-    const T r = -acc / h;
+    T r = -acc / h;
+    if (diff) r += nu * lap_at<T>(Pb + c, stride, diff) / (h * h);
     const size_t q = (size_t)b * nb * nb * nb + p;
     if (rhs_only) {
       out[q] = r;
@@ -128,7 +146,8 @@ template <int N, int NT, int SCHEME, bool VEL>
 __global__ void __launch_bounds__(1024) k_fused(Tree t, const float *__restrict__ phi, const float *__restrict__ P,
                                                const float *__restrict__ Q, int Gi, const int *__restrict__ cmask,
                                                const float *u, float *out, int stage, float dt, float ux, float uy,
-                                               float uz, int rhs_only, int *err, const float *__restrict__ vpad) {
+                                               float uz, int rhs_only, int *err, const float *__restrict__ vpad,
+                                               float nu, int diff) {
   using W = Wav<N, NT>;
   constexpr int GS = 3;
   const int b = blockIdx.x, nb = t.nb, Ws = nb + 2 * GS, Wd = nb + 2 * Gi;
@@ -291,7 +310,11 @@ __global__ void __launch_bounds__(1024) k_fused(Tree t, const float *__restrict_
   const float invh = 1.0f / h;
   for (int p = threadIdx.x; p < (int)nb3; p += blockDim.x) {
     const int i = p % nb, j = (p / nb) % nb, k = p / (nb * nb);
-    const float r = -R[p] * invh;
+    float r = -R[p] * invh;
+    if (diff) {
+      const int sts[3] = {strd[0], strd[1], strd[2]};
+      r += nu * invh * invh * lap_at<float>(tile + tix(i, j, k), sts, diff);
+    }
     const size_t q = (size_t)b * nb3 + p;
     if (rhs_only) {
       out[q] = r;
@@ -315,11 +338,11 @@ static int rhs_dispatch(mr_grid *g, const T *P, int Gi, const T *u, T *out, int 
   if (!uc) uc = zero3;
   const T ux = T(uc[0]), uy = T(uc[1]), uz = T(uc[2]);
   if (scheme == MR_CONS3)
-    MR_LAUNCH(g, MRK_RHS, k_rhs_stage<T, MR_CONS3><<<n, 256, 0, g->stream>>>(t, P, Gi, u, out, stage, T(dt), ux, uy, uz, rhs_only, vpad));
+    MR_LAUNCH(g, MRK_RHS, k_rhs_stage<T, MR_CONS3><<<n, 256, 0, g->stream>>>(t, P, Gi, u, out, stage, T(dt), ux, uy, uz, rhs_only, vpad, T(g->diff_nu), g->diff_order));
   else if (scheme == MR_CONS5)
-    MR_LAUNCH(g, MRK_RHS, k_rhs_stage<T, MR_CONS5><<<n, 256, 0, g->stream>>>(t, P, Gi, u, out, stage, T(dt), ux, uy, uz, rhs_only, vpad));
+    MR_LAUNCH(g, MRK_RHS, k_rhs_stage<T, MR_CONS5><<<n, 256, 0, g->stream>>>(t, P, Gi, u, out, stage, T(dt), ux, uy, uz, rhs_only, vpad, T(g->diff_nu), g->diff_order));
   else if (scheme == MR_WENOZ5)
-    MR_LAUNCH(g, MRK_RHS, k_rhs_stage<T, MR_WENOZ5><<<n, 256, 0, g->stream>>>(t, P, Gi, u, out, stage, T(dt), ux, uy, uz, rhs_only, vpad));
+    MR_LAUNCH(g, MRK_RHS, k_rhs_stage<T, MR_WENOZ5><<<n, 256, 0, g->stream>>>(t, P, Gi, u, out, stage, T(dt), ux, uy, uz, rhs_only, vpad, T(g->diff_nu), g->diff_order));
   else
     return MR_ERR_INVALID;
   return check_cuda(cudaGetLastError(), "k_rhs_stage") ? MR_ERR_CUDA : MR_OK;
@@ -365,7 +388,7 @@ static int fused_impl(mr_grid *g, const float *phi, const float *P, const float 
       return MR_ERR_CUDA;                                                                                 \
     MR_LAUNCH(g, MRK_RHS, k_fused<N, NT, S, VEL><<<g->nleaf, threads, sm, g->stream>>>(                       \
                               t, phi, P, Q, Gi, g->cmask, u, out, stage, (float)dt, ux, uy, uz, rhs_only, \
-                              g->counter + 1, vpad));                                                     \
+                              g->counter + 1, vpad, (float)g->diff_nu, g->diff_order));                   \
   } while (0)
   if (scheme == MR_CONS3) MR_FL(MR_CONS3);
   else if (scheme == MR_CONS5) MR_FL(MR_CONS5);

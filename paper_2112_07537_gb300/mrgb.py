@@ -29,7 +29,7 @@ EXPORTS = ["mr_last_error", "mr_workspace_size", "mr_grid_create", "mr_grid_dest
            "mr_grid_leaves", "mr_field_copy_in", "mr_field_copy_out", "mr_field_set",
            "mr_ghost_fill", "mr_ghost_fill64", "mr_sync", "mr_rhs_advect", "mr_rk_stage",
            "mr_step", "mr_criterion", "mr_adapt", "mr_adapt_iter", "mr_mass", "mr_query",
-           "mr_field_ptr", "mr_profile", "mr_profile_read", "mr_launch_count", "mr_profile_bytes",
+           "mr_field_ptr", "mr_profile", "mr_profile_read", "mr_launch_count", "mr_profile_bytes", "mr_set_diffusion",
            "mr_ghost_fill_static", "mr_rhs_advect_vel", "mr_step_vel", "mr_velocity_invalidate"]
 
 
@@ -92,6 +92,7 @@ def load(path: str = LIB_PATH):
         L.mr_profile.argtypes = [vp, C.c_int]
         L.mr_profile_read.argtypes = [vp, C.c_int, dp, C.POINTER(C.c_int), C.POINTER(C.c_char_p)]
         L.mr_profile_bytes.argtypes = [vp, C.c_int, dp]
+        L.mr_set_diffusion.argtypes = [vp, C.c_double, C.c_int]
         L.mr_launch_count.argtypes = [vp, C.POINTER(C.c_longlong)]
         _lib = L
     return _lib
@@ -280,6 +281,10 @@ class Grid:
             if n.value:
                 out[name.value.decode()] = (t.value, n.value)
         return out
+
+    def set_diffusion(self, nu, order):
+        """Add nu * (DIFF-2 or DIFF-4 Laplacian) to the stencil step (order 0: off)."""
+        _chk(load().mr_set_diffusion(self.h, float(nu), int(order)))
 
     def profile_bytes(self, kid=0):
         """Algorithmic bytes of the recorded launches of kernel id kid."""

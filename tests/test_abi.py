@@ -37,3 +37,12 @@ def test_workspace_size_and_descriptor_validation():
     assert L.mr_workspace_size(ctypes.byref(d), ctypes.byref(n)) == -1
     d.nb, d.wav_N = 16, 3
     assert L.mr_workspace_size(ctypes.byref(d), ctypes.byref(n)) == -1
+
+
+def test_set_diffusion_argument_checks():
+    """mr_set_diffusion rejects bad arguments before touching a grid (a null
+    grid is refused first, so no device is needed)."""
+    from paper_2112_07537_gb300 import build, mrgb
+    build.build()
+    L = mrgb.load()
+    assert L.mr_set_diffusion(None, 0.1, 2) == -1  # MR_ERR_INVALID

@@ -279,3 +279,47 @@ def test_profile_bytes_of_a_full_ghost_fill(mr, oracle_mod):
     Wd = nb + 2 * Gi
     assert got == og.nleaf * (Wd ** 3 - nb ** 3) * (4 + 4)
     assert g.profile_bytes(5) == 0.0
+
+
+@pytest.mark.parametrize("order", [2, 4])
+@pytest.mark.parametrize("prec", [1, 0])
+def test_advection_diffusion_rhs_and_steps(mr, oracle_mod, prec, order):
+    """DIFF-2 / DIFF-4 (Sec. 4.3) added to the WENO-Z5 advection right-hand
+    side: rhs and three RK3 steps against the oracle on the two-level tree.
+    FP32 tolerance: the Laplacian scales a ghost or rounding error of
+    ~1e-6 max|phi| by at most 64/12 / h^2, and its own size here is
+    >= 0.1 max|phi| / h^2, so a few 1e-5 of the right-hand side's maximum."""
+    O = oracle_mod
+    nt, tl, nb = (2, 2, 2), 0.5, 16
+    lev, anc = I.tree_config1()
+    g, og = _grid(mr, O, nt, tl, nb, 4, 2, lev, anc, prec, 1, nfields=2)
+    xyz = I.point_coords(nt, tl, nb, og.lev, og.anc)
+    phi = I.gaussian_images(xyz, (0.45, 0.55, 0.5), 0.1, nimg=1)
+    if prec == 0:
+        phi = phi.astype(np.float32)
+    nu, u = 0.01, (1.0, -0.5, 0.25)
+    g.set_diffusion(nu, order)
+    g.field_copy_in(0, phi)
+    g.rhs_advect(0, u, 1, mr.WENOZ5)
+    got = g.field_copy_out(1).astype(np.float64)
+    pad, _ = O.ghost_fill(og, phi.astype(np.float64), 3)
+    ref = O.rhs(og, pad, 3, O.WENOZ5, u) + nu * O.laplacian(og, pad, 3, order)
+    tol = 1e-12 if prec == 1 else 5e-5
+    assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
+    # three steps (fresh copy: the rhs call substituted phi in place)
+    g.field_copy_in(0, phi)
+    h = tl / (nb * 2)
+    dt = min(O.dt_cfl(og, 0.5, u), 0.1 * h * h / nu)
+    ref = phi.astype(np.float64)
+    for _ in range(3):
+        g.step(0, dt, u, mr.WENOZ5)
+        ref = O.rk3_step_diff(og, ref, dt, O.WENOZ5, u, nu, order)
+    err = np.abs(g.field_copy_out(0).astype(np.float64) - ref).max() / np.abs(ref).max()
+    assert err <= (1e-12 if prec == 1 else 1e-5), err
+    # the term is removed again
+    g.set_diffusion(0.0, 0)
+    g.field_copy_in(0, phi)
+    g.rhs_advect(0, u, 1, mr.WENOZ5)
+    pad, _ = O.ghost_fill(og, phi.astype(np.float64), 3)
+    ref = O.rhs(og, pad, 3, O.WENOZ5, u)
+    assert np.abs(g.field_copy_out(1).astype(np.float64) - ref).max() <= tol * np.abs(ref).max()
