@@ -173,6 +173,17 @@ def fourier_front(xyz, seed, nmodes=16, kmax=8, width=0.02, radius=0.25,
     return f + 0.5 * np.tanh((radius - r) / width)
 
 
+def compact_gaussian(xyz, centre=(0.35, 0.35, 0.35), sigma=0.1, beta=0.2, ext=(1.0, 1.0, 1.0)):
+    """exp(-(r^2/sigma^2) / (1 - r^2/beta^2)) for r < beta, else 0 (nearest
+    periodic image); the initial field of the deformation test."""
+    d = [periodic_delta(xyz[i], centre[i], ext[i]) for i in range(3)]
+    r2 = d[0] ** 2 + d[1] ** 2 + d[2] ** 2
+    out = np.zeros_like(r2)
+    m = r2 < beta * beta
+    out[m] = np.exp(-(r2[m] / sigma ** 2) / (1.0 - r2[m] / beta ** 2))
+    return out
+
+
 def tanh_sphere(xyz, radius=0.3, width=0.01, centre=(0.5, 0.5, 0.5)):
     r = np.sqrt(sum(periodic_delta(xyz[d], centre[d], 1.0) ** 2 for d in range(3)))
     return 0.5 * (1.0 - np.tanh((r - radius) / width))

@@ -138,3 +138,25 @@ def test_mr_adapt_loop_fp64(mr, oracle_mod):
     assert np.array_equal(lev, og2.lev) and np.array_equal(anc, og2.anc)
     got = g.field_copy_out(0)
     assert np.abs(got - ophi).max() <= TOL * np.abs(ophi).max()
+
+
+def test_deformation_initial_grid_on_device(mr, oracle_mod):
+    """Sec. 5.3 initial grid (compact Gaussian, 2.2, eps_r = 1e-2) built by the
+    device's criterion, policy and refinement: the same 92 leaves on levels
+    2 and 3 as the oracle and the paper."""
+    nt, tl, nb, er = (1, 1, 1), 1.0, 24, 1e-2
+    lev, anc = I.uniform_leaves(nt, 2)
+    g = mr.Grid(nt, tl, nb, 2, 8, 2, 2, lev, anc, precision=mr.F64, capacity=1000)
+    for _ in range(8):
+        glev, ganc, _ = g.leaves()
+        g.field_copy_in(0, I.compact_gaussian(I.point_coords(nt, tl, nb, glev, ganc)))
+        if g.adapt_iter(0, er, er / 100, flags=mr.ADAPT_REFINE) == 0:
+            break
+    glev, ganc, _ = g.leaves()
+    counts = np.bincount(glev, minlength=4)
+    assert len(glev) == 92 and counts[2] == 60 and counts[3] == 32
+    # the oracle's tree, leaf for leaf
+    from test_oracle_pins import _deformation_initial_grid
+    olev, oanc = _deformation_initial_grid(oracle_mod, 2, 2)
+    key = lambda lv, an: sorted(zip(lv.tolist(), map(tuple, an.tolist())))
+    assert key(glev, ganc) == key(olev, oanc)
