@@ -63,6 +63,14 @@ extern "C" {
 #define MR_INIT_TANH_SPHERE 1 /* params: cx cy cz radius width             */
 #define MR_INIT_TAYLOR_GREEN 2 /* params: component(0,1,2) scale phase    */
 #define MR_INIT_GAUSSIAN_SUM 3 /* params: n, then n x (cx cy cz sigma amp), n <= 51 */
+/* params: cx cy cz sigma beta amp; amp exp(-(r^2/sigma^2)/(1 - r^2/beta^2))
+ * for r < beta, else 0 (nearest image; the initial field of Sec. 5.3)      */
+#define MR_INIT_COMPACT_GAUSSIAN 4
+/* params: component(0,1,2) scale; the incompressible deformation field of
+ * Sec. 5.3 in its published divergence-free form
+ * (2 sin^2(pi x) sin(2 pi y) sin(2 pi z), -sin(2 pi x) sin^2(pi y) sin(2 pi z),
+ *  -sin(2 pi x) sin(2 pi y) sin^2(pi z)) times scale                     */
+#define MR_INIT_DEFORMATION 5
 
 /* adaptation flags */
 #define MR_ADAPT_REFINE 1
@@ -199,6 +207,14 @@ int mr_rhs_advect_vel(mr_grid *grid, int phi_fid, const int *vel_fid, int out_fi
 /* One RK3 step of phi (in place) advected by the velocity fields vel_fid[3]
  * (see mr_rhs_advect_vel).                                                 */
 int mr_step_vel(mr_grid *grid, int phi_fid, double dt, const int *vel_fid, int scheme);
+
+/* As mr_step_vel with a time-dependent velocity s(t) u(x): stage_scale[3]
+ * (host) are s at the three RK3 stage times t, t + dt, t + dt/2 (Sec. 5.3
+ * multiplies the deformation field by cos(pi t / 3)).  The scale multiplies
+ * the velocity before the interface velocity picks the upwind side, so a
+ * negative scale reverses the flow.  MR_ERR_INVALID for a non-finite scale. */
+int mr_step_vel_scaled(mr_grid *grid, int phi_fid, double dt, const int *vel_fid, int scheme,
+                       const double *stage_scale);
 
 /* Drop the cached ghost-filled velocity (after changing velocity values). */
 int mr_velocity_invalidate(mr_grid *grid);

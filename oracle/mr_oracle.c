@@ -727,6 +727,31 @@ int og_rk3_step_diff(const og_grid *g, double *phi, double dt, int scheme, const
   return e;
 }
 
+/* One RK3 step with padded velocity fields (shell 3, held fixed) multiplied
+ * in stage s by scale[s]: the time-dependent velocity s(t) u(x) of Sec. 5.3,
+ * with s evaluated at the stage times t, t + dt, t + dt/2.                 */
+int og_rk3_step_velpad_scaled(const og_grid *g, double *phi, const double *vpx, const double *vpy,
+                              const double *vpz, double dt, int scheme, const double *scale) {
+  const int nb = g->nb, G = 3, W = nb + 2 * G;
+  const size_t nb3 = (size_t)nb * nb * nb, n = nb3 * g->nleaf, np = (size_t)W * W * W * g->nleaf;
+  double *pad = (double *)malloc(sizeof(double) * np);
+  double *y = (double *)malloc(sizeof(double) * n);
+  double *r = (double *)malloc(sizeof(double) * n);
+  double *vs = (double *)malloc(sizeof(double) * 3 * np);
+  int e = (!pad || !y || !r || !vs) ? OG_ERR_NOMEM : OG_OK;
+  const double *vp[3] = {vpx, vpy, vpz};
+  for (int s = 0; s < 3 && !e; ++s) {
+    double *src = (s == 0) ? phi : y;
+    for (int d = 0; d < 3; ++d)
+      for (size_t i = 0; i < np; ++i) vs[d * np + i] = scale[s] * vp[d][i];
+    e = og_ghost_fill(g, src, G, pad, src);
+    if (!e) e = og_rhs(g, pad, G, scheme, NULL, vs, vs + np, vs + 2 * np, r);
+    if (!e) og_rk_combine(s, n, dt, phi, src, r, s == 2 ? phi : y);
+  }
+  free(pad), free(y), free(r), free(vs);
+  return e;
+}
+
 /* Stable time step (reading of Sec. 5.1): dt = CFL h_min / max sum_d |u_d|. */
 double og_dt(const og_grid *g, double cfl, const double *u_const) {
   int lmax = 0;

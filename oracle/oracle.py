@@ -66,6 +66,7 @@ def _declare(L):
     L.og_rhs.argtypes = [C.POINTER(_Grid), _dp, C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp]
     L.og_rk3_step.argtypes = [C.POINTER(_Grid), _dp, C.c_double, C.c_int, _dp]
     L.og_laplacian.argtypes = [C.POINTER(_Grid), _dp, C.c_int, C.c_int, _dp]
+    L.og_rk3_step_velpad_scaled.argtypes = [C.POINTER(_Grid), _dp, _dp, _dp, _dp, C.c_double, C.c_int, _dp]
     L.og_rk3_step_diff.argtypes = [C.POINTER(_Grid), _dp, C.c_double, C.c_int, _dp, C.c_double, C.c_int]
     L.og_dt.argtypes = [C.POINTER(_Grid), C.c_double, _dp]
     L.og_dt.restype = C.c_double
@@ -195,6 +196,16 @@ def rk3_step_velpad(g: Grid, phi: np.ndarray, vpads, dt: float, scheme: int):
     vp = [np.ascontiguousarray(v, dtype=np.float64) for v in vpads]
     _check(lib().og_rk3_step_velpad(g.c(), _d(phi), _d(vp[0]), _d(vp[1]), _d(vp[2]), dt, scheme),
            "rk3_step_velpad")
+    return phi.reshape(g.nleaf, g.nb, g.nb, g.nb)
+
+
+def rk3_step_velpad_scaled(g: Grid, phi: np.ndarray, vpads, dt: float, scheme: int, scale):
+    """RK3 step with the fixed padded velocities times scale[s] in stage s."""
+    phi = np.ascontiguousarray(phi, dtype=np.float64).copy()
+    vp = [np.ascontiguousarray(v, dtype=np.float64) for v in vpads]
+    sc = np.asarray(scale, dtype=np.float64)
+    _check(lib().og_rk3_step_velpad_scaled(g.c(), _d(phi), _d(vp[0]), _d(vp[1]), _d(vp[2]), dt, scheme,
+                                           _d(sc)), "rk3_step_velpad_scaled")
     return phi.reshape(g.nleaf, g.nb, g.nb, g.nb)
 
 

@@ -262,6 +262,7 @@ int mr_grid_create(const mr_grid_desc *desc, void *workspace, size_t workspace_b
   g->vel_version = -1;
   g->diff_nu = 0.0;
   g->diff_order = 0;
+  g->vel_scale = 1.0;
   g->shell_rk = srk;
   g->shell_ad = sad;
   g->map_cells = mc;
@@ -405,7 +406,9 @@ int mr_field_ptr(mr_grid *g, int fid, void **ptr) {
 }
 
 int mr_field_set(mr_grid *g, int fid, int kind, const double *params, int np) {
-  if (!fid_ok(g, fid) || !params || np < 1 || np > 256 || kind < 0 || kind > 3) return MR_ERR_INVALID;
+  if (!fid_ok(g, fid) || !params || np < 1 || np > 256 || kind < 0 || kind > 5) return MR_ERR_INVALID;
+  static const int need[6] = {5, 5, 3, 1, 6, 2};  // parameters each kind reads
+  if (np < need[kind]) return MR_ERR_INVALID;
   if (kind == MR_INIT_GAUSSIAN_SUM && (params[0] < 0 || 1 + 5 * (int)params[0] > np)) return MR_ERR_INVALID;
   return launch_field_set(g, field_ptr(g, fid), kind, params, np);
 }
@@ -519,7 +522,14 @@ int mr_rhs_advect_vel(mr_grid *g, int phi, const int *vel, int out, int scheme) 
 }
 
 int mr_step_vel(mr_grid *g, int phi, double dt, const int *vel, int scheme) {
-  if (!fid_ok(g, phi) || !vel) return MR_ERR_INVALID;
+  static const double ones[3] = {1.0, 1.0, 1.0};
+  return mr_step_vel_scaled(g, phi, dt, vel, scheme, ones);
+}
+
+int mr_step_vel_scaled(mr_grid *g, int phi, double dt, const int *vel, int scheme, const double *scale) {
+  if (!fid_ok(g, phi) || !vel || !scale) return MR_ERR_INVALID;
+  for (int s = 0; s < 3; ++s)
+    if (!std::isfinite(scale[s])) return MR_ERR_INVALID;
   int e = velocity_cache(g, vel);
   if (e) return e;
   void *un = field_ptr(g, phi);
@@ -528,6 +538,7 @@ int mr_step_vel(mr_grid *g, int phi, double dt, const int *vel, int scheme) {
   void *dst[3] = {y1, y2, un};
   for (int s = 0; s < 3 && !e; ++s) {
     int Gi;
+    g->vel_scale = scale[s];
     if (g->desc.precision == MR_F32) {
       e = launch_prep32(g, src[s], &Gi);
       if (!e) e = launch_fused(g, src[s], g->padP, g->padQ, Gi, un, dst[s], s, dt, nullptr, scheme, false, g->vpad);
@@ -538,6 +549,7 @@ int mr_step_vel(mr_grid *g, int phi, double dt, const int *vel, int scheme) {
       if (!e) e = launch_rhs_stage(g, P, Gi, un, dst[s], s, dt, nullptr, scheme, false, g->vpad);
     }
   }
+  g->vel_scale = 1.0;
   return e;
 }
 

@@ -395,6 +395,7 @@ struct mr_grid {
   int vel_fid[3];
   double diff_nu;         // diffusion coefficient of the stencil step (0: none)
   int diff_order;         // 0, 2 (DIFF-2) or 4 (DIFF-4)
+  double vel_scale;       // factor on the velocity fields in the current stage (1 outside steps)
   // launch registry: counts every kernel launch; with profiling on, brackets
   // each launch with CUDA events on the grid's stream
   long long launches[32];

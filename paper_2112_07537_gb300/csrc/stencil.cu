@@ -84,7 +84,7 @@ template <typename T, int SCHEME>
 __global__ void __launch_bounds__(256) k_rhs_stage(Tree t, const T *__restrict__ P, int Gi,
                                                    const T *u, T *out, int stage, T dt, T ux, T uy,
                                                    T uz, int rhs_only, const T *__restrict__ vpad, T nu,
-                                                   int diff) {
+                                                   int diff, T vscale) {
   // vpad: ghost-filled velocity components (shell 3) or null for constant u
   const int b = blockIdx.x;
   const int nb = t.nb, Wd = nb + 2 * Gi;
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(256) k_rhs_stage(Tree t, const T *__restrict__
       T f[7], uu[7];
 #pragma unroll
       for (int m = 0; m < 7; ++m) {
-        uu[m] = vpad ? vpad[d * vcomp + cv + (ptrdiff_t)(m - 3) * vstride[d]] : uc[d];
+        uu[m] = vpad ? vscale * vpad[d * vcomp + cv + (ptrdiff_t)(m - 3) * vstride[d]] : uc[d];
         f[m] = uu[m] * Pb[c + (ptrdiff_t)(m - 3) * stride[d]];
       }
       const bool lp = uu[3] + uu[4] >= T(0), lm = uu[2] + uu[3] >= T(0);
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(1024) k_fused(Tree t, const float *__restrict_
                                                const float *__restrict__ Q, int Gi, const int *__restrict__ cmask,
                                                const float *u, float *out, int stage, float dt, float ux, float uy,
                                                float uz, int rhs_only, int *err, const float *__restrict__ vpad,
-                                               float nu, int diff) {
+                                               float nu, int diff, float vscale) {
   using W = Wav<N, NT>;
   constexpr int GS = 3;
   const int b = blockIdx.x, nb = t.nb, Ws = nb + 2 * GS, Wd = nb + 2 * Gi;
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(1024) k_fused(Tree t, const float *__restrict_
       }
       // velocity along the line (ghost-filled component d) or the constant
       const float *vq = VEL ? vpad + d * vcomp + (size_t)b * vblk + tix(c[0], c[1], c[2]) : nullptr;
-      auto vel = [&](int m) -> float { return VEL ? __ldg(vq + m * st) : ud; };
+      auto vel = [&](int m) -> float { return VEL ? vscale * __ldg(vq + m * st) : ud; };
       // register windows: f = u*phi and u at m-3..m+3; F_{-1/2} from f_{-3..2}
       float v1 = vel(-3), v2 = vel(-2), v3 = vel(-1), v4 = vel(0), v5 = vel(1), v6 = vel(2);
       float w1 = v1 * lp[-3 * st], w2 = v2 * lp[-2 * st], w3 = v3 * lp[-st], w4 = v4 * lp[0],
@@ -338,11 +338,11 @@ static int rhs_dispatch(mr_grid *g, const T *P, int Gi, const T *u, T *out, int 
   if (!uc) uc = zero3;
   const T ux = T(uc[0]), uy = T(uc[1]), uz = T(uc[2]);
   if (scheme == MR_CONS3)
-    MR_LAUNCH(g, MRK_RHS, k_rhs_stage<T, MR_CONS3><<<n, 256, 0, g->stream>>>(t, P, Gi, u, out, stage, T(dt), ux, uy, uz, rhs_only, vpad, T(g->diff_nu), g->diff_order));
+    MR_LAUNCH(g, MRK_RHS, k_rhs_stage<T, MR_CONS3><<<n, 256, 0, g->stream>>>(t, P, Gi, u, out, stage, T(dt), ux, uy, uz, rhs_only, vpad, T(g->diff_nu), g->diff_order, T(g->vel_scale)));
   else if (scheme == MR_CONS5)
-    MR_LAUNCH(g, MRK_RHS, k_rhs_stage<T, MR_CONS5><<<n, 256, 0, g->stream>>>(t, P, Gi, u, out, stage, T(dt), ux, uy, uz, rhs_only, vpad, T(g->diff_nu), g->diff_order));
+    MR_LAUNCH(g, MRK_RHS, k_rhs_stage<T, MR_CONS5><<<n, 256, 0, g->stream>>>(t, P, Gi, u, out, stage, T(dt), ux, uy, uz, rhs_only, vpad, T(g->diff_nu), g->diff_order, T(g->vel_scale)));
   else if (scheme == MR_WENOZ5)
-    MR_LAUNCH(g, MRK_RHS, k_rhs_stage<T, MR_WENOZ5><<<n, 256, 0, g->stream>>>(t, P, Gi, u, out, stage, T(dt), ux, uy, uz, rhs_only, vpad, T(g->diff_nu), g->diff_order));
+    MR_LAUNCH(g, MRK_RHS, k_rhs_stage<T, MR_WENOZ5><<<n, 256, 0, g->stream>>>(t, P, Gi, u, out, stage, T(dt), ux, uy, uz, rhs_only, vpad, T(g->diff_nu), g->diff_order, T(g->vel_scale)));
   else
     return MR_ERR_INVALID;
   return check_cuda(cudaGetLastError(), "k_rhs_stage") ? MR_ERR_CUDA : MR_OK;
@@ -388,7 +388,8 @@ static int fused_impl(mr_grid *g, const float *phi, const float *P, const float 
       return MR_ERR_CUDA;                                                                                 \
     MR_LAUNCH(g, MRK_RHS, k_fused<N, NT, S, VEL><<<g->nleaf, threads, sm, g->stream>>>(                       \
                               t, phi, P, Q, Gi, g->cmask, u, out, stage, (float)dt, ux, uy, uz, rhs_only, \
-                              g->counter + 1, vpad, (float)g->diff_nu, g->diff_order));                   \
+                              g->counter + 1, vpad, (float)g->diff_nu, g->diff_order,                     \
+                              (float)g->vel_scale));                                                      \
   } while (0)
   if (scheme == MR_CONS3) MR_FL(MR_CONS3);
   else if (scheme == MR_CONS5) MR_FL(MR_CONS5);
@@ -475,6 +476,22 @@ __global__ void k_field_set(Tree t, T *f, int kind, InitParams ip) {
         }
         v += c[4] * exp(-r2 / (c[3] * c[3]));
       }
+    } else if (kind == MR_INIT_COMPACT_GAUSSIAN) {
+      double r2 = 0.0;
+      for (int d = 0; d < 3; ++d) {
+        const double dd = pdelta(x[d], ip.p[d], ext[d]);
+        r2 += dd * dd;
+      }
+      const double s2 = ip.p[3] * ip.p[3], b2 = ip.p[4] * ip.p[4];
+      v = r2 < b2 ? ip.p[5] * exp(-(r2 / s2) / (1.0 - r2 / b2)) : 0.0;
+    } else if (kind == MR_INIT_DEFORMATION) {
+      const double pi = M_PI, s = ip.p[1];
+      const int comp = (int)ip.p[0];
+      const double sx = sin(pi * x[0]), sy = sin(pi * x[1]), sz = sin(pi * x[2]);
+      const double s2x = sin(2 * pi * x[0]), s2y = sin(2 * pi * x[1]), s2z = sin(2 * pi * x[2]);
+      if (comp == 0) v = 2.0 * s * sx * sx * s2y * s2z;
+      else if (comp == 1) v = -s * s2x * sy * sy * s2z;
+      else v = -s * s2x * s2y * sz * sz;
     } else if (kind == MR_INIT_TAYLOR_GREEN) {
       const double w = 2.0 * M_PI, s = ip.p[1], ph = ip.p[2];
       const int comp = (int)ip.p[0];

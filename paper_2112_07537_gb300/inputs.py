@@ -184,6 +184,19 @@ def compact_gaussian(xyz, centre=(0.35, 0.35, 0.35), sigma=0.1, beta=0.2, ext=(1
     return out
 
 
+def deformation_velocity(xyz, comp, scale=1.0):
+    """Component comp of the incompressible deformation field (published
+    divergence-free form): (2 sin^2(pi x) sin(2 pi y) sin(2 pi z),
+    -sin(2 pi x) sin^2(pi y) sin(2 pi z), -sin(2 pi x) sin(2 pi y) sin^2(pi z))."""
+    x, y, z = xyz
+    p = np.pi
+    if comp == 0:
+        return 2 * scale * np.sin(p * x) ** 2 * np.sin(2 * p * y) * np.sin(2 * p * z)
+    if comp == 1:
+        return -scale * np.sin(2 * p * x) * np.sin(p * y) ** 2 * np.sin(2 * p * z)
+    return -scale * np.sin(2 * p * x) * np.sin(2 * p * y) * np.sin(p * z) ** 2
+
+
 def tanh_sphere(xyz, radius=0.3, width=0.01, centre=(0.5, 0.5, 0.5)):
     r = np.sqrt(sum(periodic_delta(xyz[d], centre[d], 1.0) ** 2 for d in range(3)))
     return 0.5 * (1.0 - np.tanh((r - radius) / width))

@@ -20,6 +20,7 @@ F32, F64 = 0, 1
 CONS3, CONS5, WENOZ5 = 0, 1, 2
 INIT_GAUSSIAN, INIT_TANH_SPHERE, INIT_TAYLOR_GREEN, INIT_GAUSSIAN_SUM = 0, 1, 2, 3
 ADAPT_REFINE, ADAPT_COARSEN = 1, 2
+INIT_COMPACT_GAUSSIAN, INIT_DEFORMATION = 4, 5
 GRID_FIXED_TREE = 1
 GRID_VELOCITY = 2
 NUM_KERNELS = 18
@@ -29,7 +30,7 @@ EXPORTS = ["mr_last_error", "mr_workspace_size", "mr_grid_create", "mr_grid_dest
            "mr_grid_leaves", "mr_field_copy_in", "mr_field_copy_out", "mr_field_set",
            "mr_ghost_fill", "mr_ghost_fill64", "mr_sync", "mr_rhs_advect", "mr_rk_stage",
            "mr_step", "mr_criterion", "mr_adapt", "mr_adapt_iter", "mr_mass", "mr_query",
-           "mr_field_ptr", "mr_profile", "mr_profile_read", "mr_launch_count", "mr_profile_bytes", "mr_set_diffusion",
+           "mr_field_ptr", "mr_profile", "mr_profile_read", "mr_launch_count", "mr_profile_bytes", "mr_set_diffusion", "mr_step_vel_scaled",
            "mr_ghost_fill_static", "mr_rhs_advect_vel", "mr_step_vel", "mr_velocity_invalidate"]
 
 
@@ -93,6 +94,7 @@ def load(path: str = LIB_PATH):
         L.mr_profile_read.argtypes = [vp, C.c_int, dp, C.POINTER(C.c_int), C.POINTER(C.c_char_p)]
         L.mr_profile_bytes.argtypes = [vp, C.c_int, dp]
         L.mr_set_diffusion.argtypes = [vp, C.c_double, C.c_int]
+        L.mr_step_vel_scaled.argtypes = [vp, C.c_int, C.c_double, ip, C.c_int, dp]
         L.mr_launch_count.argtypes = [vp, C.POINTER(C.c_longlong)]
         _lib = L
     return _lib
@@ -244,6 +246,12 @@ class Grid:
     def step_vel(self, phi_fid, dt, vel_fids, scheme):
         v = (C.c_int32 * 3)(*vel_fids)
         _chk(load().mr_step_vel(self.h, phi_fid, float(dt), v, scheme))
+
+    def step_vel_scaled(self, phi_fid, dt, vel_fids, scheme, stage_scale):
+        """RK3 step with the velocity fields times stage_scale[s] in stage s."""
+        v = (C.c_int32 * 3)(*vel_fids)
+        sc = (C.c_double * 3)(*[float(x) for x in stage_scale])
+        _chk(load().mr_step_vel_scaled(self.h, phi_fid, float(dt), v, scheme, sc))
 
     def velocity_invalidate(self):
         _chk(load().mr_velocity_invalidate(self.h))

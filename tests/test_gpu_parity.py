@@ -323,3 +323,41 @@ def test_advection_diffusion_rhs_and_steps(mr, oracle_mod, prec, order):
     pad, _ = O.ghost_fill(og, phi.astype(np.float64), 3)
     ref = O.rhs(og, pad, 3, O.WENOZ5, u)
     assert np.abs(g.field_copy_out(1).astype(np.float64) - ref).max() <= tol * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_time_dependent_velocity_steps(mr, oracle_mod, prec):
+    """Sec. 5.3 workload pieces: the device-evaluated deformation field and
+    compact Gaussian equal the host formulas, and RK3 steps with the stage
+    scales of a time-dependent velocity (one of them negative) match the
+    oracle."""
+    O = oracle_mod
+    nt, tl, nb = (2, 2, 2), 0.5, 16
+    lev, anc = I.tree_config1()
+    g = mr.Grid(nt, tl, nb, 0, 1, 4, 2, lev, anc, precision=prec, nfields=4, velocity=True)
+    glev, ganc, _ = g.leaves()
+    og = O.Grid(nt, tl, nb, 4, 2, 0, 1, glev, ganc)
+    xyz = I.point_coords(nt, tl, nb, glev, ganc)
+    g.field_set(0, mr.INIT_COMPACT_GAUSSIAN, [0.35, 0.35, 0.35, 0.1, 0.2, 1.0])
+    for d in range(3):
+        g.field_set(1 + d, mr.INIT_DEFORMATION, [d, 1.0])
+    itol = 1e-13 if prec == 1 else 1e-6
+    phi = I.compact_gaussian(xyz)
+    assert np.abs(g.field_copy_out(0).astype(np.float64) - phi).max() <= itol
+    vel = [I.deformation_velocity(xyz, d) for d in range(3)]
+    for d in range(3):
+        assert np.abs(g.field_copy_out(1 + d).astype(np.float64) - vel[d]).max() <= 2 * itol
+    # the oracle starts from the device's own values (FP32 rounding included)
+    phi64 = g.field_copy_out(0).astype(np.float64)
+    v64 = [O.ghost_fill(og, g.field_copy_out(1 + d).astype(np.float64), 3)[1] for d in range(3)]
+    vpads = [O.ghost_fill(og, v, 3)[0] for v in v64]
+    h = tl / (nb * 2)
+    dt = 0.25 * h / 3.0
+    ref = phi64
+    # stage scales with sign changes within and between steps (the factor
+    # cos(pi t / 3) of Sec. 5.3 changes sign at t = 1.5)
+    for sc in ((0.8, -0.6, 0.3), (-1.0, -0.2, 0.5), (1.2, 0.9, -0.7)):
+        g.step_vel_scaled(0, dt, (1, 2, 3), mr.WENOZ5, sc)
+        ref = O.rk3_step_velpad_scaled(og, ref, vpads, dt, O.WENOZ5, sc)
+    err = np.abs(g.field_copy_out(0).astype(np.float64) - ref).max() / np.abs(ref).max()
+    assert err <= (1e-12 if prec == 1 else 1e-5), err

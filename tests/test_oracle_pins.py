@@ -562,3 +562,28 @@ def test_deformation_initial_grid_matches_paper(oracle_mod):
     lev, _ = _deformation_initial_grid(oracle_mod, 2, 2)
     counts = np.bincount(lev, minlength=4)
     assert len(lev) == total and counts[2] == n2 and counts[3] == n3
+
+
+def test_scaled_velocity_step(oracle_mod):
+    """Time-dependent velocity s(t) u(x) (Sec. 5.3): with unit scales the
+    step equals the fixed-velocity step bit for bit; a constant field u0
+    scaled by s in every stage equals the constant-velocity step with s u0,
+    for s < 0 too (the scale acts before the upwind choice)."""
+    O = oracle_mod
+    nt, tl, nb = (2, 2, 2), 0.5, 8
+    lev, anc = I.tree_config1()
+    g = O.Grid(nt, tl, nb, 4, 2, 0, 1, lev, anc)
+    xyz = I.point_coords(nt, tl, nb, g.lev, g.anc)
+    phi = I.gaussian_images(xyz, (0.45, 0.55, 0.5), 0.1, nimg=1)
+    vel = [O.ghost_fill(g, I.deformation_velocity(xyz, d), 3)[1] for d in range(3)]
+    vp = [O.ghost_fill(g, v, 3)[0] for v in vel]
+    dt = 2e-3
+    a = O.rk3_step_velpad(g, phi, vp, dt, O.WENOZ5)
+    b = O.rk3_step_velpad_scaled(g, phi, vp, dt, O.WENOZ5, (1.0, 1.0, 1.0))
+    assert np.array_equal(a, b)
+    u0 = (0.75, -0.5, 0.25)
+    vc = [O.ghost_fill(g, np.full_like(phi, u0[d]), 3)[0] for d in range(3)]
+    for s in (0.5, -1.5):
+        c = O.rk3_step_velpad_scaled(g, phi, vc, dt, O.WENOZ5, (s, s, s))
+        ref = O.rk3_step(g, phi, dt, O.WENOZ5, tuple(s * x for x in u0))
+        assert np.array_equal(c, ref)
