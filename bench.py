@@ -25,6 +25,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -84,6 +85,32 @@ def init_large(mrgb, stream, prec, cap, gauss=GAUSS):
     for d in range(3):
         g.field_set(1 + d, mrgb.INIT_TAYLOR_GREEN, [d, TG[0], TG[1]])
     g.adapt(0, EPS_R, EPS_C)
+    return g
+
+
+# deformation of a compact Gaussian blob (Sec. 5.3): sigma 0.1, beta 2 sigma at
+# (0.35, 0.35, 0.35); eps_r 1e-2, eps_r/eps_c 100; CFL 0.5 on the finest
+# spacing present; adaptation every 12 steps; velocity times cos(pi t / 3)
+DEFORM = dict(eps_r=1e-2, ratio=100.0, cfl=0.5, adapt_every=12, umax=4.0)
+COMPACT = [0.35, 0.35, 0.35, 0.1, 0.2, 1.0]
+
+
+def init_deformation(mrgb, stream, prec, cap, wav):
+    """Initial grid of the deformation test: uniform level 2, then alternate
+    analytic sampling and refinement until no block refines, sample again,
+    set the velocity fields and run one full adaptation."""
+    lev, anc = I.uniform_leaves((1, 1, 1), 2)
+    g = mrgb.Grid((1, 1, 1), 1.0, 24, 2, 8, wav[0], wav[1], lev, anc, precision=prec, nfields=4,
+                  capacity=cap, stream=stream, velocity=True)
+    er = DEFORM["eps_r"]
+    for _ in range(12):
+        g.field_set(0, mrgb.INIT_COMPACT_GAUSSIAN, COMPACT)
+        if g.adapt_iter(0, er, er / DEFORM["ratio"], flags=mrgb.ADAPT_REFINE) == 0:
+            break
+    g.field_set(0, mrgb.INIT_COMPACT_GAUSSIAN, COMPACT)
+    for d in range(3):
+        g.field_set(1 + d, mrgb.INIT_DEFORMATION, [d, 1.0])
+    g.adapt(0, er, er / DEFORM["ratio"])
     return g
 
 
@@ -178,7 +205,10 @@ def main():
     ap.add_argument("--scheme", default="wenoz5", choices=["wenoz5", "cons5", "cons3"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="large", choices=["large", "adaptive-small"] + sorted(WORKLOADS))
+    ap.add_argument("--workload", default="large",
+                    choices=["large", "adaptive-small", "deformation"] + sorted(WORKLOADS))
+    ap.add_argument("--wavelet", default="4.2", choices=["2.2", "4.2", "6.2", "4.0", "6.0"],
+                    help="wavelet of the deformation workload")
     ap.add_argument("--capacity", type=int, default=60000)
     ap.add_argument("--diffusion", type=int, default=0, choices=[0, 2, 4],
                     help="add nu * DIFF-2/DIFF-4 Laplacian to the stencil step")
@@ -204,9 +234,15 @@ def main():
     scheme = {"wenoz5": mrgb.WENOZ5, "cons5": mrgb.CONS5, "cons3": mrgb.CONS3}[args.scheme]
     nb = 24
     adaptive = args.workload in ("large", "adaptive-small")
+    deform = args.workload == "deformation"
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        if adaptive:
+        if deform:
+            wav = tuple(int(c) for c in args.wavelet.split("."))
+            g = init_deformation(mrgb, stream, prec, min(args.capacity, 30000), wav)
+            lmax = 8
+            umax = DEFORM["umax"]
+        elif adaptive:
             g = init_large(mrgb, stream, prec, args.capacity,
                            GAUSS if args.workload == "large" else GAUSS_SMALL)
             lmax = 8
@@ -225,10 +261,24 @@ def main():
         dt = min(dt, 0.1 * hmin * hmin / args.nu)  # explicit diffusion limit
     stats0 = g.query()
 
+    dstate = {"t": 0.0, "n": 0, "lm": stats0.max_level}
+
     def one_step(i):
         """One RK3 step (+ adaptation every ADAPT_EVERY steps); returns the
         point-stage updates it performed."""
         pts = g.nleaf * nb ** 3
+        if deform:
+            # dt from the finest spacing present (reading of Sec. 5.3)
+            t = dstate["t"]
+            dtd = DEFORM["cfl"] * (1.0 / (nb * 2 ** dstate["lm"])) / umax
+            sc = [math.cos(math.pi * tt / 3) for tt in (t, t + dtd, t + dtd / 2)]
+            g.step_vel_scaled(0, dtd, (1, 2, 3), scheme, sc)
+            dstate["t"] = t + dtd
+            dstate["n"] += 1
+            if dstate["n"] % DEFORM["adapt_every"] == 0:
+                g.adapt(0, DEFORM["eps_r"], DEFORM["eps_r"] / DEFORM["ratio"])
+                dstate["lm"] = g.query().max_level
+            return 3 * pts
         if adaptive:
             g.step_vel(0, dt, (1, 2, 3), scheme)
             if (i + 1) % ADAPT_EVERY == 0:
@@ -276,7 +326,8 @@ def main():
     # end to end through the public API with host buffers: each step copies
     # the scalar in from pinned host memory and reads it back
     es = 4 if prec == mrgb.F32 else 8
-    host = torch.empty((args.capacity if adaptive else g.nleaf) * nb ** 3, dtype=g.dtype,
+    host = torch.empty((min(args.capacity, 30000) if deform else args.capacity if adaptive else g.nleaf) * nb ** 3,
+                       dtype=g.dtype,
                        pin_memory=True)
     ke = max(2, min(args.steps, 4))
     torch.cuda.synchronize()
@@ -301,7 +352,7 @@ def main():
     # algorithmic bytes per point-stage of the fused stage: phi read, RK
     # output written, u^n read in stages 1-2 (2/3 on average), plus the three
     # velocity components when the velocity is a field
-    per_pt = bpp * (1 + 1 + 2.0 / 3 + (3 if adaptive else 0))
+    per_pt = bpp * (1 + 1 + 2.0 / 3 + (3 if adaptive or deform else 0))
     alg = {"rhs_stage": mean_pts * per_pt}
     if "ghost_part1" in prof and ghost_bytes > 0:
         # shell points written + source values read, per reconstructed leaf,
@@ -310,7 +361,15 @@ def main():
     per_launch = alg.get(name, None)
     achieved = per_launch / (tot / cnt / 1e3) / 1e9 if per_launch else None
     gs = GAUSS if args.workload == "large" else GAUSS_SMALL
-    workload = (f"{args.workload} single grid, adaptive: 1 tree, 24^3 blocks, levels 3-8, "
+    if deform:
+        workload = (f"deformation of a compact Gaussian blob (sigma 0.1, beta 0.2 at 0.35^3) by the "
+                    f"incompressible deformation field times cos(pi t/3): 1 tree, 24^3 blocks, levels 2-8, "
+                    f"{args.wavelet} wavelet, eps_r {DEFORM['eps_r']}, eps_c {DEFORM['eps_r'] / DEFORM['ratio']}, "
+                    f"{args.scheme} + RK3, CFL {DEFORM['cfl']} on the finest spacing present, adapt every "
+                    f"{DEFORM['adapt_every']} steps; {stats0.nleaf}->{stats1.nleaf} leaves, t = {dstate['t']:.4f}")
+    else:
+        workload = None
+    workload = workload or (f"{args.workload} single grid, adaptive: 1 tree, 24^3 blocks, levels 3-8, "
                 f"{stats0.nleaf}->{stats1.nleaf} leaves; FP32 scalar ({gs['n']} seeded Gaussians, sigma "
                 f"{gs['smin']}-{gs['smax']}) + 3 velocity fields (Taylor-Green-like, scale "
                 f"{TG[0]}, phase {TG[1]}); 6.2 lifted wavelet, eps_r {EPS_R}, eps_c {EPS_C}; "
