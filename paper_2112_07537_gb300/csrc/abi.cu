@@ -86,7 +86,7 @@ int adapt_shell(int N, int Nt) {
 }
 
 struct Layout {
-  size_t off[25];
+  size_t off[26];
   size_t total;
 };
 
@@ -116,7 +116,7 @@ static int layout(const mr_grid_desc *d, Layout *L, int *shell_rk, int *shell_ad
   *M = d->lmax;
   *map_cells = ((size_t)d->ntree[0] << d->lmax) * ((size_t)d->ntree[1] << d->lmax) *
                ((size_t)d->ntree[2] << d->lmax);
-  size_t sz[25] = {
+  size_t sz[26] = {
       cap * 4, cap * 4,                          // lev[2]
       cap * 12, cap * 12,                        // anc[2]
       cap * 8, cap * 8,                          // keys[2]
@@ -134,9 +134,10 @@ static int layout(const mr_grid_desc *d, Layout *L, int *shell_rk, int *shell_ad
       64 * 8,                                    // dscratch
       cap * 8,                                   // cmask + new-band masks
       cap * 4,                                   // hasD
-      velo ? 3 * cap * wv * wv * wv * es : 0};   // velocity cache (shell 3)
+      velo ? 3 * cap * wv * wv * wv * es : 0,    // velocity cache (shell 3)
+      cap * 4};                                  // pneed: leaves left to the full pre-pass
   size_t o = 0;
-  for (int i = 0; i < 25; ++i) {
+  for (int i = 0; i < 26; ++i) {
     L->off[i] = o;
     o += al(sz[i]);
   }
@@ -257,6 +258,7 @@ int mr_grid_create(const mr_grid_desc *desc, void *workspace, size_t workspace_b
   g->dscratch = (double *)(w + L.off[21]);
   g->cmask = (int *)(w + L.off[22]);
   g->hasD = (int *)(w + L.off[23]);
+  g->pneed = (int *)(w + L.off[25]);
   g->vpad = (desc->flags & MR_GRID_VELOCITY) ? (void *)(w + L.off[24]) : nullptr;
   g->tree_version = 0;
   g->vel_version = -1;
@@ -303,7 +305,7 @@ int mr_grid_destroy(mr_grid *g) {
 int mr_sync(mr_grid *g) { return g ? sync_check(g) : MR_ERR_INVALID; }
 
 static const char *kernel_names[MRK_COUNT] = {
-    "ghost_part1", "ghost_part2", "ghost_merge", "ghost_crop", "rhs_stage", "rk_combine",
+    "ghost_part1", "ghost_plain", "ghost_merge", "ghost_crop", "rhs_stage", "rk_combine",
     "field_set", "mass", "owner_map", "balance_check", "criterion", "status", "policy", "scan",
     "emit", "interpolate", "update", "misc"};
 

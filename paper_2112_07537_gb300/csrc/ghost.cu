@@ -420,6 +420,101 @@ __global__ void __launch_bounds__(512, 1) k_prep(Tree t, const TI *__restrict__ 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Padded block of a leaf with no coarser neighbour -- the leaves whose ghost
+// fill (Alg. SM1) is a gather: interior, the values of same-level neighbours
+// (copy) and the coincident values of finer neighbours (their fine-to-coarse
+// values are merged afterwards, as for every leaf).  A leaf with a coarser
+// neighbour, or outside need, is flagged in pneed for the full pre-pass.
+// Finer regions are resolved through the owners of their eight one-level-
+// finer sub-blocks (one lookup per sub-block, not per point).  Every field
+// read is bounds-checked: an out-of-range index sets error bit 16 and yields
+// NaN instead of a load.
+// ---------------------------------------------------------------------------
+template <typename TI, typename TP>
+__global__ void __launch_bounds__(256) k_fill_plain(Tree t, const TI *__restrict__ phi, TP *__restrict__ P,
+                                                    int Gi, const int *__restrict__ need,
+                                                    int *__restrict__ pneed, int *__restrict__ cmask_out,
+                                                    int *err) {
+  const int b = blockIdx.x;
+  if (need && !need[b]) {
+    if (threadIdx.x == 0) pneed[b] = 0;
+    return;
+  }
+  const int nb = t.nb, Wd = nb + 2 * Gi, hb = nb / 2;
+  const size_t np = (size_t)Wd * Wd * Wd, nb3 = (size_t)nb * nb * nb;
+  const long long lim = (long long)t.nleaf * (long long)nb3;
+  const int L = __ldg(t.lev + b);
+  __shared__ int rslot[27], rlev[27], rsub[27][8];
+  __shared__ int coarse;
+  if (threadIdx.x == 0) coarse = 0;
+  __syncthreads();
+  if (threadIdx.x < 27) {
+    const int r = threadIdx.x;
+    const int dd[3] = {r % 3 - 1, (r / 3) % 3 - 1, r / 9 - 1};
+    int g[3];
+    for (int d = 0; d < 3; ++d) g[d] = __ldg(t.anc + 3 * b + d) * nb + (dd[d] < 0 ? -1 : dd[d] > 0 ? nb : 0);
+    const int o = owner(t, L, g[0], g[1], g[2]);
+    const int Lo = __ldg(t.lev + o);
+    rslot[r] = o, rlev[r] = Lo;
+    if (r != 13 && Lo < L) atomicOr(&coarse, 1);
+  }
+  __syncthreads();
+  if (coarse) {
+    if (threadIdx.x == 0) pneed[b] = 1;
+    return;
+  }
+  if (threadIdx.x == 0) pneed[b] = 0, cmask_out[b] = 0;
+  for (int q = threadIdx.x; q < 216; q += blockDim.x) {
+    const int r = q >> 3, h = q & 7;
+    int o2 = -1;
+    if (rlev[r] == L + 1 && L < t.M) {
+      const int dd[3] = {r % 3 - 1, (r / 3) % 3 - 1, r / 9 - 1};
+      int g[3];
+      for (int d = 0; d < 3; ++d) g[d] = 2 * (__ldg(t.anc + 3 * b + d) + dd[d]) * nb + ((h >> d) & 1) * nb;
+      o2 = owner(t, L + 1, g[0], g[1], g[2]);
+      if (o2 < 0 || o2 >= t.nleaf || __ldg(t.lev + o2) != L + 1) o2 = -1;
+    }
+    rsub[r][h] = o2;
+  }
+  __syncthreads();
+  const int ax = __ldg(t.anc + 3 * b) * nb, ay = __ldg(t.anc + 3 * b + 1) * nb, az = __ldg(t.anc + 3 * b + 2) * nb;
+  TP *Pb = P + (size_t)b * np;
+  const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  for (int row = threadIdx.x >> 5; row < Wd * Wd; row += nwarp) {
+    const int j = row % Wd - Gi, k = row / Wd - Gi;
+    const int ry = j < 0 ? 0 : j >= nb ? 2 : 1, rz = k < 0 ? 0 : k >= nb ? 2 : 1;
+    const int rj = j - (ry - 1) * nb, rk = k - (rz - 1) * nb;  // region-local
+    for (int i = lane - Gi; i < nb + Gi; i += 32) {
+      const int rx = i < 0 ? 0 : i >= nb ? 2 : 1, r = rx + 3 * ry + 9 * rz;
+      const int ri = i - (rx - 1) * nb;
+      const int Lo = rlev[r];
+      long long idx = -1;
+      if (Lo == L) {
+        idx = (long long)rslot[r] * (long long)nb3 + ri + nb * (rj + nb * rk);
+      } else if (Lo == L + 1) {
+        const int hx = ri >= hb, hy = rj >= hb, hz = rk >= hb;
+        const int o2 = rsub[r][hx + 2 * hy + 4 * hz];
+        if (o2 >= 0)
+          idx = (long long)o2 * (long long)nb3 + (2 * ri - hx * nb) + nb * ((2 * rj - hy * nb) + nb * (2 * rk - hz * nb));
+      }
+      TP v;
+      if (idx >= 0 && idx < lim && ri >= 0 && ri < nb && rj >= 0 && rj < nb && rk >= 0 && rk < nb) {
+        v = Cvt<TP>::f(__ldg(phi + idx));
+      } else if (idx == -1 && Lo > L) {
+        // a finer region two levels down (shells wider than half a block)
+        const int gx = ax + i, gy = ay + j, gz = az + k;
+        const int o = owner(t, L, gx, gy, gz);
+        v = Cvt<TP>::f(leaf_value(t, phi, o, L, gx, gy, gz, err));
+      } else {
+        atomicOr(err, 1 << 16);
+        v = TP(__int_as_float(0x7fc00000));
+      }
+      Pb[(size_t)row * Wd + (i + Gi)] = v;
+    }
+  }
+}
+
 // partial sums of the separable refinement of the largest coarse-region box
 // (face nb x nb x Gi, edge nb x Gi x Gi, corner Gi^3; thinnest side first)
 static size_t sep_refine_elems(int N, int nb, int Gi) {
@@ -508,22 +603,23 @@ __global__ void k_crop(const TP *__restrict__ P, int Gi, TO *__restrict__ out, i
 // Profiling only: units a launch processed (leaves whose flag is set, all
 // leaves without flags) times the algorithmic bytes of one unit, added to the
 // kernel's accumulator.
-__global__ void k_units(const int *__restrict__ flags, int n, double bytes_per_unit, double *acc) {
+__global__ void k_units(const int *__restrict__ flags, int n, double bytes_per_unit, double *acc,
+                        const int *__restrict__ exclude) {
   __shared__ int cnt;
   if (threadIdx.x == 0) cnt = 0;
   __syncthreads();
   int c = 0;
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < n; b += gridDim.x * blockDim.x)
-    c += flags ? (flags[b] != 0) : 1;
+    c += (flags ? (flags[b] != 0) : 1) && !(exclude && exclude[b]);
   atomicAdd(&cnt, c);
   __syncthreads();
   if (threadIdx.x == 0 && cnt) atomicAdd(acc, cnt * bytes_per_unit);
 }
 
-void count_units(mr_grid *g, int kid, const int *flags, int n, double bytes_per_unit) {
+void count_units(mr_grid *g, int kid, const int *flags, int n, double bytes_per_unit, const int *exclude) {
   if (!g->profiling || n < 1) return;
-  MR_LAUNCH(g, MRK_MISC, k_units<<<(n + 255) / 256, 256, 0, g->stream>>>(flags, n, bytes_per_unit,
-                                                                         g->dscratch + MR_ALG_BYTES_SLOT + kid));
+  MR_LAUNCH(g, MRK_MISC, k_units<<<(n + 255) / 256, 256, 0, g->stream>>>(
+                             flags, n, bytes_per_unit, g->dscratch + MR_ALG_BYTES_SLOT + kid, exclude));
 }
 
 // internal shell: the requested one, the substitution reach, and what the
@@ -559,13 +655,25 @@ static int ghost_impl(mr_grid *g, const TI *phi_in, TI *phi_out, int G, TP *P, T
       check_cuda(cudaFuncSetAttribute(k_prep<TI, TP, N, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
                  "k_prep smem"))
     return MR_ERR_CUDA;
+  // full fills: leaves without a coarser neighbour are gathered by the plain
+  // kernel; the pre-pass takes the others (pneed)
+  const int *need_prep = need;
+  if (!only_coarse) {
+    MR_LAUNCH(g, MRK_PART2, k_fill_plain<TI, TP><<<n, 256, 0, g->stream>>>(t, phi_in, P, Gi, need, g->pneed,
+                                                                          g->cmask, err));
+    if (check_cuda(cudaGetLastError(), "k_fill_plain")) return MR_ERR_CUDA;
+    const double wd = nb + 2.0 * Gi;
+    count_units(g, MRK_PART2, need, n, (wd * wd * wd - (double)nb * nb * nb) * (double)(sizeof(TI) + sizeof(TP)),
+                g->pneed);
+    need_prep = g->pneed;
+  }
   MR_LAUNCH(g, MRK_PART1, k_prep<TI, TP, N, NT><<<n, 512, sm, g->stream>>>(t, phi_in, P, Q, Gi, G, only_coarse,
                                                                            use_tile, (int)smT, zc, g->cmask, err,
-                                                                           need));
+                                                                           need_prep));
   if (check_cuda(cudaGetLastError(), "k_prep")) return MR_ERR_CUDA;
   {
     const double wd = nb + 2.0 * Gi;
-    count_units(g, MRK_PART1, only_coarse ? g->cmask : need, n,
+    count_units(g, MRK_PART1, only_coarse ? g->cmask : need_prep, n,
                 (wd * wd * wd - (double)nb * nb * nb) * (double)(sizeof(TI) + sizeof(TP)));
   }
   if (only_coarse) return MR_OK;

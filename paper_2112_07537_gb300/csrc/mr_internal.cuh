@@ -389,6 +389,7 @@ struct mr_grid {
   double *dscratch;       // reduction scratch
   int *cmask;             // per-leaf coarse-direction masks (ghost fill), then new-band masks
   int *hasD;              // per new leaf: the update step has discarded details
+  int *pneed;             // per leaf: 1 = left to the full ghost pre-pass (has a coarser neighbour)
   void *vpad;             // ghost-filled velocity components (shell 3), 3 * cap * (nb+6)^3
   int tree_version;       // bumped whenever the leaves change
   int vel_version;        // tree version the velocity cache was built for (-1: none)
@@ -434,7 +435,8 @@ void *field_ptr(mr_grid *g, int fid);      // fid >= nfields: temporaries
 void *next_field_ptr(mr_grid *g, int fid);
 
 // ghost.cu
-void count_units(mr_grid *g, int kid, const int *flags, int n, double bytes_per_unit);
+void count_units(mr_grid *g, int kid, const int *flags, int n, double bytes_per_unit,
+                 const int *exclude = nullptr);
 int launch_ghost(mr_grid *g, const void *phi_in, void *phi_out, int G, bool fp64, void **P,
                  int *Gi, bool *p_is64 = nullptr, const int *need = nullptr);
 int launch_crop(mr_grid *g, const void *P, int Gi, void *out, int G, bool fp64_src);
