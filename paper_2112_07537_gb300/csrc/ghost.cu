@@ -76,7 +76,7 @@ template <typename TI, typename TP, int N, int NT>
 __global__ void __launch_bounds__(512, 1) k_prep(Tree t, const TI *__restrict__ phi, TP *__restrict__ P,
                                                  TP *__restrict__ Q, int Gi, int Gpush, int only_coarse,
                                                  int use_tile, int tile_bytes, int zc, int *cmask_out,
-                                                 int *err, const int *__restrict__ need) {
+                                                 int *err, const int *__restrict__ need, int prefilled) {
   using W = Wav<N, NT>;
   const int b = blockIdx.x;
   if (need && !need[b]) return;
@@ -186,13 +186,15 @@ __global__ void __launch_bounds__(512, 1) k_prep(Tree t, const TI *__restrict__ 
   const TI *phib = phi + (size_t)b * nb3;
   // every padded point outside the coarser leaves' regions (all points when
   // the tile is off): interior, same-level copy, coincident value of a finer
-  // leaf; one padded row per warp
-  for (int row = threadIdx.x >> 5; row < Wd * Wd; row += nwarp) {
+  // leaf; one padded row per warp.  prefilled: the plain gather has written
+  // every point outside the coarser leaves' regions already.
+  for (int row = threadIdx.x >> 5; row < ((prefilled && tile) ? 0 : Wd * Wd); row += nwarp) {
     const int j = row % Wd - Gi, k = row / Wd - Gi;
     const int ryz = 3 * (j < 0 ? 0 : j >= nb ? 2 : 1) + 9 * (k < 0 ? 0 : k >= nb ? 2 : 1);
     TP *prow = Pb + (size_t)row * Wd + Gi;
     for (int i = lane - Gi; i < nb + Gi; i += 32) {
       const int r = (i < 0 ? 0 : i >= nb ? 2 : 1) + ryz;
+      if (prefilled && (r == 13 || rlev[r] >= L)) continue;
       TP v;
       if (r == 13) {
         v = Cvt<TP>::f(ld(phib + i + nb * (j + nb * k)));
@@ -421,11 +423,12 @@ __global__ void __launch_bounds__(512, 1) k_prep(Tree t, const TI *__restrict__ 
 }
 
 // ---------------------------------------------------------------------------
-// Padded block of a leaf with no coarser neighbour -- the leaves whose ghost
-// fill (Alg. SM1) is a gather: interior, the values of same-level neighbours
-// (copy) and the coincident values of finer neighbours (their fine-to-coarse
-// values are merged afterwards, as for every leaf).  A leaf with a coarser
-// neighbour, or outside need, is flagged in pneed for the full pre-pass.
+// The gather part of every leaf's padded block (Alg. SM1): interior, the
+// values of same-level neighbours (copy) and the coincident values of finer
+// neighbours (their fine-to-coarse values are merged afterwards, as for every
+// leaf) -- everything but the regions of coarser leaves.  A leaf with a
+// coarser neighbour is flagged in pneed for the full pre-pass (refinement of
+// the coarse regions, substitution, Part-2 push).
 // Finer regions are resolved through the owners of their eight one-level-
 // finer sub-blocks (one lookup per sub-block, not per point).  Every field
 // read is bounds-checked: an out-of-range index sets error bit 16 and yields
@@ -460,11 +463,12 @@ __global__ void __launch_bounds__(256) k_fill_plain(Tree t, const TI *__restrict
     if (r != 13 && Lo < L) atomicOr(&coarse, 1);
   }
   __syncthreads();
-  if (coarse) {
-    if (threadIdx.x == 0) pneed[b] = 1;
-    return;
+  // a leaf with a coarser neighbour: its coarser regions and everything
+  // after the gather are the full pre-pass's (which also writes its cmask)
+  if (threadIdx.x == 0) {
+    pneed[b] = coarse ? 1 : 0;
+    if (!coarse) cmask_out[b] = 0;
   }
-  if (threadIdx.x == 0) pneed[b] = 0, cmask_out[b] = 0;
   for (int q = threadIdx.x; q < 216; q += blockDim.x) {
     const int r = q >> 3, h = q & 7;
     int o2 = -1;
@@ -489,6 +493,7 @@ __global__ void __launch_bounds__(256) k_fill_plain(Tree t, const TI *__restrict
       const int rx = i < 0 ? 0 : i >= nb ? 2 : 1, r = rx + 3 * ry + 9 * rz;
       const int ri = i - (rx - 1) * nb;
       const int Lo = rlev[r];
+      if (Lo < L) continue;  // a coarser leaf's region: refined by the pre-pass
       long long idx = -1;
       if (Lo == L) {
         idx = (long long)rslot[r] * (long long)nb3 + ri + nb * (rj + nb * rk);
@@ -669,7 +674,7 @@ static int ghost_impl(mr_grid *g, const TI *phi_in, TI *phi_out, int G, TP *P, T
   }
   MR_LAUNCH(g, MRK_PART1, k_prep<TI, TP, N, NT><<<n, 512, sm, g->stream>>>(t, phi_in, P, Q, Gi, G, only_coarse,
                                                                            use_tile, (int)smT, zc, g->cmask, err,
-                                                                           need_prep));
+                                                                           need_prep, only_coarse ? 0 : 1));
   if (check_cuda(cudaGetLastError(), "k_prep")) return MR_ERR_CUDA;
   {
     const double wd = nb + 2.0 * Gi;
