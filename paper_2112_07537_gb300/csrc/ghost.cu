@@ -148,21 +148,24 @@ __global__ void __launch_bounds__(512, 1) k_prep(Tree t, const TI *__restrict__ 
   // cells of the substitution band: per dimension [0, eb), [eb, nb-ef),
   // [nb-ef, nb); a cell is in the band when a coarser direction covers it
   __shared__ BoxList rbox, sbox;
-  if (threadIdx.x == 0) {
-    rbox.n = sbox.n = 0;
-    for (int r = 0; r < 27; ++r) {
-      if (!((mask >> r) & 1)) continue;
+  if (threadIdx.x < 32) {
+    // warp 0, one lane per region / cell; list positions from a ballot prefix
+    // (ascending region and cell order)
+    const int r = lane;
+    const bool isr = r < 27 && ((mask >> r) & 1);
+    const unsigned br = __ballot_sync(0xffffffffu, isr);
+    if (isr) {
+      const int pos = __popc(br & ((1u << r) - 1u));
       const int dd[3] = {r % 3 - 1, (r / 3) % 3 - 1, r / 9 - 1};
       for (int d = 0; d < 3; ++d) {
-        rbox.lo[rbox.n][d] = dd[d] < 0 ? -Gi : dd[d] > 0 ? nb : 0;
-        rbox.hi[rbox.n][d] = dd[d] < 0 ? 0 : dd[d] > 0 ? nb + Gi : nb;
+        rbox.lo[pos][d] = dd[d] < 0 ? -Gi : dd[d] > 0 ? nb : 0;
+        rbox.hi[pos][d] = dd[d] < 0 ? 0 : dd[d] > 0 ? nb + Gi : nb;
       }
-      ++rbox.n;
     }
-    const int cut[4] = {0, W::ext_b, nb - W::ext_f, nb};
-    for (int c = 0; c < 27; ++c) {
-      const int cc[3] = {c % 3, (c / 3) % 3, c / 9};
-      bool in = false;
+    const int c = lane;
+    bool in = false;
+    const int cc[3] = {c % 3, (c / 3) % 3, c / 9};
+    if (c < 27)
       for (int m = 0; m < 27 && !in; ++m) {
         if (!((mask >> m) & 1)) continue;
         const int dd[3] = {m % 3 - 1, (m / 3) % 3 - 1, m / 9 - 1};
@@ -170,10 +173,13 @@ __global__ void __launch_bounds__(512, 1) k_prep(Tree t, const TI *__restrict__ 
         for (int d = 0; d < 3; ++d) cov &= dd[d] == 0 || (dd[d] < 0 && cc[d] == 0) || (dd[d] > 0 && cc[d] == 2);
         in = cov;
       }
-      if (!in) continue;
-      for (int d = 0; d < 3; ++d) sbox.lo[sbox.n][d] = cut[cc[d]], sbox.hi[sbox.n][d] = cut[cc[d] + 1];
-      ++sbox.n;
+    const unsigned bc = __ballot_sync(0xffffffffu, in);
+    if (in) {
+      const int pos = __popc(bc & ((1u << c) - 1u));
+      const int cut[4] = {0, W::ext_b, nb - W::ext_f, nb};
+      for (int d = 0; d < 3; ++d) sbox.lo[pos][d] = cut[cc[d]], sbox.hi[pos][d] = cut[cc[d] + 1];
     }
+    if (lane == 0) rbox.n = __popc(br), sbox.n = __popc(bc);
   }
   if (tile) {
     // coarse tile, one row of nq values per warp
