@@ -9,9 +9,11 @@
 //          tensor H^a coarsening of the block at every ghost point of a
 //          coarser neighbour that it owns, pushed to a side buffer (Part 2);
 //   merge: side buffer -> padded block; substituted interior -> field.
-// The wavelet arithmetic uses explicitly rounded multiply/add in the same
-// order as a plain nested-loop evaluation, so the FP64 instantiation is
-// reproducible bit for bit.
+// The wavelet sums are fused multiply-adds evaluated separably where that
+// saves work (refinement per coarse region box, substitution per band box,
+// Part-2 coarsening), so they agree with a plain nested-loop evaluation to
+// rounding, not bit for bit; each is deterministic (one writer per value, a
+// fixed order of terms).
 #include <algorithm>
 #include <cstdio>
 
@@ -60,8 +62,7 @@ __device__ TP refine_point(const Tree &t, const TI *phi, int L, int gx, int gy, 
 //
 // T tile: every level-(L-1) value the zero-detail refinement of the padded
 // cube can read, fetched once (one owner lookup per coarse point instead of
-// one per tap).  Same taps, weights and summation order as refine_point, so
-// the FP64 instantiation stays bit-identical to the direct evaluation.
+// one per tap).  Same taps and weights as refine_point.
 // After the substitution, the leaf coarsens (tensor H^a) its padded block at
 // every ghost point (shell Gpush) of each coarser neighbour c that lies in
 // the leaf's region, and writes the value into c's entry of Q: each ghost
@@ -72,11 +73,168 @@ __host__ __device__ constexpr int tq_lo(int Gi) { return -((Gi + 2) / 2) - (N / 
 template <int N>
 __host__ __device__ constexpr int tq_hi(int nb, int Gi) { return (nb + Gi - 2) / 2 + N / 2; }
 
+// ---------------------------------------------------------------------------
+// Separable substitution of the parity classes of one degree (2 or 3) over
+// the band boxes.  A band point p of a class with odd dimensions o_1..o_deg
+// becomes -S(p), S(p) = sum over t != 0 (t along the odd dimensions) of
+// prod_d G^a(t_d) P(p + t).  S is summed one odd dimension at a time,
+// thinnest box side first, with the partial sums of each (box, class) job in
+// shared memory: pass 1 reads the padded block at every point the later
+// passes need (odd dimensions not yet summed span the box plus the G^a
+// half-width), pass deg writes -S into the block.  Pass 1 drops its t = 0 term
+// where every other odd coordinate is odd -- exactly at the class points,
+// which no other term of any pass reads -- so the product over all t leaves
+// out t = 0.  Points of one degree read lower degrees only, so all jobs of a
+// degree run together, batched so that their partial sums fit in cap
+// elements; a job that does not fit alone runs point by point.
+// ---------------------------------------------------------------------------
+struct SubJob {
+  int lo[3], hi[3];
+  int om;          // odd dimensions (bit d)
+  int o0, o1, o2;  // odd dimensions, ascending box side
+  bool empty;
+};
+
+__device__ __forceinline__ SubJob sub_job(const BoxList &bl, int j, int deg) {
+  SubJob J;
+  const int ncls = deg == 2 ? 3 : 1, e = j / ncls, k = j % ncls;
+  J.om = deg == 3 ? 7 : k == 0 ? 3 : k == 1 ? 5 : 6;
+  J.empty = false;
+  for (int d = 0; d < 3; ++d) {
+    J.lo[d] = bl.lo[e][d], J.hi[d] = bl.hi[e][d];
+    J.empty |= J.hi[d] <= J.lo[d];
+  }
+  int o[3], n = 0;
+  for (int d = 0; d < 3; ++d)
+    if ((J.om >> d) & 1) o[n++] = d;
+  for (int a = 1; a < n; ++a)
+    for (int b = a; b > 0 && J.hi[o[b]] - J.lo[o[b]] < J.hi[o[b - 1]] - J.lo[o[b - 1]]; --b) {
+      const int x = o[b];
+      o[b] = o[b - 1], o[b - 1] = x;
+    }
+  J.o0 = o[0], J.o1 = n > 1 ? o[1] : 0, J.o2 = n > 2 ? o[2] : 0;
+  return J;
+}
+
+// positions start + step * i (i < count) of stage s (s odd dimensions summed)
+__device__ __forceinline__ void sub_stage(const SubJob &J, int s, int hG, int st[3], int sp[3], int cn[3]) {
+  const int sm = (s >= 1 ? 1 << J.o0 : 0) | (s >= 2 ? 1 << J.o1 : 0) | (s >= 3 ? 1 << J.o2 : 0);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int odd = (J.om >> d) & 1;
+    if (odd && !((sm >> d) & 1)) {
+      st[d] = J.lo[d] - hG, sp[d] = 1, cn[d] = J.hi[d] - J.lo[d] + 2 * hG;
+    } else {
+      st[d] = par_first(J.lo[d], odd), sp[d] = 2, cn[d] = par_count(J.lo[d], J.hi[d], odd);
+    }
+  }
+}
+
+__device__ __forceinline__ long sub_elems(const SubJob &J, int s, int hG) {
+  int st[3], sp[3], cn[3];
+  sub_stage(J, s, hG, st, sp, cn);
+  return J.empty ? 0 : (long)cn[0] * cn[1] * cn[2];
+}
+
+template <int N, int NT, typename TP>
+__device__ void subst_sep(TP *__restrict__ Pb, int Wd, int Gi, const BoxList &bl, int deg, TP *__restrict__ buf,
+                          long cap) {
+  using W = Wav<N, NT>;
+  constexpr int hG = W::hwG;
+  const long ps1 = Wd, ps2 = (long)Wd * Wd;
+  const int njob = bl.n * (deg == 2 ? 3 : 1), bd = blockDim.x;
+  // buffer elements of a job: stages 1 .. deg-1
+  auto job_buf = [&](const SubJob &J) -> long {
+    return sub_elems(J, 1, hG) + (deg == 3 ? sub_elems(J, 2, hG) : 0);
+  };
+  int j0 = 0;
+  while (j0 < njob) {
+    long used = 0;
+    int j1 = j0;
+    while (j1 < njob) {
+      const long sz = job_buf(sub_job(bl, j1, deg));
+      if (j1 > j0 && used + sz > cap) break;
+      used += sz, ++j1;
+    }
+    if (used > cap) {
+      // one job too large for the buffer: point by point
+      const SubJob J = sub_job(bl, j0, deg);
+      int st[3], sp[3], cn[3];
+      sub_stage(J, deg, hG, st, sp, cn);
+      const long n = J.empty ? 0 : (long)cn[0] * cn[1] * cn[2];
+      for (long idx = threadIdx.x; idx < n; idx += bd) {
+        const int i0 = (int)(idx % cn[0]), r = (int)(idx / cn[0]), i1 = r % cn[1], i2 = r / cn[1];
+        TP *c = Pb + (st[0] + sp[0] * i0 + Gi) + ps1 * (st[1] + sp[1] * i1 + Gi) + ps2 * (st[2] + sp[2] * i2 + Gi);
+        *c = subst_dispatch<N, NT, TP>(J.om & 1, J.om & 2, J.om & 4, [&](int tx, int ty, int tz) -> TP {
+          return c[tx + ps1 * ty + ps2 * tz];
+        });
+      }
+      __syncthreads();
+      j0 = j1;
+      continue;
+    }
+    for (int s = 1; s <= deg; ++s) {
+      long base = 0, off = 0;
+      for (int j = j0; j < j1; ++j) {
+        const SubJob J = sub_job(bl, j, deg);
+        const long n1 = sub_elems(J, 1, hG), n2 = deg == 3 ? sub_elems(J, 2, hG) : 0;
+        int st[3], sp[3], cn[3], pst[3], psp[3], pcn[3];
+        sub_stage(J, s, hG, st, sp, cn);
+        sub_stage(J, s - 1 > 0 ? s - 1 : 1, hG, pst, psp, pcn);
+        const long n = J.empty ? 0 : (long)cn[0] * cn[1] * cn[2];
+        const int d = s == 1 ? J.o0 : s == 2 ? J.o1 : J.o2;  // dimension summed in this pass
+        TP *dst = buf + off + (s == 2 ? n1 : 0);
+        const TP *prev = buf + off + (s == 3 ? n1 : 0);
+        const long q1 = pcn[0], q2 = (long)pcn[0] * pcn[1];
+        const int oth = J.om & ~(1 << d);
+        long idx = ((long)threadIdx.x - base) % bd;
+        if (idx < 0) idx += bd;
+        for (; idx < n; idx += bd) {
+          const int i0 = (int)(idx % cn[0]), r = (int)(idx / cn[0]), i1 = r % cn[1], i2 = r / cn[1];
+          const int p0 = st[0] + sp[0] * i0, p1 = st[1] + sp[1] * i1, p2 = st[2] + sp[2] * i2;
+          TP acc = TP(0);
+          if (s == 1) {
+            const TP *src = Pb + (p0 + Gi) + ps1 * (p1 + Gi) + ps2 * (p2 + Gi);
+            const long str = d == 0 ? 1 : d == 1 ? ps1 : ps2;
+            const bool keep0 = ((oth & 1) && !(p0 & 1)) || ((oth & 2) && !(p1 & 1)) || ((oth & 4) && !(p2 & 1));
+#pragma unroll
+            for (int t = -hG; t <= hG; ++t) {
+              if (W::G(t) == 0.0) continue;
+              if (t == 0) {
+                if (keep0) acc = racc(acc, TP(1), src[0]);
+              } else {
+                acc = racc(acc, TP(W::G(t)), src[t * str]);
+              }
+            }
+          } else {
+            const int c0 = d == 0 ? p0 - pst[0] : i0, c1 = d == 1 ? p1 - pst[1] : i1, c2 = d == 2 ? p2 - pst[2] : i2;
+            const TP *src = prev + c0 + q1 * c1 + q2 * c2;
+            const long str = d == 0 ? 1 : d == 1 ? q1 : q2;
+#pragma unroll
+            for (int t = -hG; t <= hG; ++t) {
+              if (W::G(t) == 0.0) continue;
+              acc = racc(acc, TP(W::G(t)), src[t * str]);
+            }
+          }
+          if (s == deg)
+            Pb[(p0 + Gi) + ps1 * (p1 + Gi) + ps2 * (p2 + Gi)] = -acc;
+          else
+            dst[idx] = acc;
+        }
+        base += n, off += n1 + n2;
+      }
+      __syncthreads();
+    }
+    j0 = j1;
+  }
+}
+
 template <typename TI, typename TP, int N, int NT>
 __global__ void __launch_bounds__(512, 1) k_prep(Tree t, const TI *__restrict__ phi, TP *__restrict__ P,
                                                  TP *__restrict__ Q, int Gi, int Gpush, int only_coarse,
                                                  int use_tile, int tile_bytes, int zc, int *cmask_out,
-                                                 int *err, const int *__restrict__ need, int prefilled) {
+                                                 int *err, const int *__restrict__ need, int prefilled,
+                                                 int dyn_bytes) {
   using W = Wav<N, NT>;
   const int b = blockIdx.x;
   if (need && !need[b]) return;
@@ -162,6 +320,11 @@ __global__ void __launch_bounds__(512, 1) k_prep(Tree t, const TI *__restrict__ 
         rbox.hi[pos][d] = dd[d] < 0 ? 0 : dd[d] > 0 ? nb + Gi : nb;
       }
     }
+    // per dimension the cuts 0 <= a <= b <= nb, a = min(ext_b, nb - ext_f),
+    // b = max(...): [0, a) lies in the band of a coarser leaf on the - side
+    // only, [b, nb) in that of the + side only, [a, b) in neither (or, when
+    // the two bands overlap -- small blocks -- in both)
+    const bool ov = W::ext_b > nb - W::ext_f;
     const int c = lane;
     bool in = false;
     const int cc[3] = {c % 3, (c / 3) % 3, c / 9};
@@ -170,16 +333,41 @@ __global__ void __launch_bounds__(512, 1) k_prep(Tree t, const TI *__restrict__ 
         if (!((mask >> m) & 1)) continue;
         const int dd[3] = {m % 3 - 1, (m / 3) % 3 - 1, m / 9 - 1};
         bool cov = true;
-        for (int d = 0; d < 3; ++d) cov &= dd[d] == 0 || (dd[d] < 0 && cc[d] == 0) || (dd[d] > 0 && cc[d] == 2);
+        for (int d = 0; d < 3; ++d)
+          cov &= dd[d] == 0 || (dd[d] < 0 && (cc[d] == 0 || (ov && cc[d] == 1))) ||
+                 (dd[d] > 0 && (cc[d] == 2 || (ov && cc[d] == 1)));
         in = cov;
       }
     const unsigned bc = __ballot_sync(0xffffffffu, in);
-    if (in) {
-      const int pos = __popc(bc & ((1u << c) - 1u));
-      const int cut[4] = {0, W::ext_b, nb - W::ext_f, nb};
-      for (int d = 0; d < 3; ++d) sbox.lo[pos][d] = cut[cc[d]], sbox.hi[pos][d] = cut[cc[d] + 1];
+    if (lane == 0) {
+      rbox.n = __popc(br);
+      // band boxes: the (disjoint) band cells merged greedily, x run first,
+      // then y, then z
+      const int cut[4] = {0, ov ? nb - W::ext_f : W::ext_b, ov ? W::ext_b : nb - W::ext_f, nb};
+      auto rect = [](int xa, int xb, int ya, int yb, int za, int zb) {
+        unsigned m = 0;
+        for (int z = za; z < zb; ++z)
+          for (int y = ya; y < yb; ++y)
+            for (int x = xa; x < xb; ++x) m |= 1u << (x + 3 * y + 9 * z);
+        return m;
+      };
+      unsigned left = bc;
+      int n = 0;
+      while (left) {
+        const int c0 = __ffs(left) - 1;
+        const int x0 = c0 % 3, y0 = (c0 / 3) % 3, z0 = c0 / 9;
+        int x1 = x0 + 1, y1 = y0 + 1, z1 = z0 + 1;
+        while (x1 < 3 && ((left >> (x1 + 3 * y0 + 9 * z0)) & 1)) ++x1;
+        while (y1 < 3 && (left & rect(x0, x1, y1, y1 + 1, z0, z0 + 1)) == rect(x0, x1, y1, y1 + 1, z0, z0 + 1)) ++y1;
+        while (z1 < 3 && (left & rect(x0, x1, y0, y1, z1, z1 + 1)) == rect(x0, x1, y0, y1, z1, z1 + 1)) ++z1;
+        left &= ~rect(x0, x1, y0, y1, z0, z1);
+        sbox.lo[n][0] = cut[x0], sbox.hi[n][0] = cut[x1];
+        sbox.lo[n][1] = cut[y0], sbox.hi[n][1] = cut[y1];
+        sbox.lo[n][2] = cut[z0], sbox.hi[n][2] = cut[z1];
+        ++n;
+      }
+      sbox.n = n;
     }
-    if (lane == 0) rbox.n = __popc(br), sbox.n = __popc(bc);
   }
   if (tile) {
     // coarse tile, one row of nq values per warp
@@ -354,11 +542,10 @@ __global__ void __launch_bounds__(512, 1) k_prep(Tree t, const TI *__restrict__ 
   subst_cls(Cls<0, 1, 0>());
   subst_cls(Cls<0, 0, 1>());
   __syncthreads();
-  subst_cls(Cls<1, 1, 0>());
-  subst_cls(Cls<1, 0, 1>());
-  subst_cls(Cls<0, 1, 1>());
-  __syncthreads();
-  subst_cls(Cls<1, 1, 1>());
+  // degrees 2 and 3 separably, partial sums in the (now free) dynamic shared
+  // memory; each batch ends with a barrier
+  subst_sep<N, NT, TP>(Pb, Wd, Gi, sbox, 2, reinterpret_cast<TP *>(smraw), (long)dyn_bytes / (long)sizeof(TP));
+  subst_sep<N, NT, TP>(Pb, Wd, Gi, sbox, 3, reinterpret_cast<TP *>(smraw), (long)dyn_bytes / (long)sizeof(TP));
   __syncthreads();
   // distinct coarser neighbours
   if (threadIdx.x == 0) {
@@ -680,7 +867,7 @@ static int ghost_impl(mr_grid *g, const TI *phi_in, TI *phi_out, int G, TP *P, T
   }
   MR_LAUNCH(g, MRK_PART1, k_prep<TI, TP, N, NT><<<n, 512, sm, g->stream>>>(t, phi_in, P, Q, Gi, G, only_coarse,
                                                                            use_tile, (int)smT, zc, g->cmask, err,
-                                                                           need_prep, only_coarse ? 0 : 1));
+                                                                           need_prep, only_coarse ? 0 : 1, (int)sm));
   if (check_cuda(cudaGetLastError(), "k_prep")) return MR_ERR_CUDA;
   {
     const double wd = nb + 2.0 * Gi;
