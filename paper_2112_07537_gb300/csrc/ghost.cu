@@ -413,6 +413,9 @@ __global__ void __launch_bounds__(512, 1) k_prep(Tree t, const TI *__restrict__ 
   // region box when the partial sums fit next to the tile (use_tile == 2),
   // else one parity class at a time (every warp runs one tap sequence)
   if (tile && use_tile == 2) {
+    // float pairs for an FP32 field in an FP64 block (the tile holds exact
+    // FP32 values and the K^s weights are dyadic, exact in FP32)
+    constexpr bool FP = sizeof(TI) == 4 && sizeof(TP) == 8 && f32_exact_taps<N, NT, FK_K>();
     TP *U = reinterpret_cast<TP *>(smraw + tile_bytes);
     constexpr int ko = N - 1;  // widest odd K^s tap
     const long ts[3] = {1, nq, (long)nq * nq}, ps[3] = {1, Wd, (long)Wd * Wd};
@@ -442,6 +445,75 @@ __global__ void __launch_bounds__(512, 1) k_prep(Tree t, const TI *__restrict__ 
       const int la = fl[a], lb = fl[bd], lc = fl[c], cb = cl[bd], cc = cl[c];
       const long tsa = ts[a], tsb = ts[bd], tsc = ts[c], psa = ps[a], psb = ps[bd], psc = ps[c];
       TP *U1 = U, *U2 = U + (size_t)nfa * ncb * ncc;
+      if constexpr (FP) {
+        // FP32 field, FP64 block: the three passes in float pairs (same
+        // layout, 8 bytes per partial sum), one conversion per written point
+        F2 *V1 = reinterpret_cast<F2 *>(U1), *V2 = reinterpret_cast<F2 *>(U2);
+        {
+          const int no = par_count(la, la + nfa, 1), ne = nfa - no, m = ncb * ncc;
+          for (int idx = threadIdx.x; idx < nfa * m; idx += blockDim.x) {
+            const bool od = idx < no * m;
+            const int q = od ? idx : idx - no * m, nh = od ? no : ne;
+            const int f = par_first(la, od) + 2 * (q % nh), r = q / nh, jb = r % ncb, kc = r / ncb;
+            const TI *tp = T + (cb + jb - qlo) * tsb + (cc + kc - qlo) * tsc;
+            F2 v;
+            if (od) {
+              v = f2_of(0.f);
+#pragma unroll
+              for (int t = -ko; t <= ko; t += 2)
+                v = f2_acc(v, float(Wav<N, NT>::K(t)), f2_of(tp[(((f + t) >> 1) - qlo) * tsa]));
+              v = f2_norm(v);
+            } else {
+              v = f2_of(tp[((f >> 1) - qlo) * tsa]);
+            }
+            V1[(f - la) + nfa * (jb + ncb * kc)] = v;
+          }
+        }
+        __syncthreads();
+        {
+          const int no = par_count(lb, lb + nfb, 1), ne = nfb - no;
+          for (int idx = threadIdx.x; idx < nfa * nfb * ncc; idx += blockDim.x) {
+            const bool od = idx < nfa * no * ncc;
+            const int q = od ? idx : idx - nfa * no * ncc, nh = od ? no : ne;
+            const int ia = q % nfa, f = par_first(lb, od) + 2 * ((q / nfa) % nh), kc = q / (nfa * nh);
+            const F2 *up = V1 + ia + (size_t)nfa * ncb * kc;
+            F2 v;
+            if (od) {
+              v = f2_of(0.f);
+#pragma unroll
+              for (int t = -ko; t <= ko; t += 2) v = f2_acc(v, float(Wav<N, NT>::K(t)), up[nfa * (((f + t) >> 1) - cb)]);
+              v = f2_norm(v);
+            } else {
+              v = up[nfa * ((f >> 1) - cb)];
+            }
+            V2[ia + nfa * ((f - lb) + nfb * kc)] = v;
+          }
+        }
+        __syncthreads();
+        {
+          const int no = par_count(lc, lc + nfc, 1), ne = nfc - no, m = nfa * nfb;
+          for (int idx = threadIdx.x; idx < m * nfc; idx += blockDim.x) {
+            const bool od = idx < m * no;
+            const int q = od ? idx : idx - m * no, nh = od ? no : ne;
+            const int ia = q % nfa, ib = (q / nfa) % nfb, f = par_first(lc, od) + 2 * (q / m);
+            const F2 *up = V2 + ia + (size_t)nfa * ib;
+            F2 v;
+            if (od) {
+              v = f2_of(0.f);
+#pragma unroll
+              for (int t = -ko; t <= ko; t += 2)
+                v = f2_acc(v, float(Wav<N, NT>::K(t)), up[(size_t)m * (((f + t) >> 1) - cc)]);
+            } else {
+              v = up[(size_t)m * ((f >> 1) - cc)];
+            }
+            const TP d = f2_dbl(v);
+            if (nan_bits(d)) atomicOr(err, 2);
+            Pb[(la + ia + Gi) * psa + (lb + ib + Gi) * psb + (f + Gi) * psc] = d;
+          }
+        }
+        __syncthreads();
+        continue;
+      }
       // pass 1: along a, coarse tile -> U1[ia][jb][kc] (odd fine points first)
       {
         const int no = par_count(la, la + nfa, 1), ne = nfa - no, m = ncb * ncc;

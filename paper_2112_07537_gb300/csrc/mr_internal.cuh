@@ -89,6 +89,47 @@ __device__ __forceinline__ double widen(float f) {
   return __longlong_as_double(
       (long long)(sgn | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29)));
 }
+// float -> double as widen(), with subnormals flushed to zero (for the small
+// part of a float pair, where they are far below the pair's precision)
+__device__ __forceinline__ double widen_ftz(float f) {
+  const unsigned u = __float_as_uint(f), e = (u >> 23) & 0xffu;
+  const unsigned long long sgn = (unsigned long long)(u >> 31) << 63;
+  if (e == 0u) return __longlong_as_double((long long)sgn);
+  if (e == 0xffu) return (double)f;
+  return __longlong_as_double(
+      (long long)(sgn | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+
+// ---------------------------------------------------------------------------
+// Float pairs: a value h + l held as two FP32 numbers (about 48 significant
+// bits), for tap sums of FP64 accuracy on the FP32 pipe, which on this part is
+// dozens of times wider than the FP64 pipe.  A product w * h with an exact
+// FP32 weight is split exactly (its rounding error recovered by an FMA), the
+// high parts are added error-free (two-sum: s = a + b, e = (a - (s - b')) +
+// (b - b'), b' = s - a), and the low parts collect those errors plus w * l.
+// A sum of a few taps then carries a relative error of a few 2^-48 of its
+// largest term.  The rounded intrinsics keep the compiler from contracting
+// the splits into FMAs.
+// ---------------------------------------------------------------------------
+struct F2 {
+  float h, l;
+};
+__device__ __forceinline__ F2 f2_of(float v) { return {v, 0.f}; }
+// s + w * v (not renormalised)
+__device__ __forceinline__ F2 f2_acc(F2 s, float w, F2 v) {
+  const float p = __fmul_rn(w, v.h);
+  const float pe = fmaf(w, v.h, -p);
+  const float sh = __fadd_rn(s.h, p);
+  const float bb = __fadd_rn(sh, -s.h);
+  const float e = __fadd_rn(__fadd_rn(s.h, -__fadd_rn(sh, -bb)), __fadd_rn(p, -bb));
+  return {sh, __fadd_rn(s.l, __fadd_rn(e, fmaf(w, v.l, pe)))};
+}
+__device__ __forceinline__ F2 f2_norm(F2 a) {
+  const float s = __fadd_rn(a.h, a.l);
+  return {s, __fadd_rn(a.l, -__fadd_rn(s, -a.h))};
+}
+__device__ __forceinline__ double f2_dbl(F2 a) { return __dadd_rn(widen(a.h), widen_ftz(a.l)); }
+
 // value of the field element type TI in the working precision TP
 template <typename TP>
 struct Cvt;
@@ -122,6 +163,14 @@ struct Taps {
     return KIND == FK_H ? W::H(t) : KIND == FK_G ? W::G(t) : KIND == FK_J ? W::J(t) : W::K(t);
   }
 };
+
+// every nonzero tap weight of the filter is an FP32 number exactly
+template <int N, int NT, int KIND>
+__host__ __device__ constexpr bool f32_exact_taps() {
+  for (int t = -Taps<N, NT, KIND>::hw; t <= Taps<N, NT, KIND>::hw; ++t)
+    if ((double)(float)Taps<N, NT, KIND>::w(t) != Taps<N, NT, KIND>::w(t)) return false;
+  return true;
+}
 template <int N, int NT, int KIND, typename F>
 __device__ __forceinline__ void for_taps(F f) {
   using TK = Taps<N, NT, KIND>;
