@@ -369,7 +369,29 @@ __global__ void __launch_bounds__(512, 1) k_prep(Tree t, const TI *__restrict__ 
       sbox.n = n;
     }
   }
-  if (tile) {
+  if (tile && use_tile == 2) {
+    // coarse tile: only the level-(L-1) points the separable refinement
+    // reads -- per coarser region box, its fine extent widened by the widest
+    // odd K^s tap and halved (overlaps of boxes load the same values twice)
+    __syncthreads();  // rbox
+    constexpr int ko = N - 1;
+    for (int e = 0; e < rbox.n; ++e) {
+      int cl[3], cn[3];
+      bool ok = true;
+      for (int d = 0; d < 3; ++d) {
+        const int fl = rbox.lo[e][d], fh = rbox.hi[e][d];
+        cl[d] = (fl - ko) >> 1;
+        cn[d] = ((fh - 1 + ko) >> 1) - cl[d] + 1;
+        ok &= cl[d] >= qlo && cl[d] + cn[d] <= qlo + nq;
+      }
+      if (!ok) continue;  // flagged by the refinement below
+      const int m = cn[0] * cn[1];
+      for (int idx = threadIdx.x; idx < m * cn[2]; idx += blockDim.x) {
+        const int qx = cl[0] + idx % cn[0], qy = cl[1] + (idx / cn[0]) % cn[1], qz = cl[2] + idx / m;
+        T[(qx - qlo) + (size_t)nq * ((qy - qlo) + (size_t)nq * (qz - qlo))] = fetch_raw(L - 1, qx, qy, qz);
+      }
+    }
+  } else if (tile) {
     // coarse tile, one row of nq values per warp
     for (int row = threadIdx.x >> 5; row < nq * nq; row += nwarp) {
       const int qy = qlo + row % nq, qz = qlo + row / nq;
