@@ -230,7 +230,7 @@ __device__ void subst_sep(TP *__restrict__ Pb, int Wd, int Gi, const BoxList &bl
 }
 
 template <typename TI, typename TP, int N, int NT>
-__global__ void __launch_bounds__(512, 1) k_prep(Tree t, const TI *__restrict__ phi, TP *__restrict__ P,
+__global__ void __launch_bounds__(512, sizeof(TP) == 4 ? 2 : 1) k_prep(Tree t, const TI *__restrict__ phi, TP *__restrict__ P,
                                                  TP *__restrict__ Q, int Gi, int Gpush, int only_coarse,
                                                  int use_tile, int tile_bytes, int zc, int *cmask_out,
                                                  int *err, const int *__restrict__ need, int prefilled,
