@@ -124,7 +124,7 @@ __device__ __forceinline__ void detail_planes(const double *__restrict__ Pb, int
 // Per leaf: max |gamma| over the extended region (Sec. 2.3, the block norm
 // that drives refinement and coarsening).
 template <int N, int NT>
-__global__ void __launch_bounds__(512) k_criterion(Tree t, const double *__restrict__ P, int Gi,
+__global__ void __launch_bounds__(1024) k_criterion(Tree t, const double *__restrict__ P, int Gi,
                                                    double *__restrict__ maxdet) {
   const int b = blockIdx.x, nb = t.nb, Wd = nb + 2 * Gi;
   extern __shared__ double sm[];
@@ -159,7 +159,7 @@ static int criterion_impl(mr_grid *g, const double *P, int Gi, double *maxdet) {
                  "criterion smem"))
     return MR_ERR_CUDA;
   Tree t = tree_view(g);
-  MR_LAUNCH(g, MRK_CRITERION, k_criterion<N, NT><<<g->nleaf, 512, sm, g->stream>>>(t, P, Gi, maxdet));
+  MR_LAUNCH(g, MRK_CRITERION, k_criterion<N, NT><<<g->nleaf, 1024, sm, g->stream>>>(t, P, Gi, maxdet));
   return check_cuda(cudaGetLastError(), "k_criterion") ? MR_ERR_CUDA : MR_OK;
 }
 
@@ -415,7 +415,7 @@ __global__ void k_newmask(Tree tn, const int *src, int *nmask) {
 // all of D in its region, an unchanged same-level leaf with newly coarsened
 // neighbours owns the part of its band next to them, finer leaves none.
 template <int N, int NT>
-__global__ void __launch_bounds__(256) k_update_gamma(Tree tn, const int *__restrict__ src,
+__global__ void __launch_bounds__(1024) k_update_gamma(Tree tn, const int *__restrict__ src,
                                                       const int *__restrict__ nmask,
                                                       const double *__restrict__ P, int Gi,
                                                       double *__restrict__ Q, int *hasD) {
@@ -633,7 +633,7 @@ static int interp_update(mr_grid *g, const Tree &to, const Tree &tn, const doubl
                                       (int)sma),
                  "update smem"))
     return MR_ERR_CUDA;
-  MR_LAUNCH(g, MRK_UPDATE, k_update_gamma<N, NT><<<tn.nleaf, 256, smg, g->stream>>>(tn, src, nmask, P, Gi,
+  MR_LAUNCH(g, MRK_UPDATE, k_update_gamma<N, NT><<<tn.nleaf, 1024, smg, g->stream>>>(tn, src, nmask, P, Gi,
                                                                                    g->padQ64, hasD));
   MR_LAUNCH(g, MRK_UPDATE, k_update_apply<TO, N, NT><<<tn.nleaf, 256, sma, g->stream>>>(
                                tn, src, hasD, g->padQ64, Gi, (TO *)next_field_ptr(g, fid)));
