@@ -163,17 +163,24 @@ int mr_ghost_fill64(mr_grid *grid, int fid, int G, double *padded);
  * memory when they call it (no cudaMalloc, no pool or framework allocator:
  * for example code running inside another runtime's fixed memory budget).
  * The paper has no counterpart: this is a packaging variant of
- * mr_ghost_fill, with the same arguments, semantics and results.
+ * mr_ghost_fill, with the same arguments, semantics and results (the same
+ * kernels in the same precision: where mr_ghost_fill computes the padded
+ * blocks of an FP32 grid in FP64 -- internal shells wider than the stencil
+ * shell -- so does this call, and it returns MR_ERR_UNSUPPORTED wherever
+ * mr_ghost_fill does).
  * Its scratch -- the padded blocks and the fine-to-coarse side buffer --
  * lives in one 64 MiB array of static device memory that every GPU loading
  * the library keeps until the process exits; grids whose
- * 2 * nleaf * (nb + 2*Gi)^3 elements (Gi >= G: the internal shell) exceed it
+ * 2 * nleaf * (nb + 2*Gi)^3 padded elements (Gi >= G: the internal shell;
+ * 8 bytes each on the FP64 path, else the field's element size) exceed it
  * are rejected with MR_ERR_NOMEM.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current,
- * so make that first call before any stream capture.  All calls share the
- * array: calls that overlap on the GPU (different streams, or grids used
- * concurrently) race on it; serialise them.  Nothing in the array needs to
- * start at zero (every value read is written first in the same call).    */
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture (a first call made while
+ * the grid's stream is capturing is refused with MR_ERR_INVALID).  All calls
+ * share the array: calls that overlap on the GPU (different streams, or
+ * grids used concurrently) race on it; serialise them.  Nothing in the array
+ * needs to start at zero (every value read is written first in the same
+ * call).                                                                  */
 int mr_ghost_fill_static(mr_grid *grid, int fid, int G, void *padded);
 
 /* Wait for the grid's stream and report device-side errors recorded by the

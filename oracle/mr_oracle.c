@@ -11,7 +11,8 @@
  * Build with -ffp-contract=off so that a*b+c is never fused: every sum is the
  * plain term-by-term evaluation of its definition.
  *
- * Conventions (the paper's readings are listed in the design notes):
+ * Conventions (where the paper leaves a choice open, the reading taken is
+ * stated at the function that implements it):
  *  - forest of nt[0] x nt[1] x nt[2] trees of edge tree_len, periodic in every
  *    direction; a leaf block at level L has anchor a (in units of blocks at
  *    level L) and nb^3 points; point i of the block sits at (a*nb + i) * h_L,
@@ -537,6 +538,19 @@ int og_ghost_fill(const og_grid *g, const double *phi_in, int G, double *out_pad
 static const double OG_WENO_EPS = 1e-30;
 static const double OG_WENO_RCAP = 1e15;
 
+/* Smoothness indicators of the three sub-stencils of Table SM4 on the five
+ * values v[0..4] of one reconstruction: beta_k from (v[k], v[k+1], v[k+2]),
+ * 1/4 (first difference at the reconstruction cell)^2 + 13/12 (second
+ * difference)^2, as printed.                                               */
+void og_weno_beta(const double *v, double *beta) {
+  double t0 = v[0] - 4 * v[1] + 3 * v[2], u0 = v[0] - 2 * v[1] + v[2];
+  double t1 = -v[1] + v[3], u1 = v[1] - 2 * v[2] + v[3];
+  double t2 = -3 * v[2] + 4 * v[3] - v[4], u2 = v[2] - 2 * v[3] + v[4];
+  beta[0] = 0.25 * t0 * t0 + (13.0 / 12) * u0 * u0;
+  beta[1] = 0.25 * t1 * t1 + (13.0 / 12) * u1 * u1;
+  beta[2] = 0.25 * t2 * t2 + (13.0 / 12) * u2 * u2;
+}
+
 /* Interface flux F_{i+1/2} from point fluxes f[0..5] = f_{i-2..i+3}, upwind
  * side chosen by the sign of the interface velocity (Tables SM3, SM4).      */
 static double iface_flux(int scheme, const double *f, int upwind_left) {
@@ -568,12 +582,8 @@ static double iface_flux(int scheme, const double *f, int upwind_left) {
   }
   if (scheme == OG_CONS5) return gam[0] * s[0] + gam[1] * s[1] + gam[2] * s[2];
   {
-    double t0 = a - 4 * b + 3 * cc, u0 = a - 2 * b + cc;
-    double t1 = -b + d, u1 = b - 2 * cc + d;
-    double t2 = -3 * cc + 4 * d - ee, u2 = cc - 2 * d + ee;
-    beta[0] = 0.25 * t0 * t0 + (13.0 / 12) * u0 * u0;
-    beta[1] = 0.25 * t1 * t1 + (13.0 / 12) * u1 * u1;
-    beta[2] = 0.25 * t2 * t2 + (13.0 / 12) * u2 * u2;
+    const double v[5] = {a, b, cc, d, ee};
+    og_weno_beta(v, beta);
   }
   double tau = fabs(beta[0] - beta[2]);
   double al[3], sum = 0.0;
@@ -584,6 +594,11 @@ static double iface_flux(int scheme, const double *f, int upwind_left) {
     sum += al[k];
   }
   return (al[0] * s[0] + al[1] * s[1] + al[2] * s[2]) / sum;
+}
+
+/* The interface flux of one scheme, exported for the pinning tests. */
+double og_iface_flux(int scheme, const double *f6, int upwind_left) {
+  return iface_flux(scheme, f6, upwind_left);
 }
 
 /* rhs = -sum_d (F_{i+1/2} - F_{i-1/2}) / h_L on every leaf, from a padded
@@ -1028,18 +1043,164 @@ int og_adapt_shell(int N, int Nt) {
 }
 
 /*
- * One iteration of Alg. SM3: ghost fill, criterion, status, policy, new tree
- * (children in Morton order at the parent's position, a parent at its first
- * child's position), interpolation, update step for lifted wavelets.
+ * Interpolation and update step of one field for a decided tree change
+ * (Alg. SM3 steps 6 and 9, applied to every field of the grid): new leaves
+ * from the field's padded blocks on the old grid (refinement of a parent,
+ * coarsening of 8 siblings, copy of the substituted values of unchanged
+ * leaves), then the update step (eq 2.22) of unchanged leaves next to a
+ * newly coarsened neighbour one level coarser: subtract the synthesis of the
+ * level-(L-1) details that the coarsening discarded.  In 3D this is needed
+ * for N.0 as well (Table 2.2 lists update ghosts for 3D N.0): a discarded
+ * 1-degree detail enters the synthesis of the adjacent 2- and 3-degree points.
+ * pad / phis: the field's padded blocks (shell G) and substituted values on
+ * the old grid; st / newidx: statuses and the new index of every old leaf;
+ * gn: the new grid (n leaves).
+ */
+static int apply_tree_change(const og_ctx *c, const og_grid *gn, const int8_t *st, const int32_t *newidx,
+                             const double *pad, int G, const double *phis, double *phi_out) {
+  const og_grid *g = c->g;
+  const int nb = g->nb, W = nb + 2 * G;
+  const size_t np = (size_t)W * W * W, nb3 = (size_t)nb * nb * nb;
+  const int n = gn->nleaf;
+  int changed = 0;
+  for (int b = 0; b < g->nleaf; ++b) {
+    const int32_t *a = g->anc + 3 * b;
+    const int L = g->lev[b];
+    const int q = newidx[b];
+    if (st[b] == OG_FINER) {
+      changed++;
+      for (int ch = 0; ch < 8; ++ch) refine_child(c, pad + b * np, G, ch, phi_out + (size_t)(q + ch) * nb3);
+    } else if (st[b] == OG_COARSER) {
+      changed++;
+      if ((a[0] | a[1] | a[2]) & 1) continue; /* not the first sibling */
+      const double *Pch[8];
+      for (int ch = 0; ch < 8; ++ch) {
+        int s = c->lut[L][(a[0] + (ch & 1)) + c->dim[L][0] * ((a[1] + ((ch >> 1) & 1)) +
+                                                            c->dim[L][1] * (long)(a[2] + (ch >> 2)))];
+        Pch[ch] = pad + s * np;
+      }
+      coarsen_children(c, Pch, G, phi_out + (size_t)q * nb3);
+    } else {
+      memcpy(phi_out + (size_t)q * nb3, phis + (size_t)b * nb3, sizeof(double) * nb3);
+    }
+  }
+  if (!changed) return OG_OK;
+  const int32_t *lev_out = gn->lev, *anc_out = gn->anc;
+  og_ctx cn;
+  int e = ctx_init(&cn, gn);
+  if (e) return e;
+  int8_t *newly_coarse = (int8_t *)calloc(n, 1);
+  for (int b = 0; b < g->nleaf; ++b) /* the parent sits at its first child's index */
+    if (st[b] == OG_COARSER && !((g->anc[3 * b] | g->anc[3 * b + 1] | g->anc[3 * b + 2]) & 1))
+      newly_coarse[newidx[b]] = 1;
+  const int ef = c->w.ext_f, eb = c->w.ext_b, E = nb + ef + eb;
+  double *gam = (double *)malloc(sizeof(double) * (size_t)E * E * E);
+  int8_t *inD = (int8_t *)malloc((size_t)E * E * E);
+  /* per new leaf: directions toward newly coarsened neighbours one level
+   * coarser (these create new substitution bands) */
+  int8_t *nmask = (int8_t *)calloc((size_t)n * 27, 1);
+  for (int b = 0; b < g->nleaf; ++b) {
+    if (st[b] != OG_SAME) continue;
+    const int F = newidx[b], L = g->lev[b];
+    for (int m = 0; m < 27; ++m) {
+      if (m == 13) continue;
+      int dd[3] = {m % 3 - 1, (m / 3) % 3 - 1, m / 9 - 1};
+      long gg[3];
+      for (int d = 0; d < 3; ++d)
+        gg[d] = (long)g->anc[3 * b + d] * nb + (dd[d] < 0 ? -1 : dd[d] > 0 ? nb : 0);
+      int o = owner(&cn, L, gg);
+      if (o >= 0 && lev_out[o] == L - 1 && newly_coarse[o]) nmask[(size_t)F * 27 + m] = 1;
+    }
+  }
+  int8_t *unchanged = (int8_t *)calloc(n, 1);
+  for (int b = 0; b < g->nleaf; ++b)
+    if (st[b] == OG_SAME) unchanged[newidx[b]] = 1;
+  for (int b = 0; b < g->nleaf && !e; ++b) {
+    if (st[b] != OG_SAME) continue;
+    const int L = g->lev[b];
+    const int32_t *a = g->anc + 3 * b;
+    /* the discarded set D on the extended region [-ef, nb-1+eb]^3: details in
+     * newly coarsened leaves, and details in the new bands of this leaf or
+     * of its unchanged same-level neighbours */
+    int nD = 0;
+    for (int k = -ef; k < nb + eb; ++k)
+      for (int j = -ef; j < nb + eb; ++j)
+        for (int i = -ef; i < nb + eb; ++i) {
+          size_t q = (size_t)(i + ef) + E * ((size_t)(j + ef) + E * (size_t)(k + ef));
+          inD[q] = 0;
+          if (!((i | j | k) & 1)) continue;
+          long gg[3] = {(long)a[0] * nb + i, (long)a[1] * nb + j, (long)a[2] * nb + k};
+          int o = owner(&cn, L, gg);
+          if (o < 0) { e = OG_ERR_INVALID; break; }
+          if (lev_out[o] == L - 1 && newly_coarse[o]) {
+            inD[q] = 1;
+          } else if (lev_out[o] == L && unchanged[o]) {
+            int mk[27], loc[3], anyb = 0;
+            for (int m = 0; m < 27; ++m) anyb |= (mk[m] = nmask[(size_t)o * 27 + m]);
+            if (anyb) {
+              for (int d = 0; d < 3; ++d) {
+                long P = npts(&cn, L, d);
+                loc[d] = pmod(gg[d] - (long)anc_out[3 * o + d] * nb, P);
+              }
+              inD[q] = (int8_t)in_band(c, mk, loc);
+            }
+          }
+          if (inD[q]) {
+            gam[q] = detail_at(c, pad + b * np, G, i, j, k);
+            ++nD;
+          }
+        }
+    if (!nD) continue;
+    double *v = phi_out + (size_t)newidx[b] * nb3;
+    for (int k = 0; k < nb; ++k)
+      for (int j = 0; j < nb; ++j)
+        for (int i = 0; i < nb; ++i) {
+          int jj[3] = {i, j, k};
+          const og_filt *fl[3];
+          for (int d = 0; d < 3; ++d) fl[d] = (jj[d] & 1) ? &c->w.Ks : &c->w.Js;
+          double s = 0.0;
+          for (int oz = -fl[2]->hw; oz <= fl[2]->hw; ++oz) {
+            int nz = k + oz;
+            if (nz < -ef || nz >= nb + eb) continue;
+            for (int oy = -fl[1]->hw; oy <= fl[1]->hw; ++oy) {
+              int ny = j + oy;
+              if (ny < -ef || ny >= nb + eb) continue;
+              for (int ox = -fl[0]->hw; ox <= fl[0]->hw; ++ox) {
+                int nx = i + ox;
+                if (nx < -ef || nx >= nb + eb) continue;
+                size_t q = (size_t)(nx + ef) + E * ((size_t)(ny + ef) + E * (size_t)(nz + ef));
+                if (!inD[q]) continue;
+                double wgt = tap(fl[0], ox) * tap(fl[1], oy) * tap(fl[2], oz);
+                if (wgt == 0.0) continue;
+                s += wgt * gam[q];
+              }
+            }
+          }
+          v[i + nb * (j + (size_t)nb * k)] -= s;
+        }
+  }
+  free(gam), free(inD), free(newly_coarse), free(nmask), free(unchanged);
+  ctx_free(&cn);
+  return e;
+}
+
+/*
+ * One iteration of Alg. SM3 on nf fields: ghost fill of field 0 (the
+ * criterion field), criterion, status, policy, new tree (children in Morton
+ * order at the parent's position, a parent at its first child's position),
+ * then for every field its ghost fill on the old grid, interpolation and
+ * update step (the velocity components of a grid are fields like any other:
+ * refined and coarsened with the same wavelet, by the decisions of field 0).
  * flags: bit0 allow refinement, bit1 allow coarsening.
  * Outputs are sized by the caller for `cap` leaves.  Returns the new leaf
  * count (>= 0) or an error; *n_changed counts blocks that refined/coarsened.
  */
-int og_adapt_iter(const og_grid *g, const double *phi, double eps_r, double eps_c,
-                  const int32_t *refined, int flags, int cap, int32_t *lev_out,
-                  int32_t *anc_out, double *phi_out, int32_t *refined_out, int *n_changed,
-                  double *maxdet_out, int8_t *status_out) {
+int og_adapt_iter_fields(const og_grid *g, int nf, const double *const *phi, double eps_r, double eps_c,
+                         const int32_t *refined, int flags, int cap, int32_t *lev_out, int32_t *anc_out,
+                         double *const *phi_out, int32_t *refined_out, int *n_changed, double *maxdet_out,
+                         int8_t *status_out) {
   og_ctx c;
+  if (nf < 1) return OG_ERR_INVALID;
   int e = ctx_init(&c, g);
   if (e) return e;
   const int nb = g->nb, G = og_adapt_shell(g->N, g->Nt), W = nb + 2 * G;
@@ -1048,13 +1209,12 @@ int og_adapt_iter(const og_grid *g, const double *phi, double eps_r, double eps_
   double *md = (double *)malloc(sizeof(double) * g->nleaf);
   int8_t *st = (int8_t *)malloc(g->nleaf);
   int32_t *newidx = (int32_t *)malloc(sizeof(int32_t) * g->nleaf);
-  double *phis = NULL;
-  if (!pad || !md || !st || !newidx) { e = OG_ERR_NOMEM; goto done; }
+  double *phis = (double *)malloc(sizeof(double) * nb3 * g->nleaf);
+  int n = 0, changed = 0;
+  if (!pad || !md || !st || !newidx || !phis) { e = OG_ERR_NOMEM; goto done; }
   /* ghost values on the current grid; the substitution they include
    * overwrites the field (Alg. SM2), so unchanged leaves keep phis */
-  phis = (double *)malloc(sizeof(double) * nb3 * g->nleaf);
-  if (!phis) { e = OG_ERR_NOMEM; goto done; }
-  e = og_ghost_fill(g, phi, G, pad, phis);
+  e = og_ghost_fill(g, phi[0], G, pad, phis);
   if (e) goto done;
   e = og_criterion(g, pad, G, md);
   if (e) goto done;
@@ -1068,7 +1228,6 @@ int og_adapt_iter(const og_grid *g, const double *phi, double eps_r, double eps_
   if (maxdet_out) memcpy(maxdet_out, md, sizeof(double) * g->nleaf);
   if (status_out) memcpy(status_out, st, g->nleaf);
   /* new tree */
-  int n = 0, changed = 0;
   for (int b = 0; b < g->nleaf; ++b) {
     const int32_t *a = g->anc + 3 * b;
     const int L = g->lev[b];
@@ -1080,7 +1239,6 @@ int og_adapt_iter(const og_grid *g, const double *phi, double eps_r, double eps_
         lev_out[n] = L + 1;
         for (int d = 0; d < 3; ++d) anc_out[3 * n + d] = 2 * a[d] + ((ch >> d) & 1);
         refined_out[n] = 1;
-        refine_child(&c, pad + b * np, G, ch, phi_out + (size_t)n * nb3);
         ++n;
       }
     } else if (st[b] == OG_COARSER) {
@@ -1090,133 +1248,40 @@ int og_adapt_iter(const og_grid *g, const double *phi, double eps_r, double eps_
       lev_out[n] = L - 1;
       for (int d = 0; d < 3; ++d) anc_out[3 * n + d] = a[d] / 2;
       refined_out[n] = 0;
-      const double *Pch[8];
-      for (int ch = 0; ch < 8; ++ch) {
-        int s = c.lut[L][(a[0] + (ch & 1)) + c.dim[L][0] * ((a[1] + ((ch >> 1) & 1)) +
-                                                            c.dim[L][1] * (long)(a[2] + (ch >> 2)))];
-        Pch[ch] = pad + s * np;
-      }
-      coarsen_children(&c, Pch, G, phi_out + (size_t)n * nb3);
       ++n;
     } else {
       if (n >= cap) { e = OG_ERR_NOMEM; goto done; }
       lev_out[n] = L;
       for (int d = 0; d < 3; ++d) anc_out[3 * n + d] = a[d];
       refined_out[n] = refined[b];
-      memcpy(phi_out + (size_t)n * nb3, phis + (size_t)b * nb3, sizeof(double) * nb3);
       ++n;
     }
   }
   *n_changed = changed;
-  /* update step (eq 2.22): unchanged leaves next to a newly coarsened
-   * neighbour one level coarser subtract the synthesis of the level-(L-1)
-   * details that the coarsening discarded.  In 3D this is needed for N.0 as
-   * well (Table 2.2 lists update ghosts for 3D N.0): a discarded 1-degree
-   * detail enters the synthesis of the adjacent 2- and 3-degree points.     */
-  if (changed) {
+  {
     og_grid gn = *g;
     gn.nleaf = n, gn.lev = lev_out, gn.anc = anc_out;
-    og_ctx cn;
-    e = ctx_init(&cn, &gn);
-    if (e) goto done;
-    int8_t *newly_coarse = (int8_t *)calloc(n, 1);
-    for (int b = 0; b < g->nleaf; ++b) /* the parent sits at its first child's index */
-      if (st[b] == OG_COARSER && !((g->anc[3 * b] | g->anc[3 * b + 1] | g->anc[3 * b + 2]) & 1))
-        newly_coarse[newidx[b]] = 1;
-    const int ef = c.w.ext_f, eb = c.w.ext_b, E = nb + ef + eb;
-    double *gam = (double *)malloc(sizeof(double) * (size_t)E * E * E);
-    int8_t *inD = (int8_t *)malloc((size_t)E * E * E);
-    /* per new leaf: directions toward newly coarsened neighbours one level
-     * coarser (these create new substitution bands) */
-    int8_t *nmask = (int8_t *)calloc((size_t)n * 27, 1);
-    for (int b = 0; b < g->nleaf; ++b) {
-      if (st[b] != OG_SAME) continue;
-      const int F = newidx[b], L = g->lev[b];
-      for (int m = 0; m < 27; ++m) {
-        if (m == 13) continue;
-        int dd[3] = {m % 3 - 1, (m / 3) % 3 - 1, m / 9 - 1};
-        long gg[3];
-        for (int d = 0; d < 3; ++d)
-          gg[d] = (long)g->anc[3 * b + d] * nb + (dd[d] < 0 ? -1 : dd[d] > 0 ? nb : 0);
-        int o = owner(&cn, L, gg);
-        if (o >= 0 && lev_out[o] == L - 1 && newly_coarse[o]) nmask[(size_t)F * 27 + m] = 1;
-      }
+    for (int f = 0; f < nf && !e; ++f) {
+      if (f > 0) e = og_ghost_fill(g, phi[f], G, pad, phis);
+      if (!e) e = apply_tree_change(&c, &gn, st, newidx, pad, G, phis, phi_out[f]);
     }
-    int8_t *unchanged = (int8_t *)calloc(n, 1);
-    for (int b = 0; b < g->nleaf; ++b)
-      if (st[b] == OG_SAME) unchanged[newidx[b]] = 1;
-    for (int b = 0; b < g->nleaf && !e; ++b) {
-      if (st[b] != OG_SAME) continue;
-      const int L = g->lev[b];
-      const int32_t *a = g->anc + 3 * b;
-      /* the discarded set D on the extended region [-ef, nb-1+eb]^3: details in
-       * newly coarsened leaves, and details in the new bands of this leaf or
-       * of its unchanged same-level neighbours */
-      int nD = 0;
-      for (int k = -ef; k < nb + eb; ++k)
-        for (int j = -ef; j < nb + eb; ++j)
-          for (int i = -ef; i < nb + eb; ++i) {
-            size_t q = (size_t)(i + ef) + E * ((size_t)(j + ef) + E * (size_t)(k + ef));
-            inD[q] = 0;
-            if (!((i | j | k) & 1)) continue;
-            long gg[3] = {(long)a[0] * nb + i, (long)a[1] * nb + j, (long)a[2] * nb + k};
-            int o = owner(&cn, L, gg);
-            if (o < 0) { e = OG_ERR_INVALID; break; }
-            if (lev_out[o] == L - 1 && newly_coarse[o]) {
-              inD[q] = 1;
-            } else if (lev_out[o] == L && unchanged[o]) {
-              int mk[27], loc[3], anyb = 0;
-              for (int m = 0; m < 27; ++m) anyb |= (mk[m] = nmask[(size_t)o * 27 + m]);
-              if (anyb) {
-                for (int d = 0; d < 3; ++d) {
-                  long P = npts(&cn, L, d);
-                  loc[d] = pmod(gg[d] - (long)anc_out[3 * o + d] * nb, P);
-                }
-                inD[q] = (int8_t)in_band(&c, mk, loc);
-              }
-            }
-            if (inD[q]) {
-              gam[q] = detail_at(&c, pad + b * np, G, i, j, k);
-              ++nD;
-            }
-          }
-      if (!nD) continue;
-      double *v = phi_out + (size_t)newidx[b] * nb3;
-      for (int k = 0; k < nb; ++k)
-        for (int j = 0; j < nb; ++j)
-          for (int i = 0; i < nb; ++i) {
-            int jj[3] = {i, j, k};
-            const og_filt *fl[3];
-            for (int d = 0; d < 3; ++d) fl[d] = (jj[d] & 1) ? &c.w.Ks : &c.w.Js;
-            double s = 0.0;
-            for (int oz = -fl[2]->hw; oz <= fl[2]->hw; ++oz) {
-              int nz = k + oz;
-              if (nz < -ef || nz >= nb + eb) continue;
-              for (int oy = -fl[1]->hw; oy <= fl[1]->hw; ++oy) {
-                int ny = j + oy;
-                if (ny < -ef || ny >= nb + eb) continue;
-                for (int ox = -fl[0]->hw; ox <= fl[0]->hw; ++ox) {
-                  int nx = i + ox;
-                  if (nx < -ef || nx >= nb + eb) continue;
-                  size_t q = (size_t)(nx + ef) + E * ((size_t)(ny + ef) + E * (size_t)(nz + ef));
-                  if (!inD[q]) continue;
-                  double wgt = tap(fl[0], ox) * tap(fl[1], oy) * tap(fl[2], oz);
-                  if (wgt == 0.0) continue;
-                  s += wgt * gam[q];
-                }
-              }
-            }
-            v[i + nb * (j + (size_t)nb * k)] -= s;
-          }
-    }
-    free(gam), free(inD), free(newly_coarse), free(nmask), free(unchanged);
-    ctx_free(&cn);
   }
   if (!e) e = n;
 done:
   free(pad), free(md), free(st), free(newidx), free(phis);
   ctx_free(&c);
   return e;
+}
+
+/* One iteration of Alg. SM3 on a single field (og_adapt_iter_fields). */
+int og_adapt_iter(const og_grid *g, const double *phi, double eps_r, double eps_c,
+                  const int32_t *refined, int flags, int cap, int32_t *lev_out,
+                  int32_t *anc_out, double *phi_out, int32_t *refined_out, int *n_changed,
+                  double *maxdet_out, int8_t *status_out) {
+  const double *in[1] = {phi};
+  double *out[1] = {phi_out};
+  return og_adapt_iter_fields(g, 1, in, eps_r, eps_c, refined, flags, cap, lev_out, anc_out, out, refined_out,
+                              n_changed, maxdet_out, status_out);
 }
 
 /* Morton key of a leaf: anchor scaled to level `kl` (>= every leaf level),

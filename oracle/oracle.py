@@ -78,6 +78,9 @@ def _declare(L):
     L.og_adapt_iter.argtypes = [C.POINTER(_Grid), _dp, C.c_double, C.c_double, _ip, C.c_int,
                                 C.c_int, _ip, _ip, _dp, _ip, C.POINTER(C.c_int), _dp,
                                 C.POINTER(C.c_int8)]
+    L.og_adapt_iter_fields.argtypes = [C.POINTER(_Grid), C.c_int, C.POINTER(_dp), C.c_double, C.c_double,
+                                       _ip, C.c_int, C.c_int, _ip, _ip, C.POINTER(_dp), _ip,
+                                       C.POINTER(C.c_int), _dp, C.POINTER(C.c_int8)]
     L.og_filter_taps.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), _dp,
                                  C.POINTER(C.c_int)]
     for f in ("og_restrict_1d", "og_detail_1d"):
@@ -86,6 +89,9 @@ def _declare(L):
     L.og_status.argtypes = [C.c_double, C.c_double, C.c_double]
     L.og_rk3_step_vel.argtypes = [C.POINTER(_Grid), _dp, _dp, _dp, _dp, C.c_double, C.c_int]
     L.og_rk3_step_velpad.argtypes = [C.POINTER(_Grid), _dp, _dp, _dp, _dp, C.c_double, C.c_int]
+    L.og_weno_beta.argtypes = [_dp, _dp]
+    L.og_iface_flux.argtypes = [C.c_int, _dp, C.c_int]
+    L.og_iface_flux.restype = C.c_double
     L.og_morton_key.argtypes = [C.c_int] * 5
     L.og_morton_key.restype = C.c_uint64
 
@@ -276,6 +282,34 @@ def adapt_iter(g: Grid, phi, eps_r, eps_c, refined=None, allow_refine=True,
     return (g2, out[:n].reshape(n, g.nb, g.nb, g.nb).copy(), rout[:n].copy(), nch.value, md, st)
 
 
+def adapt_iter_fields(g: Grid, phis, eps_r, eps_c, refined=None, allow_refine=True,
+                      allow_coarsen=True):
+    """One iteration of Alg. SM3 on several fields; field 0 drives the
+    criterion, every field is refined / coarsened / updated.  Returns
+    (grid, [fields], refined, n_changed, maxdet, status)."""
+    ins = [np.ascontiguousarray(p, dtype=np.float64).reshape(g.nleaf, -1) for p in phis]
+    nf = len(ins)
+    ref = np.zeros(g.nleaf, np.int32) if refined is None else np.ascontiguousarray(refined, np.int32)
+    cap = 8 * g.nleaf
+    lev = np.empty(cap, np.int32)
+    anc = np.empty((cap, 3), np.int32)
+    outs = [np.empty((cap, g.nb ** 3)) for _ in range(nf)]
+    rout = np.empty(cap, np.int32)
+    md = np.empty(g.nleaf)
+    st = np.empty(g.nleaf, np.int8)
+    nch = C.c_int()
+    pin = (_dp * nf)(*[_d(a) for a in ins])
+    pout = (_dp * nf)(*[_d(a) for a in outs])
+    flags = (1 if allow_refine else 0) | (2 if allow_coarsen else 0)
+    n = _check(lib().og_adapt_iter_fields(g.c(), nf, pin, eps_r, eps_c, ref.ctypes.data_as(_ip), flags, cap,
+                                          lev.ctypes.data_as(_ip), anc.ctypes.data_as(_ip), pout,
+                                          rout.ctypes.data_as(_ip), C.byref(nch), _d(md),
+                                          st.ctypes.data_as(C.POINTER(C.c_int8))), "adapt_iter_fields")
+    g2 = g.with_leaves(lev[:n].copy(), anc[:n].copy())
+    return (g2, [o[:n].reshape(n, g.nb, g.nb, g.nb).copy() for o in outs], rout[:n].copy(), nch.value,
+            md, st)
+
+
 def adapt(g: Grid, phi, eps_r, eps_c, max_iter=64, **kw):
     """Alg. SM3 to convergence (no block changes)."""
     ref = None
@@ -318,6 +352,20 @@ def synth_1d(N, Nt, lam, gam=None):
     out = np.empty(2 * lam.size)
     _check(lib().og_synth_1d(N, Nt, lam.size, _d(lam), _d(gm), _d(out)), "synth_1d")
     return out
+
+
+def weno_beta(v):
+    """Smoothness indicators (Table SM4) of the sub-stencils of 5 values."""
+    v = np.ascontiguousarray(v, np.float64)
+    out = np.empty(3)
+    lib().og_weno_beta(_d(v), _d(out))
+    return out
+
+
+def iface_flux(scheme, f6, upwind_left):
+    """Interface flux F_{i+1/2} from the point fluxes f_{i-2..i+3}."""
+    f6 = np.ascontiguousarray(f6, np.float64)
+    return lib().og_iface_flux(int(scheme), _d(f6), int(bool(upwind_left)))
 
 
 def status(maxdet, eps_r, eps_c):

@@ -1092,8 +1092,14 @@ extern "C" int mr_ghost_fill_static(mr_grid *g, int fid, int G, void *padded) {
     return MR_ERR_INVALID;
   }
   const int gi = internal_shell(g->desc.wav_N, g->desc.wav_Nt, G, nb);
+  // the same buffer rule as launch_ghost: shells wider than the stencil
+  // buffers run with FP64 padded blocks (and only where the grid has the
+  // adaptation buffers that mr_ghost_fill would use)
+  const bool fp64 = gi > g->shell_rk;
+  if (fp64 && (gi > g->shell_ad || (g->desc.flags & MR_GRID_FIXED_TREE))) return MR_ERR_UNSUPPORTED;
+  const size_t pes = fp64 ? sizeof(double) : g->esize;  // padded element size
   const size_t wd = (size_t)nb + 2 * gi;
-  const size_t half = (((size_t)g->nleaf * wd * wd * wd * g->esize) + 255) & ~(size_t)255;
+  const size_t half = (((size_t)g->nleaf * wd * wd * wd * pes) + 255) & ~(size_t)255;
   if (2 * half > MR_STATIC_SCRATCH_BYTES) {
     set_error("mr_ghost_fill_static: grid too large for the 64 MiB static scratch");
     return MR_ERR_NOMEM;
@@ -1102,6 +1108,13 @@ extern "C" int mr_ghost_fill_static(mr_grid *g, int fid, int G, void *padded) {
   {
     std::lock_guard<std::mutex> lk(g_static_mu);
     if (!g_static_addr[dev]) {
+      // the address lookup may load the module: refuse it inside a capture
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      if (check_cuda(cudaStreamIsCapturing(g->stream, &cs), "cudaStreamIsCapturing")) return MR_ERR_CUDA;
+      if (cs != cudaStreamCaptureStatusNone) {
+        set_error("mr_ghost_fill_static: the first call on a device must not be made during stream capture");
+        return MR_ERR_INVALID;
+      }
       // host code cannot take the address of a __device__ array directly
       if (check_cuda(cudaGetSymbolAddress(&g_static_addr[dev], mr_static_scratch), "cudaGetSymbolAddress")) {
         g_static_addr[dev] = nullptr;
@@ -1112,11 +1125,14 @@ extern "C" int mr_ghost_fill_static(mr_grid *g, int fid, int G, void *padded) {
   }
   void *P = base, *Q = (char *)base + half;
   void *f = field_ptr(g, fid);
+  const bool f32 = g->desc.precision == MR_F32;
   int e;
-  if (g->desc.precision == MR_F32)
+  if (fp64 && f32)
+    e = ghost_dispatch<float, double>(g, (const float *)f, (float *)f, G, (double *)P, (double *)Q, gi);
+  else if (f32)
     e = ghost_dispatch<float, float>(g, (const float *)f, (float *)f, G, (float *)P, (float *)Q, gi);
   else
     e = ghost_dispatch<double, double>(g, (const double *)f, (double *)f, G, (double *)P, (double *)Q, gi);
   if (e) return e;
-  return padded ? launch_crop(g, P, gi, padded, G, g->desc.precision == MR_F64) : MR_OK;
+  return padded ? launch_crop(g, P, gi, padded, G, fp64 || !f32) : MR_OK;
 }

@@ -1,0 +1,227 @@
+"""GPU path vs the FP64 oracle on the configuration the large-grid benchmark
+runs, through the C ABI: 6.2 lifted wavelets (and 6.0) on 24^3 blocks;
+adaptation of four fields (a scalar and three velocity components, refined,
+coarsened and updated by the scalar's decisions); the FP32 stage kernel at
+nb = 24 (576-thread CTAs, 30^3 shared tile) with WENO-Z5 and grid velocity
+fields; and the FP32 accuracy bar of 1e-5 of the field maximum after 100
+RK3 steps of the tiny configuration.
+
+Tolerances are those of the other GPU tests: trees, keys and statuses
+bit-exact; FP64 fields within 1e-12 of the field maximum (fused multiply-adds
+and separable sums on the device); FP32 grids are compared with the oracle
+run on the same FP32 snapshot (upcast): the device rounds its FP64
+adaptation results to FP32 (twice where the update step corrects a copied
+value), so they agree within 2^-22 of the field maximum.
+"""
+import numpy as np
+import pytest
+
+from paper_2112_07537_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+EPS_R, EPS_C = 1e-3, 1e-5  # eps_r / eps_c = 100 > 2^6 (Sec. 2.2.5)
+
+
+@pytest.fixture(scope="module")
+def mr():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2112_07537_gb300 import build, mrgb
+    build.build()
+    return mrgb
+
+
+def _small_tree():
+    """One periodic tree of 24^3 blocks: uniform level 1 with the leaves at
+    anchors (0,0,0) and (1,0,0) refined (6 + 16 leaves)."""
+    nt, tl = (1, 1, 1), 1.0
+    lev, anc = I.uniform_leaves(nt, 1)
+    lev, anc = I.refine_leaves(lev, anc, np.isin(np.arange(len(lev)), [0, 1]))
+    return nt, tl, lev, anc
+
+
+def _scalar(xyz):
+    """A wide Gaussian centred in the refined leaf (1,0,0) -- its children
+    keep details between the thresholds -- and a sharp one in the level-1
+    leaf (1,1,1), which refines; the refined leaf (0,0,0) is smooth enough
+    to coarsen next to the children of (1,0,0), whose update step runs."""
+    return I.gaussian(xyz, (0.75, 0.25, 0.25), 0.06) + I.gaussian(xyz, (0.75, 0.75, 0.75), 0.025)
+
+
+def _taylor_green(xyz, comp, s=1.0, ph=0.3):
+    w = 2 * np.pi
+    x, y, z = xyz
+    if comp == 0:
+        return s * np.sin(w * x + ph) * np.cos(w * y) * np.cos(w * z)
+    if comp == 1:
+        return -s * np.cos(w * x + ph) * np.sin(w * y) * np.cos(w * z)
+    return np.zeros_like(x)
+
+
+def _no_near_ties(maxdet, phi):
+    tol = TOL * np.abs(phi).max()
+    assert np.all(np.abs(maxdet - EPS_R) > tol) and np.all(np.abs(maxdet - EPS_C) > tol)
+
+
+def _grid(mr, O, N, Nt, prec, nfields=1):
+    nt, tl, lev, anc = _small_tree()
+    nb = 24
+    g = mr.Grid(nt, tl, nb, 0, 4, N, Nt, lev, anc, precision=prec, nfields=nfields, capacity=4000)
+    glev, ganc, _ = g.leaves()
+    og = O.Grid(nt, tl, nb, N, Nt, 0, 4, glev, ganc)
+    return g, og
+
+
+def _same_tree(g, og2):
+    lev, anc, keys = g.leaves()
+    assert np.array_equal(lev, og2.lev) and np.array_equal(anc, og2.anc)
+    assert np.all(np.diff(keys.astype(np.float64)) > 0)
+
+
+@pytest.mark.parametrize("N,Nt", [(6, 2), (6, 0)])
+def test_adapt_iterations_fp64_6x_nb24(mr, oracle_mod, N, Nt):
+    """Alg. SM3 iterations to convergence with 6.x wavelets on 24^3 blocks
+    (the bench's wavelet and block size; adaptation shell 11 for 6.2): trees
+    bit-exact, fields within 1e-12 of the field maximum after every
+    iteration; refinement, coarsening and (for 6.2) the update step next to
+    the newly coarsened leaf all occur."""
+    O = oracle_mod
+    g, og = _grid(mr, O, N, Nt, mr.F64)
+    phi = _scalar(I.point_coords(og.nt, og.tree_len, og.nb, og.lev, og.anc))
+    g.field_copy_in(0, phi)
+    refined, ref, cur = None, phi, og
+    seen = set()
+    for it in range(6):
+        _no_near_ties(O.block_maxdet(cur, ref), ref)
+        og2, ophi, refined, onch, _, st = O.adapt_iter(cur, ref, EPS_R, EPS_C, refined)
+        seen |= set(np.unique(st).tolist())
+        nch = g.adapt_iter(0, EPS_R, EPS_C)
+        assert nch == onch
+        _same_tree(g, og2)
+        got = g.field_copy_out(0)
+        assert np.abs(got - ophi).max() <= TOL * np.abs(ophi).max()
+        cur, ref = og2, ophi
+        if nch == 0:
+            break
+    assert it > 0 and {-1, 1} <= seen
+
+
+def test_adapt_to_convergence_fp32_6_2_nb24_flags_exact(mr, oracle_mod):
+    """The bench's adaptation path (FP32 fields, 6.2, nb = 24): every
+    iteration, the oracle runs on the device's FP32 snapshot; statuses
+    (through the trees) match exactly and the adapted field is the oracle's
+    rounded to FP32."""
+    O = oracle_mod
+    g, og = _grid(mr, O, 6, 2, mr.F32)
+    phi = _scalar(I.point_coords(og.nt, og.tree_len, og.nb, og.lev, og.anc)).astype(np.float32)
+    g.field_copy_in(0, phi)
+    refined = None
+    for it in range(6):
+        lev, anc, _ = g.leaves()
+        cur = og.with_leaves(lev, anc)
+        snap = g.field_copy_out(0).astype(np.float64)
+        _no_near_ties(O.block_maxdet(cur, snap), snap)
+        og2, ophi, refined_o, onch, _, _ = O.adapt_iter(cur, snap, EPS_R, EPS_C, refined)
+        nch = g.adapt_iter(0, EPS_R, EPS_C)
+        assert nch == onch
+        _same_tree(g, og2)
+        got = g.field_copy_out(0).astype(np.float64)
+        assert np.abs(got - ophi).max() <= 2.0 ** -22 * np.abs(ophi).max() + TOL
+        refined = refined_o
+        if nch == 0:
+            break
+    assert it > 0
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_adapt_four_fields_6_2_nb24(mr, oracle_mod, prec):
+    """Adaptation of four fields -- the scalar (criterion field) and three
+    Taylor-Green-like velocity components, as in the large workload: every
+    field is ghost-filled (the non-criterion fields only on the leaves whose
+    interpolation or update step reads ghosts), refined, coarsened and
+    updated by the scalar's decisions.  Each iteration is compared with the
+    oracle's multi-field iteration on the device's snapshot: trees exact,
+    all four fields within tolerance."""
+    O = oracle_mod
+    g, og = _grid(mr, O, 6, 2, prec, nfields=4)
+    xyz = I.point_coords(og.nt, og.tree_len, og.nb, og.lev, og.anc)
+    cast = (lambda a: a.astype(np.float32)) if prec == 0 else (lambda a: a)
+    fields = [_scalar(xyz)] + [_taylor_green(xyz, d) for d in range(3)]
+    for f, v in enumerate(fields):
+        g.field_copy_in(f, cast(v))
+    refined = None
+    for it in range(6):
+        lev, anc, _ = g.leaves()
+        cur = og.with_leaves(lev, anc)
+        snaps = [g.field_copy_out(f).astype(np.float64) for f in range(4)]
+        og2, outs, refined_o, onch, _, _ = O.adapt_iter_fields(cur, snaps, EPS_R, EPS_C, refined)
+        nch = g.adapt_iter(0, EPS_R, EPS_C)
+        assert nch == onch
+        _same_tree(g, og2)
+        for f in range(4):
+            got = g.field_copy_out(f).astype(np.float64)
+            scale = np.abs(outs[f]).max()
+            tol = TOL * scale if prec == 1 else 2.0 ** -22 * scale + TOL
+            assert np.abs(got - outs[f]).max() <= tol, (it, f)
+        refined = refined_o
+        if nch == 0:
+            break
+    assert it > 0
+
+
+def test_step_vel_fp32_nb24_wenoz5(mr, oracle_mod):
+    """The bench's stage kernel shape: FP32, 24^3 blocks (one 576-thread CTA
+    per leaf, 30^3 shared tile), 6.2 ghosts (FP32 pre-pass for leaves next to
+    a coarser leaf), WENO-Z5 with three grid velocity fields: two RK3 steps
+    on the two-level tree against the oracle with the same per-tree velocity
+    ghosts, within 1e-5 of the field maximum."""
+    O = oracle_mod
+    nt, tl, nb = (2, 2, 2), 0.5, 24
+    lev, anc = I.tree_config1()
+    g = mr.Grid(nt, tl, nb, 0, 1, 6, 2, lev, anc, precision=mr.F32, nfields=4, velocity=True)
+    glev, ganc, _ = g.leaves()
+    og = O.Grid(nt, tl, nb, 6, 2, 0, 1, glev, ganc)
+    xyz = I.point_coords(nt, tl, nb, glev, ganc)
+    phi = I.gaussian_images(xyz, (0.45, 0.5, 0.55), 0.08, nimg=1).astype(np.float32)
+    vel = [_taylor_green(xyz, d).astype(np.float32) for d in range(3)]
+    g.field_copy_in(0, phi)
+    for d in range(3):
+        g.field_copy_in(1 + d, vel[d])
+    v64 = [O.ghost_fill(og, v.astype(np.float64), 3)[1] for v in vel]
+    vpads = [O.ghost_fill(og, v, 3)[0] for v in v64]
+    ref = phi.astype(np.float64)
+    dt = 0.5 * (tl / (nb * 2)) / 2.0
+    for _ in range(2):
+        g.step_vel(0, dt, (1, 2, 3), mr.WENOZ5)
+        ref = O.rk3_step_velpad(og, ref, vpads, dt, O.WENOZ5)
+    err = np.abs(g.field_copy_out(0).astype(np.float64) - ref).max() / np.abs(ref).max()
+    assert err <= 1e-5, err
+
+
+def test_config1_hundred_steps_fp32(mr, oracle_mod):
+    """The FP32 accuracy bar: the tiny configuration (2x2x2 trees, one refined;
+    15 leaves of 16^3; 4.0 wavelet; Gaussian sigma 0.1; u = (1,1,1); WENO-Z5;
+    RK3 at CFL 0.5) advanced 100 steps in FP32 stays within 1e-5 of the
+    field maximum of the FP64 oracle's trajectory."""
+    O = oracle_mod
+    nt, tl, nb = (2, 2, 2), 0.5, 16
+    lev, anc = I.tree_config1()
+    g = mr.Grid(nt, tl, nb, 0, 1, 4, 0, lev, anc, precision=mr.F32)
+    glev, ganc, _ = g.leaves()
+    og = O.Grid(nt, tl, nb, 4, 0, 0, 1, glev, ganc)
+    phi = I.gaussian(I.point_coords(nt, tl, nb, glev, ganc), (0.5, 0.5, 0.5), 0.1)
+    g.field_copy_in(0, phi.astype(np.float32))
+    u = (1.0, 1.0, 1.0)
+    dt = O.dt_cfl(og, 0.5, u)
+    ref = phi
+    worst = 0.0
+    for step in range(1, 101):
+        g.step(0, dt, u, mr.WENOZ5)
+        ref = O.rk3_step(og, ref, dt, O.WENOZ5, u)
+        if step % 20 == 0:
+            got = g.field_copy_out(0).astype(np.float64)
+            worst = max(worst, np.abs(got - ref).max() / np.abs(ref).max())
+    assert worst <= 1e-5, worst

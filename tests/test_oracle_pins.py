@@ -242,7 +242,7 @@ def _transform(oracle_mod, N, Nt, X, inverse=False):
     return U
 
 
-@pytest.mark.parametrize("N,Nt", [(2, 2), (4, 2), (2, 0), (4, 0)])
+@pytest.mark.parametrize("N,Nt", [(2, 2), (4, 2), (2, 0), (4, 0), (6, 2), (6, 0)])
 def test_adapt_equals_dense_transform_with_discarded_details(oracle_mod, N, Nt):
     """Coarsening + update step (eq 2.22) + refinement back to the uniform
     level reproduce exactly the dense 3D wavelet synthesis of the original
@@ -252,26 +252,30 @@ def test_adapt_equals_dense_transform_with_discarded_details(oracle_mod, N, Nt):
     # 2x2x2 trees, uniform level 2; the blob sits in the middle of one sibling
     # group, far enough from the periodic seam that no stencil wrapping around
     # it sees the field (first moments would pick up the coordinate jump)
-    nt, tl, nb = (2, 2, 2), 0.5, 8
-    lev, anc = I.uniform_leaves(nt, 2)
-    g = oracle_mod.Grid(nt, tl, nb, N, Nt, 0, 2, lev, anc)
-    phi = I.gaussian(I.point_coords(nt, tl, nb, lev, anc), (0.375, 0.375, 0.375), 0.04)
-    X = _dense(nb, lev, anc, phi, 2)
+    # N = 6 reaches 10-11 points from a block (Table 2.2): blocks of 16^3
+    # at uniform level 1 in a 3x3x3 forest, the blob in the middle of the
+    # centre tree (whose bands then stay clear of the periodic seam)
+    nt, tl = ((2, 2, 2), 0.5) if N < 6 else ((3, 3, 3), 0.5)
+    nb, Lu, c = (8, 2, 0.375) if N < 6 else (16, 1, 0.75)
+    lev, anc = I.uniform_leaves(nt, Lu)
+    g = oracle_mod.Grid(nt, tl, nb, N, Nt, 0, Lu, lev, anc)
+    phi = I.gaussian(I.point_coords(nt, tl, nb, lev, anc), (c, c, c), 0.04)
+    X = _dense(nb, lev, anc, phi, Lu, nt[0])
     g2, phi2, _ = oracle_mod.adapt(g, phi, 1e9, 1e-4, allow_refine=False)
-    assert set(np.unique(g2.lev)) == {1, 2}
+    assert set(np.unique(g2.lev)) == {Lu - 1, Lu}
     g3, phi3, _ = oracle_mod.adapt(g2, phi2, 0.0, -1.0, allow_coarsen=False)
-    assert np.all(g3.lev == 2)
-    X3 = _dense(nb, g3.lev, g3.anc, phi3, 2)
+    assert np.all(g3.lev == Lu)
+    X3 = _dense(nb, g3.lev, g3.anc, phi3, Lu, nt[0])
     # dense reference
-    n = 2 * nb << 2
+    n = nt[0] * nb << Lu
     _, _, (ef, eb) = oracle_mod.filter_taps(N, Nt, "Ha")
     levmap = np.zeros((n, n, n), int)
     for b in range(g2.nleaf):
-        s = nb << (2 - g2.lev[b])
+        s = nb << (Lu - g2.lev[b])
         a = g2.anc[b] * s
         levmap[a[2]:a[2] + s, a[1]:a[1] + s, a[0]:a[0] + s] = g2.lev[b]
-    disc = levmap == 1
-    for b in np.nonzero(g2.lev == 2)[0]:
+    disc = levmap == Lu - 1
+    for b in np.nonzero(g2.lev == Lu)[0]:
         a = g2.anc[b] * nb
         for dz in (-1, 0, 1):
             for dy in (-1, 0, 1):
@@ -280,7 +284,7 @@ def test_adapt_equals_dense_transform_with_discarded_details(oracle_mod, N, Nt):
                     if dd == (0, 0, 0):
                         continue
                     p = [(a[d] + (-1 if dd[d] < 0 else nb if dd[d] > 0 else 0)) % n for d in range(3)]
-                    if levmap[p[2], p[1], p[0]] < 2:
+                    if levmap[p[2], p[1], p[0]] < Lu:
                         sl = [slice(a[d] + (0 if dd[d] <= 0 else nb - ef),
                                     a[d] + (eb if dd[d] < 0 else nb)) for d in range(3)]
                         disc[sl[2], sl[1], sl[0]] = True
@@ -587,3 +591,158 @@ def test_scaled_velocity_step(oracle_mod):
         c = O.rk3_step_velpad_scaled(g, phi, vc, dt, O.WENOZ5, (s, s, s))
         ref = O.rk3_step(g, phi, dt, O.WENOZ5, tuple(s * x for x in u0))
         assert np.array_equal(c, ref)
+
+
+# ------------------------------------------------------------ WENO-Z pins
+def _cell_avg_quadratic(cells, vals):
+    """Exact quadratic p(x) = c0 + c1 x + c2 x^2 whose averages over the unit
+    cells [j - 1/2, j + 1/2], j in cells, equal vals (Fractions)."""
+    def avg(j, m):
+        return (Fr(2 * j + 1, 2) ** (m + 1) - Fr(2 * j - 1, 2) ** (m + 1)) / (m + 1)
+    A = [[avg(j, m) for m in range(3)] + [Fr(v)] for j, v in zip(cells, vals)]
+    for c in range(3):  # Gauss-Jordan elimination in exact arithmetic
+        piv = next(r for r in range(c, 3) if A[r][c] != 0)
+        A[c], A[piv] = A[piv], A[c]
+        A[c] = [x / A[c][c] for x in A[c]]
+        for r in range(3):
+            if r != c and A[r][c] != 0:
+                A[r] = [x - A[r][c] * y for x, y in zip(A[r], A[c])]
+    return [A[m][3] for m in range(3)]
+
+
+def _jiang_shu_beta(cells, vals, centre):
+    """Smoothness of the sub-stencil's reconstruction polynomial p over the
+    cell `centre` (Jiang & Shu 1996, the indicator WENO-Z builds on):
+    sum over l = 1, 2 of the integral of (h^(l - 1/2) d^l p / dx^l)^2, h = 1."""
+    c0, c1, c2 = _cell_avg_quadratic(cells, vals)
+    a, b = Fr(2 * centre - 1, 2), Fr(2 * centre + 1, 2)
+    # p' = c1 + 2 c2 x: integral of (c1 + 2 c2 x)^2; p'' = 2 c2
+    I1 = c1 * c1 * (b - a) + 2 * c1 * c2 * (b * b - a * a) + Fr(4, 3) * c2 * c2 * (b ** 3 - a ** 3)
+    I2 = 4 * c2 * c2 * (b - a)
+    return I1 + I2
+
+
+def test_weno_smoothness_indicators_from_definition(oracle_mod):
+    """Table SM4's beta_k equal the Jiang-Shu smoothness of the quadratic
+    whose cell averages are the sub-stencil values, integrated over the
+    reconstruction cell (the centre value of the five), derived here in
+    exact arithmetic; a wrong coefficient, sign or index in any of the three
+    indicators fails."""
+    rng = np.random.default_rng(21)
+    for _ in range(20):
+        v = rng.integers(-64, 65, size=5) / 8.0
+        got = oracle_mod.weno_beta(v)
+        for k in range(3):
+            ref = _jiang_shu_beta([k, k + 1, k + 2], [Fr(x) for x in v[k:k + 3]], 2)
+            assert got[k] == pytest.approx(float(ref), rel=1e-14, abs=1e-14)
+
+
+def _piecewise_quadratic(n, j, left, right):
+    x = np.arange(n, dtype=float)
+    f = np.where(x < j, left[0] + left[1] * x + left[2] * x * x,
+                 right[0] + right[1] * x + right[2] * x * x)
+    return x, f
+
+
+def _iface_value(p, x):
+    """Interface value of the function whose unit-cell averages are the
+    point values of the quadratic p: p(x) - p''/24."""
+    return p[0] + p[1] * x + p[2] * x * x - 2 * p[2] / 24
+
+
+@pytest.mark.parametrize("upwind_left", [True, False])
+def test_wenoz_essentially_non_oscillatory_at_a_jump(oracle_mod, upwind_left):
+    """WENO-Z (Borges et al. 2008; the scheme the paper implements beside
+    Table SM4): next to a jump between two smooth (quadratic) pieces, every
+    sub-stencil that crosses the jump gets a vanishing weight, so the
+    interface flux equals the reconstruction of the smooth sub-stencils --
+    the exact interface value p(x) - p''/24 of that side -- to within 1e-6 of
+    the jump.  With the power p = 1 instead of 2 the error is 3e-4 of the
+    jump here, with tau5 = |beta0 - beta1| 7e-2; the fixed-weight CONS-5 is
+    off by O(jump)."""
+    O = oracle_mod
+    n, j = 96, 48
+    L, R = (0.3, 0.004, 1e-4), (-1.2, -0.003, 5e-5)
+    _, f = _piecewise_quadratic(n, j, L, R)
+    jump = 1.5
+    checked_near = 0
+    for i in range(6, n - 6):
+        # interface i + 1/2; the five cells of the upwind reconstruction
+        first = i - 2 if upwind_left else i - 1
+        subs = [set(range(first + k, first + k + 3)) for k in range(3)]
+        lo = [s for s in subs if max(s) < j]
+        ro = [s for s in subs if min(s) >= j]
+        f6 = f[i - 2:i + 4]
+        F = O.iface_flux(O.WENOZ5, f6, upwind_left)
+        if len(lo) == 3 or len(ro) == 3:  # smooth: exact for quadratics
+            ref = _iface_value(L if lo else R, i + 0.5)
+            assert abs(F - ref) <= 1e-12
+            continue
+        if not lo and not ro:
+            continue
+        ref = _iface_value(L if lo else R, i + 0.5)
+        assert abs(F - ref) <= 1e-6 * jump, (i, F, ref)
+        assert abs(O.iface_flux(O.CONS5, f6, upwind_left) - ref) > 1e-3 * jump
+        checked_near += 1
+    assert checked_near == 4  # the four interfaces whose five cells span the jump
+
+
+@pytest.mark.parametrize("scheme", [1, 2])
+def test_velocity_field_rhs_design_order(oracle_mod, scheme):
+    """Advection by a spatially varying velocity field (point fluxes u_i phi_i,
+    upwind side from the interface velocity): the right-hand side converges to
+    -div(u phi) of smooth fields at the schemes' 5th order when u keeps its
+    sign, and at 4th order (the upwind switch) for CONS-5 with the
+    sign-changing Taylor-Green-like field of the large workload."""
+    O = oracle_mod
+    k = 2 * np.pi
+    cases = {"positive": 4.4}
+    if scheme == O.CONS5:
+        cases["taylor_green"] = 3.5
+    for case, lo in cases.items():
+        errs = []
+        for L in (1, 2):
+            nt, tl, nb = (1, 1, 1), 1.0, 8
+            lev, anc = I.uniform_leaves(nt, L)
+            g = O.Grid(nt, tl, nb, 4, 0, 0, L, lev, anc)
+            X, Y, Z = I.point_coords(nt, tl, nb, lev, anc)
+            phi = np.sin(k * X + 0.2) * np.cos(k * Y) * np.sin(k * Z + 0.3) + 0.5
+            gphi = [k * np.cos(k * X + 0.2) * np.cos(k * Y) * np.sin(k * Z + 0.3),
+                    -k * np.sin(k * X + 0.2) * np.sin(k * Y) * np.sin(k * Z + 0.3),
+                    k * np.sin(k * X + 0.2) * np.cos(k * Y) * np.cos(k * Z + 0.3)]
+            if case == "positive":
+                u = [1.5 + 0.5 * np.sin(k * Y) * np.cos(k * Z), 1.2 + 0.4 * np.cos(k * X),
+                     1.3 + 0.3 * np.sin(k * X + k * Y)]
+                du = [0 * X, 0 * X, 0 * X]  # each component is constant along its own axis
+            else:
+                u = [np.sin(k * X + 0.3) * np.cos(k * Y) * np.cos(k * Z),
+                     -np.cos(k * X + 0.3) * np.sin(k * Y) * np.cos(k * Z), 0 * X]
+                du = [k * np.cos(k * X + 0.3) * np.cos(k * Y) * np.cos(k * Z),
+                      -k * np.cos(k * X + 0.3) * np.cos(k * Y) * np.cos(k * Z), 0 * X]
+            ex = -sum(du[d] * phi + u[d] * gphi[d] for d in range(3))
+            pad, _ = O.ghost_fill(g, phi, 3)
+            vp = [O.ghost_fill(g, u[d], 3)[0] for d in range(3)]
+            errs.append(np.abs(O.rhs(g, pad, 3, scheme, vel=vp) - ex).max())
+        assert np.log2(errs[0] / errs[1]) > lo, (case, errs)
+
+
+# ------------------------------------------------------------ moments
+def test_moments_closed_form(oracle_mod):
+    """Eq. 2.18 quadrature on the two-level tree of the tiny configuration:
+    for phi = 1, M0 is the domain volume and M1 the sum over blocks of
+    s^3 (x0 + (s - h)/2) (block edge s = nb h, first point x0), the vertex-
+    aligned point positions summed in closed form; phi = x gives M0 = M1_x."""
+    O = oracle_mod
+    nt, tl, nb = (2, 2, 2), 0.5, 8
+    lev, anc = I.tree_config1()
+    g = O.Grid(nt, tl, nb, 4, 0, 0, 1, lev, anc)
+    one = np.ones((g.nleaf, nb, nb, nb))
+    m0, m1 = O.moments(g, one)
+    h = tl / (nb * 2.0 ** g.lev)
+    s = nb * h
+    ref1 = [np.sum(s ** 3 * (g.anc[:, d] * s + (s - h) / 2)) for d in range(3)]
+    assert m0 == pytest.approx(1.0, rel=1e-14)
+    assert np.allclose(m1, ref1, rtol=1e-14, atol=0)
+    X, _, _ = I.point_coords(nt, tl, nb, g.lev, g.anc)
+    n0, _ = O.moments(g, X)
+    assert n0 == pytest.approx(ref1[0], rel=1e-14)

@@ -54,10 +54,56 @@ def test_static_ghost_fill_matches_regular(mr, prec, N, Nt):
         assert np.array_equal(a.field_copy_out(0), b.field_copy_out(0))
 
 
+@pytest.mark.parametrize("N,Nt,G", [(4, 0, 4), (4, 2, 5)])
+def test_static_ghost_fill_fp64_padded_path(mr, N, Nt, G):
+    """FP32 grids whose internal shell is wider than the stencil buffers get
+    FP64 padded blocks from mr_ghost_fill; the static variant takes the same
+    path (same kernels, same precision), so the results are bit-identical."""
+    import torch
+    nt, tl, nb = (2, 2, 2), 0.5, 16
+    lev, anc = I.tree_config1()
+    a = mr.Grid(nt, tl, nb, 0, 1, N, Nt, lev, anc, precision=mr.F32)
+    b = mr.Grid(nt, tl, nb, 0, 1, N, Nt, lev, anc, precision=mr.F32)
+    n = a.nleaf
+    for seed in (3, 4):  # two calls in a row
+        phi = np.random.default_rng(seed).normal(size=(n, nb, nb, nb)).astype(np.float32)
+        a.field_copy_in(0, phi)
+        b.field_copy_in(0, phi)
+        W = nb + 2 * G
+        pa = torch.empty((n, W, W, W), dtype=torch.float32, device="cuda")
+        pb = torch.empty_like(pa)
+        a.ghost_fill(0, G, pa)
+        b.ghost_fill_static(0, G, pb)
+        a.sync()
+        b.sync()
+        assert torch.equal(pa, pb)
+        assert np.array_equal(a.field_copy_out(0), b.field_copy_out(0))
+
+
+def test_static_ghost_fill_unsupported_where_regular_is(mr):
+    """Where mr_ghost_fill refuses a shell (wider than both buffers of the
+    grid, or an FP64 padded path on a fixed-tree grid), so does the static
+    variant."""
+    nt, tl, nb = (2, 2, 2), 0.5, 16
+    lev, anc = I.tree_config1()
+    g = mr.Grid(nt, tl, nb, 0, 1, 2, 0, lev, anc, precision=mr.F32)
+    for call in (g.ghost_fill, g.ghost_fill_static):
+        with pytest.raises(mr.MRError) as e:
+            call(0, 4)
+        assert e.value.code == -5
+    f = mr.Grid(nt, tl, nb, 0, 1, 4, 0, lev, anc, precision=mr.F32, fixed_tree=True)
+    for call in (f.ghost_fill, f.ghost_fill_static):
+        with pytest.raises(mr.MRError) as e:
+            call(0, 4)
+        assert e.value.code == -5
+
+
 def test_static_ghost_fill_rejects_oversize_grid(mr):
     nt = (2, 2, 2)
-    lev, anc = I.uniform_leaves(nt, 1)  # 64 leaves of 32^3, shell 12: > 64 MiB
+    # 64 leaves of 32^3 with shell 11 (the adaptation shell of 6.2): two
+    # padded FP64 buffers of 64 * 54^3 values, 161 MB > 64 MiB
+    lev, anc = I.uniform_leaves(nt, 1)
     g = mr.Grid(nt, 0.5, 32, 0, 1, 6, 2, lev, anc, precision=mr.F64)
     with pytest.raises(mr.MRError) as e:
-        g.ghost_fill_static(0, 12)
+        g.ghost_fill_static(0, 11)
     assert e.value.code == -2
