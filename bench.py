@@ -1,19 +1,21 @@
 """Benchmark: grid-point stage updates per second (PSU/s) of the multilevel
 stencil step (ghost reconstruction + advection RHS + RK3-TVD stage, with grid
-adaptation) and the HBM-roofline fraction of its dominant kernel, on one GB300.
+adaptation) and the HBM-roofline fraction of its dominant kernel, on one GB300,
+for the FP32 form and, on the same workload and GPU, the plain FP64 form.
 
 Default workload ("large single grid"): one periodic tree of 24^3 blocks,
-levels 3-8; FP32 scalar (sum of 48 seeded sharp Gaussians) advected by three
+levels 3-8; FP32 scalar (sum of seeded sharp Gaussians) advected by three
 FP32 velocity fields (seeded divergence-free Taylor-Green-like field);
 6.2 lifted wavelet, eps_refine = 1e-5, eps_coarsen = 1e-7; WENO-Z5 + RK3,
 CFL 0.5; adaptation every 2 steps inside the timed region.  The initial grid
 is built by alternating analytic sampling and refinement from a uniform
 level-3 grid, then one full adaptation (all untimed).  Fields are far larger
-than L2 (no flush needed).
+than L2 (no flush needed).  The same workload then runs in FP64 (per-block
+padded ghosts, FP64 stencil) for the FP32-over-FP64 speed-up.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision f32|f64]
                   [--scheme wenoz5|cons5|cons3] [--workload large|fixed-*]
-                  [--impl ours|reference]
+                  [--impl ours|reference] [--no-fp64] [--no-cpu-baseline]
 
 fixed-large / fixed-medium / fixed-small: the stencil step alone (no
 adaptation, constant velocity) on fixed nested-ball trees, used for kernel
@@ -150,50 +152,203 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def cpu_baseline(budget_s=15.0):
-    """The FP64 oracle (single-threaded C) on a bounded sample of the
-    workload: the two-level 15-leaf grid of 16^3 blocks (2x2x2 trees, one
-    refined), 6.2 ghosts, scalar + Taylor-Green-like velocity fields (all four
-    ghost-filled every stage), WENO-Z5 + RK3, as many steps as fit the
-    budget."""
+def _oracle_sample(steps=2):
+    """One bounded sample of the large workload on the FP64 oracle: a periodic
+    tree of 22 blocks of 24^3 on levels 1-2, the scalar (two Gaussians) and
+    the three Taylor-Green-like velocity components, 6.2 lifted wavelet;
+    `steps` RK3 steps of WENO-Z5 with the per-tree velocity ghosts (as the
+    device path), then one adaptation iteration of all four fields.  Returns
+    (point-stage updates, seconds)."""
     sys.path.insert(0, os.path.join(ROOT, "oracle"))
     import oracle as O
-    nt, tl, nb = (2, 2, 2), 0.5, 16
-    lev, anc = I.tree_config1()
-    og = O.Grid(nt, tl, nb, 6, 2, 0, 1, lev, anc)
-    xyz = I.point_coords(nt, tl, nb, lev, anc)
-    phi = I.gaussian(xyz, (0.5, 0.5, 0.5), 0.1)
+    nt, tl, nb = (1, 1, 1), 1.0, 24
+    lev, anc = I.uniform_leaves(nt, 1)
+    lev, anc = I.refine_leaves(lev, anc, np.isin(np.arange(len(lev)), [0, 1]))
+    og = O.Grid(nt, tl, nb, 6, 2, 0, 4, lev, anc)
+    xyz = I.point_coords(nt, tl, nb, og.lev, og.anc)
+    phi = I.gaussian(xyz, (0.75, 0.25, 0.25), 0.06) + I.gaussian(xyz, (0.75, 0.75, 0.75), 0.025)
     w = 2 * np.pi
     vel = [TG[0] * np.sin(w * xyz[0] + TG[1]) * np.cos(w * xyz[1]) * np.cos(w * xyz[2]),
            -TG[0] * np.cos(w * xyz[0] + TG[1]) * np.sin(w * xyz[1]) * np.cos(w * xyz[2]),
            np.zeros_like(xyz[0])]
-    dt = CFL * (tl / (nb * 2)) / (2 * TG[0])
+    dt = CFL * (tl / (nb * 4)) / (2 * TG[0])
     t0 = time.perf_counter()
-    steps = 0
-    while time.perf_counter() - t0 < budget_s or steps == 0:
-        phi, vel = O.rk3_step_vel(og, phi, vel, dt, O.WENOZ5)
-        steps += 1
-    el = time.perf_counter() - t0
-    pts = og.nleaf * nb ** 3
-    return {"value": pts * 3 * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} RK3 steps (WENO-Z5, 6.2 ghosts, velocity fields) of the 15-leaf "
-                      f"16^3 two-level grid, {pts} points, {el:.1f} s, single thread"}
+    vpads = [O.ghost_fill(og, O.ghost_fill(og, v, 3)[1], 3)[0] for v in vel]
+    for _ in range(steps):
+        phi = O.rk3_step_velpad(og, phi, vpads, dt, O.WENOZ5)
+    O.adapt_iter_fields(og, [phi] + vel, 1e-3, 1e-5)
+    return 3 * steps * og.nleaf * nb ** 3, time.perf_counter() - t0
+
+
+def _oracle_worker(_):
+    return _oracle_sample()
+
+
+def _cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline(all_cores=True):
+    """The FP64 oracle as it stands (plain C, one thread per process) on a
+    bounded sample of the workload (_oracle_sample), once on one core and,
+    with all_cores, as one spawned process per host core running the same
+    sample concurrently (value = all processes' updates / wall time)."""
+    psu, sec = _oracle_sample()
+    ncpu = os.cpu_count() or 1
+    out = {"value": psu / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "cpu": _cpu_model(), "nproc": ncpu, "single_thread": psu / sec,
+           "sample": f"2 RK3 steps (WENO-Z5, 6.2 ghosts, 3 velocity fields with per-tree ghosts) + one "
+                     f"4-field adaptation iteration of a 22-leaf 24^3 tree ({psu // 6} points), "
+                     f"{sec:.1f} s on one core"}
+    if all_cores and ncpu > 1:
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        t0 = time.perf_counter()
+        with ctx.Pool(ncpu) as pool:
+            res = pool.map(_oracle_worker, range(ncpu))
+        wall = time.perf_counter() - t0
+        out.update(value=sum(r[0] for r in res) / wall, cores=ncpu, all_core_wall_s=wall,
+                   sample=out["sample"] + f"; all cores: {ncpu} spawned processes each running the sample, "
+                                          f"{wall:.1f} s wall")
+    return out
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    base = cpu_baseline(budget_s=max(2.0, 60.0 / max(1, args.steps + args.warmup)))
+    base = cpu_baseline(all_cores=True)
     line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "FP64 CPU oracle on a bounded sample (see cpu_baseline)"},
+            "config": {"workload": "FP64 CPU oracle on a bounded sample of the large single-grid "
+                                   "workload (see cpu_baseline.sample)"},
             "cpu_baseline": base,
             "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def make_grid(args, mrgb, stream, prec, cap):
+    """The workload's grid (untimed set-up): returns (grid, lmax, umax)."""
+    nb = 24
+    with __import__("torch").cuda.stream(stream):
+        if args.workload == "deformation":
+            wav = tuple(int(c) for c in args.wavelet.split("."))
+            return init_deformation(mrgb, stream, prec, min(cap, 30000), wav), 8, DEFORM["umax"]
+        if args.workload in ("large", "adaptive-small"):
+            g = init_large(mrgb, stream, prec, cap, GAUSS if args.workload == "large" else GAUSS_SMALL)
+            return g, 8, 2.0 * TG[0]  # |u| + |v| <= 2 s for the Taylor-Green-like field
+        lev, anc = workload_tree(args.workload)
+        lmax = int(lev.max())
+        g = mrgb.Grid((1, 1, 1), 1.0, nb, 3, lmax, 6, 2, lev, anc, precision=prec,
+                      nfields=1, stream=stream, fixed_tree=True)
+        g.field_set(0, mrgb.INIT_GAUSSIAN, [0.5, 0.5, 0.5, 0.08, 1.0])
+        return g, lmax, sum(abs(u) for u in U)
+
+
+class Stepper:
+    """One benchmark step of the workload (RK3 step, adaptation every
+    ADAPT_EVERY steps on the adaptive workloads)."""
+
+    def __init__(self, args, mrgb, g, lmax, umax):
+        self.args, self.mrgb, self.g = args, mrgb, g
+        self.scheme = {"wenoz5": mrgb.WENOZ5, "cons5": mrgb.CONS5, "cons3": mrgb.CONS3}[args.scheme]
+        self.adaptive = args.workload in ("large", "adaptive-small")
+        self.deform = args.workload == "deformation"
+        self.nb = 24
+        self.umax = umax
+        self.dt = CFL * (1.0 / (self.nb * 2 ** lmax)) / umax
+        if args.diffusion:
+            g.set_diffusion(args.nu, args.diffusion)
+            hmin = 1.0 / (self.nb * 2 ** lmax)
+            self.dt = min(self.dt, 0.1 * hmin * hmin / args.nu)  # explicit diffusion limit
+        self.state = {"t": 0.0, "n": 0, "lm": g.query().max_level, "i": 0}
+
+    def __call__(self):
+        """One step; returns the point-stage updates it performed."""
+        g, mrgb, st = self.g, self.mrgb, self.state
+        pts = g.nleaf * self.nb ** 3
+        i = st["i"]
+        st["i"] += 1
+        if self.deform:
+            # dt from the finest spacing present (reading of Sec. 5.3)
+            t = st["t"]
+            dtd = DEFORM["cfl"] * (1.0 / (self.nb * 2 ** st["lm"])) / self.umax
+            sc = [math.cos(math.pi * tt / 3) for tt in (t, t + dtd, t + dtd / 2)]
+            g.step_vel_scaled(0, dtd, (1, 2, 3), self.scheme, sc)
+            st["t"] = t + dtd
+            st["n"] += 1
+            if st["n"] % DEFORM["adapt_every"] == 0:
+                g.adapt(0, DEFORM["eps_r"], DEFORM["eps_r"] / DEFORM["ratio"])
+                st["lm"] = g.query().max_level
+        elif self.adaptive:
+            g.step_vel(0, self.dt, (1, 2, 3), self.scheme)
+            if (i + 1) % ADAPT_EVERY == 0:
+                g.adapt(0, EPS_R, EPS_C)
+        else:
+            g.step(0, self.dt, U, self.scheme)
+        return 3 * pts
+
+
+def timed(args, g, step, stream, W, dist):
+    """W warm-up steps, then args.steps timed steps between CUDA events on the
+    grid's stream, with clocks sampled during the timed region."""
+    import torch
+    for _ in range(W):
+        step()
+    stream.synchronize()
+    samples, stop = [], threading.Event()
+    th = threading.Thread(target=clocks_sampler, args=(stop, samples), daemon=True)
+    th.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    stats0 = g.query()
+    l0 = g.launch_count()
+    cudart = torch.cuda.cudart()
+    cudart.cudaProfilerStart()  # an attached profiler captures the timed steps only
+    g.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    psu = 0
+    e0.record(stream)
+    for _ in range(args.steps):
+        psu += step()
+    e1.record(stream)
+    e1.synchronize()
+    g.profile(False)
+    cudart.cudaProfilerStop()
+    ms = e0.elapsed_time(e1)
+    launches = g.launch_count() - l0
+    torch.cuda.synchronize()
+    stop.set()
+    th.join(timeout=2)
+    prof = g.profile_read()
+    # algorithmic bytes of the ghost reconstruction: the pre-pass (id 0) and
+    # the plain gather (id 1) share one fill, so they are timed together
+    ghost_bytes = g.profile_bytes(0) + g.profile_bytes(1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return dict(ms=ms, psu=psu, launches=launches, prof=prof, ghost_bytes=ghost_bytes, stats0=stats0,
+                stats1=g.query(), clocks=summarize_clocks(samples))
 
 
 def main():
@@ -205,6 +360,8 @@ def main():
     ap.add_argument("--scheme", default="wenoz5", choices=["wenoz5", "cons5", "cons3"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain form of the workload")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) measurement")
     ap.add_argument("--workload", default="large",
                     choices=["large", "adaptive-small", "deformation"] + sorted(WORKLOADS))
     ap.add_argument("--wavelet", default="4.2", choices=["2.2", "4.2", "6.2", "4.0", "6.0"],
@@ -231,123 +388,46 @@ def main():
 
     W = max(3, args.warmup)
     prec = mrgb.F32 if args.precision == "f32" else mrgb.F64
-    scheme = {"wenoz5": mrgb.WENOZ5, "cons5": mrgb.CONS5, "cons3": mrgb.CONS3}[args.scheme]
     nb = 24
     adaptive = args.workload in ("large", "adaptive-small")
     deform = args.workload == "deformation"
     stream = torch.cuda.Stream()
-    with torch.cuda.stream(stream):
-        if deform:
-            wav = tuple(int(c) for c in args.wavelet.split("."))
-            g = init_deformation(mrgb, stream, prec, min(args.capacity, 30000), wav)
-            lmax = 8
-            umax = DEFORM["umax"]
-        elif adaptive:
-            g = init_large(mrgb, stream, prec, args.capacity,
-                           GAUSS if args.workload == "large" else GAUSS_SMALL)
-            lmax = 8
-            umax = 2.0 * TG[0]  # |u| + |v| <= 2 s for the Taylor-Green-like field
-        else:
-            lev, anc = workload_tree(args.workload)
-            lmax = int(lev.max())
-            g = mrgb.Grid((1, 1, 1), 1.0, nb, 3, lmax, 6, 2, lev, anc, precision=prec,
-                          nfields=1, stream=stream, fixed_tree=True)
-            g.field_set(0, mrgb.INIT_GAUSSIAN, [0.5, 0.5, 0.5, 0.08, 1.0])
-            umax = sum(abs(u) for u in U)
-    dt = CFL * (1.0 / (nb * 2 ** lmax)) / umax
-    if args.diffusion:
-        g.set_diffusion(args.nu, args.diffusion)
-        hmin = 1.0 / (nb * 2 ** lmax)
-        dt = min(dt, 0.1 * hmin * hmin / args.nu)  # explicit diffusion limit
-    stats0 = g.query()
-
-    dstate = {"t": 0.0, "n": 0, "lm": stats0.max_level}
-
-    def one_step(i):
-        """One RK3 step (+ adaptation every ADAPT_EVERY steps); returns the
-        point-stage updates it performed."""
-        pts = g.nleaf * nb ** 3
-        if deform:
-            # dt from the finest spacing present (reading of Sec. 5.3)
-            t = dstate["t"]
-            dtd = DEFORM["cfl"] * (1.0 / (nb * 2 ** dstate["lm"])) / umax
-            sc = [math.cos(math.pi * tt / 3) for tt in (t, t + dtd, t + dtd / 2)]
-            g.step_vel_scaled(0, dtd, (1, 2, 3), scheme, sc)
-            dstate["t"] = t + dtd
-            dstate["n"] += 1
-            if dstate["n"] % DEFORM["adapt_every"] == 0:
-                g.adapt(0, DEFORM["eps_r"], DEFORM["eps_r"] / DEFORM["ratio"])
-                dstate["lm"] = g.query().max_level
-            return 3 * pts
-        if adaptive:
-            g.step_vel(0, dt, (1, 2, 3), scheme)
-            if (i + 1) % ADAPT_EVERY == 0:
-                g.adapt(0, EPS_R, EPS_C)
-        else:
-            g.step(0, dt, U, scheme)
-        return 3 * pts
-
-    for i in range(W):
-        one_step(i)
-    stream.synchronize()
-
-    samples, stop = [], threading.Event()
-    th = threading.Thread(target=clocks_sampler, args=(stop, samples), daemon=True)
-    th.start()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    l0 = g.launch_count()
-    cudart = torch.cuda.cudart()
-    cudart.cudaProfilerStart()  # an attached profiler captures the timed steps only
-    g.profile(True)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    psu_count = 0
-    e0.record(stream)
-    for i in range(args.steps):
-        psu_count += one_step(i)
-    e1.record(stream)
-    e1.synchronize()
-    g.profile(False)
-    cudart.cudaProfilerStop()
-    ms = e0.elapsed_time(e1)
-    launches = g.launch_count() - l0
-    torch.cuda.synchronize()
-    stop.set()
-    th.join(timeout=2)
-    prof = g.profile_read()
-    # algorithmic bytes of the ghost reconstruction: the pre-pass (id 0) and
-    # the plain gather (id 1) share one step, so they are timed together
-    ghost_bytes = g.profile_bytes(0) + g.profile_bytes(1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    stats1 = g.query()
+    g, lmax, umax = make_grid(args, mrgb, stream, prec, args.capacity)
+    step = Stepper(args, mrgb, g, lmax, umax)
+    r = timed(args, g, step, stream, W, dist)
+    ms, psu_count, prof, stats0, stats1 = r["ms"], r["psu"], r["prof"], r["stats0"], r["stats1"]
 
     # end to end through the public API with host buffers: each step copies
     # the scalar in from pinned host memory and reads it back
     es = 4 if prec == mrgb.F32 else 8
-    host = torch.empty((min(args.capacity, 30000) if deform else args.capacity if adaptive else g.nleaf) * nb ** 3,
-                       dtype=g.dtype,
-                       pin_memory=True)
-    ke = max(2, min(args.steps, 4))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    e2e_psu, h2d, d2h = 0, 0, 0
-    for i in range(ke):
-        n = g.nleaf * nb ** 3
-        g.field_copy_out(0, host[:n].numpy())  # establishes the host copy
-        g.field_copy_in(0, host[:n].numpy())
-        h2d += n * es
-        e2e_psu += one_step(i)
-        n = g.nleaf * nb ** 3
-        g.field_copy_out(0, host[:n].numpy())
-        d2h += n * es
-    e2e_s = time.perf_counter() - t0
+    e2e = None
+    if not args.no_e2e:
+        cap = min(args.capacity, 30000) if deform else args.capacity if adaptive else g.nleaf
+        host = torch.empty(cap * nb ** 3, dtype=g.dtype, pin_memory=True)
+        ke = max(2, min(args.steps, 4))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_psu, h2d, d2h = 0, 0, 0
+        for i in range(ke):
+            n = g.nleaf * nb ** 3
+            g.field_copy_out(0, host[:n].numpy())  # establishes the host copy
+            g.field_copy_in(0, host[:n].numpy())
+            h2d += n * es
+            e2e_psu += step()
+            n = g.nleaf * nb ** 3
+            g.field_copy_out(0, host[:n].numpy())
+            d2h += n * es
+        e2e_s = time.perf_counter() - t0
+        e2e = {"value": e2e_psu / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d // ke,
+               "d2h_bytes_per_step": d2h // ke}
+        del host
 
     psu = world * psu_count / (ms / 1e3)
     hbm, src = peaks()
+    try:
+        cpk = mrgb.device_peaks()
+    except Exception as ex:  # reported, not fatal
+        cpk = {"error": str(ex)}
     rprof = dict(prof)
     if "ghost_part1" in rprof:
         t0_, n0_ = rprof.pop("ghost_part1")
@@ -356,15 +436,17 @@ def main():
     name, (tot, cnt) = max(rprof.items(), key=lambda kv: kv[1][0])
     bpp = 4 if prec == mrgb.F32 else 8
     mean_pts = psu_count / (3 * args.steps)
+    vel_fields = adaptive or deform
     # algorithmic bytes per point-stage of the fused stage: phi read, RK
     # output written, u^n read in stages 1-2 (2/3 on average), plus the three
     # velocity components when the velocity is a field
-    per_pt = bpp * (1 + 1 + 2.0 / 3 + (3 if adaptive or deform else 0))
+    per_pt = bpp * (1 + 1 + 2.0 / 3 + (3 if vel_fields else 0))
     alg = {"rhs_stage": mean_pts * per_pt}
-    if "ghost_fill" in rprof and ghost_bytes > 0:
-        # shell points written + source values read, per reconstructed leaf,
-        # summed by the library over the launches (mean per pre-pass launch)
-        alg["ghost_fill"] = ghost_bytes / rprof["ghost_fill"][1]
+    if "ghost_fill" in rprof and r["ghost_bytes"] > 0:
+        # requested-shell points written + source values read, per
+        # reconstructed leaf, summed by the library over the launches (mean
+        # per pre-pass launch)
+        alg["ghost_fill"] = r["ghost_bytes"] / rprof["ghost_fill"][1]
     per_launch = alg.get(name, None)
     achieved = per_launch / (tot / cnt / 1e3) / 1e9 if per_launch else None
     gs = GAUSS if args.workload == "large" else GAUSS_SMALL
@@ -373,19 +455,22 @@ def main():
                     f"incompressible deformation field times cos(pi t/3): 1 tree, 24^3 blocks, levels 2-8, "
                     f"{args.wavelet} wavelet, eps_r {DEFORM['eps_r']}, eps_c {DEFORM['eps_r'] / DEFORM['ratio']}, "
                     f"{args.scheme} + RK3, CFL {DEFORM['cfl']} on the finest spacing present, adapt every "
-                    f"{DEFORM['adapt_every']} steps; {stats0.nleaf}->{stats1.nleaf} leaves, t = {dstate['t']:.4f}")
+                    f"{DEFORM['adapt_every']} steps; {stats0.nleaf}->{stats1.nleaf} leaves, t = {step.state['t']:.4f}")
+    elif adaptive:
+        workload = (f"{args.workload} single grid, adaptive: 1 tree, 24^3 blocks, levels "
+                    f"{stats0.min_level}-{stats0.max_level} (lmin 3, lmax 8), {stats0.nleaf}->{stats1.nleaf} "
+                    f"leaves, {mean_pts / 1e6:.0f} M points; scalar ({gs['n']} seeded Gaussians, seed "
+                    f"{gs['seed']}, sigma {gs['smin']}-{gs['smax']}) + 3 velocity fields (Taylor-Green-like, "
+                    f"scale {TG[0]}, phase {TG[1]}); 6.2 lifted wavelet, eps_r {EPS_R}, eps_c {EPS_C}; "
+                    f"{args.scheme} + RK3, CFL {CFL}; adapt every {ADAPT_EVERY} steps")
     else:
-        workload = None
-    workload = workload or (f"{args.workload} single grid, adaptive: 1 tree, 24^3 blocks, levels 3-8, "
-                f"{stats0.nleaf}->{stats1.nleaf} leaves; FP32 scalar ({gs['n']} seeded Gaussians, sigma "
-                f"{gs['smin']}-{gs['smax']}) + 3 velocity fields (Taylor-Green-like, scale "
-                f"{TG[0]}, phase {TG[1]}); 6.2 lifted wavelet, eps_r {EPS_R}, eps_c {EPS_C}; "
-                f"{args.scheme} + RK3, CFL {CFL}; adapt every {ADAPT_EVERY} steps"
-                if adaptive else
-                f"{args.workload} single grid, fixed tree, stencil step only: 1 tree, 24^3 blocks, "
-                f"levels 3-{lmax} (nested balls r={WORKLOADS[args.workload]}), {g.nleaf} leaves; "
-                f"6.2 lifted wavelet ghosts; {args.scheme} + RK3; u={U}; CFL {CFL}")
+        workload = (f"{args.workload} single grid, fixed tree, stencil step only: 1 tree, 24^3 blocks, "
+                    f"levels 3-{lmax} (nested balls r={WORKLOADS[args.workload]}), {g.nleaf} leaves; "
+                    f"6.2 lifted wavelet ghosts; {args.scheme} + RK3; u={U}; CFL {CFL}")
     shares = {k: v[0] / sum(x[0] for x in prof.values()) for k, v in prof.items()}
+    # whole-step roofline: algorithmic bytes per point-stage of the stencil
+    # step (survey measurement definition) times the achieved rate
+    step_gbs = psu * per_pt / 1e9
     line = {
         "metric": METRIC, "value": psu, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": W, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -400,17 +485,45 @@ def main():
                      "frac": achieved / hbm if achieved else None, "peak_source": src,
                      "traffic": None, "alg_bytes_per_launch": per_launch,
                      "alg_bytes_per_point_stage": per_pt if name == "rhs_stage" else None},
+        "roofline_step": {"bound": "hbm", "alg_bytes_per_point_stage": per_pt, "achieved": step_gbs,
+                          "peak": hbm, "unit": "GB/s", "frac": step_gbs / hbm},
         "kernels": {k: {"ms_total": v[0], "launches": v[1], "share": shares[k]} for k, v in prof.items()},
-        "gpu_launches": launches,
-        "e2e": {"value": e2e_psu / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d // ke,
-                "d2h_bytes_per_step": d2h // ke},
-        "clocks": summarize_clocks(samples),
+        "gpu_launches": r["launches"],
+        "e2e": e2e,
+        "clocks": r["clocks"],
+        "compute_peaks": cpk,
     }
     if "rhs_stage" in prof:
         t_rhs, n_rhs = prof["rhs_stage"]
-        a_rhs = mean_pts * per_pt / (t_rhs / n_rhs / 1e3) / 1e9
+        sec = t_rhs / n_rhs / 1e3
+        a_rhs = mean_pts * per_pt / sec / 1e9
         line["roofline_stage_kernel"] = {"kernel": "rhs_stage", "achieved": a_rhs, "peak": hbm,
                                          "unit": "GB/s", "frac": a_rhs / hbm}
+        # WENO-Z5: about 235 flops per point-stage (3 directions x ~75 + the
+        # stage combination), CONS-5 about 45 (survey measurement table)
+        fl = {"wenoz5": 235.0, "cons5": 45.0, "cons3": 30.0}[args.scheme]
+        key = "fp32_fma_tflops" if prec == mrgb.F32 else "fp64_fma_tflops"
+        if key in cpk:
+            tf = mean_pts * fl / sec / 1e12
+            line["roofline_stage_kernel"]["compute"] = {"flops_per_point_stage": fl, "achieved_tflops": tf,
+                                                        "peak_tflops": cpk[key], "frac": tf / cpk[key]}
+    if adaptive and prec == mrgb.F32 and not args.no_fp64:
+        # the plain FP64 form on the same workload and GPU: free the FP32 grid
+        del step, g
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        g64, lmax64, umax64 = make_grid(args, mrgb, stream, mrgb.F64, args.capacity)
+        step64 = Stepper(args, mrgb, g64, lmax64, umax64)
+        r64 = timed(args, g64, step64, stream, W, None)
+        v64 = world * r64["psu"] / (r64["ms"] / 1e3)
+        line["fp64_plain"] = {"value": v64, "unit": UNIT, "ms_per_step": r64["ms"] / args.steps,
+                              "leaves": [r64["stats0"].nleaf, r64["stats1"].nleaf], "steps": args.steps,
+                              "gpu_launches": r64["launches"], "clocks": r64["clocks"],
+                              "tolerance": "FP64 path: 1e-12 of the field maximum vs the oracle",
+                              "kernels": {k: {"ms_total": v[0], "launches": v[1]} for k, v in r64["prof"].items()}}
+        line["fp32_over_fp64"] = psu / v64
+        line["fp32_tolerance"] = "FP32 path: 1e-5 of the field maximum vs the FP64 oracle after 100 steps"
+        del step64, g64
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:

@@ -223,6 +223,38 @@ int mr_step_vel(mr_grid *grid, int phi_fid, double dt, const int *vel_fid, int s
 int mr_step_vel_scaled(mr_grid *grid, int phi_fid, double dt, const int *vel_fid, int scheme,
                        const double *stage_scale);
 
+/* Stable time step (Sec. 5.1 takes dt = CFL h_f / U; in 3D the reading used
+ * here is dt = CFL * h_min / max_x sum_d |u_d|, which equals it for an
+ * axis-aligned velocity): h_min is the spacing of the finest leaf present,
+ * and the velocity is either the constant u_const (host, 3 doubles) or the
+ * fields vel_fid[3] (exactly one of the two non-NULL), whose maximum of
+ * |u_0| + |u_1| + |u_2| over every point is reduced on the device in FP64
+ * (max is exact, so the result is independent of the order).  *dt (host)
+ * receives +inf for a zero velocity.  Synchronises.  Errors:
+ * MR_ERR_INVALID for a non-positive or non-finite CFL, both or neither of
+ * u_const / vel_fid, or a bad field id.                                  */
+int mr_dt(mr_grid *grid, double cfl, const double *u_const, const int *vel_fid, double *dt);
+
+/* CUDA-graph mode of the RK steps (mr_step, mr_step_vel, mr_step_vel_scaled):
+ * with enable = 1 a step's kernels (the three stages) are captured once into
+ * a CUDA graph on the grid's stream and the graph is replayed by every later
+ * step with the same key -- step kind, field ids, dt, velocity or stage
+ * scales, scheme, diffusion term, leaves (any adaptation changes the key)
+ * and pools; a different key captures the step again.  Results are bit-for-
+ * bit those of the stream-ordered step.  The velocity cache is rebuilt
+ * outside the capture.  While a step is being captured the launch registry
+ * records no events (mr_profile times steps run without graphs); replays
+ * count their kernels in mr_launch_count.  enable = 0 releases the graph
+ * (synchronises).  mr_graph_replays returns the replays since creation.    */
+int mr_use_graphs(mr_grid *grid, int enable);
+int mr_graph_replays(mr_grid *grid, long long *n);
+
+/* Bounds of the adaptation loops: mr_adapt runs at most max_iter iterations
+ * (default 64) and each iteration at most max_sweeps policy sweeps (default
+ * 256); beyond either the call returns MR_ERR_TIMEOUT with the leaves of the
+ * last completed iteration in place.  MR_ERR_INVALID for values < 1.      */
+int mr_set_adapt_limits(mr_grid *grid, int max_iter, int max_sweeps);
+
 /* Drop the cached ghost-filled velocity (after changing velocity values). */
 int mr_velocity_invalidate(mr_grid *grid);
 
@@ -281,13 +313,27 @@ int mr_profile_read(mr_grid *grid, int kid, double *total_ms, int *nlaunch, cons
 int mr_launch_count(mr_grid *grid, long long *n);
 /* Algorithmic bytes of the recorded launches of kernel kid (the roofline
  * numerator), accumulated on the device while profiling is on.  Defined for
- * the ghost pre-pass (kid 0): every ghost point of the padded block of each
- * leaf the launch reconstructs is written once and its source value read
- * once, (Wd^3 - nb^3) * (source + padded element size) per leaf, Wd the
- * padded width; leaves a launch skips (need mask, stencil pre-pass of a leaf
- * without coarser neighbours) count zero.  0 for other kernels.
+ * the ghost pre-pass (kid 0) and the ghost gather (kid 1): every point of the
+ * requested shell G of each leaf the launch reconstructs is written once and
+ * its source value read once, ((nb + 2G)^3 - nb^3) * (source + padded
+ * element size) per leaf -- the internal shell the kernels also fill (wider
+ * where substitution or the fine-to-coarse coarsening reads further) counts
+ * as time, not bytes; leaves a launch skips (need mask, stencil pre-pass of
+ * a leaf without coarser neighbours) count zero.  0 for other kernels.
  * Synchronises; *bytes (host) receives the sum since the last mr_profile(1). */
 int mr_profile_bytes(mr_grid *grid, int kid, double *bytes);
+
+/* Compute throughput of the current device, measured by short probe
+ * kernels (8 CTAs of 256 threads per SM, 8 independent dependency chains per
+ * thread; about half a second): out[0] FP32 fused multiply-add TFLOP/s,
+ * out[1] FP64 FMA TFLOP/s, out[2] FP32 fast divisions (__fdividef) in G/s,
+ * out[3] FP32 IEEE divisions G/s, out[4] FP64 divisions G/s.  These are the
+ * compute-roofline denominators of the stencil and wavelet kernels beside
+ * the copy bandwidth (the paper has no counterpart: it reports CPU-cluster
+ * timings only).  Runs on the legacy stream and synchronises it; allocates
+ * nothing.  out: host array of MR_NUM_PEAKS doubles.                     */
+#define MR_NUM_PEAKS 5
+int mr_device_peaks(double *out);
 
 /* Device pointer of field fid (slot-major layout above). */
 int mr_field_ptr(mr_grid *grid, int fid, void **ptr);

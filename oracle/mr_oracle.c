@@ -776,6 +776,21 @@ double og_dt(const og_grid *g, double cfl, const double *u_const) {
   return cfl * h / us;
 }
 
+/* The same time step with velocity fields vx, vy, vz (unpadded, nleaf*nb^3):
+ * the maximum over every point of |u_x| + |u_y| + |u_z| (summed x, y, z).   */
+double og_dt_vel(const og_grid *g, double cfl, const double *vx, const double *vy, const double *vz) {
+  int lmax = 0;
+  for (int i = 0; i < g->nleaf; ++i) lmax = g->lev[i] > lmax ? g->lev[i] : lmax;
+  double h = g->tree_len / ((double)g->nb * (double)(1L << lmax));
+  const size_t n = (size_t)g->nleaf * g->nb * g->nb * g->nb;
+  double us = 0.0;
+  for (size_t i = 0; i < n; ++i) {
+    double s = fabs(vx[i]) + fabs(vy[i]) + fabs(vz[i]);
+    if (s > us) us = s;
+  }
+  return cfl * h / us;
+}
+
 /* Zeroth and first moments (eq 2.18): M0 = sum_b h_b^3 sum_i phi,
  * M1[d] = sum_b h_b^3 sum_i phi x_d, x at the vertex-aligned positions.    */
 void og_moments(const og_grid *g, const double *phi, double *m0, double *m1) {

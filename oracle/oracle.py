@@ -70,6 +70,8 @@ def _declare(L):
     L.og_rk3_step_diff.argtypes = [C.POINTER(_Grid), _dp, C.c_double, C.c_int, _dp, C.c_double, C.c_int]
     L.og_dt.argtypes = [C.POINTER(_Grid), C.c_double, _dp]
     L.og_dt.restype = C.c_double
+    L.og_dt_vel.argtypes = [C.POINTER(_Grid), C.c_double, _dp, _dp, _dp]
+    L.og_dt_vel.restype = C.c_double
     L.og_moments.argtypes = [C.POINTER(_Grid), _dp, _dp, _dp]
     L.og_criterion.argtypes = [C.POINTER(_Grid), _dp, C.c_int, _dp]
     L.og_detail_reach.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
@@ -217,6 +219,12 @@ def rk3_step_velpad_scaled(g: Grid, phi: np.ndarray, vpads, dt: float, scheme: i
 
 def dt_cfl(g: Grid, cfl: float, u) -> float:
     return lib().og_dt(g.c(), cfl, _d(np.asarray(u, dtype=np.float64)))
+
+
+def dt_cfl_vel(g: Grid, cfl: float, vel) -> float:
+    """CFL time step from velocity fields (max over points of sum |u_d|)."""
+    v = [np.ascontiguousarray(a, np.float64) for a in vel]
+    return lib().og_dt_vel(g.c(), cfl, _d(v[0]), _d(v[1]), _d(v[2]))
 
 
 def moments(g: Grid, phi: np.ndarray):

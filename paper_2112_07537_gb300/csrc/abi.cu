@@ -27,6 +27,10 @@ int check_cuda(cudaError_t e, const char *where) {
 }
 
 void kt_begin(mr_grid *g, int kid) {
+  if (g->capturing) {
+    g->cap_counts[kid]++;  // runs at every replay of the graph, not now
+    return;
+  }
   g->launches[kid]++;
   if (!g->profiling || g->nrec >= 4096) return;
   if (!g->ev_ready) {
@@ -38,7 +42,7 @@ void kt_begin(mr_grid *g, int kid) {
 }
 
 void kt_end(mr_grid *g) {
-  if (!g->profiling || g->nrec >= 4096) return;
+  if (g->capturing || !g->profiling || g->nrec >= 4096) return;
   cudaEventRecord(g->ev[1][g->nrec], g->stream);
   g->nrec++;
 }
@@ -123,7 +127,9 @@ static int layout(const mr_grid_desc *d, Layout *L, int *shell_rk, int *shell_ad
       *map_cells * 4, *map_cells * 4,            // maps[2]
       (size_t)(d->nfields + 2) * cap * nb3 * es, // pool 0
       fixed ? 0 : (size_t)(d->nfields + 2) * cap * nb3 * es,  // pool 1
-      cap * wr * wr * wr * es, cap * wr * wr * wr * es,       // padP, padQ
+      // padP, padQ (stencil shell); grids with adaptation buffers use the
+      // larger FP64 adaptation buffers for them (never live at the same time)
+      fixed ? cap * wr * wr * wr * es : 0, fixed ? cap * wr * wr * wr * es : 0,
       fixed ? 0 : cap * wa * wa * wa * 8, fixed ? 0 : cap * wa * wa * wa * 8,  // padP64, padQ64
       cap * 8,                                   // maxdet
       cap,                                       // status
@@ -244,10 +250,14 @@ int mr_grid_create(const mr_grid_desc *desc, void *workspace, size_t workspace_b
   g->maps[1] = (int *)(w + L.off[7]);
   g->pool[0] = w + L.off[8];
   g->pool[1] = w + L.off[9];
-  g->padP = w + L.off[10];
-  g->padQ = w + L.off[11];
   g->padP64 = (double *)(w + L.off[12]);
   g->padQ64 = (double *)(w + L.off[13]);
+  // the stencil-shell padded blocks (element type, internal shell shell_rk)
+  // and the adaptation-shell FP64 blocks are never needed at the same time:
+  // without MR_GRID_FIXED_TREE they share the (larger) FP64 buffers
+  const bool fixed_tree = desc->flags & MR_GRID_FIXED_TREE;
+  g->padP = fixed_tree ? (void *)(w + L.off[10]) : (void *)g->padP64;
+  g->padQ = fixed_tree ? (void *)(w + L.off[11]) : (void *)g->padQ64;
   g->maxdet = (double *)(w + L.off[14]);
   g->status = (int8_t *)(w + L.off[15]);
   g->refined = (int *)(w + L.off[16]);
@@ -265,6 +275,8 @@ int mr_grid_create(const mr_grid_desc *desc, void *workspace, size_t workspace_b
   g->diff_nu = 0.0;
   g->diff_order = 0;
   g->vel_scale = 1.0;
+  g->max_adapt_iter = 64;
+  g->max_policy_sweeps = 256;
   g->shell_rk = srk;
   g->shell_ad = sad;
   g->map_cells = mc;
@@ -296,6 +308,7 @@ int mr_grid_create(const mr_grid_desc *desc, void *workspace, size_t workspace_b
 int mr_grid_destroy(mr_grid *g) {
   if (!g) return MR_ERR_INVALID;
   cudaStreamSynchronize(g->stream);
+  if (g->gexec) cudaGraphExecDestroy(g->gexec);
   if (g->ev_ready)
     for (int i = 0; i < 4096; ++i) cudaEventDestroy(g->ev[0][i]), cudaEventDestroy(g->ev[1][i]);
   delete g;
@@ -523,17 +536,63 @@ int mr_rhs_advect_vel(mr_grid *g, int phi, const int *vel, int out, int scheme) 
   return launch_rhs_stage(g, P, Gi, nullptr, field_ptr(g, out), 0, 0.0, nullptr, scheme, true, g->vpad);
 }
 
-int mr_step_vel(mr_grid *g, int phi, double dt, const int *vel, int scheme) {
-  static const double ones[3] = {1.0, 1.0, 1.0};
-  return mr_step_vel_scaled(g, phi, dt, vel, scheme, ones);
+}  // extern "C"
+
+// ---------------------------------------------------------------- graphs
+// In graph mode an RK step is captured once into a CUDA graph (the kernels of
+// its three stages) and replayed while its key -- step kind, field ids, dt,
+// scales, velocity, scheme, diffusion, tree version, pool and leaf count --
+// stays the same; any change captures it again.  Work that must precede the
+// step (the velocity cache) is done outside the capture.
+struct GraphKey {
+  int kind, phi, vel[3], scheme, tree_version, pool_cur, nleaf, diff_order;
+  double dt, sc[3], u[3], nu;
+};
+
+template <typename F>
+static int run_step(mr_grid *g, const GraphKey &key, F body) {
+  if (!g->use_graphs) return body();
+  GraphKey k = key;
+  k.tree_version = g->tree_version, k.pool_cur = g->pool_cur, k.nleaf = g->nleaf, k.diff_order = g->diff_order;
+  k.nu = g->diff_nu;
+  if (g->gexec && g->gkey_len == (int)sizeof k && memcmp(g->gkey, &k, sizeof k) == 0) {
+    if (check_cuda(cudaGraphLaunch(g->gexec, g->stream), "cudaGraphLaunch")) return MR_ERR_CUDA;
+    for (int i = 0; i < MRK_COUNT; ++i) g->launches[i] += g->cap_counts[i];
+    g->graph_replays++;
+    return MR_OK;
+  }
+  if (g->gexec) {
+    cudaGraphExecDestroy(g->gexec);
+    g->gexec = nullptr;
+  }
+  if (check_cuda(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeRelaxed), "cudaStreamBeginCapture"))
+    return MR_ERR_CUDA;
+  memset(g->cap_counts, 0, sizeof g->cap_counts);
+  g->capturing = 1;
+  const int e = body();
+  g->capturing = 0;
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(g->stream, &graph);
+  if (e) {
+    if (graph) cudaGraphDestroy(graph);
+    return e;
+  }
+  if (check_cuda(ce, "cudaStreamEndCapture")) return MR_ERR_CUDA;
+  cudaGraphExec_t ex = nullptr;
+  const cudaError_t ie = cudaGraphInstantiate(&ex, graph, 0);
+  cudaGraphDestroy(graph);
+  if (check_cuda(ie, "cudaGraphInstantiate")) return MR_ERR_CUDA;
+  g->gexec = ex;
+  memcpy(g->gkey, &k, sizeof k);
+  g->gkey_len = (int)sizeof k;
+  if (check_cuda(cudaGraphLaunch(g->gexec, g->stream), "cudaGraphLaunch")) return MR_ERR_CUDA;
+  for (int i = 0; i < MRK_COUNT; ++i) g->launches[i] += g->cap_counts[i];
+  return MR_OK;
 }
 
-int mr_step_vel_scaled(mr_grid *g, int phi, double dt, const int *vel, int scheme, const double *scale) {
-  if (!fid_ok(g, phi) || !vel || !scale) return MR_ERR_INVALID;
-  for (int s = 0; s < 3; ++s)
-    if (!std::isfinite(scale[s])) return MR_ERR_INVALID;
-  int e = velocity_cache(g, vel);
-  if (e) return e;
+
+static int step_vel_body(mr_grid *g, int phi, double dt, int scheme, const double *scale) {
+  int e = MR_OK;
   void *un = field_ptr(g, phi);
   void *y1 = field_ptr(g, g->desc.nfields), *y2 = field_ptr(g, g->desc.nfields + 1);
   void *src[3] = {un, y1, y2};
@@ -555,16 +614,7 @@ int mr_step_vel_scaled(mr_grid *g, int phi, double dt, const int *vel, int schem
   return e;
 }
 
-int mr_rk_stage(mr_grid *g, int stage, double dt, int u_fid, int y_fid, int rhs_fid, int out_fid) {
-  if (!fid_ok(g, u_fid) || !fid_ok(g, y_fid) || !fid_ok(g, rhs_fid) || !fid_ok(g, out_fid) || stage < 0 ||
-      stage > 2)
-    return MR_ERR_INVALID;
-  return launch_rk_combine(g, stage, dt, field_ptr(g, u_fid), field_ptr(g, y_fid), field_ptr(g, rhs_fid),
-                           field_ptr(g, out_fid));
-}
-
-int mr_step(mr_grid *g, int phi, double dt, const double *u, int scheme) {
-  if (!fid_ok(g, phi) || !u) return MR_ERR_INVALID;
+static int step_body(mr_grid *g, int phi, double dt, const double *u, int scheme) {
   void *un = field_ptr(g, phi);
   void *y1 = field_ptr(g, g->desc.nfields), *y2 = field_ptr(g, g->desc.nfields + 1);
   void *src[3] = {un, y1, y2};
@@ -587,6 +637,79 @@ int mr_step(mr_grid *g, int phi, double dt, const double *u, int scheme) {
     if (e) return e;
   }
   return MR_OK;
+}
+
+extern "C" {
+
+int mr_use_graphs(mr_grid *g, int enable) {
+  if (!g) return MR_ERR_INVALID;
+  g->use_graphs = enable ? 1 : 0;
+  if (!enable && g->gexec) {
+    if (check_cuda(cudaStreamSynchronize(g->stream), "graph sync")) return MR_ERR_CUDA;
+    cudaGraphExecDestroy(g->gexec);
+    g->gexec = nullptr;
+    g->gkey_len = 0;
+  }
+  return MR_OK;
+}
+
+int mr_graph_replays(mr_grid *g, long long *n) {
+  if (!g || !n) return MR_ERR_INVALID;
+  *n = g->graph_replays;
+  return MR_OK;
+}
+
+int mr_set_adapt_limits(mr_grid *g, int max_iter, int max_sweeps) {
+  if (!g || max_iter < 1 || max_sweeps < 1) return MR_ERR_INVALID;
+  g->max_adapt_iter = max_iter;
+  g->max_policy_sweeps = max_sweeps;
+  return MR_OK;
+}
+
+int mr_dt(mr_grid *g, double cfl, const double *u, const int *vel, double *dt) {
+  if (!g || !dt || !(cfl > 0.0) || !std::isfinite(cfl) || (!u) == (!vel)) return MR_ERR_INVALID;
+  if (vel) {
+    for (int d = 0; d < 3; ++d)
+      if (!fid_ok(g, vel[d])) return MR_ERR_INVALID;
+    const void *vp[3] = {field_ptr(g, vel[0]), field_ptr(g, vel[1]), field_ptr(g, vel[2])};
+    return launch_dt(g, cfl, nullptr, vp, dt);
+  }
+  for (int d = 0; d < 3; ++d)
+    if (!std::isfinite(u[d])) return MR_ERR_INVALID;
+  return launch_dt(g, cfl, u, nullptr, dt);
+}
+
+int mr_step_vel(mr_grid *g, int phi, double dt, const int *vel, int scheme) {
+  static const double ones[3] = {1.0, 1.0, 1.0};
+  return mr_step_vel_scaled(g, phi, dt, vel, scheme, ones);
+}
+
+int mr_step_vel_scaled(mr_grid *g, int phi, double dt, const int *vel, int scheme, const double *scale) {
+  if (!fid_ok(g, phi) || !vel || !scale) return MR_ERR_INVALID;
+  for (int s = 0; s < 3; ++s)
+    if (!std::isfinite(scale[s])) return MR_ERR_INVALID;
+  int e = velocity_cache(g, vel);
+  if (e) return e;
+  GraphKey key{};
+  key.kind = 1, key.phi = phi, key.scheme = scheme, key.dt = dt;
+  for (int d = 0; d < 3; ++d) key.vel[d] = vel[d], key.sc[d] = scale[d];
+  return run_step(g, key, [&]() { return step_vel_body(g, phi, dt, scheme, scale); });
+}
+
+int mr_rk_stage(mr_grid *g, int stage, double dt, int u_fid, int y_fid, int rhs_fid, int out_fid) {
+  if (!fid_ok(g, u_fid) || !fid_ok(g, y_fid) || !fid_ok(g, rhs_fid) || !fid_ok(g, out_fid) || stage < 0 ||
+      stage > 2)
+    return MR_ERR_INVALID;
+  return launch_rk_combine(g, stage, dt, field_ptr(g, u_fid), field_ptr(g, y_fid), field_ptr(g, rhs_fid),
+                           field_ptr(g, out_fid));
+}
+
+int mr_step(mr_grid *g, int phi, double dt, const double *u, int scheme) {
+  if (!fid_ok(g, phi) || !u) return MR_ERR_INVALID;
+  GraphKey key{};
+  key.kind = 0, key.phi = phi, key.scheme = scheme, key.dt = dt;
+  for (int d = 0; d < 3; ++d) key.u[d] = u[d];
+  return run_step(g, key, [&]() { return step_body(g, phi, dt, u, scheme); });
 }
 
 int mr_criterion(mr_grid *g, int fid, double *maxdet) {
@@ -613,8 +736,9 @@ int mr_adapt(mr_grid *g, int crit, double er, double ec, int flags, int *nch) {
   if (!fid_ok(g, crit)) return MR_ERR_INVALID;
   if (!adapt_ok(g)) return MR_ERR_UNSUPPORTED;
   int total = 0;
-  cudaMemsetAsync(g->refined, 0, 4 * (size_t)g->desc.capacity, g->stream);
-  for (int it = 0; it < 64; ++it) {
+  if (check_cuda(cudaMemsetAsync(g->refined, 0, 4 * (size_t)g->desc.capacity, g->stream), "refined reset"))
+    return MR_ERR_CUDA;
+  for (int it = 0; it < g->max_adapt_iter; ++it) {
     int n = 0;
     int e = adapt_iteration(g, crit, er, ec, flags, &n);
     if (e) return e;
@@ -625,7 +749,7 @@ int mr_adapt(mr_grid *g, int crit, double er, double ec, int flags, int *nch) {
     }
   }
   if (nch) *nch = total;
-  set_error("adaptation did not converge within 64 iterations");
+  set_error("adaptation did not converge within the iteration limit");
   return MR_ERR_TIMEOUT;
 }
 

@@ -677,8 +677,8 @@ int adapt_iteration(mr_grid *g, int crit, double er, double ec, int flags, int *
   int8_t *sa = g->status, *sb = (int8_t *)g->newsrc;
   int it = 0;
   for (;; ++it) {
-    if (it > 256) {
-      set_error("policy did not reach a fixed point within 256 sweeps");
+    if (it >= g->max_policy_sweeps) {
+      set_error("policy did not reach a fixed point within the sweep limit");
       return MR_ERR_TIMEOUT;
     }
     if (check_cuda(cudaMemsetAsync(g->counter, 0, sizeof(int), st), "memset")) return MR_ERR_CUDA;
@@ -703,7 +703,17 @@ int adapt_iteration(mr_grid *g, int crit, double er, double ec, int flags, int *
   if (e) return e;
   const int changed = hc[0], nn = hc[1];
   if (check_cuda(cudaGetLastError(), "policy")) return MR_ERR_CUDA;
-  if (changed == 0) return MR_OK;
+  if (changed == 0) {
+    // Alg. SM3 step 1 ghost-fills every field in every iteration; with no
+    // leaf changing, what remains of it for the other fields is the
+    // substitution next to coarser leaves, which overwrites their values
+    for (int fid = 0; fid < g->desc.nfields; ++fid) {
+      if (fid == crit) continue;
+      e = launch_substitute(g, field_ptr(g, fid));
+      if (e) return e;
+    }
+    return MR_OK;
+  }
   if (nn > g->desc.capacity) {
     set_error("adaptation exceeds the leaf capacity");
     return MR_ERR_NOMEM;

@@ -641,6 +641,7 @@ __global__ void __launch_bounds__(512, sizeof(TP) == 4 ? 2 : 1) k_prep(Tree t, c
   subst_sep<N, NT, TP>(Pb, Wd, Gi, sbox, 2, reinterpret_cast<TP *>(smraw), (long)dyn_bytes / (long)sizeof(TP));
   subst_sep<N, NT, TP>(Pb, Wd, Gi, sbox, 3, reinterpret_cast<TP *>(smraw), (long)dyn_bytes / (long)sizeof(TP));
   __syncthreads();
+  if (only_coarse == 2) return;  // substitution only: no fine-to-coarse push
   // distinct coarser neighbours
   if (threadIdx.x == 0) {
     for (int m = 0; m < 27; ++m) {
@@ -954,7 +955,7 @@ static int ghost_impl(mr_grid *g, const TI *phi_in, TI *phi_out, int G, TP *P, T
     MR_LAUNCH(g, MRK_PART2, k_fill_plain<TI, TP><<<n, 256, 0, g->stream>>>(t, phi_in, P, Gi, need, g->pneed,
                                                                           g->cmask, err));
     if (check_cuda(cudaGetLastError(), "k_fill_plain")) return MR_ERR_CUDA;
-    const double wd = nb + 2.0 * Gi;
+    const double wd = nb + 2.0 * G;  // the requested shell (not the internal one)
     count_units(g, MRK_PART2, need, n, (wd * wd * wd - (double)nb * nb * nb) * (double)(sizeof(TI) + sizeof(TP)),
                 g->pneed);
     need_prep = g->pneed;
@@ -964,7 +965,7 @@ static int ghost_impl(mr_grid *g, const TI *phi_in, TI *phi_out, int G, TP *P, T
                                                                            need_prep, only_coarse ? 0 : 1, (int)sm));
   if (check_cuda(cudaGetLastError(), "k_prep")) return MR_ERR_CUDA;
   {
-    const double wd = nb + 2.0 * Gi;
+    const double wd = nb + 2.0 * G;
     count_units(g, MRK_PART1, only_coarse ? g->cmask : need_prep, n,
                 (wd * wd * wd - (double)nb * nb * nb) * (double)(sizeof(TI) + sizeof(TP)));
   }
@@ -1037,6 +1038,31 @@ int launch_prep32(mr_grid *g, const void *phi, int *Gi) {
   const int gi = internal_shell(g->desc.wav_N, g->desc.wav_Nt, 3, g->desc.nb);
   *Gi = gi;
   return ghost_dispatch<float, float>(g, (const float *)phi, nullptr, 3, (float *)g->padP, (float *)g->padQ, gi, 1);
+}
+
+// Substitution alone (the first step of Alg. SM2) of every leaf next to a
+// coarser leaf: the pre-pass at the shell the substitution reads (the G^a
+// half-width) computes the padded block, substitutes the band in FP64 and
+// the substituted values are written back to the field -- the field values a
+// full ghost fill leaves, without the padded blocks of the other leaves.
+int launch_substitute(mr_grid *g, void *phi) {
+  const int N = g->desc.wav_N, Nt = g->desc.wav_Nt, nb = g->desc.nb;
+  const int G = N - 1, gi = internal_shell(N, Nt, G, nb);
+  if (gi > g->shell_ad || (g->desc.flags & MR_GRID_FIXED_TREE)) return MR_ERR_UNSUPPORTED;
+  int e;
+  if (g->desc.precision == MR_F32) {
+    e = ghost_dispatch<float, double>(g, (const float *)phi, nullptr, G, g->padP64, g->padQ64, gi, 2);
+    if (!e)
+      MR_LAUNCH(g, MRK_MERGE, k_writeback<float, double><<<g->nleaf, 256, 0, g->stream>>>(
+                                  nb, g->padP64, gi, g->cmask, (float *)phi));
+  } else {
+    e = ghost_dispatch<double, double>(g, (const double *)phi, nullptr, G, g->padP64, g->padQ64, gi, 2);
+    if (!e)
+      MR_LAUNCH(g, MRK_MERGE, k_writeback<double, double><<<g->nleaf, 256, 0, g->stream>>>(
+                                  nb, g->padP64, gi, g->cmask, (double *)phi));
+  }
+  if (e) return e;
+  return check_cuda(cudaGetLastError(), "k_writeback") ? MR_ERR_CUDA : MR_OK;
 }
 
 int launch_writeback32(mr_grid *g, int Gi, void *phi) {

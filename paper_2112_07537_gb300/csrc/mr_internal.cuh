@@ -421,8 +421,8 @@ struct mr_grid {
   void *pool[2];          // each: (nfields+2) * capacity * nb3 elements
   int pool_cur;
   // ghost buffers: padded P and part-2 Q, FP64 (adaptation) and element type
-  void *padP;             // capacity * W^3 * esize (RK shell)
-  void *padQ;
+  void *padP;             // capacity * W^3 * esize (RK shell); aliases padP64
+  void *padQ;             // unless the grid is a fixed tree (likewise padQ64)
   double *padP64;         // capacity * Wa^3 doubles (adaptation shell)
   double *padQ64;
   int shell_rk;           // internal shell of padP
@@ -454,6 +454,18 @@ struct mr_grid {
   int rec_kid[4096];
   cudaEvent_t ev[2][4096];
   int ev_ready;
+  // adaptation loop bounds (mr_set_adapt_limits)
+  int max_adapt_iter;     // mr_adapt iterations before MR_ERR_TIMEOUT (default 64)
+  int max_policy_sweeps;  // policy sweeps per iteration before MR_ERR_TIMEOUT (default 256)
+  // CUDA-graph mode of the RK steps (mr_use_graphs): one captured step,
+  // replayed while its key (fields, dt, scales, tree, pools) is unchanged
+  int use_graphs;
+  int capturing;          // launches are being captured: count them in cap_counts
+  long long cap_counts[32];
+  cudaGraphExec_t gexec;
+  unsigned char gkey[160];
+  int gkey_len;
+  long long graph_replays;
 };
 
 // dscratch[MR_ALG_BYTES_SLOT + kid]: algorithmic bytes of kernel kid while
@@ -492,6 +504,7 @@ int launch_crop(mr_grid *g, const void *P, int Gi, void *out, int G, bool fp64_s
 int launch_crop64(mr_grid *g, const double *P, int Gi, double *out, int G);
 int launch_prep32(mr_grid *g, const void *phi, int *Gi);
 int launch_writeback32(mr_grid *g, int Gi, void *phi);
+int launch_substitute(mr_grid *g, void *phi);
 int launch_fused(mr_grid *g, const void *phi, const void *P, const void *Q, int Gi, const void *u, void *out,
                  int stage, double dt, const double *uc, int scheme, bool rhs_only, const void *vpad = nullptr);
 int adapt_shell(int N, int Nt);
@@ -502,6 +515,7 @@ int launch_rk_combine(mr_grid *g, int stage, double dt, const void *u, const voi
                       const void *r, void *out);
 int launch_field_set(mr_grid *g, void *f, int kind, const double *p, int np);
 int launch_mass(mr_grid *g, const void *f, double *host_out);
+int launch_dt(mr_grid *g, double cfl, const double *uc, const void *const *vel, double *host_out);
 // adapt.cu
 int launch_criterion(mr_grid *g, const double *P64, int Gi, double *maxdet);
 int adapt_iteration(mr_grid *g, int crit_fid, double er, double ec, int flags, int *nch);

@@ -559,4 +559,76 @@ int launch_mass(mr_grid *g, const void *f, double *host_out) {
   return check_cuda(cudaStreamSynchronize(g->stream), "mass sync") ? MR_ERR_CUDA : MR_OK;
 }
 
+// Time step (reading of Sec. 5.1): dt = CFL h_min / max_x sum_d |u_d|.  Per
+// leaf: max over its points of |u_0| + |u_1| + |u_2| (FP64 sums of the stored
+// values, x, then y, then z) and its level; one CTA then takes the maxima --
+// max is exact, so the result does not depend on the order.
+template <typename T>
+__global__ void __launch_bounds__(256) k_umax_leaf(int nb, const T *__restrict__ u0, const T *__restrict__ u1,
+                                                   const T *__restrict__ u2, double *part) {
+  const int b = blockIdx.x;
+  const size_t nb3 = (size_t)nb * nb * nb, o = (size_t)b * nb3;
+  unsigned long long m = 0;
+  for (size_t p = threadIdx.x; p < nb3; p += blockDim.x) {
+    const double s = fabs((double)u0[o + p]) + fabs((double)u1[o + p]) + fabs((double)u2[o + p]);
+    m = max(m, abs_key(s));
+  }
+  for (int w = 16; w > 0; w >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, w));
+  __shared__ unsigned long long red[8];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = max(m, red[w]);
+    part[b] = __longlong_as_double((long long)max(m, red[0]));
+  }
+}
+
+__global__ void __launch_bounds__(256) k_dt_reduce(const double *__restrict__ part, const int *__restrict__ lev, int n,
+                                                   double usum_const, double cfl, double tree_len, int nb,
+                                                   double *out) {
+  unsigned long long m = 0;
+  int lm = 0;
+  for (int b = threadIdx.x; b < n; b += blockDim.x) {
+    if (part) m = max(m, abs_key(part[b]));
+    lm = max(lm, lev[b]);
+  }
+  for (int w = 16; w > 0; w >>= 1) {
+    m = max(m, __shfl_xor_sync(0xffffffffu, m, w));
+    lm = max(lm, __shfl_xor_sync(0xffffffffu, lm, w));
+  }
+  __shared__ unsigned long long rm[8];
+  __shared__ int rl[8];
+  if ((threadIdx.x & 31) == 0) rm[threadIdx.x >> 5] = m, rl[threadIdx.x >> 5] = lm;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = max(m, rm[w]), lm = max(lm, rl[w]);
+    const double us = part ? __longlong_as_double((long long)m) : usum_const;
+    const double h = tree_len / ((double)nb * (double)(1LL << lm));
+    out[0] = us > 0.0 ? cfl * h / us : __longlong_as_double(0x7ff0000000000000LL);
+  }
+}
+
+int launch_dt(mr_grid *g, double cfl, const double *uc, const void *const *vel, double *host_out) {
+  Tree t = tree_view(g);
+  const int n = g->nleaf, nb = g->desc.nb;
+  double *part = nullptr;
+  if (vel) {
+    part = g->maxdet;
+    if (g->desc.precision == MR_F32)
+      MR_LAUNCH(g, MRK_MISC, k_umax_leaf<float><<<n, 256, 0, g->stream>>>(
+                                 nb, (const float *)vel[0], (const float *)vel[1], (const float *)vel[2], part));
+    else
+      MR_LAUNCH(g, MRK_MISC, k_umax_leaf<double><<<n, 256, 0, g->stream>>>(
+                                 nb, (const double *)vel[0], (const double *)vel[1], (const double *)vel[2], part));
+  }
+  const double us = uc ? fabs(uc[0]) + fabs(uc[1]) + fabs(uc[2]) : 0.0;
+  MR_LAUNCH(g, MRK_MISC, k_dt_reduce<<<1, 256, 0, g->stream>>>(part, t.lev, n, us, cfl, t.tree_len, nb,
+                                                              g->dscratch + 1));
+  if (check_cuda(cudaGetLastError(), "k_dt")) return MR_ERR_CUDA;
+  if (check_cuda(cudaMemcpyAsync(host_out, g->dscratch + 1, sizeof(double), cudaMemcpyDeviceToHost, g->stream),
+                 "dt copy"))
+    return MR_ERR_CUDA;
+  return check_cuda(cudaStreamSynchronize(g->stream), "dt sync") ? MR_ERR_CUDA : MR_OK;
+}
+
 }  // namespace mr

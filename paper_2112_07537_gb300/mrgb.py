@@ -31,7 +31,8 @@ EXPORTS = ["mr_last_error", "mr_workspace_size", "mr_grid_create", "mr_grid_dest
            "mr_ghost_fill", "mr_ghost_fill64", "mr_sync", "mr_rhs_advect", "mr_rk_stage",
            "mr_step", "mr_criterion", "mr_adapt", "mr_adapt_iter", "mr_mass", "mr_query",
            "mr_field_ptr", "mr_profile", "mr_profile_read", "mr_launch_count", "mr_profile_bytes", "mr_set_diffusion", "mr_step_vel_scaled",
-           "mr_ghost_fill_static", "mr_rhs_advect_vel", "mr_step_vel", "mr_velocity_invalidate"]
+           "mr_ghost_fill_static", "mr_rhs_advect_vel", "mr_step_vel", "mr_velocity_invalidate",
+           "mr_device_peaks", "mr_dt", "mr_use_graphs", "mr_graph_replays", "mr_set_adapt_limits"]
 
 
 class MRError(RuntimeError):
@@ -96,8 +97,24 @@ def load(path: str = LIB_PATH):
         L.mr_set_diffusion.argtypes = [vp, C.c_double, C.c_int]
         L.mr_step_vel_scaled.argtypes = [vp, C.c_int, C.c_double, ip, C.c_int, dp]
         L.mr_launch_count.argtypes = [vp, C.POINTER(C.c_longlong)]
+        L.mr_device_peaks.argtypes = [dp]
+        L.mr_dt.argtypes = [vp, C.c_double, dp, ip, dp]
+        L.mr_use_graphs.argtypes = [vp, C.c_int]
+        L.mr_graph_replays.argtypes = [vp, C.POINTER(C.c_longlong)]
+        L.mr_set_adapt_limits.argtypes = [vp, C.c_int, C.c_int]
         _lib = L
     return _lib
+
+
+PEAK_NAMES = ("fp32_fma_tflops", "fp64_fma_tflops", "fp32_fast_div_gps", "fp32_div_gps",
+              "fp64_div_gps")
+
+
+def device_peaks():
+    """Measured compute throughput of the current device (mr_device_peaks)."""
+    out = (C.c_double * len(PEAK_NAMES))()
+    _chk(load().mr_device_peaks(out))
+    return dict(zip(PEAK_NAMES, list(out)))
 
 
 def _chk(code):
@@ -304,6 +321,26 @@ class Grid:
         n = C.c_longlong()
         _chk(load().mr_launch_count(self.h, C.byref(n)))
         return n.value
+
+    def dt(self, cfl, u=None, vel_fids=None):
+        """CFL time step from the constant velocity u or the fields vel_fids."""
+        out = C.c_double()
+        uu = _u3(u) if u is not None else None
+        vv = (C.c_int32 * 3)(*vel_fids) if vel_fids is not None else None
+        _chk(load().mr_dt(self.h, float(cfl), uu, vv, C.byref(out)))
+        return out.value
+
+    def use_graphs(self, enable=True):
+        """Capture each RK step into a CUDA graph and replay it while unchanged."""
+        _chk(load().mr_use_graphs(self.h, int(enable)))
+
+    def graph_replays(self):
+        n = C.c_longlong()
+        _chk(load().mr_graph_replays(self.h, C.byref(n)))
+        return n.value
+
+    def set_adapt_limits(self, max_iter=64, max_sweeps=256):
+        _chk(load().mr_set_adapt_limits(self.h, int(max_iter), int(max_sweeps)))
 
     def mass(self, fid):
         m = C.c_double()
