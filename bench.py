@@ -47,7 +47,9 @@ UNIT = "PSU/s"
 WORKLOADS = {"fixed-large": (0.35, 0.25, 0.17, 0.11, 0.06),   # 42 400 leaves, 586 M points
              "fixed-medium": (0.35, 0.25, 0.17),              # 11 768 leaves, 163 M points
              "fixed-small": (0.3, 0.2)}                       # 3 424 leaves, 47 M points
-GAUSS = dict(seed=5, n=48, smin=0.0015, smax=0.006)  # large single grid scalar
+# large single grid scalar: ~570 leaves per Gaussian, so 70 give the ~40 000
+# leaves (~550 M points) of the large configuration
+GAUSS = dict(seed=5, n=70, smin=0.0015, smax=0.006)
 # the same adaptive path on a small grid (for profiler captures of a few GB)
 GAUSS_SMALL = dict(seed=5, n=3, smin=0.0015, smax=0.006)
 EPS_R, EPS_C, CFL, ADAPT_EVERY = 1e-5, 1e-7, 0.5, 2
@@ -59,13 +61,20 @@ def workload_tree(name="fixed-large"):
 
 
 def gauss_params(seed, n, smin, smax):
-    """n seeded Gaussians: centres U[0.15, 0.85]^3, sigma U[smin, smax], amp 1."""
+    """n seeded Gaussians: centres U[0.15, 0.85]^3, sigma U[smin, smax], amp 1,
+    as MR_INIT_GAUSSIAN_SUM parameter lists of at most 51 Gaussians each."""
     rng = np.random.default_rng(seed)
-    p = [n]
+    rows = []
     for _ in range(n):
         c = rng.uniform(0.15, 0.85, 3)
-        p += [*c, rng.uniform(smin, smax), 1.0]
-    return p
+        rows.append([*c, rng.uniform(smin, smax), 1.0])
+    return [[len(ch)] + [x for r in ch for x in r] for ch in (rows[i:i + 51] for i in range(0, n, 51))]
+
+
+def set_gaussians(mrgb, g, fid, chunks):
+    """The field = the sum of the Gaussians of every chunk."""
+    for k, p in enumerate(chunks):
+        g.field_set(fid, mrgb.INIT_GAUSSIAN_SUM if k == 0 else mrgb.INIT_GAUSSIAN_SUM_ADD, p)
 
 
 TG = (1.0, 0.3)  # Taylor-Green scale and phase (seeded constants of the velocity field)
@@ -80,10 +89,10 @@ def init_large(mrgb, stream, prec, cap, gauss=GAUSS):
                   capacity=cap, stream=stream, velocity=True)
     p = gauss_params(**gauss)
     for _ in range(12):
-        g.field_set(0, mrgb.INIT_GAUSSIAN_SUM, p)
+        set_gaussians(mrgb, g, 0, p)
         if g.adapt_iter(0, EPS_R, EPS_C, flags=mrgb.ADAPT_REFINE) == 0:
             break
-    g.field_set(0, mrgb.INIT_GAUSSIAN_SUM, p)
+    set_gaussians(mrgb, g, 0, p)
     for d in range(3):
         g.field_set(1 + d, mrgb.INIT_TAYLOR_GREEN, [d, TG[0], TG[1]])
     g.adapt(0, EPS_R, EPS_C)
@@ -362,6 +371,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain form of the workload")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) measurement")
+    ap.add_argument("--no-autotune", action="store_true", help="default launch shapes (no autotuner)")
     ap.add_argument("--workload", default="large",
                     choices=["large", "adaptive-small", "deformation"] + sorted(WORKLOADS))
     ap.add_argument("--wavelet", default="4.2", choices=["2.2", "4.2", "6.2", "4.0", "6.0"],
@@ -393,6 +403,8 @@ def main():
     deform = args.workload == "deformation"
     stream = torch.cuda.Stream()
     g, lmax, umax = make_grid(args, mrgb, stream, prec, args.capacity)
+    if not args.no_autotune:
+        g.autotune(True)  # launch shapes tuned on this grid during the warm-up steps
     step = Stepper(args, mrgb, g, lmax, umax)
     r = timed(args, g, step, stream, W, dist)
     ms, psu_count, prof, stats0, stats1 = r["ms"], r["psu"], r["prof"], r["stats0"], r["stats1"]
@@ -421,6 +433,26 @@ def main():
         e2e = {"value": e2e_psu / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d // ke,
                "d2h_bytes_per_step": d2h // ke}
         del host
+
+    # RK steps alone (no adaptation), stream-ordered and replayed as one CUDA
+    # graph per step, on the same grid and velocity
+    graph_cmp = None
+    if adaptive or deform:
+        import torch as _t
+        ev = _t.cuda.Event(enable_timing=True), _t.cuda.Event(enable_timing=True)
+        res = {}
+        for mode in (0, 1):
+            g.use_graphs(bool(mode))
+            g.step_vel(0, step.dt, (1, 2, 3), step.scheme)  # capture (graph mode) / warm
+            ev[0].record(stream)
+            for _ in range(4):
+                g.step_vel(0, step.dt, (1, 2, 3), step.scheme)
+            ev[1].record(stream)
+            ev[1].synchronize()
+            res[mode] = ev[0].elapsed_time(ev[1]) / 4
+        graph_cmp = {"ms_per_rk_step_stream": res[0], "ms_per_rk_step_graph": res[1],
+                     "graph_replays": g.graph_replays(), "leaves": g.nleaf}
+        g.use_graphs(False)
 
     psu = world * psu_count / (ms / 1e3)
     hbm, src = peaks()
@@ -492,6 +524,8 @@ def main():
         "e2e": e2e,
         "clocks": r["clocks"],
         "compute_peaks": cpk,
+        "rk_step_graph": graph_cmp,
+        "autotune": mrgb.autotune_table(),
     }
     if "rhs_stage" in prof:
         t_rhs, n_rhs = prof["rhs_stage"]
@@ -514,10 +548,16 @@ def main():
         torch.cuda.empty_cache()
         g64, lmax64, umax64 = make_grid(args, mrgb, stream, mrgb.F64, args.capacity)
         step64 = Stepper(args, mrgb, g64, lmax64, umax64)
-        r64 = timed(args, g64, step64, stream, W, None)
+        # the FP64 form is ~4x slower: at most 8 timed steps (an even count
+        # keeps the one-adaptation-per-two-steps mix of the FP32 run)
+        import copy
+        a64 = copy.copy(args)
+        a64.steps = max(2, min(args.steps, 8) // 2 * 2)
+        r64 = timed(a64, g64, step64, stream, 3, None)
         v64 = world * r64["psu"] / (r64["ms"] / 1e3)
-        line["fp64_plain"] = {"value": v64, "unit": UNIT, "ms_per_step": r64["ms"] / args.steps,
-                              "leaves": [r64["stats0"].nleaf, r64["stats1"].nleaf], "steps": args.steps,
+        line["fp64_plain"] = {"value": v64, "unit": UNIT, "ms_per_step": r64["ms"] / a64.steps,
+                              "leaves": [r64["stats0"].nleaf, r64["stats1"].nleaf], "steps": a64.steps,
+                              "warmup": 3,
                               "gpu_launches": r64["launches"], "clocks": r64["clocks"],
                               "tolerance": "FP64 path: 1e-12 of the field maximum vs the oracle",
                               "kernels": {k: {"ms_total": v[0], "launches": v[1]} for k, v in r64["prof"].items()}}

@@ -71,6 +71,9 @@ extern "C" {
  * (2 sin^2(pi x) sin(2 pi y) sin(2 pi z), -sin(2 pi x) sin^2(pi y) sin(2 pi z),
  *  -sin(2 pi x) sin(2 pi y) sin^2(pi z)) times scale                     */
 #define MR_INIT_DEFORMATION 5
+/* params as MR_INIT_GAUSSIAN_SUM; the sum is added to the field's current
+ * values (sums of more than 51 Gaussians in several calls)                */
+#define MR_INIT_GAUSSIAN_SUM_ADD 6
 
 /* adaptation flags */
 #define MR_ADAPT_REFINE 1
@@ -249,6 +252,26 @@ int mr_dt(mr_grid *grid, double cfl, const double *u_const, const int *vel_fid, 
 int mr_use_graphs(mr_grid *grid, int enable);
 int mr_graph_replays(mr_grid *grid, long long *n);
 
+/* Launch-shape autotuner.  With enable = 1, the first launch of each tunable
+ * kernel configuration (kernel, wavelet, nb, precision, shell, mode) on this
+ * grid times every candidate CTA size on the grid's own data -- the ghost
+ * gather, pre-pass and merge, the criterion, the interpolation, and the fused
+ * stage kernel (one grid line per thread or two), each only on launches that
+ * overwrite their outputs from unchanged inputs, so repeating them changes
+ * nothing -- and keeps the fastest in a table shared by every grid of the
+ * process (later launches of that configuration use it whether or not their
+ * grid tunes).  Results do not depend on the choice: every output point is
+ * computed with the same arithmetic whatever the CTA size.  No tuning happens
+ * while a step is being captured into a CUDA graph.  The paper has no
+ * counterpart (its code runs one block after the other per MPI rank).
+ * mr_autotune_table writes one line per tuned configuration (chosen size
+ * and the time of every candidate) into buf (NUL-terminated; MR_ERR_NOMEM
+ * if truncated); *nentries receives the number of entries.
+ * mr_autotune_clear empties the table.                                   */
+int mr_autotune(mr_grid *grid, int enable);
+int mr_autotune_table(char *buf, size_t len, int *nentries);
+int mr_autotune_clear(void);
+
 /* Bounds of the adaptation loops: mr_adapt runs at most max_iter iterations
  * (default 64) and each iteration at most max_sweeps policy sweeps (default
  * 256); beyond either the call returns MR_ERR_TIMEOUT with the leaves of the
@@ -279,6 +302,16 @@ int mr_adapt(mr_grid *grid, int crit_fid, double eps_refine, double eps_coarsen,
 /* One iteration of mr_adapt; *n_changed receives the leaves changed. */
 int mr_adapt_iter(mr_grid *grid, int crit_fid, double eps_refine, double eps_coarsen,
                   int flags, int *n_changed);
+
+/* Block norms (max |detail| per leaf, Sec. 2.2.5) that the last adaptation
+ * iteration took its decisions with, in the slot order of the tree that
+ * iteration started from (*n leaves; after an mr_adapt that converged, the
+ * current tree).  Within one mr_adapt call the second and later iterations
+ * recompute the norm only for leaves within two neighbour rings of the
+ * previous iteration's changes and carry the others; these are the values
+ * that decided.  dst: nleaf doubles (host or device), or NULL to query *n.
+ * Synchronises.                                                           */
+int mr_last_block_norms(mr_grid *grid, double *dst, int cap, int *n);
 
 /* Sum over leaves of h^3 * sum(phi) in FP64 (eq 2.18 with p = 0), written
  * to *mass (host).  Synchronises.                                          */

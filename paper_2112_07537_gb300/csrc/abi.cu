@@ -90,7 +90,7 @@ int adapt_shell(int N, int Nt) {
 }
 
 struct Layout {
-  size_t off[26];
+  size_t off[29];
   size_t total;
 };
 
@@ -120,7 +120,7 @@ static int layout(const mr_grid_desc *d, Layout *L, int *shell_rk, int *shell_ad
   *M = d->lmax;
   *map_cells = ((size_t)d->ntree[0] << d->lmax) * ((size_t)d->ntree[1] << d->lmax) *
                ((size_t)d->ntree[2] << d->lmax);
-  size_t sz[26] = {
+  size_t sz[29] = {
       cap * 4, cap * 4,                          // lev[2]
       cap * 12, cap * 12,                        // anc[2]
       cap * 8, cap * 8,                          // keys[2]
@@ -141,9 +141,12 @@ static int layout(const mr_grid_desc *d, Layout *L, int *shell_rk, int *shell_ad
       cap * 8,                                   // cmask + new-band masks
       cap * 4,                                   // hasD
       velo ? 3 * cap * wv * wv * wv * es : 0,    // velocity cache (shell 3)
-      cap * 4};                                  // pneed: leaves left to the full pre-pass
+      cap * 4,                                   // pneed: leaves left to the full pre-pass
+      fixed ? 0 : cap * 8,                       // mdcarry
+      fixed ? 0 : cap * 8,                       // mdlast
+      fixed ? 0 : 2 * cap * 4};                  // cneed
   size_t o = 0;
-  for (int i = 0; i < 26; ++i) {
+  for (int i = 0; i < 29; ++i) {
     L->off[i] = o;
     o += al(sz[i]);
   }
@@ -269,6 +272,9 @@ int mr_grid_create(const mr_grid_desc *desc, void *workspace, size_t workspace_b
   g->cmask = (int *)(w + L.off[22]);
   g->hasD = (int *)(w + L.off[23]);
   g->pneed = (int *)(w + L.off[25]);
+  g->mdcarry = (double *)(w + L.off[26]);
+  g->mdlast = (double *)(w + L.off[27]);
+  g->cneed = (int *)(w + L.off[28]);
   g->vpad = (desc->flags & MR_GRID_VELOCITY) ? (void *)(w + L.off[24]) : nullptr;
   g->tree_version = 0;
   g->vel_version = -1;
@@ -309,6 +315,7 @@ int mr_grid_destroy(mr_grid *g) {
   if (!g) return MR_ERR_INVALID;
   cudaStreamSynchronize(g->stream);
   if (g->gexec) cudaGraphExecDestroy(g->gexec);
+  if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
   if (g->ev_ready)
     for (int i = 0; i < 4096; ++i) cudaEventDestroy(g->ev[0][i]), cudaEventDestroy(g->ev[1][i]);
   delete g;
@@ -421,10 +428,12 @@ int mr_field_ptr(mr_grid *g, int fid, void **ptr) {
 }
 
 int mr_field_set(mr_grid *g, int fid, int kind, const double *params, int np) {
-  if (!fid_ok(g, fid) || !params || np < 1 || np > 256 || kind < 0 || kind > 5) return MR_ERR_INVALID;
-  static const int need[6] = {5, 5, 3, 1, 6, 2};  // parameters each kind reads
+  if (!fid_ok(g, fid) || !params || np < 1 || np > 256 || kind < 0 || kind > 6) return MR_ERR_INVALID;
+  static const int need[7] = {5, 5, 3, 1, 6, 2, 1};  // parameters each kind reads
   if (np < need[kind]) return MR_ERR_INVALID;
-  if (kind == MR_INIT_GAUSSIAN_SUM && (params[0] < 0 || 1 + 5 * (int)params[0] > np)) return MR_ERR_INVALID;
+  if ((kind == MR_INIT_GAUSSIAN_SUM || kind == MR_INIT_GAUSSIAN_SUM_ADD) &&
+      (params[0] < 0 || 1 + 5 * (int)params[0] > np))
+    return MR_ERR_INVALID;
   return launch_field_set(g, field_ptr(g, fid), kind, params, np);
 }
 
@@ -565,14 +574,23 @@ static int run_step(mr_grid *g, const GraphKey &key, F body) {
     cudaGraphExecDestroy(g->gexec);
     g->gexec = nullptr;
   }
-  if (check_cuda(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeRelaxed), "cudaStreamBeginCapture"))
+  // capture on a private stream (the legacy stream cannot be captured;
+  // capturing executes nothing, so no ordering is needed), replay on the
+  // grid's stream
+  if (!g->cap_stream &&
+      check_cuda(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking), "capture stream"))
+    return MR_ERR_CUDA;
+  if (check_cuda(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeRelaxed), "cudaStreamBeginCapture"))
     return MR_ERR_CUDA;
   memset(g->cap_counts, 0, sizeof g->cap_counts);
+  cudaStream_t own = g->stream;
+  g->stream = g->cap_stream;
   g->capturing = 1;
   const int e = body();
   g->capturing = 0;
+  g->stream = own;
   cudaGraph_t graph = nullptr;
-  const cudaError_t ce = cudaStreamEndCapture(g->stream, &graph);
+  const cudaError_t ce = cudaStreamEndCapture(g->cap_stream, &graph);
   if (e) {
     if (graph) cudaGraphDestroy(graph);
     return e;
@@ -727,7 +745,7 @@ int mr_adapt_iter(mr_grid *g, int crit, double er, double ec, int flags, int *nc
   if (!fid_ok(g, crit)) return MR_ERR_INVALID;
   if (!adapt_ok(g)) return MR_ERR_UNSUPPORTED;
   int n = 0;
-  int e = adapt_iteration(g, crit, er, ec, flags, &n);
+  int e = adapt_iteration(g, crit, er, ec, flags, &n, false);
   if (nch) *nch = n;
   return e;
 }
@@ -740,7 +758,9 @@ int mr_adapt(mr_grid *g, int crit, double er, double ec, int flags, int *nch) {
     return MR_ERR_CUDA;
   for (int it = 0; it < g->max_adapt_iter; ++it) {
     int n = 0;
-    int e = adapt_iteration(g, crit, er, ec, flags, &n);
+    // the fields change only through this loop from the second iteration on:
+    // block norms far from the previous iteration's changes are carried
+    int e = adapt_iteration(g, crit, er, ec, flags, &n, it > 0);
     if (e) return e;
     total += n;
     if (n == 0) {
@@ -751,6 +771,19 @@ int mr_adapt(mr_grid *g, int crit, double er, double ec, int flags, int *nch) {
   if (nch) *nch = total;
   set_error("adaptation did not converge within the iteration limit");
   return MR_ERR_TIMEOUT;
+}
+
+int mr_last_block_norms(mr_grid *g, double *dst, int cap, int *n) {
+  if (!g || !n) return MR_ERR_INVALID;
+  if (!adapt_ok(g)) return MR_ERR_UNSUPPORTED;
+  *n = g->nleaf_last;
+  if (!dst) return MR_OK;
+  if (cap < g->nleaf_last) return MR_ERR_NOMEM;
+  if (check_cuda(cudaMemcpyAsync(dst, g->mdlast, sizeof(double) * (size_t)g->nleaf_last, cudaMemcpyDefault,
+                                 g->stream),
+                 "block norms"))
+    return MR_ERR_CUDA;
+  return check_cuda(cudaStreamSynchronize(g->stream), "block norms sync") ? MR_ERR_CUDA : MR_OK;
 }
 
 int mr_mass(mr_grid *g, int fid, double *mass) {

@@ -125,8 +125,13 @@ __device__ __forceinline__ void detail_planes(const double *__restrict__ Pb, int
 // that drives refinement and coarsening).
 template <int N, int NT>
 __global__ void __launch_bounds__(1024) k_criterion(Tree t, const double *__restrict__ P, int Gi,
-                                                   double *__restrict__ maxdet) {
+                                                   double *__restrict__ maxdet, const int *__restrict__ need,
+                                                   const double *__restrict__ carry) {
   const int b = blockIdx.x, nb = t.nb, Wd = nb + 2 * Gi;
+  if (need && !need[b]) {  // norm carried from the previous iteration
+    if (threadIdx.x == 0) maxdet[b] = carry[b];
+    return;
+  }
   extern __shared__ double sm[];
   unsigned long long mx = 0;  // max |gamma| as an integer key (integer pipe)
   detail_planes<N, NT>(P + (size_t)b * Wd * Wd * Wd, nb, Gi, sm,
@@ -151,7 +156,8 @@ static size_t crit_smem(int nb) {
 }
 
 template <int N, int NT>
-static int criterion_impl(mr_grid *g, const double *P, int Gi, double *maxdet) {
+static int criterion_impl(mr_grid *g, const double *P, int Gi, double *maxdet, const int *need,
+                          const double *carry) {
   const size_t sm = crit_smem<N, NT>(g->desc.nb);
   if (sm > 227 * 1024) return MR_ERR_UNSUPPORTED;
   if (check_cuda(cudaFuncSetAttribute(k_criterion<N, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -159,14 +165,18 @@ static int criterion_impl(mr_grid *g, const double *P, int Gi, double *maxdet) {
                  "criterion smem"))
     return MR_ERR_CUDA;
   Tree t = tree_view(g);
-  MR_LAUNCH(g, MRK_CRITERION, k_criterion<N, NT><<<g->nleaf, 1024, sm, g->stream>>>(t, P, Gi, maxdet));
+  static const int cc[2] = {1024, 512};
+  const int th = tune_threads(g, TuneKey{2, N, NT, g->desc.nb, 8, Gi, 0}, cc, 2, [&](int thr) {
+    k_criterion<N, NT><<<g->nleaf, thr, sm, g->stream>>>(t, P, Gi, maxdet, need, carry);
+  });
+  MR_LAUNCH(g, MRK_CRITERION, k_criterion<N, NT><<<g->nleaf, th, sm, g->stream>>>(t, P, Gi, maxdet, need, carry));
   return check_cuda(cudaGetLastError(), "k_criterion") ? MR_ERR_CUDA : MR_OK;
 }
 
-int launch_criterion(mr_grid *g, const double *P, int Gi, double *maxdet) {
+int launch_criterion(mr_grid *g, const double *P, int Gi, double *maxdet, const int *need, const double *carry) {
   const int N = g->desc.wav_N, Nt = g->desc.wav_Nt;
 #define MR_CCASE(n_, nt_) \
-  if (N == n_ && Nt == nt_) return criterion_impl<n_, nt_>(g, P, Gi, maxdet);
+  if (N == n_ && Nt == nt_) return criterion_impl<n_, nt_>(g, P, Gi, maxdet, need, carry);
   MR_CCASE(2, 0) MR_CCASE(2, 2) MR_CCASE(4, 0) MR_CCASE(4, 2) MR_CCASE(6, 0) MR_CCASE(6, 2)
 #undef MR_CCASE
   return MR_ERR_UNSUPPORTED;
@@ -322,7 +332,7 @@ __global__ void k_emit(int n, int M, const int8_t *st, const int *pos, const int
 // New leaf values: copy, zero-detail refinement of the parent's padded block
 // (J^s / K^s), or tensor H^a coarsening of the 8 children's padded blocks.
 template <typename TO, int N, int NT>
-__global__ void __launch_bounds__(256) k_interp(Tree to, const int *__restrict__ src,
+__global__ void __launch_bounds__(512) k_interp(Tree to, const int *__restrict__ src,
                                                 const double *__restrict__ P, int Gi,
                                                 const TO *__restrict__ fold, TO *__restrict__ fnew) {
   using W = Wav<N, NT>;
@@ -598,14 +608,55 @@ __global__ void k_need2(Tree t, const int8_t *st, const int *nb1, int *need) {
 
 // finer neighbours of needed leaves push the fine-to-coarse ghost values the
 // needed leaves read; leaves next to a coarser leaf substitute their band
-// (the adaptation's ghost fill overwrites every field)
-__global__ void k_need3(Tree t, const int *need, int *need2) {
+// (the adaptation's ghost fill overwrites every field) -- all of them, or
+// with `dirty` (later iterations of one adaptation) those whose band inputs
+// may have changed since their last substitution (marked in dirty)
+__global__ void k_need3(Tree t, const int *need, const int *__restrict__ dirty, int *need2) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= t.nleaf) return;
   const int L = __ldg(t.lev + b);
   int any = need[b];
-  if (!any) for_each_nbr(t, b, [&](int o) { any |= (__ldg(t.lev + o) < L); });
+  const bool sub = !dirty || dirty[b];
+  if (!any) for_each_nbr(t, b, [&](int o) { any |= __ldg(t.lev + o) < L && (sub || need[o]); });
   need2[b] = any;
+}
+
+// ------------------------------------------------- incremental criterion
+// Block norms of unchanged leaves carried to their new slots (new leaves get
+// theirs recomputed).
+__global__ void k_carry(int nn, const int *__restrict__ src, const double *__restrict__ md_old,
+                        double *__restrict__ md_new) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nn) return;
+  md_new[q] = src[2 * q] == KIND_COPY ? md_old[src[2 * q + 1]] : 0.0;
+}
+
+// Leaves of the new tree whose values the iteration changed: new leaves and
+// unchanged leaves corrected by the update step.
+__global__ void k_dirty(int nn, const int *__restrict__ src, const int *__restrict__ hasD, int *out) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nn) return;
+  out[q] = src[2 * q] != KIND_COPY || hasD[q];
+}
+
+// one ring of neighbours (face, edge, corner) around the marked leaves
+__global__ void k_ring(Tree t, const int *__restrict__ in, int *__restrict__ out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= t.nleaf) return;
+  int any = in[b];
+  if (!any) for_each_nbr(t, b, [&](int o) { any |= in[o]; });
+  out[b] = any;
+}
+
+// the marked leaves and every leaf that pushes fine-to-coarse values into
+// one of them (a finer neighbour of a marked leaf)
+__global__ void k_pushers(Tree t, const int *__restrict__ in, int *__restrict__ out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= t.nleaf) return;
+  const int L = __ldg(t.lev + b);
+  int any = in[b];
+  if (!any) for_each_nbr(t, b, [&](int o) { any |= in[o] && __ldg(t.lev + o) < L; });
+  out[b] = any;
 }
 
 // ------------------------------------------------------------- driver
@@ -623,7 +674,12 @@ template <typename TO, int N, int NT>
 static int interp_update(mr_grid *g, const Tree &to, const Tree &tn, const double *P, int Gi, int fid,
                          int *nmask, int *hasD) {
   const int *src = g->newsrc;
-  MR_LAUNCH(g, MRK_INTERP, k_interp<TO, N, NT><<<tn.nleaf, 256, 0, g->stream>>>(
+  static const int ci[3] = {256, 128, 512};
+  const int thi = tune_threads(g, TuneKey{4, N, NT, g->desc.nb, sizeof(TO) == 4 ? 5 : 8, Gi, 0}, ci, 3, [&](int th) {
+    k_interp<TO, N, NT><<<tn.nleaf, th, 0, g->stream>>>(to, src, P, Gi, (const TO *)field_ptr(g, fid),
+                                                        (TO *)next_field_ptr(g, fid));
+  });
+  MR_LAUNCH(g, MRK_INTERP, k_interp<TO, N, NT><<<tn.nleaf, thi, 0, g->stream>>>(
                                to, src, P, Gi, (const TO *)field_ptr(g, fid), (TO *)next_field_ptr(g, fid)));
   const size_t smg = crit_smem<N, NT>(g->desc.nb), sma = apply_smem<N, NT>(g->desc.nb);
   if (smg > 227 * 1024 || sma > 227 * 1024) return MR_ERR_UNSUPPORTED;
@@ -657,18 +713,33 @@ static int read_ints(mr_grid *g, const int *dev, int *host, int n) {
   return check_cuda(cudaStreamSynchronize(g->stream), "readback sync") ? MR_ERR_CUDA : MR_OK;
 }
 
-int adapt_iteration(mr_grid *g, int crit, double er, double ec, int flags, int *nch) {
+int adapt_iteration(mr_grid *g, int crit, double er, double ec, int flags, int *nch, bool incremental) {
   *nch = 0;
-  const int n = g->nleaf, G = adapt_shell(g->desc.wav_N, g->desc.wav_Nt);
+  const int n = g->nleaf, G = adapt_shell(g->desc.wav_N, g->desc.wav_Nt), cap = g->desc.capacity;
   cudaStream_t st = g->stream;
   void *Pv;
   int Gi;
+  // Incremental criterion (second and later iterations of one mr_adapt): a
+  // leaf's block norm depends on the field within two neighbour rings (its
+  // padded block reads its neighbours and the fine-to-coarse values of its
+  // finer neighbours, which read theirs), so only leaves within two rings of
+  // what the previous iteration changed are filled and evaluated; the others
+  // keep the norm carried from that iteration -- the same bits, since their
+  // inputs are unchanged and a repeated substitution is bitwise idempotent.
+  const bool incr = incremental && g->incr_ready;
+  g->incr_ready = 0;
+  const int *cneed = incr ? g->cneed : nullptr, *cfill = incr ? g->cneed + cap : nullptr;
   // 1-2: ghosts of the criterion field, block criterion
-  int e = launch_ghost(g, field_ptr(g, crit), field_ptr(g, crit), G, true, &Pv, &Gi);
+  int e = launch_ghost(g, field_ptr(g, crit), field_ptr(g, crit), G, true, &Pv, &Gi, nullptr, cfill);
   if (e) return e;
   const double *P = (const double *)Pv;
-  e = launch_criterion(g, P, Gi, g->maxdet);
+  e = launch_criterion(g, P, Gi, g->maxdet, cneed, g->mdcarry);
   if (e) return e;
+  // the norms this iteration decides with (mr_last_block_norms)
+  if (check_cuda(cudaMemcpyAsync(g->mdlast, g->maxdet, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, st),
+                 "block norms copy"))
+    return MR_ERR_CUDA;
+  g->nleaf_last = n;
   // 3-4: status and policy
   Tree t = tree_view(g);
   const int tb = 128, nblk = (n + tb - 1) / tb;
@@ -707,9 +778,10 @@ int adapt_iteration(mr_grid *g, int crit, double er, double ec, int flags, int *
     // Alg. SM3 step 1 ghost-fills every field in every iteration; with no
     // leaf changing, what remains of it for the other fields is the
     // substitution next to coarser leaves, which overwrites their values
+    // (later iterations: only where its inputs may have changed)
     for (int fid = 0; fid < g->desc.nfields; ++fid) {
       if (fid == crit) continue;
-      e = launch_substitute(g, field_ptr(g, fid));
+      e = launch_substitute(g, field_ptr(g, fid), cneed);
       if (e) return e;
     }
     return MR_OK;
@@ -733,18 +805,21 @@ int adapt_iteration(mr_grid *g, int crit, double er, double ec, int flags, int *
   }
   int *nmask = g->cmask + g->desc.capacity;  // second half of the mask buffer
   int *hasD = g->hasD;
+  // block norms of unchanged leaves carried to the new slots (before maxdet
+  // becomes scratch below)
+  MR_LAUNCH(g, MRK_MISC, k_carry<<<(nn + tb - 1) / tb, tb, 0, st>>>(nn, g->newsrc, g->maxdet, g->mdcarry));
   // leaves whose ghosts the other fields need (statuses are final; maxdet and
   // scan are free from here on)
   int *nb1 = reinterpret_cast<int *>(g->maxdet), *need2 = nb1 + g->desc.capacity, *need = g->scan;
   MR_LAUNCH(g, MRK_MISC, k_need1<<<nblk, tb, 0, st>>>(t, g->status, nb1));
   MR_LAUNCH(g, MRK_MISC, k_need2<<<nblk, tb, 0, st>>>(t, g->status, nb1, need));
-  MR_LAUNCH(g, MRK_MISC, k_need3<<<nblk, tb, 0, st>>>(t, need, need2));
+  MR_LAUNCH(g, MRK_MISC, k_need3<<<nblk, tb, 0, st>>>(t, need, cneed, need2));
   MR_LAUNCH(g, MRK_UPDATE, k_newmask<<<(nn + tb - 1) / tb, tb, 0, st>>>(tn, g->newsrc, nmask));
   // 6-9: every field: ghosts (criterion field first: P is current), interpolate, update
   const bool f32 = g->desc.precision == MR_F32;
   for (int pass = 0; pass < g->desc.nfields; ++pass) {
     const int fid = pass == 0 ? crit : (pass <= crit ? pass - 1 : pass);
-    if (pass > 0) {
+    if (pass > 0 || incr) {  // incremental: the criterion fill covered fewer leaves
       e = launch_ghost(g, field_ptr(g, fid), field_ptr(g, fid), G, true, &Pv, &Gi, nullptr, need2);
       if (e) return e;
       P = (const double *)Pv;
@@ -752,6 +827,16 @@ int adapt_iteration(mr_grid *g, int crit, double er, double ec, int flags, int *
     e = f32 ? interp_dispatch<float>(g, t, tn, P, Gi, fid, nmask, hasD)
             : interp_dispatch<double>(g, t, tn, P, Gi, fid, nmask, hasD);
     if (e) return e;
+  }
+  // leaves of the new tree whose block norm the next iteration recomputes:
+  // two rings around the changed leaves, and the fill set that needs (their
+  // finer neighbours push fine-to-coarse values into them)
+  {
+    const int nblk2 = (nn + tb - 1) / tb;
+    MR_LAUNCH(g, MRK_MISC, k_dirty<<<nblk2, tb, 0, st>>>(nn, g->newsrc, hasD, nb1));
+    MR_LAUNCH(g, MRK_MISC, k_ring<<<nblk2, tb, 0, st>>>(tn, nb1, need2));
+    MR_LAUNCH(g, MRK_MISC, k_ring<<<nblk2, tb, 0, st>>>(tn, need2, g->cneed));
+    MR_LAUNCH(g, MRK_MISC, k_pushers<<<nblk2, tb, 0, st>>>(tn, g->cneed, g->cneed + cap));
   }
   // swap to the new tree and pool
   g->cur = nx;
@@ -763,7 +848,9 @@ int adapt_iteration(mr_grid *g, int crit, double er, double ec, int flags, int *
   g->refined = g->refined2;
   g->refined2 = tmp;
   *nch = changed;
-  return check_cuda(cudaGetLastError(), "adapt") ? MR_ERR_CUDA : MR_OK;
+  if (check_cuda(cudaGetLastError(), "adapt")) return MR_ERR_CUDA;
+  g->incr_ready = 1;
+  return MR_OK;
 }
 
 }  // namespace mr

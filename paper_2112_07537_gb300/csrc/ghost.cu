@@ -723,7 +723,7 @@ __global__ void __launch_bounds__(512, sizeof(TP) == 4 ? 2 : 1) k_prep(Tree t, c
 // NaN instead of a load.
 // ---------------------------------------------------------------------------
 template <typename TI, typename TP>
-__global__ void __launch_bounds__(256) k_fill_plain(Tree t, const TI *__restrict__ phi, TP *__restrict__ P,
+__global__ void __launch_bounds__(512) k_fill_plain(Tree t, const TI *__restrict__ phi, TP *__restrict__ P,
                                                     int Gi, const int *__restrict__ need,
                                                     int *__restrict__ pneed, int *__restrict__ cmask_out,
                                                     int *err) {
@@ -839,7 +839,7 @@ static size_t push_smem(int nb, int zc, size_t es) {
 // leaves hold them) and write the substituted interior back to the field of
 // leaves that have a coarser neighbour.
 template <typename TO, typename TP>
-__global__ void __launch_bounds__(256) k_merge(Tree t, TP *__restrict__ P, const TP *__restrict__ Q,
+__global__ void __launch_bounds__(512) k_merge(Tree t, TP *__restrict__ P, const TP *__restrict__ Q,
                                                int Gi, int G, const int *__restrict__ cmask,
                                                TO *__restrict__ phi_out, const int *__restrict__ need) {
   const int b = blockIdx.x;
@@ -951,8 +951,13 @@ static int ghost_impl(mr_grid *g, const TI *phi_in, TI *phi_out, int G, TP *P, T
   // full fills: leaves without a coarser neighbour are gathered by the plain
   // kernel; the pre-pass takes the others (pneed)
   const int *need_prep = need;
+  const int tp = sizeof(TP) == 4 ? 4 : sizeof(TI) == 4 ? 5 : 8;
   if (!only_coarse) {
-    MR_LAUNCH(g, MRK_PART2, k_fill_plain<TI, TP><<<n, 256, 0, g->stream>>>(t, phi_in, P, Gi, need, g->pneed,
+    static const int cf[3] = {256, 128, 512};
+    const int thr = tune_threads(g, TuneKey{0, N, NT, nb, tp, Gi, 0}, cf, 3, [&](int th) {
+      k_fill_plain<TI, TP><<<n, th, 0, g->stream>>>(t, phi_in, P, Gi, need, g->pneed, g->cmask, err);
+    });
+    MR_LAUNCH(g, MRK_PART2, k_fill_plain<TI, TP><<<n, thr, 0, g->stream>>>(t, phi_in, P, Gi, need, g->pneed,
                                                                           g->cmask, err));
     if (check_cuda(cudaGetLastError(), "k_fill_plain")) return MR_ERR_CUDA;
     const double wd = nb + 2.0 * G;  // the requested shell (not the internal one)
@@ -960,17 +965,26 @@ static int ghost_impl(mr_grid *g, const TI *phi_in, TI *phi_out, int G, TP *P, T
                 g->pneed);
     need_prep = g->pneed;
   }
-  MR_LAUNCH(g, MRK_PART1, k_prep<TI, TP, N, NT><<<n, 512, sm, g->stream>>>(t, phi_in, P, Q, Gi, G, only_coarse,
+  static const int cp[2] = {512, 256};
+  const int thp = tune_threads(g, TuneKey{1, N, NT, nb, tp, Gi, only_coarse}, cp, 2, [&](int th) {
+    k_prep<TI, TP, N, NT><<<n, th, sm, g->stream>>>(t, phi_in, P, Q, Gi, G, only_coarse, use_tile, (int)smT, zc,
+                                                    g->cmask, err, need_prep, only_coarse ? 0 : 1, (int)sm);
+  });
+  MR_LAUNCH(g, MRK_PART1, k_prep<TI, TP, N, NT><<<n, thp, sm, g->stream>>>(t, phi_in, P, Q, Gi, G, only_coarse,
                                                                            use_tile, (int)smT, zc, g->cmask, err,
                                                                            need_prep, only_coarse ? 0 : 1, (int)sm));
   if (check_cuda(cudaGetLastError(), "k_prep")) return MR_ERR_CUDA;
-  {
+  if (only_coarse != 2) {  // the substitution-only pass fills no shell
     const double wd = nb + 2.0 * G;
     count_units(g, MRK_PART1, only_coarse ? g->cmask : need_prep, n,
                 (wd * wd * wd - (double)nb * nb * nb) * (double)(sizeof(TI) + sizeof(TP)));
   }
   if (only_coarse) return MR_OK;
-  MR_LAUNCH(g, MRK_MERGE, k_merge<TI, TP><<<n, 256, 0, g->stream>>>(t, P, Q, Gi, G, g->cmask, phi_out, need));
+  static const int cm[3] = {256, 128, 512};
+  const int thm = tune_threads(g, TuneKey{5, N, NT, nb, tp, Gi, 0}, cm, 3, [&](int th) {
+    k_merge<TI, TP><<<n, th, 0, g->stream>>>(t, P, Q, Gi, G, g->cmask, phi_out, need);
+  });
+  MR_LAUNCH(g, MRK_MERGE, k_merge<TI, TP><<<n, thm, 0, g->stream>>>(t, P, Q, Gi, G, g->cmask, phi_out, need));
   if (check_cuda(cudaGetLastError(), "k_merge")) return MR_ERR_CUDA;
   return MR_OK;
 }
@@ -1020,9 +1034,9 @@ int launch_ghost(mr_grid *g, const void *phi_in, void *phi_out, int G, bool fp64
 // substituted band of leaves with a coarser neighbour -> field
 template <typename TO, typename TP>
 __global__ void __launch_bounds__(256) k_writeback(int nb, const TP *__restrict__ P, int Gi, const int *__restrict__ cmask,
-                                                   TO *__restrict__ phi) {
+                                                   TO *__restrict__ phi, const int *__restrict__ need = nullptr) {
   const int b = blockIdx.x;
-  if (!cmask[b]) return;
+  if ((need && !need[b]) || !cmask[b]) return;  // cmask is stale where need is 0
   const int Wd = nb + 2 * Gi;
   const size_t np = (size_t)Wd * Wd * Wd;
   for (int p = threadIdx.x; p < nb * nb * nb; p += blockDim.x) {
@@ -1041,25 +1055,26 @@ int launch_prep32(mr_grid *g, const void *phi, int *Gi) {
 }
 
 // Substitution alone (the first step of Alg. SM2) of every leaf next to a
-// coarser leaf: the pre-pass at the shell the substitution reads (the G^a
+// coarser leaf (with need: of those marked): the pre-pass at the shell the
+// substitution reads (the G^a
 // half-width) computes the padded block, substitutes the band in FP64 and
 // the substituted values are written back to the field -- the field values a
 // full ghost fill leaves, without the padded blocks of the other leaves.
-int launch_substitute(mr_grid *g, void *phi) {
+int launch_substitute(mr_grid *g, void *phi, const int *need) {
   const int N = g->desc.wav_N, Nt = g->desc.wav_Nt, nb = g->desc.nb;
   const int G = N - 1, gi = internal_shell(N, Nt, G, nb);
   if (gi > g->shell_ad || (g->desc.flags & MR_GRID_FIXED_TREE)) return MR_ERR_UNSUPPORTED;
   int e;
   if (g->desc.precision == MR_F32) {
-    e = ghost_dispatch<float, double>(g, (const float *)phi, nullptr, G, g->padP64, g->padQ64, gi, 2);
+    e = ghost_dispatch<float, double>(g, (const float *)phi, nullptr, G, g->padP64, g->padQ64, gi, 2, need);
     if (!e)
       MR_LAUNCH(g, MRK_MERGE, k_writeback<float, double><<<g->nleaf, 256, 0, g->stream>>>(
-                                  nb, g->padP64, gi, g->cmask, (float *)phi));
+                                  nb, g->padP64, gi, g->cmask, (float *)phi, need));
   } else {
-    e = ghost_dispatch<double, double>(g, (const double *)phi, nullptr, G, g->padP64, g->padQ64, gi, 2);
+    e = ghost_dispatch<double, double>(g, (const double *)phi, nullptr, G, g->padP64, g->padQ64, gi, 2, need);
     if (!e)
       MR_LAUNCH(g, MRK_MERGE, k_writeback<double, double><<<g->nleaf, 256, 0, g->stream>>>(
-                                  nb, g->padP64, gi, g->cmask, (double *)phi));
+                                  nb, g->padP64, gi, g->cmask, (double *)phi, need));
   }
   if (e) return e;
   return check_cuda(cudaGetLastError(), "k_writeback") ? MR_ERR_CUDA : MR_OK;

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
+
 #include "../../include/mrgb.h"
 
 #define MR_MAX_SHELL 12
@@ -439,6 +441,14 @@ struct mr_grid {
   int *cmask;             // per-leaf coarse-direction masks (ghost fill), then new-band masks
   int *hasD;              // per new leaf: the update step has discarded details
   int *pneed;             // per leaf: 1 = left to the full ghost pre-pass (has a coarser neighbour)
+  // incremental criterion inside one mr_adapt call: block norms carried to
+  // the next tree (mdcarry), the leaves whose norm must be recomputed and the
+  // leaves whose ghost fill that needs (cneed[0..cap), cneed[cap..2cap))
+  double *mdcarry;
+  double *mdlast;         // block norms the last iteration decided with
+  int *cneed;
+  int incr_ready;         // mdcarry / cneed describe the current tree
+  int nleaf_last;         // leaves of the tree mdlast belongs to
   void *vpad;             // ghost-filled velocity components (shell 3), 3 * cap * (nb+6)^3
   int tree_version;       // bumped whenever the leaves change
   int vel_version;        // tree version the velocity cache was built for (-1: none)
@@ -463,9 +473,12 @@ struct mr_grid {
   int capturing;          // launches are being captured: count them in cap_counts
   long long cap_counts[32];
   cudaGraphExec_t gexec;
+  cudaStream_t cap_stream; // private stream the steps are captured on (the
+                           // grid's own stream may be the legacy stream)
   unsigned char gkey[160];
   int gkey_len;
   long long graph_replays;
+  int autotune;           // tune launch shapes at first use (mr_autotune)
 };
 
 // dscratch[MR_ALG_BYTES_SLOT + kid]: algorithmic bytes of kernel kid while
@@ -495,6 +508,16 @@ int check_cuda(cudaError_t e, const char *where);
 void *field_ptr(mr_grid *g, int fid);      // fid >= nfields: temporaries
 void *next_field_ptr(mr_grid *g, int fid);
 
+// tune.cu: launch-shape autotuner (kid: 0 k_fill_plain, 1 k_prep,
+// 2 k_criterion, 3 k_fused, 4 k_interp, 5 k_merge; tp: 4 FP32, 5 FP32
+// field with FP64 padded blocks, 8 FP64)
+struct TuneKey {
+  int kid, N, Nt, nb, tp, shell, mode;
+};
+bool operator<(const TuneKey &a, const TuneKey &b);
+int tune_threads(mr_grid *g, const TuneKey &key, const int *cand, int ncand,
+                 const std::function<void(int)> &launch);
+
 // ghost.cu
 void count_units(mr_grid *g, int kid, const int *flags, int n, double bytes_per_unit,
                  const int *exclude = nullptr);
@@ -504,7 +527,7 @@ int launch_crop(mr_grid *g, const void *P, int Gi, void *out, int G, bool fp64_s
 int launch_crop64(mr_grid *g, const double *P, int Gi, double *out, int G);
 int launch_prep32(mr_grid *g, const void *phi, int *Gi);
 int launch_writeback32(mr_grid *g, int Gi, void *phi);
-int launch_substitute(mr_grid *g, void *phi);
+int launch_substitute(mr_grid *g, void *phi, const int *need = nullptr);
 int launch_fused(mr_grid *g, const void *phi, const void *P, const void *Q, int Gi, const void *u, void *out,
                  int stage, double dt, const double *uc, int scheme, bool rhs_only, const void *vpad = nullptr);
 int adapt_shell(int N, int Nt);
@@ -517,8 +540,9 @@ int launch_field_set(mr_grid *g, void *f, int kind, const double *p, int np);
 int launch_mass(mr_grid *g, const void *f, double *host_out);
 int launch_dt(mr_grid *g, double cfl, const double *uc, const void *const *vel, double *host_out);
 // adapt.cu
-int launch_criterion(mr_grid *g, const double *P64, int Gi, double *maxdet);
-int adapt_iteration(mr_grid *g, int crit_fid, double er, double ec, int flags, int *nch);
+int launch_criterion(mr_grid *g, const double *P64, int Gi, double *maxdet, const int *need = nullptr,
+                     const double *carry = nullptr);
+int adapt_iteration(mr_grid *g, int crit_fid, double er, double ec, int flags, int *nch, bool incremental);
 int build_map(mr_grid *g);
 int check_balance(mr_grid *g);
 }  // namespace mr

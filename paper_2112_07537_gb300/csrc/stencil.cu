@@ -378,14 +378,25 @@ static int fused_impl(mr_grid *g, const float *phi, const float *P, const float 
   const int nb = g->desc.nb, Ws = nb + 6;
   const size_t sm = sizeof(float) * ((size_t)Ws * Ws * Ws + (size_t)(N + 1) * (nb / 2 + N) * (nb / 2 + N) +
                                      (size_t)nb * nb * nb);
-  const int threads = nb * nb > 1024 ? 1024 : nb * nb;
+  const int full = nb * nb > 1024 ? 1024 : nb * nb;
   const float ux = (float)uc[0], uy = (float)uc[1], uz = (float)uc[2];
+  // one thread per grid line, or half as many threads walking two lines
+  // each; tuned on launches that do not overwrite their input (the bare
+  // right-hand side, stage 0)
+  const int cand[2] = {full, ((full / 2 + 31) / 32) * 32};
+  const bool can_tune = rhs_only || stage == 0;
 #define MR_FL(S)                                                                                          \
   do {                                                                                                    \
     if (check_cuda(cudaFuncSetAttribute(k_fused<N, NT, S, VEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                         (int)sm),                                                         \
                    "fused smem"))                                                                         \
       return MR_ERR_CUDA;                                                                                 \
+    const int threads = tune_threads(                                                                     \
+        g, TuneKey{3, N, NT, nb, 4, Gi, 2 * S + (VEL ? 1 : 0)}, cand, can_tune ? 2 : 1, [&](int th) {       \
+          k_fused<N, NT, S, VEL><<<g->nleaf, th, sm, g->stream>>>(                                         \
+              t, phi, P, Q, Gi, g->cmask, u, out, stage, (float)dt, ux, uy, uz, rhs_only, g->counter + 1,  \
+              vpad, (float)g->diff_nu, g->diff_order, (float)g->vel_scale);                                \
+        });                                                                                               \
     MR_LAUNCH(g, MRK_RHS, k_fused<N, NT, S, VEL><<<g->nleaf, threads, sm, g->stream>>>(                       \
                               t, phi, P, Q, Gi, g->cmask, u, out, stage, (float)dt, ux, uy, uz, rhs_only, \
                               g->counter + 1, vpad, (float)g->diff_nu, g->diff_order,                     \
@@ -465,7 +476,7 @@ __global__ void k_field_set(Tree t, T *f, int kind, InitParams ip) {
         r2 += dd * dd;
       }
       v = 0.5 * (1.0 - tanh((sqrt(r2) - ip.p[3]) / ip.p[4]));
-    } else if (kind == MR_INIT_GAUSSIAN_SUM) {
+    } else if (kind == MR_INIT_GAUSSIAN_SUM || kind == MR_INIT_GAUSSIAN_SUM_ADD) {
       const int ng = (int)ip.p[0];
       for (int q = 0; q < ng; ++q) {
         const double *c = ip.p + 1 + 5 * q;
@@ -499,7 +510,9 @@ __global__ void k_field_set(Tree t, T *f, int kind, InitParams ip) {
       else if (comp == 1) v = -s * cos(w * x[0] + ph) * sin(w * x[1]) * cos(w * x[2]);
       else v = 0.0;
     }
-    f[(size_t)b * nb * nb * nb + p] = T(v);
+    const size_t q = (size_t)b * nb * nb * nb + p;
+    if (kind == MR_INIT_GAUSSIAN_SUM_ADD) v += (double)f[q];  // the field value, then the sum
+    f[q] = T(v);
   }
 }
 

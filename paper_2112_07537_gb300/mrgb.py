@@ -20,7 +20,7 @@ F32, F64 = 0, 1
 CONS3, CONS5, WENOZ5 = 0, 1, 2
 INIT_GAUSSIAN, INIT_TANH_SPHERE, INIT_TAYLOR_GREEN, INIT_GAUSSIAN_SUM = 0, 1, 2, 3
 ADAPT_REFINE, ADAPT_COARSEN = 1, 2
-INIT_COMPACT_GAUSSIAN, INIT_DEFORMATION = 4, 5
+INIT_COMPACT_GAUSSIAN, INIT_DEFORMATION, INIT_GAUSSIAN_SUM_ADD = 4, 5, 6
 GRID_FIXED_TREE = 1
 GRID_VELOCITY = 2
 NUM_KERNELS = 18
@@ -32,7 +32,8 @@ EXPORTS = ["mr_last_error", "mr_workspace_size", "mr_grid_create", "mr_grid_dest
            "mr_step", "mr_criterion", "mr_adapt", "mr_adapt_iter", "mr_mass", "mr_query",
            "mr_field_ptr", "mr_profile", "mr_profile_read", "mr_launch_count", "mr_profile_bytes", "mr_set_diffusion", "mr_step_vel_scaled",
            "mr_ghost_fill_static", "mr_rhs_advect_vel", "mr_step_vel", "mr_velocity_invalidate",
-           "mr_device_peaks", "mr_dt", "mr_use_graphs", "mr_graph_replays", "mr_set_adapt_limits"]
+           "mr_device_peaks", "mr_dt", "mr_use_graphs", "mr_graph_replays", "mr_set_adapt_limits",
+           "mr_last_block_norms", "mr_autotune", "mr_autotune_table", "mr_autotune_clear"]
 
 
 class MRError(RuntimeError):
@@ -102,6 +103,9 @@ def load(path: str = LIB_PATH):
         L.mr_use_graphs.argtypes = [vp, C.c_int]
         L.mr_graph_replays.argtypes = [vp, C.POINTER(C.c_longlong)]
         L.mr_set_adapt_limits.argtypes = [vp, C.c_int, C.c_int]
+        L.mr_last_block_norms.argtypes = [vp, vp, C.c_int, C.POINTER(C.c_int)]
+        L.mr_autotune.argtypes = [vp, C.c_int]
+        L.mr_autotune_table.argtypes = [C.c_char_p, C.c_size_t, C.POINTER(C.c_int)]
         _lib = L
     return _lib
 
@@ -115,6 +119,18 @@ def device_peaks():
     out = (C.c_double * len(PEAK_NAMES))()
     _chk(load().mr_device_peaks(out))
     return dict(zip(PEAK_NAMES, list(out)))
+
+
+def autotune_table():
+    """Lines of the process-wide autotuner table (one per tuned launch shape)."""
+    n = C.c_int()
+    buf = C.create_string_buffer(1 << 16)
+    _chk(load().mr_autotune_table(buf, len(buf), C.byref(n)))
+    return [ln for ln in buf.value.decode().splitlines() if ln]
+
+
+def autotune_clear():
+    _chk(load().mr_autotune_clear())
 
 
 def _chk(code):
@@ -330,6 +346,10 @@ class Grid:
         _chk(load().mr_dt(self.h, float(cfl), uu, vv, C.byref(out)))
         return out.value
 
+    def autotune(self, enable=True):
+        """Tune launch shapes on this grid's data at first use (mr_autotune)."""
+        _chk(load().mr_autotune(self.h, int(enable)))
+
     def use_graphs(self, enable=True):
         """Capture each RK step into a CUDA graph and replay it while unchanged."""
         _chk(load().mr_use_graphs(self.h, int(enable)))
@@ -341,6 +361,14 @@ class Grid:
 
     def set_adapt_limits(self, max_iter=64, max_sweeps=256):
         _chk(load().mr_set_adapt_limits(self.h, int(max_iter), int(max_sweeps)))
+
+    def last_block_norms(self):
+        """Block norms the last adaptation iteration decided with (numpy)."""
+        n = C.c_int()
+        _chk(load().mr_last_block_norms(self.h, None, 0, C.byref(n)))
+        out = np.empty(n.value)
+        _chk(load().mr_last_block_norms(self.h, out.ctypes.data_as(C.c_void_p), n.value, C.byref(n)))
+        return out
 
     def mass(self, fid):
         m = C.c_double()

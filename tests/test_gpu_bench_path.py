@@ -225,3 +225,37 @@ def test_config1_hundred_steps_fp32(mr, oracle_mod):
             got = g.field_copy_out(0).astype(np.float64)
             worst = max(worst, np.abs(got - ref).max() / np.abs(ref).max())
     assert worst <= 1e-5, worst
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_incremental_block_norms_equal_full_criterion(mr, oracle_mod, prec):
+    """mr_adapt recomputes block norms from its second iteration on only within
+    two neighbour rings of the previous iteration's changes and carries the
+    rest.  After convergence, the norms the last iteration decided with equal
+    a full recomputation (mr_criterion) bit for bit, and (FP64) the whole
+    four-field adaptation equals the oracle's Alg. SM3 loop."""
+    import torch
+    O = oracle_mod
+    g, og = _grid(mr, O, 6, 2, prec, nfields=4)
+    xyz = I.point_coords(og.nt, og.tree_len, og.nb, og.lev, og.anc)
+    cast = (lambda a: a.astype(np.float32)) if prec == 0 else (lambda a: a)
+    fields = [cast(_scalar(xyz))] + [cast(_taylor_green(xyz, d)) for d in range(3)]
+    for f, v in enumerate(fields):
+        g.field_copy_in(f, v)
+    total = g.adapt(0, EPS_R, EPS_C)
+    assert total > 0
+    carried = g.last_block_norms()
+    full = torch.empty(g.nleaf, dtype=torch.float64, device="cuda")
+    g.criterion(0, full)
+    g.sync()
+    assert np.array_equal(carried, full.cpu().numpy())
+    if prec == 1:
+        cur, outs, refined = og, [f.astype(np.float64) for f in fields], None
+        for _ in range(8):
+            cur, outs, refined, nch, _, _ = O.adapt_iter_fields(cur, outs, EPS_R, EPS_C, refined)
+            if nch == 0:
+                break
+        _same_tree(g, cur)
+        for f in range(4):
+            got = g.field_copy_out(f)
+            assert np.abs(got - outs[f]).max() <= TOL * np.abs(outs[f]).max(), f

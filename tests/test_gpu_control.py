@@ -138,3 +138,46 @@ def test_adaptation_beyond_capacity_is_refused(mr):
     g.sync()
     g.step(0, 1e-3, (1.0, 0.0, 0.0), mr.CONS5)
     g.sync()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_autotuned_launches_give_identical_results(mr, prec):
+    """The autotuner changes CTA sizes only: ghost fills, RK steps with
+    velocity fields and an adaptation on a tuning grid equal those of an
+    untuned twin bit for bit, and the table lists the tuned shapes."""
+    import torch
+    mr.autotune_clear()
+    nt, tl, nb = (2, 2, 2), 0.5, 16
+    lev, anc = I.tree_config1()
+    grids = [mr.Grid(nt, tl, nb, 0, 2, 4, 2, lev, anc, precision=prec, nfields=4, velocity=True,
+                     capacity=4000) for _ in range(2)]
+    glev, ganc, _ = grids[0].leaves()
+    xyz = I.point_coords(nt, tl, nb, glev, ganc)
+    dtype = np.float32 if prec == 0 else np.float64
+    phi = I.gaussian(xyz, (0.4, 0.4, 0.4), 0.04).astype(dtype)
+    for g in grids:
+        g.field_copy_in(0, phi)
+        for d in range(3):
+            g.field_copy_in(1 + d, _tg(xyz, d).astype(dtype))
+    # the untuned grid runs first: the table is still empty, so it uses the
+    # default shapes; then the tuning grid fills the table
+    W = nb + 6
+    pads = []
+    for k, g in enumerate(grids):
+        if k == 1:
+            g.autotune(True)
+        pad = torch.empty((g.nleaf, W, W, W), dtype=torch.float32 if prec == 0 else torch.float64,
+                          device="cuda")
+        g.ghost_fill(0, 3, pad)
+        for _ in range(2):
+            g.step_vel(0, 1e-3, (1, 2, 3), mr.WENOZ5)
+        g.adapt(0, 1e-3, 1e-6)
+        g.sync()
+        pads.append(pad.cpu().numpy())
+    assert np.array_equal(pads[0], pads[1])
+    assert np.array_equal(grids[0].leaves()[0], grids[1].leaves()[0])
+    for f in range(4):
+        assert np.array_equal(grids[0].field_copy_out(f), grids[1].field_copy_out(f))
+    table = mr.autotune_table()
+    assert len(table) >= 4, table
+    assert any(ln.startswith("k_fused") for ln in table) and any(ln.startswith("k_criterion") for ln in table)
