@@ -282,6 +282,7 @@ int mr_grid_create(const mr_grid_desc *desc, void *workspace, size_t workspace_b
   g->diff_order = 0;
   g->vel_scale = 1.0;
   g->max_adapt_iter = 64;
+  for (int f = 0; f < 32; ++f) g->field_subst[f] = -1;
   g->max_policy_sweeps = 256;
   g->shell_rk = srk;
   g->shell_ad = sad;
@@ -403,6 +404,7 @@ static int fid_ok(mr_grid *g, int fid) { return g && fid >= 0 && fid < g->desc.n
 
 int mr_field_copy_in(mr_grid *g, int fid, const void *src, int on_dev) {
   if (!fid_ok(g, fid) || !src) return MR_ERR_INVALID;
+  field_written(g, fid);
   const size_t bytes = (size_t)g->nleaf * g->nb3 * g->esize;
   return check_cuda(cudaMemcpyAsync(field_ptr(g, fid), src, bytes,
                                     on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->stream),
@@ -423,6 +425,7 @@ int mr_field_copy_out(mr_grid *g, int fid, void *dst, int on_dev) {
 
 int mr_field_ptr(mr_grid *g, int fid, void **ptr) {
   if (!fid_ok(g, fid) || !ptr) return MR_ERR_INVALID;
+  field_written(g, fid);  // the caller may write through the pointer
   *ptr = field_ptr(g, fid);
   return MR_OK;
 }
@@ -434,11 +437,13 @@ int mr_field_set(mr_grid *g, int fid, int kind, const double *params, int np) {
   if ((kind == MR_INIT_GAUSSIAN_SUM || kind == MR_INIT_GAUSSIAN_SUM_ADD) &&
       (params[0] < 0 || 1 + 5 * (int)params[0] > np))
     return MR_ERR_INVALID;
+  field_written(g, fid);
   return launch_field_set(g, field_ptr(g, fid), kind, params, np);
 }
 
 int mr_ghost_fill(mr_grid *g, int fid, int G, void *padded) {
   if (!fid_ok(g, fid)) return MR_ERR_INVALID;
+  field_written(g, fid);  // substituted in place, in the padded blocks' precision
   void *P;
   int Gi;
   bool is64;
@@ -460,6 +465,7 @@ static int adapt_ok(mr_grid *g) {
 // FP64 ghost fill (the adaptation path) into a double padded buffer.
 int mr_ghost_fill64(mr_grid *g, int fid, int G, double *padded) {
   if (!fid_ok(g, fid)) return MR_ERR_INVALID;
+  field_written(g, fid);
   if (!adapt_ok(g)) return MR_ERR_UNSUPPORTED;
   void *P;
   int Gi;
@@ -472,6 +478,8 @@ int mr_ghost_fill64(mr_grid *g, int fid, int G, double *padded) {
 
 int mr_rhs_advect(mr_grid *g, int phi, const double *u, int out, int scheme) {
   if (!fid_ok(g, phi) || !fid_ok(g, out) || !u) return MR_ERR_INVALID;
+  field_written(g, phi);
+  field_written(g, out);
   void *f = field_ptr(g, phi);
   if (g->desc.precision == MR_F32) {
     int Gi;
@@ -507,9 +515,15 @@ static int velocity_cache(mr_grid *g, const int *vel) {
     void *f = field_ptr(g, vel[d]);
     // the first fill substitutes the component in place; substitution is
     // idempotent, so the second fill yields the ghosts every later stage
-    // would compute
-    int e = launch_ghost(g, f, f, 3, false, &P, &Gi, &is64);
-    if (!e) e = launch_ghost(g, f, f, 3, false, &P, &Gi, &is64);
+    // would compute.  A component the adaptation left substituted for this
+    // tree needs only the second fill, without writing the field back.
+    int e = MR_OK;
+    if (field_substituted(g, vel[d])) {
+      e = launch_ghost(g, f, nullptr, 3, false, &P, &Gi, &is64);
+    } else {
+      e = launch_ghost(g, f, f, 3, false, &P, &Gi, &is64);
+      if (!e) e = launch_ghost(g, f, f, 3, false, &P, &Gi, &is64);
+    }
     // component d at offset d * nleaf blocks (the kernels' indexing)
     if (!e) e = launch_crop(g, P, Gi, (char *)g->vpad + (size_t)d * g->nleaf * blk, 3, is64);
     if (e) return e;
@@ -527,6 +541,8 @@ int mr_velocity_invalidate(mr_grid *g) {
 
 int mr_rhs_advect_vel(mr_grid *g, int phi, const int *vel, int out, int scheme) {
   if (!fid_ok(g, phi) || !fid_ok(g, out) || !vel) return MR_ERR_INVALID;
+  field_written(g, phi);
+  field_written(g, out);
   int e = velocity_cache(g, vel);
   if (e) return e;
   void *f = field_ptr(g, phi);
@@ -704,6 +720,7 @@ int mr_step_vel(mr_grid *g, int phi, double dt, const int *vel, int scheme) {
 
 int mr_step_vel_scaled(mr_grid *g, int phi, double dt, const int *vel, int scheme, const double *scale) {
   if (!fid_ok(g, phi) || !vel || !scale) return MR_ERR_INVALID;
+  field_written(g, phi);
   for (int s = 0; s < 3; ++s)
     if (!std::isfinite(scale[s])) return MR_ERR_INVALID;
   int e = velocity_cache(g, vel);
@@ -718,12 +735,14 @@ int mr_rk_stage(mr_grid *g, int stage, double dt, int u_fid, int y_fid, int rhs_
   if (!fid_ok(g, u_fid) || !fid_ok(g, y_fid) || !fid_ok(g, rhs_fid) || !fid_ok(g, out_fid) || stage < 0 ||
       stage > 2)
     return MR_ERR_INVALID;
+  field_written(g, out_fid);
   return launch_rk_combine(g, stage, dt, field_ptr(g, u_fid), field_ptr(g, y_fid), field_ptr(g, rhs_fid),
                            field_ptr(g, out_fid));
 }
 
 int mr_step(mr_grid *g, int phi, double dt, const double *u, int scheme) {
   if (!fid_ok(g, phi) || !u) return MR_ERR_INVALID;
+  field_written(g, phi);
   GraphKey key{};
   key.kind = 0, key.phi = phi, key.scheme = scheme, key.dt = dt;
   for (int d = 0; d < 3; ++d) key.u[d] = u[d];
@@ -732,6 +751,7 @@ int mr_step(mr_grid *g, int phi, double dt, const double *u, int scheme) {
 
 int mr_criterion(mr_grid *g, int fid, double *maxdet) {
   if (!fid_ok(g, fid) || !maxdet) return MR_ERR_INVALID;
+  field_written(g, fid);
   if (!adapt_ok(g)) return MR_ERR_UNSUPPORTED;
   void *P;
   int Gi;
@@ -744,6 +764,7 @@ int mr_criterion(mr_grid *g, int fid, double *maxdet) {
 int mr_adapt_iter(mr_grid *g, int crit, double er, double ec, int flags, int *nch) {
   if (!fid_ok(g, crit)) return MR_ERR_INVALID;
   if (!adapt_ok(g)) return MR_ERR_UNSUPPORTED;
+  field_written(g, crit);
   int n = 0;
   int e = adapt_iteration(g, crit, er, ec, flags, &n, false);
   if (nch) *nch = n;
@@ -754,6 +775,7 @@ int mr_adapt(mr_grid *g, int crit, double er, double ec, int flags, int *nch) {
   if (!fid_ok(g, crit)) return MR_ERR_INVALID;
   if (!adapt_ok(g)) return MR_ERR_UNSUPPORTED;
   int total = 0;
+  field_written(g, crit);  // the criterion field changes between adaptations
   if (check_cuda(cudaMemsetAsync(g->refined, 0, 4 * (size_t)g->desc.capacity, g->stream), "refined reset"))
     return MR_ERR_CUDA;
   for (int it = 0; it < g->max_adapt_iter; ++it) {
@@ -764,6 +786,9 @@ int mr_adapt(mr_grid *g, int crit, double er, double ec, int flags, int *nch) {
     if (e) return e;
     total += n;
     if (n == 0) {
+      // every field now holds the adaptation ghost fill's substituted values
+      // for the current tree
+      for (int f = 0; f < g->desc.nfields && f < 32; ++f) g->field_subst[f] = g->tree_version;
       if (nch) *nch = total;
       return MR_OK;
     }

@@ -611,12 +611,14 @@ __global__ void k_need2(Tree t, const int8_t *st, const int *nb1, int *need) {
 // (the adaptation's ghost fill overwrites every field) -- all of them, or
 // with `dirty` (later iterations of one adaptation) those whose band inputs
 // may have changed since their last substitution (marked in dirty)
-__global__ void k_need3(Tree t, const int *need, const int *__restrict__ dirty, int *need2) {
+__global__ void k_need3(Tree t, const int *need, const int *__restrict__ dirty, int sub_mode, int *need2) {
+  // sub_mode 1: every leaf next to a coarser leaf substitutes; 2: those
+  // marked in dirty; 0: none (the field is substituted for this tree already)
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= t.nleaf) return;
   const int L = __ldg(t.lev + b);
   int any = need[b];
-  const bool sub = !dirty || dirty[b];
+  const bool sub = sub_mode == 1 || (sub_mode == 2 && dirty[b]);
   if (!any) for_each_nbr(t, b, [&](int o) { any |= __ldg(t.lev + o) < L && (sub || need[o]); });
   need2[b] = any;
 }
@@ -780,7 +782,7 @@ int adapt_iteration(mr_grid *g, int crit, double er, double ec, int flags, int *
     // substitution next to coarser leaves, which overwrites their values
     // (later iterations: only where its inputs may have changed)
     for (int fid = 0; fid < g->desc.nfields; ++fid) {
-      if (fid == crit) continue;
+      if (fid == crit || field_substituted(g, fid)) continue;  // nothing would change
       e = launch_substitute(g, field_ptr(g, fid), cneed);
       if (e) return e;
     }
@@ -813,14 +815,28 @@ int adapt_iteration(mr_grid *g, int crit, double er, double ec, int flags, int *
   int *nb1 = reinterpret_cast<int *>(g->maxdet), *need2 = nb1 + g->desc.capacity, *need = g->scan;
   MR_LAUNCH(g, MRK_MISC, k_need1<<<nblk, tb, 0, st>>>(t, g->status, nb1));
   MR_LAUNCH(g, MRK_MISC, k_need2<<<nblk, tb, 0, st>>>(t, g->status, nb1, need));
-  MR_LAUNCH(g, MRK_MISC, k_need3<<<nblk, tb, 0, st>>>(t, need, cneed, need2));
+  MR_LAUNCH(g, MRK_MISC, k_need3<<<nblk, tb, 0, st>>>(t, need, cneed, cneed ? 2 : 1, need2));
+  // fields the previous adaptation left substituted for this tree (and that
+  // nothing wrote since) need no substitution in the first iteration: only
+  // the leaves their interpolation and update read, and the finer leaves
+  // pushing into those (in the second half of cneed, free until the rings)
+  int *need2_min = nullptr;
+  if (!incr) {
+    bool any_clean = false;
+    for (int f = 0; f < g->desc.nfields; ++f) any_clean |= f != crit && field_substituted(g, f);
+    if (any_clean) {
+      need2_min = g->cneed + cap;
+      MR_LAUNCH(g, MRK_MISC, k_need3<<<nblk, tb, 0, st>>>(t, need, nullptr, 0, need2_min));
+    }
+  }
   MR_LAUNCH(g, MRK_UPDATE, k_newmask<<<(nn + tb - 1) / tb, tb, 0, st>>>(tn, g->newsrc, nmask));
   // 6-9: every field: ghosts (criterion field first: P is current), interpolate, update
   const bool f32 = g->desc.precision == MR_F32;
   for (int pass = 0; pass < g->desc.nfields; ++pass) {
     const int fid = pass == 0 ? crit : (pass <= crit ? pass - 1 : pass);
     if (pass > 0 || incr) {  // incremental: the criterion fill covered fewer leaves
-      e = launch_ghost(g, field_ptr(g, fid), field_ptr(g, fid), G, true, &Pv, &Gi, nullptr, need2);
+      const int *nd = (pass > 0 && need2_min && field_substituted(g, fid)) ? need2_min : need2;
+      e = launch_ghost(g, field_ptr(g, fid), field_ptr(g, fid), G, true, &Pv, &Gi, nullptr, nd);
       if (e) return e;
       P = (const double *)Pv;
     }

@@ -479,7 +479,20 @@ struct mr_grid {
   int gkey_len;
   long long graph_replays;
   int autotune;           // tune launch shapes at first use (mr_autotune)
+  // field_subst[f] = tree_version while field f holds exactly the values the
+  // adaptation's ghost fill leaves (every band next to a coarser leaf
+  // substituted in FP64 for the current tree), -1 once anything may have
+  // written it; a repeated substitution would give the same bits
+  int field_subst[32];
 };
+namespace mr {
+inline void field_written(mr_grid *g, int fid) {
+  if (fid >= 0 && fid < 32) g->field_subst[fid] = -1;
+}
+inline bool field_substituted(const mr_grid *g, int fid) {
+  return fid >= 0 && fid < 32 && g->field_subst[fid] == g->tree_version;
+}
+}  // namespace mr
 
 // dscratch[MR_ALG_BYTES_SLOT + kid]: algorithmic bytes of kernel kid while
 // profiling (dscratch holds 64 doubles; [0] is the mass reduction)

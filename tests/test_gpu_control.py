@@ -181,3 +181,46 @@ def test_autotuned_launches_give_identical_results(mr, prec):
     table = mr.autotune_table()
     assert len(table) >= 4, table
     assert any(ln.startswith("k_fused") for ln in table) and any(ln.startswith("k_criterion") for ln in table)
+
+
+def test_substituted_field_tracking(mr):
+    """After a converged mr_adapt every field holds the substituted values of
+    the current tree; the next adaptation skips re-substituting fields that
+    nothing wrote since, and the velocity-cache rebuild fills such a
+    component once without writing it back.  A twin grid whose velocity
+    fields are marked written (mr_field_ptr) before every adaptation does
+    the full work: its adaptations give the same bits; marked written after
+    the adaptation too, its cache re-substitutes in FP32 and the steps agree
+    within FP32 rounding."""
+    nt, tl, nb = (2, 2, 2), 0.5, 16
+    lev, anc = I.tree_config1()
+    grids = [mr.Grid(nt, tl, nb, 0, 2, 4, 2, lev, anc, precision=mr.F32, nfields=4, velocity=True,
+                     capacity=4000) for _ in range(3)]
+    glev, ganc, _ = grids[0].leaves()
+    xyz = I.point_coords(nt, tl, nb, glev, ganc)
+    phi = I.gaussian(xyz, (0.4, 0.4, 0.4), 0.05).astype(np.float32)
+    for g in grids:
+        g.field_copy_in(0, phi)
+        for d in range(3):
+            g.field_copy_in(1 + d, _tg(xyz, d).astype(np.float32))
+    for cycle in range(3):
+        for k, g in enumerate(grids if cycle == 0 else grids[:2]):
+            if k >= 1:
+                for f in range(1, 4):
+                    g.field_view(f)  # hands out the pointer: the field counts as written
+            g.adapt(0, 1e-3, 1e-6)
+            if k == 1:  # adaptation-side check: bit for bit
+                for f in range(4):
+                    assert np.array_equal(grids[0].field_copy_out(f), g.field_copy_out(f)), (cycle, f)
+                a, b = grids[0].leaves(), g.leaves()
+                assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+            if k == 2:
+                for f in range(1, 4):
+                    g.field_view(f)
+            for _ in range(2):
+                g.step_vel(0, 2e-3, (1, 2, 3), mr.WENOZ5)
+        assert np.array_equal(grids[1].field_copy_out(0), grids[0].field_copy_out(0))
+        if cycle == 0:  # same tree, velocity ghosts differing by FP32 rounding
+            ref = grids[0].field_copy_out(0).astype(np.float64)
+            other = grids[2].field_copy_out(0).astype(np.float64)
+            assert np.abs(other - ref).max() <= 1e-6 * np.abs(ref).max()
