@@ -306,10 +306,7 @@ int mr_adapt_iter(mr_grid *grid, int crit_fid, double eps_refine, double eps_coa
 /* Block norms (max |detail| per leaf, Sec. 2.2.5) that the last adaptation
  * iteration took its decisions with, in the slot order of the tree that
  * iteration started from (*n leaves; after an mr_adapt that converged, the
- * current tree).  Within one mr_adapt call the second and later iterations
- * recompute the norm only for leaves within two neighbour rings of the
- * previous iteration's changes and carry the others; these are the values
- * that decided.  dst: nleaf doubles (host or device), or NULL to query *n.
+ * current tree).  dst: nleaf doubles (host or device), or NULL to query *n.
  * Synchronises.                                                           */
 int mr_last_block_norms(mr_grid *grid, double *dst, int cap, int *n);
 

@@ -90,7 +90,7 @@ int adapt_shell(int N, int Nt) {
 }
 
 struct Layout {
-  size_t off[29];
+  size_t off[27];
   size_t total;
 };
 
@@ -120,7 +120,7 @@ static int layout(const mr_grid_desc *d, Layout *L, int *shell_rk, int *shell_ad
   *M = d->lmax;
   *map_cells = ((size_t)d->ntree[0] << d->lmax) * ((size_t)d->ntree[1] << d->lmax) *
                ((size_t)d->ntree[2] << d->lmax);
-  size_t sz[29] = {
+  size_t sz[27] = {
       cap * 4, cap * 4,                          // lev[2]
       cap * 12, cap * 12,                        // anc[2]
       cap * 8, cap * 8,                          // keys[2]
@@ -142,11 +142,9 @@ static int layout(const mr_grid_desc *d, Layout *L, int *shell_rk, int *shell_ad
       cap * 4,                                   // hasD
       velo ? 3 * cap * wv * wv * wv * es : 0,    // velocity cache (shell 3)
       cap * 4,                                   // pneed: leaves left to the full pre-pass
-      fixed ? 0 : cap * 8,                       // mdcarry
-      fixed ? 0 : cap * 8,                       // mdlast
-      fixed ? 0 : 2 * cap * 4};                  // cneed
+      fixed ? 0 : cap * 8};                      // mdlast
   size_t o = 0;
-  for (int i = 0; i < 29; ++i) {
+  for (int i = 0; i < 27; ++i) {
     L->off[i] = o;
     o += al(sz[i]);
   }
@@ -272,9 +270,7 @@ int mr_grid_create(const mr_grid_desc *desc, void *workspace, size_t workspace_b
   g->cmask = (int *)(w + L.off[22]);
   g->hasD = (int *)(w + L.off[23]);
   g->pneed = (int *)(w + L.off[25]);
-  g->mdcarry = (double *)(w + L.off[26]);
-  g->mdlast = (double *)(w + L.off[27]);
-  g->cneed = (int *)(w + L.off[28]);
+  g->mdlast = (double *)(w + L.off[26]);
   g->vpad = (desc->flags & MR_GRID_VELOCITY) ? (void *)(w + L.off[24]) : nullptr;
   g->tree_version = 0;
   g->vel_version = -1;
@@ -513,10 +509,10 @@ static int velocity_cache(mr_grid *g, const int *vel) {
     int Gi;
     bool is64;
     void *f = field_ptr(g, vel[d]);
-    // the first fill substitutes the component in place; substitution is
-    // idempotent, so the second fill yields the ghosts every later stage
-    // would compute.  A component the adaptation left substituted for this
-    // tree needs only the second fill, without writing the field back.
+    // the first fill substitutes the component in place, the second yields
+    // the ghosts of the substituted field, which every stage of this tree
+    // uses.  A component a converged adaptation left substituted (in FP64)
+    // for this tree needs only the second fill, without writing it back.
     int e = MR_OK;
     if (field_substituted(g, vel[d])) {
       e = launch_ghost(g, f, nullptr, 3, false, &P, &Gi, &is64);
@@ -766,7 +762,7 @@ int mr_adapt_iter(mr_grid *g, int crit, double er, double ec, int flags, int *nc
   if (!adapt_ok(g)) return MR_ERR_UNSUPPORTED;
   field_written(g, crit);
   int n = 0;
-  int e = adapt_iteration(g, crit, er, ec, flags, &n, false);
+  int e = adapt_iteration(g, crit, er, ec, flags, &n);
   if (nch) *nch = n;
   return e;
 }
@@ -780,14 +776,12 @@ int mr_adapt(mr_grid *g, int crit, double er, double ec, int flags, int *nch) {
     return MR_ERR_CUDA;
   for (int it = 0; it < g->max_adapt_iter; ++it) {
     int n = 0;
-    // the fields change only through this loop from the second iteration on:
-    // block norms far from the previous iteration's changes are carried
-    int e = adapt_iteration(g, crit, er, ec, flags, &n, it > 0);
+    int e = adapt_iteration(g, crit, er, ec, flags, &n);
     if (e) return e;
     total += n;
     if (n == 0) {
-      // every field now holds the adaptation ghost fill's substituted values
-      // for the current tree
+      // every field now holds the values the adaptation's ghost fill leaves
+      // (substituted next to coarser leaves) for the current tree
       for (int f = 0; f < g->desc.nfields && f < 32; ++f) g->field_subst[f] = g->tree_version;
       if (nch) *nch = total;
       return MR_OK;

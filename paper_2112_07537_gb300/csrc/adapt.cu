@@ -125,13 +125,8 @@ __device__ __forceinline__ void detail_planes(const double *__restrict__ Pb, int
 // that drives refinement and coarsening).
 template <int N, int NT>
 __global__ void __launch_bounds__(1024) k_criterion(Tree t, const double *__restrict__ P, int Gi,
-                                                   double *__restrict__ maxdet, const int *__restrict__ need,
-                                                   const double *__restrict__ carry) {
+                                                   double *__restrict__ maxdet) {
   const int b = blockIdx.x, nb = t.nb, Wd = nb + 2 * Gi;
-  if (need && !need[b]) {  // norm carried from the previous iteration
-    if (threadIdx.x == 0) maxdet[b] = carry[b];
-    return;
-  }
   extern __shared__ double sm[];
   unsigned long long mx = 0;  // max |gamma| as an integer key (integer pipe)
   detail_planes<N, NT>(P + (size_t)b * Wd * Wd * Wd, nb, Gi, sm,
@@ -156,8 +151,7 @@ static size_t crit_smem(int nb) {
 }
 
 template <int N, int NT>
-static int criterion_impl(mr_grid *g, const double *P, int Gi, double *maxdet, const int *need,
-                          const double *carry) {
+static int criterion_impl(mr_grid *g, const double *P, int Gi, double *maxdet) {
   const size_t sm = crit_smem<N, NT>(g->desc.nb);
   if (sm > 227 * 1024) return MR_ERR_UNSUPPORTED;
   if (check_cuda(cudaFuncSetAttribute(k_criterion<N, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -167,16 +161,16 @@ static int criterion_impl(mr_grid *g, const double *P, int Gi, double *maxdet, c
   Tree t = tree_view(g);
   static const int cc[2] = {1024, 512};
   const int th = tune_threads(g, TuneKey{2, N, NT, g->desc.nb, 8, Gi, 0}, cc, 2, [&](int thr) {
-    k_criterion<N, NT><<<g->nleaf, thr, sm, g->stream>>>(t, P, Gi, maxdet, need, carry);
+    k_criterion<N, NT><<<g->nleaf, thr, sm, g->stream>>>(t, P, Gi, maxdet);
   });
-  MR_LAUNCH(g, MRK_CRITERION, k_criterion<N, NT><<<g->nleaf, th, sm, g->stream>>>(t, P, Gi, maxdet, need, carry));
+  MR_LAUNCH(g, MRK_CRITERION, k_criterion<N, NT><<<g->nleaf, th, sm, g->stream>>>(t, P, Gi, maxdet));
   return check_cuda(cudaGetLastError(), "k_criterion") ? MR_ERR_CUDA : MR_OK;
 }
 
-int launch_criterion(mr_grid *g, const double *P, int Gi, double *maxdet, const int *need, const double *carry) {
+int launch_criterion(mr_grid *g, const double *P, int Gi, double *maxdet) {
   const int N = g->desc.wav_N, Nt = g->desc.wav_Nt;
 #define MR_CCASE(n_, nt_) \
-  if (N == n_ && Nt == nt_) return criterion_impl<n_, nt_>(g, P, Gi, maxdet, need, carry);
+  if (N == n_ && Nt == nt_) return criterion_impl<n_, nt_>(g, P, Gi, maxdet);
   MR_CCASE(2, 0) MR_CCASE(2, 2) MR_CCASE(4, 0) MR_CCASE(4, 2) MR_CCASE(6, 0) MR_CCASE(6, 2)
 #undef MR_CCASE
   return MR_ERR_UNSUPPORTED;
@@ -607,58 +601,14 @@ __global__ void k_need2(Tree t, const int8_t *st, const int *nb1, int *need) {
 }
 
 // finer neighbours of needed leaves push the fine-to-coarse ghost values the
-// needed leaves read; leaves next to a coarser leaf substitute their band
-// (the adaptation's ghost fill overwrites every field) -- all of them, or
-// with `dirty` (later iterations of one adaptation) those whose band inputs
-// may have changed since their last substitution (marked in dirty)
-__global__ void k_need3(Tree t, const int *need, const int *__restrict__ dirty, int sub_mode, int *need2) {
-  // sub_mode 1: every leaf next to a coarser leaf substitutes; 2: those
-  // marked in dirty; 0: none (the field is substituted for this tree already)
+// needed leaves read: the needed leaves and those finer neighbours
+__global__ void k_need3(Tree t, const int *need, int *need2) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= t.nleaf) return;
   const int L = __ldg(t.lev + b);
   int any = need[b];
-  const bool sub = sub_mode == 1 || (sub_mode == 2 && dirty[b]);
-  if (!any) for_each_nbr(t, b, [&](int o) { any |= __ldg(t.lev + o) < L && (sub || need[o]); });
+  if (!any) for_each_nbr(t, b, [&](int o) { any |= __ldg(t.lev + o) < L && need[o]; });
   need2[b] = any;
-}
-
-// ------------------------------------------------- incremental criterion
-// Block norms of unchanged leaves carried to their new slots (new leaves get
-// theirs recomputed).
-__global__ void k_carry(int nn, const int *__restrict__ src, const double *__restrict__ md_old,
-                        double *__restrict__ md_new) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= nn) return;
-  md_new[q] = src[2 * q] == KIND_COPY ? md_old[src[2 * q + 1]] : 0.0;
-}
-
-// Leaves of the new tree whose values the iteration changed: new leaves and
-// unchanged leaves corrected by the update step.
-__global__ void k_dirty(int nn, const int *__restrict__ src, const int *__restrict__ hasD, int *out) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= nn) return;
-  out[q] = src[2 * q] != KIND_COPY || hasD[q];
-}
-
-// one ring of neighbours (face, edge, corner) around the marked leaves
-__global__ void k_ring(Tree t, const int *__restrict__ in, int *__restrict__ out) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= t.nleaf) return;
-  int any = in[b];
-  if (!any) for_each_nbr(t, b, [&](int o) { any |= in[o]; });
-  out[b] = any;
-}
-
-// the marked leaves and every leaf that pushes fine-to-coarse values into
-// one of them (a finer neighbour of a marked leaf)
-__global__ void k_pushers(Tree t, const int *__restrict__ in, int *__restrict__ out) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= t.nleaf) return;
-  const int L = __ldg(t.lev + b);
-  int any = in[b];
-  if (!any) for_each_nbr(t, b, [&](int o) { any |= in[o] && __ldg(t.lev + o) < L; });
-  out[b] = any;
 }
 
 // ------------------------------------------------------------- driver
@@ -715,27 +665,17 @@ static int read_ints(mr_grid *g, const int *dev, int *host, int n) {
   return check_cuda(cudaStreamSynchronize(g->stream), "readback sync") ? MR_ERR_CUDA : MR_OK;
 }
 
-int adapt_iteration(mr_grid *g, int crit, double er, double ec, int flags, int *nch, bool incremental) {
+int adapt_iteration(mr_grid *g, int crit, double er, double ec, int flags, int *nch) {
   *nch = 0;
-  const int n = g->nleaf, G = adapt_shell(g->desc.wav_N, g->desc.wav_Nt), cap = g->desc.capacity;
+  const int n = g->nleaf, G = adapt_shell(g->desc.wav_N, g->desc.wav_Nt);
   cudaStream_t st = g->stream;
   void *Pv;
   int Gi;
-  // Incremental criterion (second and later iterations of one mr_adapt): a
-  // leaf's block norm depends on the field within two neighbour rings (its
-  // padded block reads its neighbours and the fine-to-coarse values of its
-  // finer neighbours, which read theirs), so only leaves within two rings of
-  // what the previous iteration changed are filled and evaluated; the others
-  // keep the norm carried from that iteration -- the same bits, since their
-  // inputs are unchanged and a repeated substitution is bitwise idempotent.
-  const bool incr = incremental && g->incr_ready;
-  g->incr_ready = 0;
-  const int *cneed = incr ? g->cneed : nullptr, *cfill = incr ? g->cneed + cap : nullptr;
   // 1-2: ghosts of the criterion field, block criterion
-  int e = launch_ghost(g, field_ptr(g, crit), field_ptr(g, crit), G, true, &Pv, &Gi, nullptr, cfill);
+  int e = launch_ghost(g, field_ptr(g, crit), field_ptr(g, crit), G, true, &Pv, &Gi);
   if (e) return e;
   const double *P = (const double *)Pv;
-  e = launch_criterion(g, P, Gi, g->maxdet, cneed, g->mdcarry);
+  e = launch_criterion(g, P, Gi, g->maxdet);
   if (e) return e;
   // the norms this iteration decides with (mr_last_block_norms)
   if (check_cuda(cudaMemcpyAsync(g->mdlast, g->maxdet, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, st),
@@ -782,8 +722,8 @@ int adapt_iteration(mr_grid *g, int crit, double er, double ec, int flags, int *
     // substitution next to coarser leaves, which overwrites their values
     // (later iterations: only where its inputs may have changed)
     for (int fid = 0; fid < g->desc.nfields; ++fid) {
-      if (fid == crit || field_substituted(g, fid)) continue;  // nothing would change
-      e = launch_substitute(g, field_ptr(g, fid), cneed);
+      if (fid == crit) continue;
+      e = launch_substitute(g, field_ptr(g, fid));
       if (e) return e;
     }
     return MR_OK;
@@ -807,52 +747,34 @@ int adapt_iteration(mr_grid *g, int crit, double er, double ec, int flags, int *
   }
   int *nmask = g->cmask + g->desc.capacity;  // second half of the mask buffer
   int *hasD = g->hasD;
-  // block norms of unchanged leaves carried to the new slots (before maxdet
-  // becomes scratch below)
-  MR_LAUNCH(g, MRK_MISC, k_carry<<<(nn + tb - 1) / tb, tb, 0, st>>>(nn, g->newsrc, g->maxdet, g->mdcarry));
   // leaves whose ghosts the other fields need (statuses are final; maxdet and
   // scan are free from here on)
   int *nb1 = reinterpret_cast<int *>(g->maxdet), *need2 = nb1 + g->desc.capacity, *need = g->scan;
   MR_LAUNCH(g, MRK_MISC, k_need1<<<nblk, tb, 0, st>>>(t, g->status, nb1));
   MR_LAUNCH(g, MRK_MISC, k_need2<<<nblk, tb, 0, st>>>(t, g->status, nb1, need));
-  MR_LAUNCH(g, MRK_MISC, k_need3<<<nblk, tb, 0, st>>>(t, need, cneed, cneed ? 2 : 1, need2));
-  // fields the previous adaptation left substituted for this tree (and that
-  // nothing wrote since) need no substitution in the first iteration: only
-  // the leaves their interpolation and update read, and the finer leaves
-  // pushing into those (in the second half of cneed, free until the rings)
-  int *need2_min = nullptr;
-  if (!incr) {
-    bool any_clean = false;
-    for (int f = 0; f < g->desc.nfields; ++f) any_clean |= f != crit && field_substituted(g, f);
-    if (any_clean) {
-      need2_min = g->cneed + cap;
-      MR_LAUNCH(g, MRK_MISC, k_need3<<<nblk, tb, 0, st>>>(t, need, nullptr, 0, need2_min));
-    }
-  }
+  MR_LAUNCH(g, MRK_MISC, k_need3<<<nblk, tb, 0, st>>>(t, need, need2));
   MR_LAUNCH(g, MRK_UPDATE, k_newmask<<<(nn + tb - 1) / tb, tb, 0, st>>>(tn, g->newsrc, nmask));
-  // 6-9: every field: ghosts (criterion field first: P is current), interpolate, update
+  // 6-9: every field: ghosts (criterion field first: P is current), interpolate, update.
+  // Alg. SM3 step 1 ghost-fills every field, so the substitution next to
+  // coarser leaves overwrites every field; the padded blocks themselves are
+  // read only by the interpolation and update of the leaves in need2.  The
+  // other fields therefore take (A) the adaptation-shell fill of the need2
+  // leaves, without writing substituted values back, and (B) the
+  // substitution-only pass of every leaf next to a coarser leaf (its padded
+  // blocks in the side buffer, free here), which writes them back; both read
+  // the field as it was, like one full ghost fill.
   const bool f32 = g->desc.precision == MR_F32;
   for (int pass = 0; pass < g->desc.nfields; ++pass) {
     const int fid = pass == 0 ? crit : (pass <= crit ? pass - 1 : pass);
-    if (pass > 0 || incr) {  // incremental: the criterion fill covered fewer leaves
-      const int *nd = (pass > 0 && need2_min && field_substituted(g, fid)) ? need2_min : need2;
-      e = launch_ghost(g, field_ptr(g, fid), field_ptr(g, fid), G, true, &Pv, &Gi, nullptr, nd);
+    if (pass > 0) {
+      e = launch_ghost(g, field_ptr(g, fid), nullptr, G, true, &Pv, &Gi, nullptr, need2);
+      if (!e) e = launch_substitute(g, field_ptr(g, fid), nullptr, true);
       if (e) return e;
       P = (const double *)Pv;
     }
     e = f32 ? interp_dispatch<float>(g, t, tn, P, Gi, fid, nmask, hasD)
             : interp_dispatch<double>(g, t, tn, P, Gi, fid, nmask, hasD);
     if (e) return e;
-  }
-  // leaves of the new tree whose block norm the next iteration recomputes:
-  // two rings around the changed leaves, and the fill set that needs (their
-  // finer neighbours push fine-to-coarse values into them)
-  {
-    const int nblk2 = (nn + tb - 1) / tb;
-    MR_LAUNCH(g, MRK_MISC, k_dirty<<<nblk2, tb, 0, st>>>(nn, g->newsrc, hasD, nb1));
-    MR_LAUNCH(g, MRK_MISC, k_ring<<<nblk2, tb, 0, st>>>(tn, nb1, need2));
-    MR_LAUNCH(g, MRK_MISC, k_ring<<<nblk2, tb, 0, st>>>(tn, need2, g->cneed));
-    MR_LAUNCH(g, MRK_MISC, k_pushers<<<nblk2, tb, 0, st>>>(tn, g->cneed, g->cneed + cap));
   }
   // swap to the new tree and pool
   g->cur = nx;
@@ -864,9 +786,7 @@ int adapt_iteration(mr_grid *g, int crit, double er, double ec, int flags, int *
   g->refined = g->refined2;
   g->refined2 = tmp;
   *nch = changed;
-  if (check_cuda(cudaGetLastError(), "adapt")) return MR_ERR_CUDA;
-  g->incr_ready = 1;
-  return MR_OK;
+  return check_cuda(cudaGetLastError(), "adapt") ? MR_ERR_CUDA : MR_OK;
 }
 
 }  // namespace mr

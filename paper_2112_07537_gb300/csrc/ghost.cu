@@ -1060,21 +1060,24 @@ int launch_prep32(mr_grid *g, const void *phi, int *Gi) {
 // half-width) computes the padded block, substitutes the band in FP64 and
 // the substituted values are written back to the field -- the field values a
 // full ghost fill leaves, without the padded blocks of the other leaves.
-int launch_substitute(mr_grid *g, void *phi, const int *need) {
+int launch_substitute(mr_grid *g, void *phi, const int *need, bool in_side_buffer) {
   const int N = g->desc.wav_N, Nt = g->desc.wav_Nt, nb = g->desc.nb;
   const int G = N - 1, gi = internal_shell(N, Nt, G, nb);
   if (gi > g->shell_ad || (g->desc.flags & MR_GRID_FIXED_TREE)) return MR_ERR_UNSUPPORTED;
+  // the padded blocks go to the side buffer when the main one must survive
+  // (the pass pushes nothing, so the other buffer is only passed along)
+  double *Pb = in_side_buffer ? g->padQ64 : g->padP64, *Qb = in_side_buffer ? g->padP64 : g->padQ64;
   int e;
   if (g->desc.precision == MR_F32) {
-    e = ghost_dispatch<float, double>(g, (const float *)phi, nullptr, G, g->padP64, g->padQ64, gi, 2, need);
+    e = ghost_dispatch<float, double>(g, (const float *)phi, nullptr, G, Pb, Qb, gi, 2, need);
     if (!e)
       MR_LAUNCH(g, MRK_MERGE, k_writeback<float, double><<<g->nleaf, 256, 0, g->stream>>>(
-                                  nb, g->padP64, gi, g->cmask, (float *)phi, need));
+                                  nb, Pb, gi, g->cmask, (float *)phi, need));
   } else {
-    e = ghost_dispatch<double, double>(g, (const double *)phi, nullptr, G, g->padP64, g->padQ64, gi, 2, need);
+    e = ghost_dispatch<double, double>(g, (const double *)phi, nullptr, G, Pb, Qb, gi, 2, need);
     if (!e)
       MR_LAUNCH(g, MRK_MERGE, k_writeback<double, double><<<g->nleaf, 256, 0, g->stream>>>(
-                                  nb, g->padP64, gi, g->cmask, (double *)phi, need));
+                                  nb, Pb, gi, g->cmask, (double *)phi, need));
   }
   if (e) return e;
   return check_cuda(cudaGetLastError(), "k_writeback") ? MR_ERR_CUDA : MR_OK;

@@ -441,13 +441,7 @@ struct mr_grid {
   int *cmask;             // per-leaf coarse-direction masks (ghost fill), then new-band masks
   int *hasD;              // per new leaf: the update step has discarded details
   int *pneed;             // per leaf: 1 = left to the full ghost pre-pass (has a coarser neighbour)
-  // incremental criterion inside one mr_adapt call: block norms carried to
-  // the next tree (mdcarry), the leaves whose norm must be recomputed and the
-  // leaves whose ghost fill that needs (cneed[0..cap), cneed[cap..2cap))
-  double *mdcarry;
-  double *mdlast;         // block norms the last iteration decided with
-  int *cneed;
-  int incr_ready;         // mdcarry / cneed describe the current tree
+  double *mdlast;         // block norms the last adaptation iteration decided with
   int nleaf_last;         // leaves of the tree mdlast belongs to
   void *vpad;             // ghost-filled velocity components (shell 3), 3 * cap * (nb+6)^3
   int tree_version;       // bumped whenever the leaves change
@@ -479,10 +473,9 @@ struct mr_grid {
   int gkey_len;
   long long graph_replays;
   int autotune;           // tune launch shapes at first use (mr_autotune)
-  // field_subst[f] = tree_version while field f holds exactly the values the
-  // adaptation's ghost fill leaves (every band next to a coarser leaf
-  // substituted in FP64 for the current tree), -1 once anything may have
-  // written it; a repeated substitution would give the same bits
+  // field_subst[f] = tree_version while field f holds the values a converged
+  // mr_adapt left (every band next to a coarser leaf substituted in FP64 for
+  // the current tree), -1 once anything may have written it
   int field_subst[32];
 };
 namespace mr {
@@ -540,7 +533,7 @@ int launch_crop(mr_grid *g, const void *P, int Gi, void *out, int G, bool fp64_s
 int launch_crop64(mr_grid *g, const double *P, int Gi, double *out, int G);
 int launch_prep32(mr_grid *g, const void *phi, int *Gi);
 int launch_writeback32(mr_grid *g, int Gi, void *phi);
-int launch_substitute(mr_grid *g, void *phi, const int *need = nullptr);
+int launch_substitute(mr_grid *g, void *phi, const int *need = nullptr, bool in_side_buffer = false);
 int launch_fused(mr_grid *g, const void *phi, const void *P, const void *Q, int Gi, const void *u, void *out,
                  int stage, double dt, const double *uc, int scheme, bool rhs_only, const void *vpad = nullptr);
 int adapt_shell(int N, int Nt);
@@ -553,9 +546,8 @@ int launch_field_set(mr_grid *g, void *f, int kind, const double *p, int np);
 int launch_mass(mr_grid *g, const void *f, double *host_out);
 int launch_dt(mr_grid *g, double cfl, const double *uc, const void *const *vel, double *host_out);
 // adapt.cu
-int launch_criterion(mr_grid *g, const double *P64, int Gi, double *maxdet, const int *need = nullptr,
-                     const double *carry = nullptr);
-int adapt_iteration(mr_grid *g, int crit_fid, double er, double ec, int flags, int *nch, bool incremental);
+int launch_criterion(mr_grid *g, const double *P64, int Gi, double *maxdet);
+int adapt_iteration(mr_grid *g, int crit_fid, double er, double ec, int flags, int *nch);
 int build_map(mr_grid *g);
 int check_balance(mr_grid *g);
 }  // namespace mr
