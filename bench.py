@@ -47,9 +47,9 @@ UNIT = "PSU/s"
 WORKLOADS = {"fixed-large": (0.35, 0.25, 0.17, 0.11, 0.06),   # 42 400 leaves, 586 M points
              "fixed-medium": (0.35, 0.25, 0.17),              # 11 768 leaves, 163 M points
              "fixed-small": (0.3, 0.2)}                       # 3 424 leaves, 47 M points
-# large single grid scalar: ~570 leaves per Gaussian, so 70 give the ~40 000
+# large single grid scalar: ~535 leaves per Gaussian, so 75 give the ~40 000
 # leaves (~550 M points) of the large configuration
-GAUSS = dict(seed=5, n=70, smin=0.0015, smax=0.006)
+GAUSS = dict(seed=5, n=75, smin=0.0015, smax=0.006)
 # the same adaptive path on a small grid (for profiler captures of a few GB)
 GAUSS_SMALL = dict(seed=5, n=3, smin=0.0015, smax=0.006)
 EPS_R, EPS_C, CFL, ADAPT_EVERY = 1e-5, 1e-7, 0.5, 2
