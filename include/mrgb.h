@@ -98,6 +98,16 @@ typedef struct {
 #define MR_GRID_FIXED_TREE 1
 #define MR_GRID_VELOCITY 2 /* reserve the ghost-filled velocity cache used by
                               mr_step_vel / mr_rhs_advect_vel              */
+/* Every tree of the forest is its own periodic domain: a batch of
+ * independent grids (one per tree, each with its own leaves, fields and
+ * adaptation) advanced together -- every call is one launch per phase over
+ * the leaves of all of them.  2:1 balance, ghosts, neighbours and the
+ * adaptation policy never cross a tree boundary; each tree wraps onto
+ * itself.  mr_field_set evaluates its analytic fields in every tree's own
+ * coordinates [0, tree_len)^3.  The paper has no counterpart (its instances
+ * are separate runs); each tree computes exactly what a one-tree grid with
+ * the same leaves and values computes. */
+#define MR_GRID_INDEPENDENT_TREES 4
 
 typedef struct {
   int nleaf;

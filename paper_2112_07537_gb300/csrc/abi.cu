@@ -57,6 +57,7 @@ Tree tree_view(const mr_grid *g) {
   t.anc = g->anc[g->cur];
   t.map = g->maps[g->cur];
   t.tree_len = g->desc.tree_len;
+  t.indep = (g->desc.flags & MR_GRID_INDEPENDENT_TREES) ? 1 : 0;
   return t;
 }
 

@@ -215,7 +215,7 @@ __global__ void k_policy(Tree t, const int8_t *__restrict__ sin, int8_t *__restr
           int g[3];
           for (int d = 0; d < 3; ++d)
             g[d] = dd[d] < 0 ? base[d] - 1 : dd[d] > 0 ? base[d] + span : base[d] + cc[d] * (span / 2);
-          const int o = owner(t, Ls, g[0], g[1], g[2]);
+          const int o = owner(t, Ls, g[0], g[1], g[2], b);
           if (o == b) continue;
           const int Lo = __ldg(t.lev + o), so = sin[o];
           if (Lo > L && so == ST_FINER) raise = true;
@@ -228,7 +228,7 @@ __global__ void k_policy(Tree t, const int8_t *__restrict__ sin, int8_t *__restr
     for (int c = 0; c < 8 && ns == ST_COARSER; ++c) {
       int a[3];
       for (int d = 0; d < 3; ++d) a[d] = (__ldg(t.anc + 3 * b + d) & ~1) + ((c >> d) & 1);
-      const int o = owner(t, L, a[0] * nb, a[1] * nb, a[2] * nb);
+      const int o = owner(t, L, a[0] * nb, a[1] * nb, a[2] * nb, b);
       const bool leaf = __ldg(t.lev + o) == L && __ldg(t.anc + 3 * o) == a[0] &&
                         __ldg(t.anc + 3 * o + 1) == a[1] && __ldg(t.anc + 3 * o + 2) == a[2];
       if (!leaf || sin[o] != ST_COARSER) ns = ST_SAME;
@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(512) k_interp(Tree to, const int *__restrict__
       const int c = threadIdx.x;
       int a[3];
       for (int d = 0; d < 3; ++d) a[d] = __ldg(to.anc + 3 * s + d) + ((c >> d) & 1);
-      chs[c] = owner(to, L, a[0] * nb, a[1] * nb, a[2] * nb);
+      chs[c] = owner(to, L, a[0] * nb, a[1] * nb, a[2] * nb, s);
     }
     __syncthreads();
     for (int p = threadIdx.x; p < (int)nb3; p += blockDim.x) {
@@ -404,7 +404,7 @@ __global__ void k_newmask(Tree tn, const int *src, int *nmask) {
       const int dd[3] = {m % 3 - 1, (m / 3) % 3 - 1, m / 9 - 1};
       int g[3];
       for (int d = 0; d < 3; ++d) g[d] = __ldg(tn.anc + 3 * q + d) * nb + (dd[d] < 0 ? -1 : dd[d] > 0 ? nb : 0);
-      const int o = owner(tn, L, g[0], g[1], g[2]);
+      const int o = owner(tn, L, g[0], g[1], g[2], q);
       if (__ldg(tn.lev + o) == L - 1 && src[2 * o] == KIND_PARENT) mask |= 1 << m;
     }
   }
@@ -437,7 +437,7 @@ __global__ void __launch_bounds__(1024) k_update_gamma(Tree tn, const int *__res
     const int dd[3] = {r % 3 - 1, (r / 3) % 3 - 1, r / 9 - 1};
     int g[3];
     for (int d = 0; d < 3; ++d) g[d] = __ldg(tn.anc + 3 * q + d) * nb + (dd[d] < 0 ? -1 : dd[d] > 0 ? nb : 0);
-    const int o = owner(tn, L, g[0], g[1], g[2]);
+    const int o = owner(tn, L, g[0], g[1], g[2], q);
     const int Lo = __ldg(tn.lev + o), ko = src[2 * o];
     int v = 0;
     if (Lo == L - 1 && ko == KIND_PARENT) v = -1;
@@ -575,7 +575,7 @@ __device__ __forceinline__ void for_each_nbr(const Tree &t, int b, F f) {
           int g[3];
           for (int d = 0; d < 3; ++d)
             g[d] = dd[d] < 0 ? base[d] - 1 : dd[d] > 0 ? base[d] + span : base[d] + cc[d] * (span / 2);
-          const int o = owner(t, Ls, g[0], g[1], g[2]);
+          const int o = owner(t, Ls, g[0], g[1], g[2], b);
           if (o != b) f(o);
         }
   }

@@ -44,10 +44,10 @@ __device__ __forceinline__ TI leaf_value(const Tree &t, const TI *phi, int o, in
 // Zero-detail refinement at level-L point g from the level-(L-1) values
 // (J^s on even, K^s on odd coordinates; taps landing on details skipped).
 template <typename TI, typename TP, int N, int NT>
-__device__ TP refine_point(const Tree &t, const TI *phi, int L, int gx, int gy, int gz, int *err) {
+__device__ TP refine_point(const Tree &t, const TI *phi, int L, int gx, int gy, int gz, int *err, int hb) {
   return refine_dispatch<N, NT, TP>(gx & 1, gy & 1, gz & 1, [&](int ox, int oy, int oz) -> TP {
     const int qx = (gx + ox) / 2, qy = (gy + oy) / 2, qz = (gz + oz) / 2;
-    const int o = owner(t, L - 1, qx, qy, qz);
+    const int o = owner(t, L - 1, qx, qy, qz, hb);
     if (__ldg(t.lev + o) < L - 1) {
       atomicOr(err, 2);
       return TP(0);
@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(512, sizeof(TP) == 4 ? 2 : 1) k_prep(Tree t, c
     int g[3];
     for (int d = 0; d < 3; ++d)
       g[d] = __ldg(t.anc + 3 * b + d) * nb + (dd[d] < 0 ? -1 : dd[d] > 0 ? nb : 0);
-    const int o = owner(t, L, g[0], g[1], g[2]);
+    const int o = owner(t, L, g[0], g[1], g[2], b);
     const int Lo = __ldg(t.lev + o);
     rslot[r] = o, rlev[r] = Lo;
     for (int d = 0; d < 3; ++d) ranc[r][d] = __ldg(t.anc + 3 * o + d);
@@ -287,12 +287,12 @@ __global__ void __launch_bounds__(512, sizeof(TP) == 4 ? 2 : 1) k_prep(Tree t, c
         // coarse leaf: level-(L-1) index of the point, relative to its anchor
         const int gq[3] = {(ax + fi) / 2, (ay + fj) / 2, (az + fk) / 2};
         int l[3];
-        for (int d = 0; d < 3; ++d) l[d] = pwrap(gq[d] - ranc[r][d] * nb, npts(t, L - 1, d));
+        for (int d = 0; d < 3; ++d) l[d] = pwrap(gq[d] - ranc[r][d] * nb, period(t, L - 1, d));
         return ld(phi + (size_t)o * nb3 + l[0] + nb * (l[1] + nb * l[2]));
       }
     }
     const int gx = (Lq == L ? ax : ax / 2) + i, gy = (Lq == L ? ay : ay / 2) + j, gz = (Lq == L ? az : az / 2) + k;
-    const int o = owner(t, Lq, gx, gy, gz);
+    const int o = owner(t, Lq, gx, gy, gz, b);
     if (__ldg(t.lev + o) < Lq) return TI(__int_as_float(0x7fc00000));
     return leaf_value(t, phi, o, Lq, gx, gy, gz, err);
   };
@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(512, sizeof(TP) == 4 ? 2 : 1) k_prep(Tree t, c
         const int Lo = rlev[r];
         if (Lo == L - 1) {
           if (tile) continue;
-          v = refine_point<TI, TP, N, NT>(t, phi, L, ax + i, ay + j, az + k, err);
+          v = refine_point<TI, TP, N, NT>(t, phi, L, ax + i, ay + j, az + k, err, b);
         } else if (Lo >= L) {
           v = fetch(L, i, j, k);  // copy, or the coincident value of a finer leaf
         } else {
@@ -686,7 +686,7 @@ __global__ void __launch_bounds__(512, sizeof(TP) == 4 ? 2 : 1) k_prep(Tree t, c
         int cand[3][3], ncand[3];
         bool any = true;
         for (int d = 0; d < 3; ++d) {
-          const int Pn = npts(t, L - 1, d);
+          const int Pn = period(t, L - 1, d);
           const int off = pwrap(G[d] - __ldg(t.anc + 3 * c + d) * nb, Pn);
           ncand[d] = 0;
           for (int sh = -1; sh <= 1; ++sh) {
@@ -745,7 +745,7 @@ __global__ void __launch_bounds__(512) k_fill_plain(Tree t, const TI *__restrict
     const int dd[3] = {r % 3 - 1, (r / 3) % 3 - 1, r / 9 - 1};
     int g[3];
     for (int d = 0; d < 3; ++d) g[d] = __ldg(t.anc + 3 * b + d) * nb + (dd[d] < 0 ? -1 : dd[d] > 0 ? nb : 0);
-    const int o = owner(t, L, g[0], g[1], g[2]);
+    const int o = owner(t, L, g[0], g[1], g[2], b);
     const int Lo = __ldg(t.lev + o);
     rslot[r] = o, rlev[r] = Lo;
     if (r != 13 && Lo < L) atomicOr(&coarse, 1);
@@ -764,7 +764,7 @@ __global__ void __launch_bounds__(512) k_fill_plain(Tree t, const TI *__restrict
       const int dd[3] = {r % 3 - 1, (r / 3) % 3 - 1, r / 9 - 1};
       int g[3];
       for (int d = 0; d < 3; ++d) g[d] = 2 * (__ldg(t.anc + 3 * b + d) + dd[d]) * nb + ((h >> d) & 1) * nb;
-      o2 = owner(t, L + 1, g[0], g[1], g[2]);
+      o2 = owner(t, L + 1, g[0], g[1], g[2], b);
       if (o2 < 0 || o2 >= t.nleaf || __ldg(t.lev + o2) != L + 1) o2 = -1;
     }
     rsub[r][h] = o2;
@@ -797,7 +797,7 @@ __global__ void __launch_bounds__(512) k_fill_plain(Tree t, const TI *__restrict
       } else if (idx == -1 && Lo > L) {
         // a finer region two levels down (shells wider than half a block)
         const int gx = ax + i, gy = ay + j, gz = az + k;
-        const int o = owner(t, L, gx, gy, gz);
+        const int o = owner(t, L, gx, gy, gz, b);
         v = Cvt<TP>::f(leaf_value(t, phi, o, L, gx, gy, gz, err));
       } else {
         atomicOr(err, 1 << 16);
@@ -853,7 +853,7 @@ __global__ void __launch_bounds__(512) k_merge(Tree t, TP *__restrict__ P, const
     const int dd[3] = {r % 3 - 1, (r / 3) % 3 - 1, r / 9 - 1};
     int g[3];
     for (int d = 0; d < 3; ++d) g[d] = __ldg(t.anc + 3 * b + d) * nb + (dd[d] < 0 ? -1 : dd[d] > 0 ? nb : 0);
-    rfin[r] = r != 13 && __ldg(t.lev + owner(t, L, g[0], g[1], g[2])) > L;
+    rfin[r] = r != 13 && __ldg(t.lev + owner(t, L, g[0], g[1], g[2], b)) > L;
   }
   __syncthreads();
   for (int r = 0; r < 27; ++r) {

@@ -362,6 +362,7 @@ struct Tree {
   const int *anc; // [3*slot + d], anchor at the leaf's own level
   const int *map; // mdim[0]*mdim[1]*mdim[2]
   double tree_len;
+  int indep;      // every tree is its own periodic domain (independent grids)
 };
 
 __device__ __forceinline__ int pwrap(int g, int P) {
@@ -372,19 +373,34 @@ __device__ __forceinline__ int pwrap(int g, int P) {
 // points along dimension d at level L
 __device__ __forceinline__ int npts(const Tree &t, int L, int d) { return (t.nt[d] * t.nb) << L; }
 
-// slot owning level-L point g (any integers; wrapped periodically)
-__device__ __forceinline__ int owner(const Tree &t, int L, int gx, int gy, int gz) {
+// Level-L point g along dimension d wrapped into the periodic domain of leaf
+// hb: the whole forest, or -- independent trees -- hb's own tree.
+__device__ __forceinline__ int wrap_pt(const Tree &t, int L, int g, int d, int hb) {
+  if (!t.indep) return pwrap(g, npts(t, L, d));
+  const int P = t.nb << L;  // points of one tree along d at level L
+  const int T = __ldg(t.anc + 3 * hb + d) >> __ldg(t.lev + hb);
+  return T * P + pwrap(g - T * P, P);
+}
+
+// period of the domain of leaf hb along d at level L
+__device__ __forceinline__ int period(const Tree &t, int L, int d) {
+  return t.indep ? (t.nb << L) : npts(t, L, d);
+}
+
+// slot owning level-L point g (any integers; wrapped periodically into the
+// domain of leaf hb, the leaf whose neighbourhood is being read)
+__device__ __forceinline__ int owner(const Tree &t, int L, int gx, int gy, int gz, int hb) {
   const int s = t.M - L;
-  int cx = (pwrap(gx, npts(t, L, 0)) << s) / t.nb;
-  int cy = (pwrap(gy, npts(t, L, 1)) << s) / t.nb;
-  int cz = (pwrap(gz, npts(t, L, 2)) << s) / t.nb;
+  int cx = (wrap_pt(t, L, gx, 0, hb) << s) / t.nb;
+  int cy = (wrap_pt(t, L, gy, 1, hb) << s) / t.nb;
+  int cz = (wrap_pt(t, L, gz, 2, hb) << s) / t.nb;
   return __ldg(t.map + cx + t.mdim[0] * (cy + t.mdim[1] * cz));
 }
 
 // local index (in leaf o, level Lo >= L... or grid point of a coarser leaf)
 // of level-L point g along dimension d; returns -1 if not a grid point.
 __device__ __forceinline__ int local_index(const Tree &t, int o, int Lo, int L, int g, int d) {
-  int gg = pwrap(g, npts(t, L, d));
+  int gg = wrap_pt(t, L, g, d, o);
   int q;
   if (Lo >= L) {
     q = gg << (Lo - L);

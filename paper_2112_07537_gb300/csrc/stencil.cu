@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(1024) k_fused(Tree t, const float *__restrict_
     const int ax = f >> 1, sg = (f & 1) ? 1 : -1;
     int g0[3] = {a[0], a[1], a[2]};
     g0[ax] += sg < 0 ? -1 : nb;
-    const int o = owner(t, L, g0[0], g0[1], g0[2]);
+    const int o = owner(t, L, g0[0], g0[1], g0[2], b);
     const int Lo = __ldg(t.lev + o);
     // slab index ranges (block-local, level L)
     int lo[3] = {0, 0, 0}, ext[3] = {nb, nb, nb};
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(1024) k_fused(Tree t, const float *__restrict_
         float v;
         if (NT == 0) {
           const int gx = a[0] + c[0], gy = a[1] + c[1], gz = a[2] + c[2];
-          const int of = owner(t, L, gx, gy, gz);
+          const int of = owner(t, L, gx, gy, gz, b);
           const int Lf = __ldg(t.lev + of);
           const int lx = local_index(t, of, Lf, L, gx, 0), ly = local_index(t, of, Lf, L, gy, 1),
                     lz = local_index(t, of, Lf, L, gz, 2);
@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(1024) k_fused(Tree t, const float *__restrict_
       for (int p = threadIdx.x; p < nqt; p += blockDim.x) {
         const int qx = a[0] / 2 + q0[0] + p % nqd[0], qy = a[1] / 2 + q0[1] + (p / nqd[0]) % nqd[1],
                   qz = a[2] / 2 + q0[2] + p / (nqd[0] * nqd[1]);
-        const int oc = owner(t, L - 1, qx, qy, qz);
+        const int oc = owner(t, L - 1, qx, qy, qz, b);
         const int Lc = __ldg(t.lev + oc);
         float v = __int_as_float(0x7fc00000);
         if (Lc >= L - 1) {
@@ -456,11 +456,17 @@ __global__ void k_field_set(Tree t, T *f, int kind, InitParams ip) {
   const int b = blockIdx.x, nb = t.nb;
   const int L = __ldg(t.lev + b);
   const double h = t.tree_len / ((double)nb * (double)(1 << L));
-  const double ext[3] = {t.nt[0] * t.tree_len, t.nt[1] * t.tree_len, t.nt[2] * t.tree_len};
+  // independent trees: every tree holds the field in its own coordinates
+  const double ext[3] = {(t.indep ? 1 : t.nt[0]) * t.tree_len, (t.indep ? 1 : t.nt[1]) * t.tree_len,
+                         (t.indep ? 1 : t.nt[2]) * t.tree_len};
+  int a[3];
+  for (int d = 0; d < 3; ++d) {
+    a[d] = __ldg(t.anc + 3 * b + d);
+    if (t.indep) a[d] &= (1 << L) - 1;  // anchor within the leaf's tree
+  }
   for (int p = threadIdx.x; p < nb * nb * nb; p += blockDim.x) {
     const int i = p % nb, j = (p / nb) % nb, k = p / (nb * nb);
-    const double x[3] = {(__ldg(t.anc + 3 * b) * nb + i) * h, (__ldg(t.anc + 3 * b + 1) * nb + j) * h,
-                         (__ldg(t.anc + 3 * b + 2) * nb + k) * h};
+    const double x[3] = {(a[0] * nb + i) * h, (a[1] * nb + j) * h, (a[2] * nb + k) * h};
     double v = 0.0;
     if (kind == MR_INIT_GAUSSIAN) {
       double r2 = 0.0;

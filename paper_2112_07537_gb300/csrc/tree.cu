@@ -61,7 +61,7 @@ __global__ void k_check_balance(Tree t, int *err) {
             else if (dd[d] > 0) g[d] = base[d] + span;
             else g[d] = base[d] + cc[d] * (span / 2);  // one point per adjacent child cell
           }
-          const int o = owner(t, Ls, g[0], g[1], g[2]);
+          const int o = owner(t, Ls, g[0], g[1], g[2], b);
           const int Lo = __ldg(t.lev + o);
           if (Lo > L + 1 || Lo < L - 1) atomicOr(err, 256);
         }

@@ -273,3 +273,18 @@ def tree_shell(nt, tree_len, base, top, radius, widths, centre=(0.5, 0.5, 0.5)):
         lev, anc = refine_leaves(lev, anc, hit)
         lev, anc = balance_fast(nt, lev, anc)
     return lev, anc
+
+
+# --------------------------------------------------- independent-tree batch
+def batch_leaves(per_tree, nt):
+    """Leaves of a batch of independent one-tree grids laid out as the trees
+    of an nt[0] x nt[1] x nt[2] forest: per_tree[k] = (lev, anc) of grid k
+    (anchors within its own tree), tree k at (k % nt0, (k // nt0) % nt1,
+    k // (nt0 nt1)).  Returns (lev, anc, tree index of every leaf)."""
+    ls, as_, ts = [], [], []
+    for k, (lev, anc) in enumerate(per_tree):
+        t = np.array([k % nt[0], (k // nt[0]) % nt[1], k // (nt[0] * nt[1])], np.int64)
+        ls.append(np.asarray(lev, np.int32))
+        as_.append((np.asarray(anc, np.int64) + t[None, :] * (1 << np.asarray(lev, np.int64))[:, None]).astype(np.int32))
+        ts.append(np.full(len(lev), k, np.int32))
+    return np.concatenate(ls), np.concatenate(as_), np.concatenate(ts)

@@ -23,6 +23,7 @@ ADAPT_REFINE, ADAPT_COARSEN = 1, 2
 INIT_COMPACT_GAUSSIAN, INIT_DEFORMATION, INIT_GAUSSIAN_SUM_ADD = 4, 5, 6
 GRID_FIXED_TREE = 1
 GRID_VELOCITY = 2
+GRID_INDEPENDENT_TREES = 4
 NUM_KERNELS = 18
 
 # every entry point include/mrgb.h declares
@@ -159,7 +160,7 @@ class Grid:
 
     def __init__(self, ntree, tree_len, nb, lmin, lmax, N, Nt, lev, anc, precision=F32,
                  nfields=1, capacity=None, device="cuda", stream=None, fixed_tree=False,
-                 velocity=False):
+                 velocity=False, independent_trees=False):
         import torch
         L = load()
         lev = np.ascontiguousarray(lev, np.int32)
@@ -174,7 +175,8 @@ class Grid:
         d.tree_len, d.nb, d.lmin, d.lmax = float(tree_len), nb, lmin, lmax
         d.wav_N, d.wav_Nt, d.precision, d.nfields, d.capacity = N, Nt, precision, nfields, cap
         d.stream = s.cuda_stream
-        d.flags = (GRID_FIXED_TREE if fixed_tree else 0) | (GRID_VELOCITY if velocity else 0)
+        d.flags = ((GRID_FIXED_TREE if fixed_tree else 0) | (GRID_VELOCITY if velocity else 0) |
+                   (GRID_INDEPENDENT_TREES if independent_trees else 0))
         self.desc = d
         nbytes = C.c_size_t()
         _chk(L.mr_workspace_size(C.byref(d), C.byref(nbytes)))
