@@ -125,6 +125,98 @@ def init_deformation(mrgb, stream, prec, cap, wav):
     return g
 
 
+# batched uneven instances: 64 independent periodic grids (trees of a 4x4x4
+# forest in independent-tree mode), blocks of 16^3, levels 1-5, 1-3 seeded
+# Gaussians each (sigma U[0.05, 0.2], centres U[0, 1]^3), a constant velocity
+# of unit norm per grid (held in the three velocity fields), 4.2 lifted
+# wavelet, FP32, one eps for all grids (their block counts differ through
+# their fields)
+BATCH = dict(ngrid=64, nt=(4, 4, 4), nb=16, lmin=1, lmax=5, seed=11, eps_r=1e-3, eps_c=1e-5)
+
+
+def batch_specs():
+    rng = np.random.default_rng(BATCH["seed"])
+    specs = []
+    for _ in range(BATCH["ngrid"]):
+        nblob = int(rng.integers(1, 4))
+        blobs = [(rng.uniform(0, 1, 3), rng.uniform(0.05, 0.2)) for _ in range(nblob)]
+        u = rng.normal(size=3)
+        specs.append((blobs, u / np.linalg.norm(u)))
+    return specs
+
+
+def batch_fields(g, specs):
+    """Host-evaluated fields of every tree in its own coordinates (scalar:
+    sum of the tree's Gaussians, nearest periodic image; velocity: the
+    tree's constant)."""
+    lev, anc, _ = g.leaves()
+    nt, nb = BATCH["nt"], BATCH["nb"]
+    tree = (anc[:, 0] >> lev) + nt[0] * ((anc[:, 1] >> lev) + nt[1] * (anc[:, 2] >> lev))
+    loc = anc - np.stack([tree % nt[0], (tree // nt[0]) % nt[1], tree // (nt[0] * nt[1])], 1) * \
+        (1 << lev)[:, None]
+    xyz = I.point_coords((1, 1, 1), 1.0, nb, lev, loc)
+    phi = np.zeros((len(lev), nb, nb, nb), np.float32)
+    vel = [np.zeros_like(phi) for _ in range(3)]
+    for k, (blobs, u) in enumerate(specs):
+        sel = np.nonzero(tree == k)[0]
+        if not len(sel):
+            continue
+        sub = [a[sel] for a in xyz]
+        acc = np.zeros((len(sel), nb, nb, nb))
+        for c, sg in blobs:
+            acc += I.gaussian(sub, tuple(c), sg)
+        phi[sel] = acc
+        for d in range(3):
+            vel[d][sel] = u[d]
+    return phi, vel
+
+
+def init_batched(mrgb, stream, prec, cap):
+    """Initial grids of the batch (untimed): uniform at lmin, alternate
+    sampling and refinement until no block refines, sample, one full
+    adaptation."""
+    nt = BATCH["nt"]
+    lev, anc = I.uniform_leaves(nt, BATCH["lmin"])
+    g = mrgb.Grid(nt, 1.0, BATCH["nb"], BATCH["lmin"], BATCH["lmax"], 4, 2, lev, anc, precision=prec,
+                  nfields=4, capacity=cap, stream=stream, velocity=True, independent_trees=True)
+    specs = batch_specs()
+    for _ in range(12):
+        phi, _ = batch_fields(g, specs)
+        g.field_copy_in(0, phi)
+        if g.adapt_iter(0, BATCH["eps_r"], BATCH["eps_c"], flags=mrgb.ADAPT_REFINE) == 0:
+            break
+    phi, vel = batch_fields(g, specs)
+    g.field_copy_in(0, phi)
+    for d in range(3):
+        g.field_copy_in(1 + d, vel[d])
+    g.adapt(0, BATCH["eps_r"], BATCH["eps_c"])
+    return g
+
+
+def split_batch(mrgb, stream, g):
+    """The grids of a batch as separate one-tree grids (same leaves, same
+    field values), for the sequential comparison."""
+    lev, anc, _ = g.leaves()
+    nt, nb = BATCH["nt"], BATCH["nb"]
+    tree = (anc[:, 0] >> lev) + nt[0] * ((anc[:, 1] >> lev) + nt[1] * (anc[:, 2] >> lev))
+    loc = anc - np.stack([tree % nt[0], (tree // nt[0]) % nt[1], tree // (nt[0] * nt[1])], 1) * \
+        (1 << lev)[:, None]
+    vals = [g.field_copy_out(f) for f in range(4)]
+    out = []
+    for k in range(BATCH["ngrid"]):
+        sel = np.nonzero(tree == k)[0]
+        s = mrgb.Grid((1, 1, 1), 1.0, nb, BATCH["lmin"], BATCH["lmax"], 4, 2, lev[sel], loc[sel],
+                      precision=g.precision, nfields=4, capacity=max(64, 4 * len(sel)), stream=stream,
+                      velocity=True)
+        sl, sa, _ = s.leaves()
+        pos = {(int(l), tuple(int(x) for x in a)): i for i, (l, a) in enumerate(zip(lev[sel], loc[sel]))}
+        order = np.array([sel[pos[(int(l), tuple(int(x) for x in a))]] for l, a in zip(sl, sa)])
+        for f in range(4):
+            s.field_copy_in(f, np.ascontiguousarray(vals[f][order]))
+        out.append(s)
+    return out
+
+
 def clocks_sampler(stop, out):
     cmd = ["nvidia-smi", "--query-gpu=clocks.sm,clocks.max.sm,power.draw,"
            "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -264,6 +356,9 @@ def make_grid(args, mrgb, stream, prec, cap):
         if args.workload in ("large", "adaptive-small"):
             g = init_large(mrgb, stream, prec, cap, GAUSS if args.workload == "large" else GAUSS_SMALL)
             return g, 8, 2.0 * TG[0]  # |u| + |v| <= 2 s for the Taylor-Green-like field
+        if args.workload == "batched":
+            # one dt for the batch: sum_d |u_d| <= sqrt(3) for unit velocities
+            return init_batched(mrgb, stream, prec, min(cap, 60000)), BATCH["lmax"], 3 ** 0.5
         lev, anc = workload_tree(args.workload)
         lmax = int(lev.max())
         g = mrgb.Grid((1, 1, 1), 1.0, nb, 3, lmax, 6, 2, lev, anc, precision=prec,
@@ -279,9 +374,10 @@ class Stepper:
     def __init__(self, args, mrgb, g, lmax, umax):
         self.args, self.mrgb, self.g = args, mrgb, g
         self.scheme = {"wenoz5": mrgb.WENOZ5, "cons5": mrgb.CONS5, "cons3": mrgb.CONS3}[args.scheme]
-        self.adaptive = args.workload in ("large", "adaptive-small")
+        self.adaptive = args.workload in ("large", "adaptive-small", "batched")
+        self.eps = (BATCH["eps_r"], BATCH["eps_c"]) if args.workload == "batched" else (EPS_R, EPS_C)
         self.deform = args.workload == "deformation"
-        self.nb = 24
+        self.nb = BATCH["nb"] if args.workload == "batched" else 24
         self.umax = umax
         self.dt = CFL * (1.0 / (self.nb * 2 ** lmax)) / umax
         if args.diffusion:
@@ -310,7 +406,7 @@ class Stepper:
         elif self.adaptive:
             g.step_vel(0, self.dt, (1, 2, 3), self.scheme)
             if (i + 1) % ADAPT_EVERY == 0:
-                g.adapt(0, EPS_R, EPS_C)
+                g.adapt(0, *self.eps)
         else:
             g.step(0, self.dt, U, self.scheme)
         return 3 * pts
@@ -373,7 +469,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) measurement")
     ap.add_argument("--no-autotune", action="store_true", help="default launch shapes (no autotuner)")
     ap.add_argument("--workload", default="large",
-                    choices=["large", "adaptive-small", "deformation"] + sorted(WORKLOADS))
+                    choices=["large", "adaptive-small", "deformation", "batched"] + sorted(WORKLOADS))
     ap.add_argument("--wavelet", default="4.2", choices=["2.2", "4.2", "6.2", "4.0", "6.0"],
                     help="wavelet of the deformation workload")
     ap.add_argument("--capacity", type=int, default=60000)
@@ -398,8 +494,9 @@ def main():
 
     W = max(3, args.warmup)
     prec = mrgb.F32 if args.precision == "f32" else mrgb.F64
-    nb = 24
-    adaptive = args.workload in ("large", "adaptive-small")
+    batched = args.workload == "batched"
+    nb = BATCH["nb"] if batched else 24
+    adaptive = args.workload in ("large", "adaptive-small", "batched")
     deform = args.workload == "deformation"
     stream = torch.cuda.Stream()
     g, lmax, umax = make_grid(args, mrgb, stream, prec, args.capacity)
@@ -488,6 +585,14 @@ def main():
                     f"{args.wavelet} wavelet, eps_r {DEFORM['eps_r']}, eps_c {DEFORM['eps_r'] / DEFORM['ratio']}, "
                     f"{args.scheme} + RK3, CFL {DEFORM['cfl']} on the finest spacing present, adapt every "
                     f"{DEFORM['adapt_every']} steps; {stats0.nleaf}->{stats1.nleaf} leaves, t = {step.state['t']:.4f}")
+    elif batched:
+        workload = (f"batched uneven instances: {BATCH['ngrid']} independent periodic grids (trees of a "
+                    f"{BATCH['nt']} forest, each its own domain) advanced with one launch per phase, 16^3 blocks, "
+                    f"levels {BATCH['lmin']}-{BATCH['lmax']}, {stats0.nleaf}->{stats1.nleaf} leaves in all, "
+                    f"{mean_pts / 1e6:.1f} M points; per grid 1-3 seeded Gaussians (sigma U[0.05,0.2]) and a "
+                    f"constant unit velocity (seed {BATCH['seed']}); 4.2 lifted wavelet, eps_r {BATCH['eps_r']}, "
+                    f"eps_c {BATCH['eps_c']}; {args.scheme} + RK3, CFL {CFL}, one dt for the batch; adapt every "
+                    f"{ADAPT_EVERY} steps")
     elif adaptive:
         workload = (f"{args.workload} single grid, adaptive: 1 tree, 24^3 blocks, levels "
                     f"{stats0.min_level}-{stats0.max_level} (lmin 3, lmax 8), {stats0.nleaf}->{stats1.nleaf} "
@@ -541,7 +646,33 @@ def main():
             tf = mean_pts * fl / sec / 1e12
             line["roofline_stage_kernel"]["compute"] = {"flops_per_point_stage": fl, "achieved_tflops": tf,
                                                         "peak_tflops": cpk[key], "frac": tf / cpk[key]}
-    if adaptive and prec == mrgb.F32 and not args.no_fp64:
+    if batched:
+        # the same grids as separate one-tree grids, stepped one after another
+        # (same steps, same adaptations): what batching saves
+        per_grid = g.query().count_per_level
+        singles = split_batch(mrgb, stream, g)
+        del g
+        steppers = [Stepper(args, mrgb, s_, BATCH["lmax"], 3 ** 0.5) for s_ in singles]
+        for st_ in steppers:
+            st_.dt = step.dt
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        psu_seq = 0
+        e0.record(stream)
+        for _ in range(args.steps):
+            for st_ in steppers:
+                psu_seq += st_()
+        e1.record(stream)
+        e1.synchronize()
+        ms_seq = e0.elapsed_time(e1)
+        counts = sorted(s_.nleaf for s_ in singles)
+        line["sequential"] = {"value": psu_seq / (ms_seq / 1e3), "unit": UNIT, "ms_per_step": ms_seq / args.steps,
+                              "grids": len(singles), "leaves_per_grid": {"min": counts[0], "max": counts[-1],
+                                                                         "median": counts[len(counts) // 2]},
+                              "gpu_launches": sum(s_.launch_count() for s_ in singles)}
+        line["batched_over_sequential"] = psu / line["sequential"]["value"]
+        del per_grid
+    if adaptive and not batched and prec == mrgb.F32 and not args.no_fp64:
         # the plain FP64 form on the same workload and GPU: free the FP32 grid
         del step, g
         torch.cuda.synchronize()

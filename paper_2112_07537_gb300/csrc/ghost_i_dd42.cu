@@ -1,0 +1,8 @@
+// ghost_i_dd42.cu -- the ghost kernels instantiated for double fields, double
+// padded blocks and the 4.2 wavelet, compiled on their own so that the
+// instantiations build in parallel.
+#include "ghost_kernels.cuh"
+
+namespace mr {
+template int ghost_impl<double, double, 4, 2>(mr_grid *, const double *, double *, int, double *, double *, int, int, const int *);
+}  // namespace mr

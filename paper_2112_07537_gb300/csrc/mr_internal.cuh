@@ -540,7 +540,13 @@ bool operator<(const TuneKey &a, const TuneKey &b);
 int tune_threads(mr_grid *g, const TuneKey &key, const int *cand, int ncand,
                  const std::function<void(int)> &launch);
 
-// ghost.cu
+// ghost.cu / ghost_kernels.cuh (ghost_impl instantiated in ghost_i_*.cu)
+template <typename TI, typename TP, int N, int NT>
+int ghost_impl(mr_grid *g, const TI *phi_in, TI *phi_out, int G, TP *P, TP *Q, int Gi, int only_coarse,
+               const int *need);
+template <typename TI, typename TP>
+int ghost_dispatch(mr_grid *g, const TI *phi_in, TI *phi_out, int G, TP *P, TP *Q, int Gi, int only_coarse = 0,
+                   const int *need = nullptr);
 void count_units(mr_grid *g, int kid, const int *flags, int n, double bytes_per_unit,
                  const int *exclude = nullptr);
 int launch_ghost(mr_grid *g, const void *phi_in, void *phi_out, int G, bool fp64, void **P,
