@@ -296,9 +296,11 @@ int mr_velocity_invalidate(mr_grid *grid);
 int mr_step(mr_grid *grid, int phi_fid, double dt, const double *u_const, int scheme);
 
 /* Per-leaf max |detail| over the block and its coarse-region extension
- * (Sec. 2.2.5, eqs 2.24-2.26), computed in FP64 from the field as stored,
- * after a ghost fill with the adaptation shell.  maxdet: device array of
- * nleaf doubles.                                                           */
+ * (Sec. 2.2.5, eqs 2.24-2.26), from the field as stored after a ghost fill
+ * with the adaptation shell in FP64: evaluated in FP64 on FP64 grids and in
+ * float pairs (two FP32 numbers, about 48 significant bits, on the FP32
+ * pipe) on FP32 grids; either agrees with exact arithmetic to about 1e-14 of
+ * the field maximum.  maxdet: device array of nleaf doubles.               */
 int mr_criterion(mr_grid *grid, int fid, double *maxdet);
 
 /* Grid adaptation (Alg. SM3) of every field, driven by field crit_fid, run

@@ -121,16 +121,120 @@ __device__ __forceinline__ void detail_planes(const double *__restrict__ Pb, int
   }
 }
 
+// detail_planes in float pairs (about 48 significant bits) on the FP32 pipe:
+// the same lifting-form passes in the same order, each FP64 input split
+// once into a pair when its plane is staged in shared memory; gamma reaches
+// emit as a double.  |error| <= a few 2^-47 of the largest input, far inside
+// the 1e-12 tolerance of the block norms.
+template <int N, int NT, typename F>
+__device__ __forceinline__ void detail_planes_f2(const double *__restrict__ Pb, int nb, int Gi, F2 *sm, F emit) {
+  using W = Wav<N, NT>;
+  constexpr int ko = N - 1, R = 2 * ko + 1;
+  constexpr float U = NT ? 0.25f : 0.0f;  // lifting update weight
+  const int Wd = nb + 2 * Gi;
+  const int r0 = -W::ext_f, r1 = nb - 1 + W::ext_b, nR = r1 - r0 + 1, nA = nR + 2 * ko;
+  const int lo = -Gi, hi = nb - 1 + Gi;
+  const int nodd = par_count(r0, r1 + 1, 1), nev = nR - nodd;
+  const int fo = par_first(r0, 1), fe = par_first(r0, 0);
+  const size_t pl = (size_t)nR * nR;
+  F2 *ring = sm;              // [R][nR][nR]
+  F2 *dz = sm + R * pl;       // [2][nR][nR]
+  F2 *A = dz + 2 * pl;        // [nA][nR]
+  F2 *S = A + (size_t)nA * nR;  // [nA][nA] the staged plane (rows, columns r0-ko .. r1+ko)
+  auto gsum = [](const F2 *v, long stride) {
+    F2 s = v[0];
+#pragma unroll
+    for (int t = -ko; t <= ko; t += 2) s = f2_acc(s, -float(Wav<N, NT>::K(t)), v[t * stride]);
+    return f2_norm(s);
+  };
+  auto lift = [](F2 v, F2 a, F2 b) { return NT ? f2_norm(f2_acc(v, U, f2_add(a, b))) : v; };
+  for (int kk = r0 - ko; kk <= r1 + ko + 1; ++kk) {
+    const int slot = (kk - (r0 - ko)) % R;
+    const bool kin = kk >= lo && kk <= hi;
+    const double *pk = Pb + (size_t)(kk + Gi) * Wd * Wd;
+    // stage rows jj = r0-ko .. r1+ko of the plane, columns r0-ko .. r1+ko
+    for (int idx = threadIdx.x; idx < nA * nA; idx += blockDim.x) {
+      const int jj = r0 - ko + idx / nA, ii = r0 - ko + idx % nA;
+      const bool in = kin && jj >= lo && jj <= hi;
+      S[idx] = in ? f2_split(pk[(size_t)(jj + Gi) * Wd + (ii + Gi)]) : F2{0.f, 0.f};
+    }
+    __syncthreads();
+    // x pass: odd columns, then even columns
+    for (int idx = threadIdx.x; idx < nodd * nA; idx += blockDim.x) {
+      const int i = fo + 2 * (idx % nodd), jr = idx / nodd;
+      A[(i - r0) + nR * jr] = gsum(S + (size_t)jr * nA + (i - r0 + ko), 1);
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nev * nA; idx += blockDim.x) {
+      const int i = fe + 2 * (idx % nev), jr = idx / nev;
+      F2 *a = A + (i - r0) + nR * jr;
+      const F2 v = S[(size_t)jr * nA + (i - r0 + ko)];
+      *a = lift(v, a[-1], a[1]);
+    }
+    __syncthreads();
+    // y pass into ring plane kk: odd rows, then even rows
+    F2 *rp = ring + slot * pl;
+    for (int idx = threadIdx.x; idx < nR * nodd; idx += blockDim.x) {
+      const int ii = idx % nR, j = fo + 2 * (idx / nR);
+      rp[ii + nR * (j - r0)] = gsum(A + ii + nR * (j - (r0 - ko)), nR);
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nR * nev; idx += blockDim.x) {
+      const int ii = idx % nR, j = fe + 2 * (idx / nR);
+      F2 *r = rp + ii + nR * (j - r0);
+      *r = lift(A[ii + nR * (j - (r0 - ko))], r[-(long)nR], r[nR]);
+    }
+    __syncthreads();
+    // z: odd plane k1 = kk - ko, then the even plane k1 - 1
+    const int k1 = kk - ko;
+    if ((k1 & 1) && k1 >= r0 && k1 <= r1 + 1) {
+      const int s1 = (slot + ko + 1) % R;
+      F2 *d1 = dz + (((k1 - fo) >> 1) & 1) * pl, *d0 = dz + ((((k1 - fo) >> 1) + 1) & 1) * pl;
+      if (k1 <= r1) {
+        for (int idx = threadIdx.x; idx < (int)pl; idx += blockDim.x) {
+          const F2 *c = ring + idx;
+          F2 v = c[s1 * pl];
+#pragma unroll
+          for (int t = -ko; t <= ko; t += 2) {
+            int sl = s1 + t;
+            sl += sl < 0 ? R : 0;
+            sl -= sl >= R ? R : 0;
+            v = f2_acc(v, -float(Wav<N, NT>::K(t)), c[sl * pl]);
+          }
+          v = f2_norm(v);
+          d1[idx] = v;
+          emit(r0 + idx % nR, r0 + idx / nR, k1, idx, f2_dbl(v));
+        }
+      }
+      __syncthreads();
+      const int k0 = k1 - 1;
+      if (k0 >= r0 && k0 <= r1) {
+        const int s0 = s1 == 0 ? R - 1 : s1 - 1;
+        for (int idx = threadIdx.x; idx < (int)pl; idx += blockDim.x) {
+          const int i = r0 + idx % nR, j = r0 + idx / nR;
+          double v = 0.0;
+          if ((i | j) & 1) v = f2_dbl(lift(ring[s0 * pl + idx], d0[idx], d1[idx]));
+          emit(i, j, k0, idx, v);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // Per leaf: max |gamma| over the extended region (Sec. 2.3, the block norm
 // that drives refinement and coarsening).
-template <int N, int NT>
+template <int N, int NT, bool PAIRS>
 __global__ void __launch_bounds__(1024) k_criterion(Tree t, const double *__restrict__ P, int Gi,
                                                    double *__restrict__ maxdet) {
   const int b = blockIdx.x, nb = t.nb, Wd = nb + 2 * Gi;
   extern __shared__ double sm[];
   unsigned long long mx = 0;  // max |gamma| as an integer key (integer pipe)
-  detail_planes<N, NT>(P + (size_t)b * Wd * Wd * Wd, nb, Gi, sm,
-                       [&](int, int, int, int, double g) { mx = max(mx, abs_key(g)); });
+  auto emit = [&](int, int, int, int, double g) { mx = max(mx, abs_key(g)); };
+  if constexpr (PAIRS)
+    detail_planes_f2<N, NT>(P + (size_t)b * Wd * Wd * Wd, nb, Gi, reinterpret_cast<F2 *>(sm), emit);
+  else
+    detail_planes<N, NT>(P + (size_t)b * Wd * Wd * Wd, nb, Gi, sm, emit);
   // block max
   for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   __shared__ unsigned long long red[32];
@@ -150,21 +254,31 @@ static size_t crit_smem(int nb) {
   return sizeof(double) * ((size_t)(2 * ko + 3) * nR * nR + (size_t)nR * (nR + 2 * ko));
 }
 
-template <int N, int NT>
-static int criterion_impl(mr_grid *g, const double *P, int Gi, double *maxdet) {
-  const size_t sm = crit_smem<N, NT>(g->desc.nb);
+// FP32 grids evaluate the details in float pairs (FP32 pipe), FP64 grids in
+// FP64 (the plain form)
+template <int N, int NT, bool PAIRS>
+static int criterion_launch(mr_grid *g, const double *P, int Gi, double *maxdet) {
+  using W = Wav<N, NT>;
+  const int nR = g->desc.nb + W::ext_f + W::ext_b, nA = nR + 2 * (N - 1);
+  const size_t sm = crit_smem<N, NT>(g->desc.nb) + (PAIRS ? sizeof(F2) * (size_t)nA * nA : 0);
   if (sm > 227 * 1024) return MR_ERR_UNSUPPORTED;
-  if (check_cuda(cudaFuncSetAttribute(k_criterion<N, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (check_cuda(cudaFuncSetAttribute(k_criterion<N, NT, PAIRS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)sm),
                  "criterion smem"))
     return MR_ERR_CUDA;
   Tree t = tree_view(g);
   static const int cc[2] = {1024, 512};
-  const int th = tune_threads(g, TuneKey{2, N, NT, g->desc.nb, 8, Gi, 0}, cc, 2, [&](int thr) {
-    k_criterion<N, NT><<<g->nleaf, thr, sm, g->stream>>>(t, P, Gi, maxdet);
+  const int th = tune_threads(g, TuneKey{2, N, NT, g->desc.nb, PAIRS ? 5 : 8, Gi, 0}, cc, 2, [&](int thr) {
+    k_criterion<N, NT, PAIRS><<<g->nleaf, thr, sm, g->stream>>>(t, P, Gi, maxdet);
   });
-  MR_LAUNCH(g, MRK_CRITERION, k_criterion<N, NT><<<g->nleaf, th, sm, g->stream>>>(t, P, Gi, maxdet));
+  MR_LAUNCH(g, MRK_CRITERION, k_criterion<N, NT, PAIRS><<<g->nleaf, th, sm, g->stream>>>(t, P, Gi, maxdet));
   return check_cuda(cudaGetLastError(), "k_criterion") ? MR_ERR_CUDA : MR_OK;
+}
+
+template <int N, int NT>
+static int criterion_impl(mr_grid *g, const double *P, int Gi, double *maxdet) {
+  return g->desc.precision == MR_F32 ? criterion_launch<N, NT, true>(g, P, Gi, maxdet)
+                                     : criterion_launch<N, NT, false>(g, P, Gi, maxdet);
 }
 
 int launch_criterion(mr_grid *g, const double *P, int Gi, double *maxdet) {

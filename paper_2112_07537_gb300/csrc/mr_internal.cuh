@@ -131,6 +131,32 @@ __device__ __forceinline__ F2 f2_norm(F2 a) {
   return {s, __fadd_rn(a.l, -__fadd_rn(s, -a.h))};
 }
 __device__ __forceinline__ double f2_dbl(F2 a) { return __dadd_rn(widen(a.h), widen_ftz(a.l)); }
+// a + b (two-sum of the high parts, low parts added)
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
+  const float s = __fadd_rn(a.h, b.h);
+  const float bb = __fadd_rn(s, -a.h);
+  const float e = __fadd_rn(__fadd_rn(a.h, -__fadd_rn(s, -bb)), __fadd_rn(b.h, -bb));
+  return {s, __fadd_rn(__fadd_rn(a.l, b.l), e)};
+}
+// FP64 x as a float pair on the integer pipe: h = x truncated to 24
+// significant bits, l = the remainder truncated to 24 bits, so
+// |x - (h + l)| <= 2^-47 |x| + 2^-126 (values below the FP32 normal range
+// lose their remainder: an absolute error far below every tolerance here);
+// |x| >= 2^128, infinities and NaN go through the hardware conversion.
+__device__ __forceinline__ F2 f2_split(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned hw = (unsigned)(u >> 32), sgn = hw & 0x80000000u;
+  const int e = (int)((hw >> 20) & 0x7ffu) - 896;  // FP32 biased exponent
+  if (e <= 0) return {__uint_as_float(sgn), 0.f};
+  if (e >= 255) return {(float)x, 0.f};
+  const unsigned long long m = u & 0xfffffffffffffULL;  // 52 mantissa bits
+  const unsigned hi = sgn | ((unsigned)e << 23) | (unsigned)(m >> 29);
+  const unsigned r = (unsigned)(m & 0x1fffffffu);  // the 29 bits below: r * 2^(e - 179)
+  if (!r) return {__uint_as_float(hi), 0.f};
+  const int lz = __clz(r), le = e - 52 + (31 - lz);  // biased exponent of the remainder
+  if (le <= 0) return {__uint_as_float(hi), 0.f};
+  return {__uint_as_float(hi), __uint_as_float(sgn | ((unsigned)le << 23) | (((r << lz) >> 8) & 0x7fffffu))};
+}
 
 // value of the field element type TI in the working precision TP
 template <typename TP>
