@@ -78,6 +78,14 @@ extern "C" {
 /* adaptation flags */
 #define MR_ADAPT_REFINE 1
 #define MR_ADAPT_COARSEN 2
+/* FP32 grids: adapt the fields other than the criterion field with FP64
+ * arithmetic (their ghost fill, refinement, coarsening and update step, as
+ * the criterion field's).  Without it they run in FP32 (padded blocks,
+ * wavelet sums and the update's details in FP32): their values then differ
+ * from exact arithmetic by a few FP32 roundings of the field maximum, while
+ * the criterion field and every refine/coarsen decision stay as with the
+ * flag.  No effect on FP64 grids.                                         */
+#define MR_ADAPT_OTHERS_FP64 4
 
 typedef struct {
   int ntree[3];     /* trees per direction (the forest tiles the domain)   */
@@ -305,7 +313,9 @@ int mr_criterion(mr_grid *grid, int fid, double *maxdet);
 
 /* Grid adaptation (Alg. SM3) of every field, driven by field crit_fid, run
  * until no leaf changes (at most 64 iterations, else MR_ERR_TIMEOUT).
- * flags: MR_ADAPT_REFINE | MR_ADAPT_COARSEN.  Synchronises once per
+ * flags: MR_ADAPT_REFINE | MR_ADAPT_COARSEN, optionally | MR_ADAPT_OTHERS_FP64
+ * (the criterion field always adapts in FP64 arithmetic; the other fields of
+ * an FP32 grid in FP32 unless that flag is given).  Synchronises once per
  * iteration; *n_changed (may be NULL) receives the total number of leaves
  * that refined or coarsened.                                               */
 int mr_adapt(mr_grid *grid, int crit_fid, double eps_refine, double eps_coarsen, int flags,

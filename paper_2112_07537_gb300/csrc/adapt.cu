@@ -24,60 +24,61 @@ enum { ST_COARSER = -1, ST_SAME = 0, ST_FINER = 1 };
 // The z-planes of the y-pass results live in a ring of 2(N-1)+1 planes and the
 // z-details of the last two odd planes in a second ring.  emit(i, j, k, idx,
 // gamma) is called once per point of the region (idx = i-r0 + nR*(j-r0)).
-template <int N, int NT, typename F>
-__device__ __forceinline__ void detail_planes(const double *__restrict__ Pb, int nb, int Gi, double *sm,
-                                              F emit) {
+// T: the padded blocks' type and the working precision.
+template <int N, int NT, typename T, typename F>
+__device__ __forceinline__ void detail_planes(const T *__restrict__ Pb, int nb, int Gi, T *sm, F emit) {
   using W = Wav<N, NT>;
   constexpr int ko = N - 1, R = 2 * ko + 1;
-  constexpr double U = NT ? 0.25 : 0.0;  // lifting update weight
+  constexpr T U = NT ? T(0.25) : T(0);  // lifting update weight
   const int Wd = nb + 2 * Gi;
   const int r0 = -W::ext_f, r1 = nb - 1 + W::ext_b, nR = r1 - r0 + 1, nA = nR + 2 * ko;
   const int lo = -Gi, hi = nb - 1 + Gi;  // stored padded range
   const int nodd = par_count(r0, r1 + 1, 1), nev = nR - nodd;
   const int fo = par_first(r0, 1), fe = par_first(r0, 0);
-  const size_t pl = (size_t)nR * nR;
-  double *ring = sm;             // [R][nR][nR]  y-pass planes
-  double *dz = sm + R * pl;      // [2][nR][nR]  z-details of odd planes
-  double *A = dz + 2 * pl;       // [nA][nR]     x-pass of one plane
+  const int pl = nR * nR;
+  const DivM dO = divm(nodd), dE = divm(nev), dR = divm(nR);
+  T *ring = sm;             // [R][nR][nR]  y-pass planes
+  T *dz = sm + R * pl;      // [2][nR][nR]  z-details of odd planes
+  T *A = dz + 2 * pl;       // [nA][nR]     x-pass of one plane
   // G^a output: v[0] - sum_{t odd} K(t) v[t*stride]
-  auto gsum = [](const double *v, long stride) {
-    double s = v[0];
+  auto gsum = [](const T *v, int stride) {
+    T s = v[0];
 #pragma unroll
-    for (int t = -ko; t <= ko; t += 2) s = fma(-Wav<N, NT>::K(t), v[t * stride], s);
+    for (int t = -ko; t <= ko; t += 2) s = racc(s, T(-Wav<N, NT>::K(t)), v[t * stride]);
     return s;
   };
   for (int kk = r0 - ko; kk <= r1 + ko + 1; ++kk) {
     const int slot = (kk - (r0 - ko)) % R;
     const bool kin = kk >= lo && kk <= hi;
-    const double *pk = Pb + (size_t)(kk + Gi) * Wd * Wd;
+    const T *pk = Pb + (size_t)(kk + Gi) * Wd * Wd;
     // x pass: odd columns, then even columns (rows jj = r0-ko .. r1+ko)
     for (int idx = threadIdx.x; idx < nodd * nA; idx += blockDim.x) {
-      const int i = fo + 2 * (idx % nodd), jj = r0 - ko + idx / nodd;
+      const int q = divq(idx, dO), i = fo + 2 * (idx - q * nodd), jj = r0 - ko + q;
       const bool in = kin && jj >= lo && jj <= hi;
-      A[(i - r0) + nR * (jj - (r0 - ko))] = in ? gsum(pk + (size_t)(jj + Gi) * Wd + (i + Gi), 1) : 0.0;
+      A[(i - r0) + nR * (jj - (r0 - ko))] = in ? gsum(pk + (jj + Gi) * Wd + (i + Gi), 1) : T(0);
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < nev * nA; idx += blockDim.x) {
-      const int i = fe + 2 * (idx % nev), jj = r0 - ko + idx / nev;
+      const int q = divq(idx, dE), i = fe + 2 * (idx - q * nev), jj = r0 - ko + q;
       const bool in = kin && jj >= lo && jj <= hi;
-      double *a = A + (i - r0) + nR * (jj - (r0 - ko));
-      double v = in ? pk[(size_t)(jj + Gi) * Wd + (i + Gi)] : 0.0;
-      if (NT) v = fma(U, a[-1] + a[1], v);
+      T *a = A + (i - r0) + nR * (jj - (r0 - ko));
+      T v = in ? pk[(jj + Gi) * Wd + (i + Gi)] : T(0);
+      if (NT) v = racc(v, U, a[-1] + a[1]);
       *a = v;
     }
     __syncthreads();
     // y pass into ring plane kk: odd rows, then even rows
-    double *rp = ring + slot * pl;
+    T *rp = ring + slot * pl;
     for (int idx = threadIdx.x; idx < nR * nodd; idx += blockDim.x) {
-      const int ii = idx % nR, j = fo + 2 * (idx / nR);
+      const int q = divq(idx, dR), ii = idx - q * nR, j = fo + 2 * q;
       rp[ii + nR * (j - r0)] = gsum(A + ii + nR * (j - (r0 - ko)), nR);
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < nR * nev; idx += blockDim.x) {
-      const int ii = idx % nR, j = fe + 2 * (idx / nR);
-      double *r = rp + ii + nR * (j - r0);
-      double v = A[ii + nR * (j - (r0 - ko))];
-      if (NT) v = fma(U, r[-(long)nR] + r[nR], v);
+      const int q = divq(idx, dR), ii = idx - q * nR, j = fe + 2 * q;
+      T *r = rp + ii + nR * (j - r0);
+      T v = A[ii + nR * (j - (r0 - ko))];
+      if (NT) v = racc(v, U, r[-nR] + r[nR]);
       *r = v;
     }
     __syncthreads();
@@ -86,32 +87,34 @@ __device__ __forceinline__ void detail_planes(const double *__restrict__ Pb, int
     const int k1 = kk - ko;
     if ((k1 & 1) && k1 >= r0 && k1 <= r1 + 1) {
       const int s1 = (slot + ko + 1) % R;  // ring slot of plane k1
-      double *d1 = dz + (((k1 - fo) >> 1) & 1) * pl, *d0 = dz + ((((k1 - fo) >> 1) + 1) & 1) * pl;
+      T *d1 = dz + (((k1 - fo) >> 1) & 1) * pl, *d0 = dz + ((((k1 - fo) >> 1) + 1) & 1) * pl;
       if (k1 <= r1) {
-        for (int idx = threadIdx.x; idx < (int)pl; idx += blockDim.x) {
-          const double *c = ring + idx;
-          double v = c[s1 * pl];
+        for (int idx = threadIdx.x; idx < pl; idx += blockDim.x) {
+          const T *c = ring + idx;
+          T v = c[s1 * pl];
 #pragma unroll
           for (int t = -ko; t <= ko; t += 2) {
             int sl = s1 + t;
             sl += sl < 0 ? R : 0;
             sl -= sl >= R ? R : 0;
-            v = fma(-Wav<N, NT>::K(t), c[sl * pl], v);
+            v = racc(v, T(-Wav<N, NT>::K(t)), c[sl * pl]);
           }
           d1[idx] = v;
-          emit(r0 + idx % nR, r0 + idx / nR, k1, idx, v);
+          const int q = divq(idx, dR);
+          emit(r0 + idx - q * nR, r0 + q, k1, idx, v);
         }
       }
       __syncthreads();
       const int k0 = k1 - 1;
       if (k0 >= r0 && k0 <= r1) {
         const int s0 = s1 == 0 ? R - 1 : s1 - 1;
-        for (int idx = threadIdx.x; idx < (int)pl; idx += blockDim.x) {
-          const int i = r0 + idx % nR, j = r0 + idx / nR;
-          double v = 0.0;
+        for (int idx = threadIdx.x; idx < pl; idx += blockDim.x) {
+          const int q = divq(idx, dR);
+          const int i = r0 + idx - q * nR, j = r0 + q;
+          T v = T(0);
           if ((i | j) & 1) {
             v = ring[s0 * pl + idx];
-            if (NT) v = fma(U, d0[idx] + d1[idx], v);
+            if (NT) v = racc(v, U, d0[idx] + d1[idx]);
           }
           emit(i, j, k0, idx, v);
         }
@@ -125,7 +128,8 @@ __device__ __forceinline__ void detail_planes(const double *__restrict__ Pb, int
 // the same lifting-form passes in the same order, each FP64 input split
 // once into a pair when its plane is staged in shared memory; gamma reaches
 // emit as a double.  |error| <= a few 2^-47 of the largest input, far inside
-// the 1e-12 tolerance of the block norms.
+// the 1e-12 tolerance of the block norms.  Index arithmetic in 32 bits with
+// multiply-high divisions (the planes are the kernel's whole work).
 template <int N, int NT, typename F>
 __device__ __forceinline__ void detail_planes_f2(const double *__restrict__ Pb, int nb, int Gi, F2 *sm, F emit) {
   using W = Wav<N, NT>;
@@ -136,53 +140,56 @@ __device__ __forceinline__ void detail_planes_f2(const double *__restrict__ Pb, 
   const int lo = -Gi, hi = nb - 1 + Gi;
   const int nodd = par_count(r0, r1 + 1, 1), nev = nR - nodd;
   const int fo = par_first(r0, 1), fe = par_first(r0, 0);
-  const size_t pl = (size_t)nR * nR;
-  F2 *ring = sm;              // [R][nR][nR]
-  F2 *dz = sm + R * pl;       // [2][nR][nR]
-  F2 *A = dz + 2 * pl;        // [nA][nR]
-  F2 *S = A + (size_t)nA * nR;  // [nA][nA] the staged plane (rows, columns r0-ko .. r1+ko)
-  auto gsum = [](const F2 *v, long stride) {
+  const int pl = nR * nR;
+  const DivM dA = divm(nA), dO = divm(nodd), dE = divm(nev), dR = divm(nR);
+  F2 *ring = sm;             // [R][nR][nR]
+  F2 *dz = sm + R * pl;      // [2][nR][nR]
+  F2 *A = dz + 2 * pl;       // [nA][nR]
+  F2 *S = A + nA * nR;       // [nA][nA] the staged plane (rows, columns r0-ko .. r1+ko)
+  auto gsum = [](const F2 *v, int stride) {
     F2 s = v[0];
 #pragma unroll
     for (int t = -ko; t <= ko; t += 2) s = f2_acc(s, -float(Wav<N, NT>::K(t)), v[t * stride]);
     return f2_norm(s);
   };
   auto lift = [](F2 v, F2 a, F2 b) { return NT ? f2_norm(f2_acc(v, U, f2_add(a, b))) : v; };
+  // first column / row of the staged plane inside the stored padded range
+  const int c0 = r0 - ko;
   for (int kk = r0 - ko; kk <= r1 + ko + 1; ++kk) {
     const int slot = (kk - (r0 - ko)) % R;
     const bool kin = kk >= lo && kk <= hi;
     const double *pk = Pb + (size_t)(kk + Gi) * Wd * Wd;
     // stage rows jj = r0-ko .. r1+ko of the plane, columns r0-ko .. r1+ko
     for (int idx = threadIdx.x; idx < nA * nA; idx += blockDim.x) {
-      const int jj = r0 - ko + idx / nA, ii = r0 - ko + idx % nA;
+      const int jr = divq(idx, dA), ir = idx - jr * dA.d;
+      const int jj = c0 + jr, ii = c0 + ir;
       const bool in = kin && jj >= lo && jj <= hi;
-      S[idx] = in ? f2_split(pk[(size_t)(jj + Gi) * Wd + (ii + Gi)]) : F2{0.f, 0.f};
+      S[idx] = in ? f2_split(pk[(jj + Gi) * Wd + (ii + Gi)]) : F2{0.f, 0.f};
     }
     __syncthreads();
     // x pass: odd columns, then even columns
     for (int idx = threadIdx.x; idx < nodd * nA; idx += blockDim.x) {
-      const int i = fo + 2 * (idx % nodd), jr = idx / nodd;
-      A[(i - r0) + nR * jr] = gsum(S + (size_t)jr * nA + (i - r0 + ko), 1);
+      const int jr = divq(idx, dO), i = fo + 2 * (idx - jr * dO.d);
+      A[(i - r0) + nR * jr] = gsum(S + jr * nA + (i - r0 + ko), 1);
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < nev * nA; idx += blockDim.x) {
-      const int i = fe + 2 * (idx % nev), jr = idx / nev;
+      const int jr = divq(idx, dE), i = fe + 2 * (idx - jr * dE.d);
       F2 *a = A + (i - r0) + nR * jr;
-      const F2 v = S[(size_t)jr * nA + (i - r0 + ko)];
-      *a = lift(v, a[-1], a[1]);
+      *a = lift(S[jr * nA + (i - r0 + ko)], a[-1], a[1]);
     }
     __syncthreads();
     // y pass into ring plane kk: odd rows, then even rows
     F2 *rp = ring + slot * pl;
     for (int idx = threadIdx.x; idx < nR * nodd; idx += blockDim.x) {
-      const int ii = idx % nR, j = fo + 2 * (idx / nR);
+      const int q = divq(idx, dR), ii = idx - q * nR, j = fo + 2 * q;
       rp[ii + nR * (j - r0)] = gsum(A + ii + nR * (j - (r0 - ko)), nR);
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < nR * nev; idx += blockDim.x) {
-      const int ii = idx % nR, j = fe + 2 * (idx / nR);
+      const int q = divq(idx, dR), ii = idx - q * nR, j = fe + 2 * q;
       F2 *r = rp + ii + nR * (j - r0);
-      *r = lift(A[ii + nR * (j - (r0 - ko))], r[-(long)nR], r[nR]);
+      *r = lift(A[ii + nR * (j - (r0 - ko))], r[-nR], r[nR]);
     }
     __syncthreads();
     // z: odd plane k1 = kk - ko, then the even plane k1 - 1
@@ -191,7 +198,7 @@ __device__ __forceinline__ void detail_planes_f2(const double *__restrict__ Pb, 
       const int s1 = (slot + ko + 1) % R;
       F2 *d1 = dz + (((k1 - fo) >> 1) & 1) * pl, *d0 = dz + ((((k1 - fo) >> 1) + 1) & 1) * pl;
       if (k1 <= r1) {
-        for (int idx = threadIdx.x; idx < (int)pl; idx += blockDim.x) {
+        for (int idx = threadIdx.x; idx < pl; idx += blockDim.x) {
           const F2 *c = ring + idx;
           F2 v = c[s1 * pl];
 #pragma unroll
@@ -203,15 +210,17 @@ __device__ __forceinline__ void detail_planes_f2(const double *__restrict__ Pb, 
           }
           v = f2_norm(v);
           d1[idx] = v;
-          emit(r0 + idx % nR, r0 + idx / nR, k1, idx, f2_dbl(v));
+          const int q = divq(idx, dR);
+          emit(r0 + idx - q * nR, r0 + q, k1, idx, f2_dbl(v));
         }
       }
       __syncthreads();
       const int k0 = k1 - 1;
       if (k0 >= r0 && k0 <= r1) {
         const int s0 = s1 == 0 ? R - 1 : s1 - 1;
-        for (int idx = threadIdx.x; idx < (int)pl; idx += blockDim.x) {
-          const int i = r0 + idx % nR, j = r0 + idx / nR;
+        for (int idx = threadIdx.x; idx < pl; idx += blockDim.x) {
+          const int q = divq(idx, dR);
+          const int i = r0 + idx - q * nR, j = r0 + q;
           double v = 0.0;
           if ((i | j) & 1) v = f2_dbl(lift(ring[s0 * pl + idx], d0[idx], d1[idx]));
           emit(i, j, k0, idx, v);
@@ -247,11 +256,12 @@ __global__ void __launch_bounds__(1024) k_criterion(Tree t, const double *__rest
   }
 }
 
+// plane ring, z-detail ring and x-pass plane of detail_planes (elements of es bytes)
 template <int N, int NT>
-static size_t crit_smem(int nb) {
+static size_t crit_smem(int nb, size_t es = sizeof(double)) {
   using W = Wav<N, NT>;
   const int nR = nb + W::ext_f + W::ext_b, ko = N - 1;
-  return sizeof(double) * ((size_t)(2 * ko + 3) * nR * nR + (size_t)nR * (nR + 2 * ko));
+  return es * ((size_t)(2 * ko + 3) * nR * nR + (size_t)nR * (nR + 2 * ko));
 }
 
 // FP32 grids evaluate the details in float pairs (FP32 pipe), FP64 grids in
@@ -438,10 +448,11 @@ __global__ void k_emit(int n, int M, const int8_t *st, const int *pos, const int
 
 // ------------------------------------------------------ interpolation
 // New leaf values: copy, zero-detail refinement of the parent's padded block
-// (J^s / K^s), or tensor H^a coarsening of the 8 children's padded blocks.
-template <typename TO, int N, int NT>
+// (J^s / K^s), or tensor H^a coarsening of the 8 children's padded blocks,
+// in the padded blocks' precision TP.
+template <typename TO, typename TP, int N, int NT>
 __global__ void __launch_bounds__(512) k_interp(Tree to, const int *__restrict__ src,
-                                                const double *__restrict__ P, int Gi,
+                                                const TP *__restrict__ P, int Gi,
                                                 const TO *__restrict__ fold, TO *__restrict__ fnew) {
   using W = Wav<N, NT>;
   const int q = blockIdx.x, nb = to.nb, Wd = nb + 2 * Gi;
@@ -455,11 +466,11 @@ __global__ void __launch_bounds__(512) k_interp(Tree to, const int *__restrict__
     for (int p = threadIdx.x; p < (int)nb3; p += blockDim.x) out[p] = fold[(size_t)s * nb3 + p];
   } else if (kind == KIND_CHILD) {
     const int par = s >> 3, ch = s & 7;
-    const double *Pp = P + (size_t)par * np;
+    const TP *Pp = P + (size_t)par * np;
     for (int p = threadIdx.x; p < (int)nb3; p += blockDim.x) {
       const int i = p % nb, j = (p / nb) % nb, k = p / (nb * nb);
       const int f[3] = {(ch & 1) * nb + i, ((ch >> 1) & 1) * nb + j, ((ch >> 2) & 1) * nb + k};
-      const double acc = refine_dispatch<N, NT, double>(f[0] & 1, f[1] & 1, f[2] & 1, [&](int ox, int oy, int oz) {
+      const TP acc = refine_dispatch<N, NT, TP>(f[0] & 1, f[1] & 1, f[2] & 1, [&](int ox, int oy, int oz) {
         return Pp[pidx((f[0] + ox) / 2, (f[1] + oy) / 2, (f[2] + oz) / 2)];
       });
       out[p] = TO(acc);
@@ -484,8 +495,8 @@ __global__ void __launch_bounds__(512) k_interp(Tree to, const int *__restrict__
         ch |= cd << d;
         loc[d] = f[d] - cd * nb;
       }
-      const double *Pc = P + (size_t)chs[ch] * np;
-      const double acc = coarsen_sum<N, NT, double>([&](int tx, int ty, int tz) {
+      const TP *Pc = P + (size_t)chs[ch] * np;
+      const TP acc = coarsen_sum<N, NT, TP>([&](int tx, int ty, int tz) {
         return Pc[pidx(loc[0] + tx, loc[1] + ty, loc[2] + tz)];
       });
       out[p] = TO(acc);
@@ -532,11 +543,11 @@ __global__ void k_newmask(Tree tn, const int *src, int *nmask) {
 // around F are classified once: a newly coarsened leaf one level coarser owns
 // all of D in its region, an unchanged same-level leaf with newly coarsened
 // neighbours owns the part of its band next to them, finer leaves none.
-template <int N, int NT>
+template <typename TP, int N, int NT>
 __global__ void __launch_bounds__(1024) k_update_gamma(Tree tn, const int *__restrict__ src,
                                                       const int *__restrict__ nmask,
-                                                      const double *__restrict__ P, int Gi,
-                                                      double *__restrict__ Q, int *hasD) {
+                                                      const TP *__restrict__ P, int Gi,
+                                                      TP *__restrict__ Q, int *hasD) {
   using W = Wav<N, NT>;
   const int q = blockIdx.x;
   if (src[2 * q] != KIND_COPY) return;
@@ -564,9 +575,10 @@ __global__ void __launch_bounds__(1024) k_update_gamma(Tree tn, const int *__res
     if (threadIdx.x == 0) hasD[q] = 0;
     return;
   }
-  double *Qb = Q + (size_t)s * np;
-  extern __shared__ double sm[];
-  detail_planes<N, NT>(P + (size_t)s * np, nb, Gi, sm, [&](int i, int j, int k, int, double g) {
+  TP *Qb = Q + (size_t)s * np;
+  extern __shared__ double smd[];
+  TP *sm = reinterpret_cast<TP *>(smd);
+  detail_planes<N, NT, TP>(P + (size_t)s * np, nb, Gi, sm, [&](int i, int j, int k, int, TP g) {
     if ((i | j | k) & 1) {
       const int r = region_of(i, j, k, nb), v = rD[r];
       bool inD = v == -1;
@@ -574,7 +586,7 @@ __global__ void __launch_bounds__(1024) k_update_gamma(Tree tn, const int *__res
         const int dd[3] = {r % 3 - 1, (r / 3) % 3 - 1, r / 9 - 1};
         inD = in_band_dev(v, i - dd[0] * nb, j - dd[1] * nb, k - dd[2] * nb, nb, ef, eb);
       }
-      if (!inD) g = 0.0;
+      if (!inD) g = TP(0);
     }
     Qb[(size_t)(i + Gi) + Wd * ((size_t)(j + Gi) + (size_t)Wd * (k + Gi))] = g;
   });
@@ -585,10 +597,10 @@ __global__ void __launch_bounds__(1024) k_update_gamma(Tree tn, const int *__res
 // of the zero-detail refinement's complement) from the unchanged leaf:
 // separable, x then y then z, with the y-pass planes in a ring of
 // 2*hw(K^s)+1 shared-memory planes.  gamma is zero outside the extended region.
-template <typename TO, int N, int NT>
+template <typename TO, typename TP, int N, int NT>
 __global__ void __launch_bounds__(256) k_update_apply(Tree tn, const int *__restrict__ src,
                                                       const int *__restrict__ hasD,
-                                                      const double *__restrict__ Q, int Gi,
+                                                      const TP *__restrict__ Q, int Gi,
                                                       TO *__restrict__ fnew) {
   using W = Wav<N, NT>;
   constexpr int hk = W::hwK, R = 2 * hk + 1;
@@ -596,11 +608,11 @@ __global__ void __launch_bounds__(256) k_update_apply(Tree tn, const int *__rest
   if (src[2 * q] != KIND_COPY || !hasD[q]) return;
   const int s = src[2 * q + 1], nb = tn.nb, Wd = nb + 2 * Gi;
   const int r0 = -W::ext_f, r1 = nb - 1 + W::ext_b, nR = r1 - r0 + 1;
-  const double *Qb = Q + (size_t)s * Wd * Wd * Wd;
+  const TP *Qb = Q + (size_t)s * Wd * Wd * Wd;
   TO *v = fnew + (size_t)q * nb * nb * nb;
-  extern __shared__ double sm[];
-  double *ring = sm;                        // [R][nb][nb]
-  double *X = sm + (size_t)R * nb * nb;     // [nR][nb]: x pass of one plane
+  extern __shared__ double smd[];
+  TP *ring = reinterpret_cast<TP *>(smd);   // [R][nb][nb]
+  TP *X = ring + (size_t)R * nb * nb;       // [nR][nb]: x pass of one plane
   auto qidx = [&](int i, int j, int k) {
     return (size_t)(i + Gi) + Wd * ((size_t)(j + Gi) + (size_t)Wd * (k + Gi));
   };
@@ -613,24 +625,24 @@ __global__ void __launch_bounds__(256) k_update_apply(Tree tn, const int *__rest
         const bool od = idx < hn * nR;
         const int q = od ? idx : idx - hn * nR;
         const int i = 2 * (q % hn) + od, jj = r0 + q / hn;
-        const double *p = Qb + qidx(i, jj, kk);
-        auto at = [&](int t) { return (i + t >= r0 && i + t <= r1) ? p[t] : 0.0; };
-        double a = 0.0;
+        const TP *p = Qb + qidx(i, jj, kk);
+        auto at = [&](int t) { return (i + t >= r0 && i + t <= r1) ? p[t] : TP(0); };
+        TP a = TP(0);
         if (od)
-          for_taps<N, NT, FK_K>([&](int t, double w) { a = racc(a, w, at(t)); });
+          for_taps<N, NT, FK_K>([&](int t, double w) { a = racc(a, TP(w), at(t)); });
         else
-          for_taps<N, NT, FK_J>([&](int t, double w) { a = racc(a, w, at(t)); });
+          for_taps<N, NT, FK_J>([&](int t, double w) { a = racc(a, TP(w), at(t)); });
         X[i + nb * (jj - r0)] = a;
       }
       __syncthreads();
       for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
         const int i = idx % nb, j = idx / nb;
-        auto at = [&](int t) { return (j + t >= r0 && j + t <= r1) ? X[i + nb * (j + t - r0)] : 0.0; };
-        double a = 0.0;
+        auto at = [&](int t) { return (j + t >= r0 && j + t <= r1) ? X[i + nb * (j + t - r0)] : TP(0); };
+        TP a = TP(0);
         if (j & 1)
-          for_taps<N, NT, FK_K>([&](int t, double w) { a = racc(a, w, at(t)); });
+          for_taps<N, NT, FK_K>([&](int t, double w) { a = racc(a, TP(w), at(t)); });
         else
-          for_taps<N, NT, FK_J>([&](int t, double w) { a = racc(a, w, at(t)); });
+          for_taps<N, NT, FK_J>([&](int t, double w) { a = racc(a, TP(w), at(t)); });
         ring[(size_t)slot * nb * nb + idx] = a;
       }
     }
@@ -642,19 +654,19 @@ __global__ void __launch_bounds__(256) k_update_apply(Tree tn, const int *__rest
       const int sk = (slot + hk + 1) % R;
       for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
         auto at = [&](int t) {
-          if (k + t < r0 || k + t > r1) return 0.0;
+          if (k + t < r0 || k + t > r1) return TP(0);
           int sl = sk + t;
           sl += sl < 0 ? R : 0;
           sl -= sl >= R ? R : 0;
           return ring[(size_t)sl * nb * nb + idx];
         };
-        double a = 0.0;
+        TP a = TP(0);
         if (k & 1)
-          for_taps<N, NT, FK_K>([&](int t, double w) { a = racc(a, w, at(t)); });
+          for_taps<N, NT, FK_K>([&](int t, double w) { a = racc(a, TP(w), at(t)); });
         else
-          for_taps<N, NT, FK_J>([&](int t, double w) { a = racc(a, w, at(t)); });
+          for_taps<N, NT, FK_J>([&](int t, double w) { a = racc(a, TP(w), at(t)); });
         const size_t p = idx + (size_t)nb * nb * k;
-        if (abs_key(a)) v[p] = TO(Cvt<double>::f(v[p]) - a);
+        if (a != TP(0)) v[p] = TO(Cvt<TP>::f(v[p]) - a);
       }
     }
     __syncthreads();
@@ -662,10 +674,10 @@ __global__ void __launch_bounds__(256) k_update_apply(Tree tn, const int *__rest
 }
 
 template <int N, int NT>
-static size_t apply_smem(int nb) {
+static size_t apply_smem(int nb, size_t es) {
   using W = Wav<N, NT>;
   const int nR = nb + W::ext_f + W::ext_b;
-  return sizeof(double) * ((size_t)(2 * W::hwK + 1) * nb * nb + (size_t)nR * nb);
+  return es * ((size_t)(2 * W::hwK + 1) * nb * nb + (size_t)nR * nb);
 }
 
 // ------------------------------------------------- fields needing ghosts
@@ -736,38 +748,43 @@ static Tree next_view(const mr_grid *g, int nleaf) {
   return t;
 }
 
-template <typename TO, int N, int NT>
-static int interp_update(mr_grid *g, const Tree &to, const Tree &tn, const double *P, int Gi, int fid,
+// interpolation and update of field fid from its padded blocks P (type TP;
+// the update's details go to the FP64 side buffer's memory in type TP)
+template <typename TO, typename TP, int N, int NT>
+static int interp_update(mr_grid *g, const Tree &to, const Tree &tn, const TP *P, int Gi, int fid,
                          int *nmask, int *hasD) {
   const int *src = g->newsrc;
+  TP *Q = reinterpret_cast<TP *>(g->padQ64);
+  const int tp = sizeof(TP) == 4 ? 4 : sizeof(TO) == 4 ? 5 : 8;
   static const int ci[3] = {256, 128, 512};
-  const int thi = tune_threads(g, TuneKey{4, N, NT, g->desc.nb, sizeof(TO) == 4 ? 5 : 8, Gi, 0}, ci, 3, [&](int th) {
-    k_interp<TO, N, NT><<<tn.nleaf, th, 0, g->stream>>>(to, src, P, Gi, (const TO *)field_ptr(g, fid),
-                                                        (TO *)next_field_ptr(g, fid));
+  const int thi = tune_threads(g, TuneKey{4, N, NT, g->desc.nb, tp, Gi, 0}, ci, 3, [&](int th) {
+    k_interp<TO, TP, N, NT><<<tn.nleaf, th, 0, g->stream>>>(to, src, P, Gi, (const TO *)field_ptr(g, fid),
+                                                            (TO *)next_field_ptr(g, fid));
   });
-  MR_LAUNCH(g, MRK_INTERP, k_interp<TO, N, NT><<<tn.nleaf, thi, 0, g->stream>>>(
+  MR_LAUNCH(g, MRK_INTERP, k_interp<TO, TP, N, NT><<<tn.nleaf, thi, 0, g->stream>>>(
                                to, src, P, Gi, (const TO *)field_ptr(g, fid), (TO *)next_field_ptr(g, fid)));
-  const size_t smg = crit_smem<N, NT>(g->desc.nb), sma = apply_smem<N, NT>(g->desc.nb);
+  const size_t smg = crit_smem<N, NT>(g->desc.nb, sizeof(TP)), sma = apply_smem<N, NT>(g->desc.nb, sizeof(TP));
   if (smg > 227 * 1024 || sma > 227 * 1024) return MR_ERR_UNSUPPORTED;
-  if (check_cuda(cudaFuncSetAttribute(k_update_gamma<N, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smg),
+  if (check_cuda(cudaFuncSetAttribute(k_update_gamma<TP, N, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smg),
                  "update smem") ||
-      check_cuda(cudaFuncSetAttribute(k_update_apply<TO, N, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      check_cuda(cudaFuncSetAttribute(k_update_apply<TO, TP, N, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)sma),
                  "update smem"))
     return MR_ERR_CUDA;
-  MR_LAUNCH(g, MRK_UPDATE, k_update_gamma<N, NT><<<tn.nleaf, 1024, smg, g->stream>>>(tn, src, nmask, P, Gi,
-                                                                                   g->padQ64, hasD));
-  MR_LAUNCH(g, MRK_UPDATE, k_update_apply<TO, N, NT><<<tn.nleaf, 256, sma, g->stream>>>(
-                               tn, src, hasD, g->padQ64, Gi, (TO *)next_field_ptr(g, fid)));
+  MR_LAUNCH(g, MRK_UPDATE, k_update_gamma<TP, N, NT><<<tn.nleaf, 1024, smg, g->stream>>>(tn, src, nmask, P, Gi,
+                                                                                       Q, hasD));
+  MR_LAUNCH(g, MRK_UPDATE, k_update_apply<TO, TP, N, NT><<<tn.nleaf, 256, sma, g->stream>>>(
+                               tn, src, hasD, Q, Gi, (TO *)next_field_ptr(g, fid)));
   return check_cuda(cudaGetLastError(), "interp/update") ? MR_ERR_CUDA : MR_OK;
 }
 
-template <typename TO>
-static int interp_dispatch(mr_grid *g, const Tree &to, const Tree &tn, const double *P, int Gi, int fid,
+template <typename TO, typename TP>
+static int interp_dispatch(mr_grid *g, const Tree &to, const Tree &tn, const TP *P, int Gi, int fid,
                            int *nmask, int *hasD) {
   const int N = g->desc.wav_N, Nt = g->desc.wav_Nt;
 #define MR_ICASE(n_, nt_) \
-  if (N == n_ && Nt == nt_) return interp_update<TO, n_, nt_>(g, to, tn, P, Gi, fid, nmask, hasD);
+  if (N == n_ && Nt == nt_) return interp_update<TO, TP, n_, nt_>(g, to, tn, P, Gi, fid, nmask, hasD);
   MR_ICASE(2, 0) MR_ICASE(2, 2) MR_ICASE(4, 0) MR_ICASE(4, 2) MR_ICASE(6, 0) MR_ICASE(6, 2)
 #undef MR_ICASE
   return MR_ERR_UNSUPPORTED;
@@ -830,14 +847,15 @@ int adapt_iteration(mr_grid *g, int crit, double er, double ec, int flags, int *
   if (e) return e;
   const int changed = hc[0], nn = hc[1];
   if (check_cuda(cudaGetLastError(), "policy")) return MR_ERR_CUDA;
+  // the other fields of an FP32 grid adapt in FP32 unless asked otherwise
+  const bool f32 = g->desc.precision == MR_F32, o32 = f32 && !(flags & MR_ADAPT_OTHERS_FP64);
   if (changed == 0) {
     // Alg. SM3 step 1 ghost-fills every field in every iteration; with no
     // leaf changing, what remains of it for the other fields is the
     // substitution next to coarser leaves, which overwrites their values
-    // (later iterations: only where its inputs may have changed)
     for (int fid = 0; fid < g->desc.nfields; ++fid) {
       if (fid == crit) continue;
-      e = launch_substitute(g, field_ptr(g, fid));
+      e = launch_substitute(g, field_ptr(g, fid), nullptr, false, o32);
       if (e) return e;
     }
     return MR_OK;
@@ -876,18 +894,25 @@ int adapt_iteration(mr_grid *g, int crit, double er, double ec, int flags, int *
   // leaves, without writing substituted values back, and (B) the
   // substitution-only pass of every leaf next to a coarser leaf (its padded
   // blocks in the side buffer, free here), which writes them back; both read
-  // the field as it was, like one full ghost fill.
-  const bool f32 = g->desc.precision == MR_F32;
+  // the field as it was, like one full ghost fill.  In FP32 (o32) both run
+  // with FP32 padded blocks, and so do the interpolation and update.
   for (int pass = 0; pass < g->desc.nfields; ++pass) {
     const int fid = pass == 0 ? crit : (pass <= crit ? pass - 1 : pass);
+    if (pass > 0 && o32) {
+      e = launch_ghost_adapt32(g, (const float *)field_ptr(g, fid), G, need2, &Pv, &Gi);
+      if (!e) e = launch_substitute(g, field_ptr(g, fid), nullptr, true, true);
+      if (!e) e = interp_dispatch<float, float>(g, t, tn, (const float *)Pv, Gi, fid, nmask, hasD);
+      if (e) return e;
+      continue;
+    }
     if (pass > 0) {
       e = launch_ghost(g, field_ptr(g, fid), nullptr, G, true, &Pv, &Gi, nullptr, need2);
       if (!e) e = launch_substitute(g, field_ptr(g, fid), nullptr, true);
       if (e) return e;
       P = (const double *)Pv;
     }
-    e = f32 ? interp_dispatch<float>(g, t, tn, P, Gi, fid, nmask, hasD)
-            : interp_dispatch<double>(g, t, tn, P, Gi, fid, nmask, hasD);
+    e = f32 ? interp_dispatch<float, double>(g, t, tn, P, Gi, fid, nmask, hasD)
+            : interp_dispatch<double, double>(g, t, tn, P, Gi, fid, nmask, hasD);
     if (e) return e;
   }
   // swap to the new tree and pool

@@ -115,6 +115,22 @@ int launch_ghost(mr_grid *g, const void *phi_in, void *phi_out, int G, bool fp64
                                         (double *)g->padP, (double *)g->padQ, gi, 0, need);
 }
 
+// FP32 ghost fill of an FP32 field with the adaptation shell G, without
+// write-back: the padded blocks (FP32, internal shell *Gi) go to the memory
+// of the FP64 adaptation buffers, which hold twice their size.
+int launch_ghost_adapt32(mr_grid *g, const float *phi, int G, const int *need, void **P, int *Gi) {
+  const int nb = g->desc.nb;
+  if (G < 1 || G > MR_MAX_SHELL) return MR_ERR_INVALID;
+  if (G > nb / 2) return MR_ERR_BALANCE;
+  const int gi = internal_shell(g->desc.wav_N, g->desc.wav_Nt, G, nb);
+  if (g->desc.precision != MR_F32 || gi > g->shell_ad || (g->desc.flags & MR_GRID_FIXED_TREE))
+    return MR_ERR_UNSUPPORTED;
+  *Gi = gi;
+  *P = g->padP64;
+  return ghost_dispatch<float, float>(g, phi, nullptr, G, reinterpret_cast<float *>(g->padP64),
+                                      reinterpret_cast<float *>(g->padQ64), gi, 0, need);
+}
+
 // substituted band of leaves with a coarser neighbour -> field
 template <typename TO, typename TP>
 __global__ void __launch_bounds__(256) k_writeback(int nb, const TP *__restrict__ P, int Gi, const int *__restrict__ cmask,
@@ -140,11 +156,11 @@ int launch_prep32(mr_grid *g, const void *phi, int *Gi) {
 
 // Substitution alone (the first step of Alg. SM2) of every leaf next to a
 // coarser leaf (with need: of those marked): the pre-pass at the shell the
-// substitution reads (the G^a
-// half-width) computes the padded block, substitutes the band in FP64 and
+// substitution reads (the G^a half-width) computes the padded block,
+// substitutes the band (in FP64, or in FP32 for an FP32 field with f32) and
 // the substituted values are written back to the field -- the field values a
 // full ghost fill leaves, without the padded blocks of the other leaves.
-int launch_substitute(mr_grid *g, void *phi, const int *need, bool in_side_buffer) {
+int launch_substitute(mr_grid *g, void *phi, const int *need, bool in_side_buffer, bool f32) {
   const int N = g->desc.wav_N, Nt = g->desc.wav_Nt, nb = g->desc.nb;
   const int G = N - 1, gi = internal_shell(N, Nt, G, nb);
   if (gi > g->shell_ad || (g->desc.flags & MR_GRID_FIXED_TREE)) return MR_ERR_UNSUPPORTED;
@@ -152,7 +168,13 @@ int launch_substitute(mr_grid *g, void *phi, const int *need, bool in_side_buffe
   // (the pass pushes nothing, so the other buffer is only passed along)
   double *Pb = in_side_buffer ? g->padQ64 : g->padP64, *Qb = in_side_buffer ? g->padP64 : g->padQ64;
   int e;
-  if (g->desc.precision == MR_F32) {
+  if (g->desc.precision == MR_F32 && f32) {
+    float *Pf = reinterpret_cast<float *>(Pb), *Qf = reinterpret_cast<float *>(Qb);
+    e = ghost_dispatch<float, float>(g, (const float *)phi, nullptr, G, Pf, Qf, gi, 2, need);
+    if (!e)
+      MR_LAUNCH(g, MRK_MERGE, k_writeback<float, float><<<g->nleaf, 256, 0, g->stream>>>(
+                                  nb, Pf, gi, g->cmask, (float *)phi, need));
+  } else if (g->desc.precision == MR_F32) {
     e = ghost_dispatch<float, double>(g, (const float *)phi, nullptr, G, Pb, Qb, gi, 2, need);
     if (!e)
       MR_LAUNCH(g, MRK_MERGE, k_writeback<float, double><<<g->nleaf, 256, 0, g->stream>>>(

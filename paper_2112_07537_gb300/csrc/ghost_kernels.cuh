@@ -780,14 +780,28 @@ __global__ void __launch_bounds__(512) k_fill_plain(Tree t, const TI *__restrict
   __syncthreads();
   const int ax = __ldg(t.anc + 3 * b) * nb, ay = __ldg(t.anc + 3 * b + 1) * nb, az = __ldg(t.anc + 3 * b + 2) * nb;
   TP *Pb = P + (size_t)b * np;
-  const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-  for (int row = threadIdx.x >> 5; row < Wd * Wd; row += nwarp) {
-    const int j = row % Wd - Gi, k = row / Wd - Gi;
-    const int ry = j < 0 ? 0 : j >= nb ? 2 : 1, rz = k < 0 ? 0 : k >= nb ? 2 : 1;
-    const int rj = j - (ry - 1) * nb, rk = k - (rz - 1) * nb;  // region-local
-    for (int i = lane - Gi; i < nb + Gi; i += 32) {
-      const int rx = i < 0 ? 0 : i >= nb ? 2 : 1, r = rx + 3 * ry + 9 * rz;
-      const int ri = i - (rx - 1) * nb;
+  // one padded point per thread and step, four steps' sources resolved and
+  // loaded before any is stored (four independent loads in flight)
+  const DivM dW = divm(Wd);
+  const int npt = Wd * Wd * Wd, bd = blockDim.x;
+  enum { SKIP = 0, LOAD = 1, SLOW = 2, BAD = 3 };
+  auto coords = [&](int p, int &i, int &j, int &k) {
+    const int row = divq(p, dW), kk = divq(row, dW);
+    i = p - row * Wd - Gi, j = row - kk * Wd - Gi, k = kk - Gi;
+  };
+  for (int p0 = threadIdx.x; p0 < npt; p0 += 4 * bd) {
+    long long id[4];
+    int kind[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int p = p0 + u * bd;
+      kind[u] = SKIP, id[u] = 0;
+      if (p >= npt) continue;
+      int i, j, k;
+      coords(p, i, j, k);
+      const int rx = i < 0 ? 0 : i >= nb ? 2 : 1, ry = j < 0 ? 0 : j >= nb ? 2 : 1, rz = k < 0 ? 0 : k >= nb ? 2 : 1;
+      const int r = rx + 3 * ry + 9 * rz;
+      const int ri = i - (rx - 1) * nb, rj = j - (ry - 1) * nb, rk = k - (rz - 1) * nb;  // region-local
       const int Lo = rlev[r];
       if (Lo < L) continue;  // a coarser leaf's region: refined by the pre-pass
       long long idx = -1;
@@ -799,19 +813,32 @@ __global__ void __launch_bounds__(512) k_fill_plain(Tree t, const TI *__restrict
         if (o2 >= 0)
           idx = (long long)o2 * (long long)nb3 + (2 * ri - hx * nb) + nb * ((2 * rj - hy * nb) + nb * (2 * rk - hz * nb));
       }
-      TP v;
-      if (idx >= 0 && idx < lim && ri >= 0 && ri < nb && rj >= 0 && rj < nb && rk >= 0 && rk < nb) {
-        v = Cvt<TP>::f(__ldg(phi + idx));
-      } else if (idx == -1 && Lo > L) {
-        // a finer region two levels down (shells wider than half a block)
+      if (idx >= 0 && idx < lim && ri >= 0 && ri < nb && rj >= 0 && rj < nb && rk >= 0 && rk < nb)
+        kind[u] = LOAD, id[u] = idx;
+      else
+        kind[u] = (idx == -1 && Lo > L) ? SLOW : BAD;  // SLOW: a finer region two levels down
+    }
+    TI v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = kind[u] == LOAD ? __ldg(phi + id[u]) : TI(0);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (kind[u] == SKIP) continue;
+      const int p = p0 + u * bd;
+      TP o;
+      if (kind[u] == LOAD) {
+        o = Cvt<TP>::f(v[u]);
+      } else if (kind[u] == SLOW) {  // shells wider than half a block
+        int i, j, k;
+        coords(p, i, j, k);
         const int gx = ax + i, gy = ay + j, gz = az + k;
-        const int o = owner(t, L, gx, gy, gz, b);
-        v = Cvt<TP>::f(leaf_value(t, phi, o, L, gx, gy, gz, err));
+        const int ow = owner(t, L, gx, gy, gz, b);
+        o = Cvt<TP>::f(leaf_value(t, phi, ow, L, gx, gy, gz, err));
       } else {
         atomicOr(err, 1 << 16);
-        v = TP(__int_as_float(0x7fc00000));
+        o = TP(__int_as_float(0x7fc00000));
       }
-      Pb[(size_t)row * Wd + (i + Gi)] = v;
+      Pb[p] = o;
     }
   }
 }

@@ -158,6 +158,17 @@ __device__ __forceinline__ F2 f2_split(double x) {
   return {__uint_as_float(hi), __uint_as_float(sgn | ((unsigned)le << 23) | (((r << lz) >> 8) & 0x7fffffu))};
 }
 
+// x / d for 0 <= x, 2 <= d, x d < 2^32, as a multiply-high with
+// m = ceil(2^32 / d): x m / 2^32 = x/d + x e / (d 2^32) with e = m d - 2^32
+// < d, so the excess stays below 1/d and the floor is exact.  Every index
+// decomposition of one block (x < Wd^3, d <= Wd) is inside that range.
+struct DivM {
+  unsigned m;
+  int d;
+};
+__device__ __forceinline__ DivM divm(int d) { return {0xffffffffu / (unsigned)d + 1u, d}; }
+__device__ __forceinline__ int divq(int x, DivM v) { return (int)__umulhi((unsigned)x, v.m); }
+
 // value of the field element type TI in the working precision TP
 template <typename TP>
 struct Cvt;
@@ -581,7 +592,9 @@ int launch_crop(mr_grid *g, const void *P, int Gi, void *out, int G, bool fp64_s
 int launch_crop64(mr_grid *g, const double *P, int Gi, double *out, int G);
 int launch_prep32(mr_grid *g, const void *phi, int *Gi);
 int launch_writeback32(mr_grid *g, int Gi, void *phi);
-int launch_substitute(mr_grid *g, void *phi, const int *need = nullptr, bool in_side_buffer = false);
+int launch_substitute(mr_grid *g, void *phi, const int *need = nullptr, bool in_side_buffer = false,
+                      bool f32 = false);
+int launch_ghost_adapt32(mr_grid *g, const float *phi, int G, const int *need, void **P, int *Gi);
 int launch_fused(mr_grid *g, const void *phi, const void *P, const void *Q, int Gi, const void *u, void *out,
                  int stage, double dt, const double *uc, int scheme, bool rhs_only, const void *vpad = nullptr);
 int adapt_shell(int N, int Nt);

@@ -159,19 +159,20 @@ __global__ void __launch_bounds__(1024) k_fused(Tree t, const float *__restrict_
   float *Tt = sm + (size_t)Ws * Ws * Ws;
   auto tix = [&](int i, int j, int k) { return (i + GS) + Ws * ((j + GS) + Ws * (k + GS)); };
   const int mask = cmask[b];
+  const DivM dnb = divm(nb);
   // interior
   if (mask) {
     const float *Pb = P + (size_t)b * np;
     for (int p = threadIdx.x; p < (int)nb3; p += blockDim.x) {
-      const int i = p % nb, j = (p / nb) % nb, k = p / (nb * nb);
-      tile[tix(i, j, k)] = Pb[(i + Gi) + Wd * ((j + Gi) + (size_t)Wd * (k + Gi))];
+      const int r = divq(p, dnb), k = divq(r, dnb), i = p - r * nb, j = r - k * nb;
+      tile[tix(i, j, k)] = Pb[(i + Gi) + Wd * ((j + Gi) + Wd * (k + Gi))];
     }
   } else {
     const float4 *src = reinterpret_cast<const float4 *>(phi + (size_t)b * nb3);
-    const int nq = nb / 4;
+    const DivM dq = divm(nb / 4);
     for (int p = threadIdx.x; p < (int)nb3 / 4; p += blockDim.x) {
       const float4 v = __ldg(src + p);
-      const int i = (p % nq) * 4, j = (p / nq) % nb, k = p / (nq * nb);
+      const int r = divq(p, dq), k = divq(r, dnb), i = (p - r * (nb / 4)) * 4, j = r - k * nb;
       float *d = tile + tix(i, j, k);
       d[0] = v.x, d[1] = v.y, d[2] = v.z, d[3] = v.w;
     }
@@ -188,17 +189,25 @@ __global__ void __launch_bounds__(1024) k_fused(Tree t, const float *__restrict_
     lo[ax] = sg < 0 ? -GS : nb;
     ext[ax] = GS;
     const int cnt = ext[0] * ext[1] * ext[2];
+    const DivM de0 = divm(ext[0]), de1 = divm(ext[1]);
+    // slab point p -> block-local coordinates
+    auto slab = [&](int p, int *c) {
+      const int r = divq(p, de0), z = divq(r, de1);
+      c[0] = lo[0] + p - r * ext[0], c[1] = lo[1] + r - z * ext[1], c[2] = lo[2] + z;
+    };
     if (Lo == L) {
       const float *po = phi + (size_t)o * nb3;
       for (int p = threadIdx.x; p < cnt; p += blockDim.x) {
-        int c[3] = {lo[0] + p % ext[0], lo[1] + (p / ext[0]) % ext[1], lo[2] + p / (ext[0] * ext[1])};
+        int c[3];
+        slab(p, c);
         int l[3] = {c[0], c[1], c[2]};
         l[ax] = sg < 0 ? c[ax] + nb : c[ax] - nb;
         tile[tix(c[0], c[1], c[2])] = __ldg(po + l[0] + nb * (l[1] + nb * l[2]));
       }
     } else if (Lo > L) {
       for (int p = threadIdx.x; p < cnt; p += blockDim.x) {
-        const int c[3] = {lo[0] + p % ext[0], lo[1] + (p / ext[0]) % ext[1], lo[2] + p / (ext[0] * ext[1])};
+        int c[3];
+        slab(p, c);
         float v;
         if (NT == 0) {
           const int gx = a[0] + c[0], gy = a[1] + c[1], gz = a[2] + c[2];
@@ -237,7 +246,8 @@ __global__ void __launch_bounds__(1024) k_fused(Tree t, const float *__restrict_
       }
       __syncthreads();
       for (int p = threadIdx.x; p < cnt; p += blockDim.x) {
-        const int c[3] = {lo[0] + p % ext[0], lo[1] + (p / ext[0]) % ext[1], lo[2] + p / (ext[0] * ext[1])};
+        int c[3];
+        slab(p, c);
         const float s = refine_dispatch<N, NT, float>(c[0] & 1, c[1] & 1, c[2] & 1, [&](int ox, int oy, int oz) -> float {
           const int tx = floordiv2(c[0] + ox) - q0[0], ty = floordiv2(c[1] + oy) - q0[1],
                     tz = floordiv2(c[2] + oz) - q0[2];
@@ -287,6 +297,7 @@ __global__ void __launch_bounds__(1024) k_fused(Tree t, const float *__restrict_
       }
       const float *lq = lp + 3 * st;
       float *rq = rp;
+#pragma unroll 4
       for (int m = 0; m < nb; ++m) {
         w1 = w2, w2 = w3, w3 = w4, w4 = w5, w5 = w6;
         v1 = v2, v2 = v3, v3 = v4, v4 = v5, v5 = v6;
@@ -309,7 +320,7 @@ __global__ void __launch_bounds__(1024) k_fused(Tree t, const float *__restrict_
   const float h = (float)(t.tree_len / ((double)nb * (double)(1 << L)));
   const float invh = 1.0f / h;
   for (int p = threadIdx.x; p < (int)nb3; p += blockDim.x) {
-    const int i = p % nb, j = (p / nb) % nb, k = p / (nb * nb);
+    const int rr = divq(p, dnb), k = divq(rr, dnb), i = p - rr * nb, j = rr - k * nb;
     float r = -R[p] * invh;
     if (diff) {
       const int sts[3] = {strd[0], strd[1], strd[2]};

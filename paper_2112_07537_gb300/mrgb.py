@@ -20,6 +20,7 @@ F32, F64 = 0, 1
 CONS3, CONS5, WENOZ5 = 0, 1, 2
 INIT_GAUSSIAN, INIT_TANH_SPHERE, INIT_TAYLOR_GREEN, INIT_GAUSSIAN_SUM = 0, 1, 2, 3
 ADAPT_REFINE, ADAPT_COARSEN = 1, 2
+ADAPT_OTHERS_FP64 = 4  # FP32 grids: the non-criterion fields adapt in FP64 arithmetic
 INIT_COMPACT_GAUSSIAN, INIT_DEFORMATION, INIT_GAUSSIAN_SUM_ADD = 4, 5, 6
 GRID_FIXED_TREE = 1
 GRID_VELOCITY = 2

@@ -11,7 +11,9 @@ bit-exact; FP64 fields within 1e-12 of the field maximum (fused multiply-adds
 and separable sums on the device); FP32 grids are compared with the oracle
 run on the same FP32 snapshot (upcast): the device rounds its FP64
 adaptation results to FP32 (twice where the update step corrects a copied
-value), so they agree within 2^-22 of the field maximum.
+value), so they agree within 2^-22 of the field maximum -- for every field
+with MR_ADAPT_OTHERS_FP64, else for the criterion field, while the other
+fields, adapted in FP32 arithmetic, stay within 1e-5 of their maximum.
 """
 import numpy as np
 import pytest
@@ -136,15 +138,24 @@ def test_adapt_to_convergence_fp32_6_2_nb24_flags_exact(mr, oracle_mod):
     assert it > 0
 
 
-@pytest.mark.parametrize("prec", [1, 0])
-def test_adapt_four_fields_6_2_nb24(mr, oracle_mod, prec):
+@pytest.mark.parametrize("prec,others64", [(1, False), (0, True), (0, False)])
+def test_adapt_four_fields_6_2_nb24(mr, oracle_mod, prec, others64):
     """Adaptation of four fields -- the scalar (criterion field) and three
     Taylor-Green-like velocity components, as in the large workload: every
     field is ghost-filled (the non-criterion fields only on the leaves whose
     interpolation or update step reads ghosts), refined, coarsened and
     updated by the scalar's decisions.  Each iteration is compared with the
     oracle's multi-field iteration on the device's snapshot: trees exact,
-    all four fields within tolerance."""
+    all four fields within tolerance.
+
+    FP32 grids without MR_ADAPT_OTHERS_FP64 adapt the three velocity fields
+    in FP32 arithmetic.  Bound for them: one FP32 pass of at most 6 taps
+    errs by <= 6u sum|w x| (u = 2^-24), sum|K^s| = 1.39 for 6.x, so the
+    separable refinement of a ghost value (3 passes) errs by
+    <= 3 * 6u * 1.39^3 M = 2.9e-6 M; the substitution and the children's
+    refinement from those ghosts (3 more passes) bring the total to
+    about 1e-5 M -- the FP32 tolerance of the path.  The scalar (criterion
+    field) and every decision stay as in FP64."""
     O = oracle_mod
     g, og = _grid(mr, O, 6, 2, prec, nfields=4)
     xyz = I.point_coords(og.nt, og.tree_len, og.nb, og.lev, og.anc)
@@ -158,14 +169,21 @@ def test_adapt_four_fields_6_2_nb24(mr, oracle_mod, prec):
         cur = og.with_leaves(lev, anc)
         snaps = [g.field_copy_out(f).astype(np.float64) for f in range(4)]
         og2, outs, refined_o, onch, _, _ = O.adapt_iter_fields(cur, snaps, EPS_R, EPS_C, refined)
-        nch = g.adapt_iter(0, EPS_R, EPS_C)
+        flags = mr.ADAPT_REFINE | mr.ADAPT_COARSEN | (mr.ADAPT_OTHERS_FP64 if others64 else 0)
+        nch = g.adapt_iter(0, EPS_R, EPS_C, flags=flags)
         assert nch == onch
         _same_tree(g, og2)
         for f in range(4):
             got = g.field_copy_out(f).astype(np.float64)
             scale = np.abs(outs[f]).max()
-            tol = TOL * scale if prec == 1 else 2.0 ** -22 * scale + TOL
-            assert np.abs(got - outs[f]).max() <= tol, (it, f)
+            if prec == 1:
+                tol = TOL * scale
+            elif f == 0 or others64:
+                tol = 2.0 ** -22 * scale + TOL
+            else:
+                tol = 1e-5 * scale
+            err = np.abs(got - outs[f]).max()
+            assert err <= tol, (it, f, err / scale)
         refined = refined_o
         if nch == 0:
             break
