@@ -58,6 +58,7 @@ Tree tree_view(const mr_grid *g) {
   t.map = g->maps[g->cur];
   t.tree_len = g->desc.tree_len;
   t.indep = (g->desc.flags & MR_GRID_INDEPENDENT_TREES) ? 1 : 0;
+  t.dnb = divm(t.nb);
   return t;
 }
 
@@ -107,8 +108,12 @@ static int layout(const mr_grid_desc *d, Layout *L, int *shell_rk, int *shell_ad
   if (d->nfields < 1 || d->capacity < 1 || d->lmax < 0 || d->lmax > MR_MAX_LEVEL || d->lmin < 0 ||
       d->lmin > d->lmax || !(d->tree_len > 0))
     return MR_ERR_INVALID;
-  for (int k = 0; k < 3; ++k)
+  for (int k = 0; k < 3; ++k) {
     if (d->ntree[k] < 1 || d->ntree[k] > 64) return MR_ERR_INVALID;
+    // level-lmax point indices times nb stay below 2^32 (owner-map lookups
+    // divide by nb with a multiply-high)
+    if (((unsigned long long)d->ntree[k] << d->lmax) * d->nb * d->nb >= (1ull << 32)) return MR_ERR_INVALID;
+  }
   const size_t es = d->precision == MR_F32 ? 4 : 8;
   const size_t nb3 = (size_t)d->nb * d->nb * d->nb, cap = (size_t)d->capacity;
   const bool fixed = d->flags & MR_GRID_FIXED_TREE;

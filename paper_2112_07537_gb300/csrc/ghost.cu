@@ -139,8 +139,9 @@ __global__ void __launch_bounds__(256) k_writeback(int nb, const TP *__restrict_
   if ((need && !need[b]) || !cmask[b]) return;  // cmask is stale where need is 0
   const int Wd = nb + 2 * Gi;
   const size_t np = (size_t)Wd * Wd * Wd;
+  const DivM dnb = divm(nb);
   for (int p = threadIdx.x; p < nb * nb * nb; p += blockDim.x) {
-    const int i = p % nb, j = (p / nb) % nb, k = p / (nb * nb);
+    const int r = divq(p, dnb), k = divq(r, dnb), i = p - r * nb, j = r - k * nb;
     if (!((i | j | k) & 1)) continue;
     phi[(size_t)b * nb * nb * nb + p] = TO(P[(size_t)b * np + (i + Gi) + Wd * ((j + Gi) + (size_t)Wd * (k + Gi))]);
   }

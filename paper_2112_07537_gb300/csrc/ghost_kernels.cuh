@@ -148,7 +148,7 @@ __device__ void subst_sep(TP *__restrict__ Pb, int Wd, int Gi, const BoxList &bl
                           long cap) {
   using W = Wav<N, NT>;
   constexpr int hG = W::hwG;
-  const long ps1 = Wd, ps2 = (long)Wd * Wd;
+  const int ps1 = Wd, ps2 = Wd * Wd;
   const int njob = bl.n * (deg == 2 ? 3 : 1), bd = blockDim.x;
   // buffer elements of a job: stages 1 .. deg-1
   auto job_buf = [&](const SubJob &J) -> long {
@@ -168,9 +168,10 @@ __device__ void subst_sep(TP *__restrict__ Pb, int Wd, int Gi, const BoxList &bl
       const SubJob J = sub_job(bl, j0, deg);
       int st[3], sp[3], cn[3];
       sub_stage(J, deg, hG, st, sp, cn);
-      const long n = J.empty ? 0 : (long)cn[0] * cn[1] * cn[2];
-      for (long idx = threadIdx.x; idx < n; idx += bd) {
-        const int i0 = (int)(idx % cn[0]), r = (int)(idx / cn[0]), i1 = r % cn[1], i2 = r / cn[1];
+      const int n = J.empty ? 0 : cn[0] * cn[1] * cn[2];
+      const DivM dc0 = divm(cn[0]), dc1 = divm(cn[1]);
+      for (int idx = threadIdx.x; idx < n; idx += bd) {
+        const int r = divq(idx, dc0), i2 = divq(r, dc1), i0 = idx - r * cn[0], i1 = r - i2 * cn[1];
         TP *c = Pb + (st[0] + sp[0] * i0 + Gi) + ps1 * (st[1] + sp[1] * i1 + Gi) + ps2 * (st[2] + sp[2] * i2 + Gi);
         *c = subst_dispatch<N, NT, TP>(J.om & 1, J.om & 2, J.om & 4, [&](int tx, int ty, int tz) -> TP {
           return c[tx + ps1 * ty + ps2 * tz];
@@ -188,21 +189,23 @@ __device__ void subst_sep(TP *__restrict__ Pb, int Wd, int Gi, const BoxList &bl
         int st[3], sp[3], cn[3], pst[3], psp[3], pcn[3];
         sub_stage(J, s, hG, st, sp, cn);
         sub_stage(J, s - 1 > 0 ? s - 1 : 1, hG, pst, psp, pcn);
-        const long n = J.empty ? 0 : (long)cn[0] * cn[1] * cn[2];
+        const int n = J.empty ? 0 : cn[0] * cn[1] * cn[2];
         const int d = s == 1 ? J.o0 : s == 2 ? J.o1 : J.o2;  // dimension summed in this pass
         TP *dst = buf + off + (s == 2 ? n1 : 0);
         const TP *prev = buf + off + (s == 3 ? n1 : 0);
-        const long q1 = pcn[0], q2 = (long)pcn[0] * pcn[1];
+        const int q1 = pcn[0], q2 = pcn[0] * pcn[1];
         const int oth = J.om & ~(1 << d);
-        long idx = ((long)threadIdx.x - base) % bd;
+        const DivM dc0 = divm(cn[0]), dc1 = divm(cn[1]);
+        // this job's items continue the thread rotation of the previous jobs
+        int idx = (int)(((long)threadIdx.x - base) % bd);
         if (idx < 0) idx += bd;
         for (; idx < n; idx += bd) {
-          const int i0 = (int)(idx % cn[0]), r = (int)(idx / cn[0]), i1 = r % cn[1], i2 = r / cn[1];
+          const int r = divq(idx, dc0), i2 = divq(r, dc1), i0 = idx - r * cn[0], i1 = r - i2 * cn[1];
           const int p0 = st[0] + sp[0] * i0, p1 = st[1] + sp[1] * i1, p2 = st[2] + sp[2] * i2;
           TP acc = TP(0);
           if (s == 1) {
             const TP *src = Pb + (p0 + Gi) + ps1 * (p1 + Gi) + ps2 * (p2 + Gi);
-            const long str = d == 0 ? 1 : d == 1 ? ps1 : ps2;
+            const int str = d == 0 ? 1 : d == 1 ? ps1 : ps2;
             const bool keep0 = ((oth & 1) && !(p0 & 1)) || ((oth & 2) && !(p1 & 1)) || ((oth & 4) && !(p2 & 1));
 #pragma unroll
             for (int t = -hG; t <= hG; ++t) {
@@ -216,7 +219,7 @@ __device__ void subst_sep(TP *__restrict__ Pb, int Wd, int Gi, const BoxList &bl
           } else {
             const int c0 = d == 0 ? p0 - pst[0] : i0, c1 = d == 1 ? p1 - pst[1] : i1, c2 = d == 2 ? p2 - pst[2] : i2;
             const TP *src = prev + c0 + q1 * c1 + q2 * c2;
-            const long str = d == 0 ? 1 : d == 1 ? q1 : q2;
+            const int str = d == 0 ? 1 : d == 1 ? q1 : q2;
 #pragma unroll
             for (int t = -hG; t <= hG; ++t) {
               if (W::G(t) == 0.0) continue;
@@ -277,31 +280,60 @@ __global__ void __launch_bounds__(512, sizeof(TP) == 4 ? 2 : 1) k_prep(Tree t, c
   const int mask = cmask;
   if (threadIdx.x == 0 && cmask_out) cmask_out[b] = mask;
   if (only_coarse && !mask) return;
-  // value stored at level-Lq point (block-local, level L coords when Lq == L;
-  // coarse-local coords when Lq == L-1) -- via the region table when the
-  // owning region is same-level or coarser, else through the owner map
-  auto fetch_raw = [&](int Lq, int i, int j, int k) -> TI {
+  // finer regions: the owners of their eight one-level-finer sub-blocks (-1:
+  // the sub-block is refined further), so their values need no owner lookup
+  const int hb = nb / 2;
+  __shared__ int rsub[27][8];
+  for (int q = threadIdx.x; q < 216; q += blockDim.x) {
+    const int r = q >> 3, h = q & 7;
+    int o2 = -1;
+    if (rlev[r] == L + 1 && L < t.M) {
+      const int dd[3] = {r % 3 - 1, (r / 3) % 3 - 1, r / 9 - 1};
+      int g[3];
+      for (int d = 0; d < 3; ++d) g[d] = 2 * (__ldg(t.anc + 3 * b + d) + dd[d]) * nb + ((h >> d) & 1) * nb;
+      o2 = owner(t, L + 1, g[0], g[1], g[2], b);
+      if (o2 < 0 || o2 >= t.nleaf || __ldg(t.lev + o2) != L + 1) o2 = -1;
+    }
+    rsub[r][h] = o2;
+  }
+  __syncthreads();  // rsub is read by every fetch below
+  // index into phi of the value stored at level-Lq point (i, j, k) (block-
+  // local level-L coords when Lq == L, coarse-local when Lq == L-1) from the
+  // region tables, or -1 where only the owner map resolves it
+  auto src_index = [&](int Lq, int i, int j, int k) -> long long {
     const int sc = (Lq == L) ? 1 : 2;  // fine-index scale of the point
     const int fi = i * sc, fj = j * sc, fk = k * sc;
-    if (fi >= -nb && fi < 2 * nb && fj >= -nb && fj < 2 * nb && fk >= -nb && fk < 2 * nb) {
-      const int r = region_of(fi, fj, fk, nb);
-      const int Lo = rlev[r], o = rslot[r];
-      if (Lo == L) {
-        const int dx = r % 3 - 1, dy = (r / 3) % 3 - 1, dz = r / 9 - 1;
-        return ld(phi + (size_t)o * nb3 + (fi - dx * nb) + nb * ((fj - dy * nb) + nb * (fk - dz * nb)));
-      }
-      if (Lo == L - 1) {
-        // coarse leaf: level-(L-1) index of the point, relative to its anchor
-        const int gq[3] = {(ax + fi) / 2, (ay + fj) / 2, (az + fk) / 2};
-        int l[3];
-        for (int d = 0; d < 3; ++d) l[d] = pwrap(gq[d] - ranc[r][d] * nb, period(t, L - 1, d));
-        return ld(phi + (size_t)o * nb3 + l[0] + nb * (l[1] + nb * l[2]));
-      }
+    if (fi < -nb || fi >= 2 * nb || fj < -nb || fj >= 2 * nb || fk < -nb || fk >= 2 * nb) return -1;
+    const int rx = fi < 0 ? 0 : fi >= nb ? 2 : 1, ry = fj < 0 ? 0 : fj >= nb ? 2 : 1, rz = fk < 0 ? 0 : fk >= nb ? 2 : 1;
+    const int r = rx + 3 * ry + 9 * rz;
+    const int Lo = rlev[r], o = rslot[r];
+    const int ri = fi - (rx - 1) * nb, rj = fj - (ry - 1) * nb, rk = fk - (rz - 1) * nb;  // region-local
+    if (Lo == L) return (long long)o * (long long)nb3 + ri + nb * (rj + nb * rk);
+    if (Lo == L - 1) {
+      // coarse leaf: level-(L-1) index of the point, relative to its anchor
+      const int gq[3] = {(ax + fi) / 2, (ay + fj) / 2, (az + fk) / 2};
+      int l[3];
+      for (int d = 0; d < 3; ++d) l[d] = pwrap(gq[d] - ranc[r][d] * nb, period(t, L - 1, d));
+      return (long long)o * (long long)nb3 + l[0] + nb * (l[1] + nb * l[2]);
     }
+    if (Lo == L + 1) {
+      // the coincident point of the finer leaf holding the sub-block
+      const int hx = ri >= hb, hy = rj >= hb, hz = rk >= hb;
+      const int o2 = rsub[r][hx + 2 * hy + 4 * hz];
+      if (o2 >= 0)
+        return (long long)o2 * (long long)nb3 + (2 * ri - hx * nb) + nb * ((2 * rj - hy * nb) + nb * (2 * rk - hz * nb));
+    }
+    return -1;
+  };
+  auto fetch_slow = [&](int Lq, int i, int j, int k) -> TI {
     const int gx = (Lq == L ? ax : ax / 2) + i, gy = (Lq == L ? ay : ay / 2) + j, gz = (Lq == L ? az : az / 2) + k;
     const int o = owner(t, Lq, gx, gy, gz, b);
     if (__ldg(t.lev + o) < Lq) return TI(__int_as_float(0x7fc00000));
     return leaf_value(t, phi, o, Lq, gx, gy, gz, err);
+  };
+  auto fetch_raw = [&](int Lq, int i, int j, int k) -> TI {
+    const long long s = src_index(Lq, i, j, k);
+    return s >= 0 ? ld(phi + s) : fetch_slow(Lq, i, j, k);
   };
   auto fetch = [&](int Lq, int i, int j, int k) -> TP { return Cvt<TP>::f(fetch_raw(Lq, i, j, k)); };
   extern __shared__ unsigned char smraw[];
@@ -314,19 +346,6 @@ __global__ void __launch_bounds__(512, sizeof(TP) == 4 ? 2 : 1) k_prep(Tree t, c
   // [nb-ef, nb); a cell is in the band when a coarser direction covers it
   __shared__ BoxList rbox, sbox;
   if (threadIdx.x < 32) {
-    // warp 0, one lane per region / cell; list positions from a ballot prefix
-    // (ascending region and cell order)
-    const int r = lane;
-    const bool isr = r < 27 && ((mask >> r) & 1);
-    const unsigned br = __ballot_sync(0xffffffffu, isr);
-    if (isr) {
-      const int pos = __popc(br & ((1u << r) - 1u));
-      const int dd[3] = {r % 3 - 1, (r / 3) % 3 - 1, r / 9 - 1};
-      for (int d = 0; d < 3; ++d) {
-        rbox.lo[pos][d] = dd[d] < 0 ? -Gi : dd[d] > 0 ? nb : 0;
-        rbox.hi[pos][d] = dd[d] < 0 ? 0 : dd[d] > 0 ? nb + Gi : nb;
-      }
-    }
     // per dimension the cuts 0 <= a <= b <= nb, a = min(ext_b, nb - ext_f),
     // b = max(...): [0, a) lies in the band of a coarser leaf on the - side
     // only, [b, nb) in that of the + side only, [a, b) in neither (or, when
@@ -347,10 +366,6 @@ __global__ void __launch_bounds__(512, sizeof(TP) == 4 ? 2 : 1) k_prep(Tree t, c
       }
     const unsigned bc = __ballot_sync(0xffffffffu, in);
     if (lane == 0) {
-      rbox.n = __popc(br);
-      // band boxes: the (disjoint) band cells merged greedily, x run first,
-      // then y, then z
-      const int cut[4] = {0, ov ? nb - W::ext_f : W::ext_b, ov ? W::ext_b : nb - W::ext_f, nb};
       auto rect = [](int xa, int xb, int ya, int yb, int za, int zb) {
         unsigned m = 0;
         for (int z = za; z < zb; ++z)
@@ -358,6 +373,52 @@ __global__ void __launch_bounds__(512, sizeof(TP) == 4 ? 2 : 1) k_prep(Tree t, c
             for (int x = xa; x < xb; ++x) m |= 1u << (x + 3 * y + 9 * z);
         return m;
       };
+      // boxes of the coarser leaves' regions: the regions merged greedily (x
+      // run, then y, then z) as long as the separable refinement's partial
+      // sums of the box fit in the shared memory beside the coarse tile
+      {
+        const int cutr[4] = {-Gi, 0, nb, nb + Gi};
+        const long capU = use_tile == 2 ? ((long)dyn_bytes - tile_bytes) / (long)sizeof(TP) : 0x7fffffffL;
+        auto fits = [&](int xa, int xb, int ya, int yb, int za, int zb) {
+          const int lo3[3] = {cutr[xa], cutr[ya], cutr[za]}, hi3[3] = {cutr[xb], cutr[yb], cutr[zb]};
+          int fn[3], cn[3];
+          for (int d = 0; d < 3; ++d) {
+            fn[d] = hi3[d] - lo3[d];
+            cn[d] = ((hi3[d] - 1 + (N - 1)) >> 1) - ((lo3[d] - (N - 1)) >> 1) + 1;
+          }
+          int a = 0, c = 0;  // the refinement's order: thinnest side first, thickest last
+          for (int d = 1; d < 3; ++d) {
+            if (fn[d] < fn[a]) a = d;
+            if (fn[d] >= fn[c]) c = d;
+          }
+          if (a == c) c = (a + 2) % 3;
+          const int m = 3 - a - c;
+          return (long)fn[a] * cn[m] * cn[c] + (long)fn[a] * fn[m] * cn[c] <= capU;
+        };
+        unsigned left = (unsigned)mask & ~(1u << 13);
+        int n = 0;
+        while (left) {
+          const int c0 = __ffs(left) - 1;
+          const int x0 = c0 % 3, y0 = (c0 / 3) % 3, z0 = c0 / 9;
+          int x1 = x0 + 1, y1 = y0 + 1, z1 = z0 + 1;
+          while (x1 < 3 && ((left >> (x1 + 3 * y0 + 9 * z0)) & 1) && fits(x0, x1 + 1, y0, y1, z0, z1)) ++x1;
+          while (y1 < 3 && (left & rect(x0, x1, y1, y1 + 1, z0, z0 + 1)) == rect(x0, x1, y1, y1 + 1, z0, z0 + 1) &&
+                 fits(x0, x1, y0, y1 + 1, z0, z1))
+            ++y1;
+          while (z1 < 3 && (left & rect(x0, x1, y0, y1, z1, z1 + 1)) == rect(x0, x1, y0, y1, z1, z1 + 1) &&
+                 fits(x0, x1, y0, y1, z0, z1 + 1))
+            ++z1;
+          left &= ~rect(x0, x1, y0, y1, z0, z1);
+          rbox.lo[n][0] = cutr[x0], rbox.hi[n][0] = cutr[x1];
+          rbox.lo[n][1] = cutr[y0], rbox.hi[n][1] = cutr[y1];
+          rbox.lo[n][2] = cutr[z0], rbox.hi[n][2] = cutr[z1];
+          ++n;
+        }
+        rbox.n = n;
+      }
+      // band boxes: the (disjoint) band cells merged greedily, x run first,
+      // then y, then z
+      const int cut[4] = {0, ov ? nb - W::ext_f : W::ext_b, ov ? W::ext_b : nb - W::ext_f, nb};
       unsigned left = bc;
       int n = 0;
       while (left) {
@@ -392,17 +453,42 @@ __global__ void __launch_bounds__(512, sizeof(TP) == 4 ? 2 : 1) k_prep(Tree t, c
         ok &= cl[d] >= qlo && cl[d] + cn[d] <= qlo + nq;
       }
       if (!ok) continue;  // flagged by the refinement below
-      const int m = cn[0] * cn[1];
-      for (int idx = threadIdx.x; idx < m * cn[2]; idx += blockDim.x) {
-        const int qx = cl[0] + idx % cn[0], qy = cl[1] + (idx / cn[0]) % cn[1], qz = cl[2] + idx / m;
-        T[(qx - qlo) + (size_t)nq * ((qy - qlo) + (size_t)nq * (qz - qlo))] = fetch_raw(L - 1, qx, qy, qz);
+      // four points per thread and step, their loads issued together
+      const int cnt = cn[0] * cn[1] * cn[2], nthr = blockDim.x;
+      const DivM dc0 = divm(cn[0]), dc1 = divm(cn[1]);
+      auto qpt = [&](int idx, int &qx, int &qy, int &qz) {
+        const int r = divq(idx, dc0), z = divq(r, dc1);
+        qx = cl[0] + idx - r * cn[0], qy = cl[1] + r - z * cn[1], qz = cl[2] + z;
+      };
+      for (int i0 = threadIdx.x; i0 < cnt; i0 += 4 * nthr) {
+        long long si[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          si[u] = -2;
+          if (i0 + u * nthr < cnt) {
+            int qx, qy, qz;
+            qpt(i0 + u * nthr, qx, qy, qz);
+            si[u] = src_index(L - 1, qx, qy, qz);
+          }
+        }
+        TI v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = si[u] >= 0 ? ld(phi + si[u]) : TI(0);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (si[u] == -2) continue;
+          int qx, qy, qz;
+          qpt(i0 + u * nthr, qx, qy, qz);
+          T[(qx - qlo) + nq * ((qy - qlo) + nq * (qz - qlo))] = si[u] >= 0 ? v[u] : fetch_slow(L - 1, qx, qy, qz);
+        }
       }
     }
   } else if (tile) {
     // coarse tile, one row of nq values per warp
+    const DivM dnq = divm(nq);
     for (int row = threadIdx.x >> 5; row < nq * nq; row += nwarp) {
-      const int qy = qlo + row % nq, qz = qlo + row / nq;
-      for (int x = lane; x < nq; x += 32) T[x + (size_t)nq * row] = fetch_raw(L - 1, qlo + x, qy, qz);
+      const int z = divq(row, dnq), qy = qlo + row - z * nq, qz = qlo + z;
+      for (int x = lane; x < nq; x += 32) T[x + nq * row] = fetch_raw(L - 1, qlo + x, qy, qz);
     }
   }
   TP *Pb = P + (size_t)b * np;
@@ -447,7 +533,7 @@ __global__ void __launch_bounds__(512, sizeof(TP) == 4 ? 2 : 1) k_prep(Tree t, c
     constexpr bool FP = sizeof(TI) == 4 && sizeof(TP) == 8 && f32_exact_taps<N, NT, FK_K>();
     TP *U = reinterpret_cast<TP *>(smraw + tile_bytes);
     constexpr int ko = N - 1;  // widest odd K^s tap
-    const long ts[3] = {1, nq, (long)nq * nq}, ps[3] = {1, Wd, (long)Wd * Wd};
+    const int ts[3] = {1, nq, nq * nq}, ps[3] = {1, Wd, Wd * Wd};
     for (int e = 0; e < rbox.n; ++e) {
       int fl[3], fn[3], cl[3], cn[3];
       bool ok = true;
@@ -472,7 +558,7 @@ __global__ void __launch_bounds__(512, sizeof(TP) == 4 ? 2 : 1) k_prep(Tree t, c
       // per-box scalars (the loops below index nothing dynamically)
       const int nfa = fn[a], nfb = fn[bd], nfc = fn[c], ncb = cn[bd], ncc = cn[c];
       const int la = fl[a], lb = fl[bd], lc = fl[c], cb = cl[bd], cc = cl[c];
-      const long tsa = ts[a], tsb = ts[bd], tsc = ts[c], psa = ps[a], psb = ps[bd], psc = ps[c];
+      const int tsa = ts[a], tsb = ts[bd], tsc = ts[c], psa = ps[a], psb = ps[bd], psc = ps[c];
       TP *U1 = U, *U2 = U + (size_t)nfa * ncb * ncc;
       if constexpr (FP) {
         // FP32 field, FP64 block: the three passes in float pairs (same
@@ -480,10 +566,12 @@ __global__ void __launch_bounds__(512, sizeof(TP) == 4 ? 2 : 1) k_prep(Tree t, c
         F2 *V1 = reinterpret_cast<F2 *>(U1), *V2 = reinterpret_cast<F2 *>(U2);
         {
           const int no = par_count(la, la + nfa, 1), ne = nfa - no, m = ncb * ncc;
+          const DivM dno = divm(no > 0 ? no : 1), dne = divm(ne > 0 ? ne : 1), dcb = divm(ncb);
           for (int idx = threadIdx.x; idx < nfa * m; idx += blockDim.x) {
             const bool od = idx < no * m;
             const int q = od ? idx : idx - no * m, nh = od ? no : ne;
-            const int f = par_first(la, od) + 2 * (q % nh), r = q / nh, jb = r % ncb, kc = r / ncb;
+            const int r = divq(q, od ? dno : dne), kc = divq(r, dcb);
+            const int f = par_first(la, od) + 2 * (q - r * nh), jb = r - kc * ncb;
             const TI *tp = T + (cb + jb - qlo) * tsb + (cc + kc - qlo) * tsc;
             F2 v;
             if (od) {
@@ -501,11 +589,13 @@ __global__ void __launch_bounds__(512, sizeof(TP) == 4 ? 2 : 1) k_prep(Tree t, c
         __syncthreads();
         {
           const int no = par_count(lb, lb + nfb, 1), ne = nfb - no;
+          const DivM dfa = divm(nfa), dno = divm(no > 0 ? no : 1), dne = divm(ne > 0 ? ne : 1);
           for (int idx = threadIdx.x; idx < nfa * nfb * ncc; idx += blockDim.x) {
             const bool od = idx < nfa * no * ncc;
             const int q = od ? idx : idx - nfa * no * ncc, nh = od ? no : ne;
-            const int ia = q % nfa, f = par_first(lb, od) + 2 * ((q / nfa) % nh), kc = q / (nfa * nh);
-            const F2 *up = V1 + ia + (size_t)nfa * ncb * kc;
+            const int r = divq(q, dfa), kc = divq(r, od ? dno : dne);
+            const int ia = q - r * nfa, f = par_first(lb, od) + 2 * (r - kc * nh);
+            const F2 *up = V1 + ia + nfa * ncb * kc;
             F2 v;
             if (od) {
               v = f2_of(0.f);
@@ -521,19 +611,21 @@ __global__ void __launch_bounds__(512, sizeof(TP) == 4 ? 2 : 1) k_prep(Tree t, c
         __syncthreads();
         {
           const int no = par_count(lc, lc + nfc, 1), ne = nfc - no, m = nfa * nfb;
+          const DivM dfa = divm(nfa), dfb = divm(nfb);
           for (int idx = threadIdx.x; idx < m * nfc; idx += blockDim.x) {
             const bool od = idx < m * no;
             const int q = od ? idx : idx - m * no;
-            const int ia = q % nfa, ib = (q / nfa) % nfb, f = par_first(lc, od) + 2 * (q / m);
-            const F2 *up = V2 + ia + (size_t)nfa * ib;
+            const int r = divq(q, dfa), z = divq(r, dfb);
+            const int ia = q - r * nfa, ib = r - z * nfb, f = par_first(lc, od) + 2 * z;
+            const F2 *up = V2 + ia + nfa * ib;
             F2 v;
             if (od) {
               v = f2_of(0.f);
 #pragma unroll
               for (int t = -ko; t <= ko; t += 2)
-                v = f2_acc(v, float(Wav<N, NT>::K(t)), up[(size_t)m * (((f + t) >> 1) - cc)]);
+                v = f2_acc(v, float(Wav<N, NT>::K(t)), up[m * (((f + t) >> 1) - cc)]);
             } else {
-              v = up[(size_t)m * ((f >> 1) - cc)];
+              v = up[m * ((f >> 1) - cc)];
             }
             const TP d = f2_dbl(v);
             if (nan_bits(d)) atomicOr(err, 2);
@@ -546,10 +638,12 @@ __global__ void __launch_bounds__(512, sizeof(TP) == 4 ? 2 : 1) k_prep(Tree t, c
       // pass 1: along a, coarse tile -> U1[ia][jb][kc] (odd fine points first)
       {
         const int no = par_count(la, la + nfa, 1), ne = nfa - no, m = ncb * ncc;
+        const DivM dno = divm(no > 0 ? no : 1), dne = divm(ne > 0 ? ne : 1), dcb = divm(ncb);
         for (int idx = threadIdx.x; idx < nfa * m; idx += blockDim.x) {
           const bool od = idx < no * m;
           const int q = od ? idx : idx - no * m, nh = od ? no : ne;
-          const int f = par_first(la, od) + 2 * (q % nh), r = q / nh, jb = r % ncb, kc = r / ncb;
+          const int r = divq(q, od ? dno : dne), kc = divq(r, dcb);
+          const int f = par_first(la, od) + 2 * (q - r * nh), jb = r - kc * ncb;
           const TI *tp = T + (cb + jb - qlo) * tsb + (cc + kc - qlo) * tsc;
           TP v;
           if (od) {
@@ -567,11 +661,13 @@ __global__ void __launch_bounds__(512, sizeof(TP) == 4 ? 2 : 1) k_prep(Tree t, c
       // pass 2: along b, U1 -> U2[ia][ib][kc]
       {
         const int no = par_count(lb, lb + nfb, 1), ne = nfb - no;
+        const DivM dfa = divm(nfa), dno = divm(no > 0 ? no : 1), dne = divm(ne > 0 ? ne : 1);
         for (int idx = threadIdx.x; idx < nfa * nfb * ncc; idx += blockDim.x) {
           const bool od = idx < nfa * no * ncc;
           const int q = od ? idx : idx - nfa * no * ncc, nh = od ? no : ne;
-          const int ia = q % nfa, f = par_first(lb, od) + 2 * ((q / nfa) % nh), kc = q / (nfa * nh);
-          const TP *up = U1 + ia + (size_t)nfa * ncb * kc;
+          const int r = divq(q, dfa), kc = divq(r, od ? dno : dne);
+          const int ia = q - r * nfa, f = par_first(lb, od) + 2 * (r - kc * nh);
+          const TP *up = U1 + ia + nfa * ncb * kc;
           TP v;
           if (od) {
             v = TP(0);
@@ -587,18 +683,20 @@ __global__ void __launch_bounds__(512, sizeof(TP) == 4 ? 2 : 1) k_prep(Tree t, c
       // pass 3: along c, U2 -> padded block
       {
         const int no = par_count(lc, lc + nfc, 1), ne = nfc - no, m = nfa * nfb;
+        const DivM dfa = divm(nfa), dfb = divm(nfb);
         for (int idx = threadIdx.x; idx < m * nfc; idx += blockDim.x) {
           const bool od = idx < m * no;
           const int q = od ? idx : idx - m * no;
-          const int ia = q % nfa, ib = (q / nfa) % nfb, f = par_first(lc, od) + 2 * (q / m);
-          const TP *up = U2 + ia + (size_t)nfa * ib;
+          const int r = divq(q, dfa), z = divq(r, dfb);
+          const int ia = q - r * nfa, ib = r - z * nfb, f = par_first(lc, od) + 2 * z;
+          const TP *up = U2 + ia + nfa * ib;
           TP v;
           if (od) {
             v = TP(0);
 #pragma unroll
-            for (int t = -ko; t <= ko; t += 2) v = racc(v, TP(Wav<N, NT>::K(t)), up[(size_t)m * (((f + t) >> 1) - cc)]);
+            for (int t = -ko; t <= ko; t += 2) v = racc(v, TP(Wav<N, NT>::K(t)), up[m * (((f + t) >> 1) - cc)]);
           } else {
-            v = up[(size_t)m * ((f >> 1) - cc)];
+            v = up[m * ((f >> 1) - cc)];
           }
           if (nan_bits(v)) atomicOr(err, 2);
           Pb[(la + ia + Gi) * psa + (lb + ib + Gi) * psb + (f + Gi) * psc] = v;
@@ -615,7 +713,7 @@ __global__ void __launch_bounds__(512, sizeof(TP) == 4 ? 2 : 1) k_prep(Tree t, c
           return Cvt<TP>::f(T[qx + nq * (qy + nq * qz)]);
         });
         if (nan_bits(v)) atomicOr(err, 2);
-        Pb[(i + Gi) + Wd * ((j + Gi) + (size_t)Wd * (k + Gi))] = v;
+        Pb[(i + Gi) + Wd * ((j + Gi) + Wd * (k + Gi))] = v;
       });
     };
     refine_cls(Cls<0, 0, 0>());
@@ -633,9 +731,9 @@ __global__ void __launch_bounds__(512, sizeof(TP) == 4 ? 2 : 1) k_prep(Tree t, c
   auto subst_cls = [&](auto cls) {
     constexpr int OX = decltype(cls)::x, OY = decltype(cls)::y, OZ = decltype(cls)::z;
     for_class_points<OX, OY, OZ>(sbox, [&](int i, int j, int k) {
-      TP *c = Pb + (i + Gi) + Wd * ((j + Gi) + (size_t)Wd * (k + Gi));
+      TP *c = Pb + (i + Gi) + Wd * ((j + Gi) + Wd * (k + Gi));
       *c = subst_sum<N, NT, OX, OY, OZ, TP>([&](int tx, int ty, int tz) -> TP {
-        return c[tx + Wd * (ty + (long)Wd * tz)];
+        return c[tx + Wd * (ty + Wd * tz)];
       });
     });
   };
@@ -649,71 +747,125 @@ __global__ void __launch_bounds__(512, sizeof(TP) == 4 ? 2 : 1) k_prep(Tree t, c
   subst_sep<N, NT, TP>(Pb, Wd, Gi, sbox, 3, reinterpret_cast<TP *>(smraw), (long)dyn_bytes / (long)sizeof(TP));
   __syncthreads();
   if (only_coarse == 2) return;  // substitution only: no fine-to-coarse push
-  // distinct coarser neighbours
+  // distinct coarser neighbours, and the boxes of this leaf's coarse points
+  // that lie in their ghost shells: per coarser direction, the Gpush coarse
+  // layers next to it (whole extent along the other dimensions); boxes inside
+  // another box dropped
+  const int gp = min(Gpush, hb);
+  __shared__ int pbox[27][6];  // coarse-local [x0, x1) [y0, y1) [z0, z1)
+  __shared__ int npb;
   if (threadIdx.x == 0) {
+    int n = 0;
     for (int m = 0; m < 27; ++m) {
       if (!((mask >> m) & 1)) continue;
       const int o = rslot[m];
       bool seen = false;
       for (int q = 0; q < ncs; ++q) seen |= cslots[q] == o;
       if (!seen) cslots[ncs++] = o;
+      const int dd[3] = {m % 3 - 1, (m / 3) % 3 - 1, m / 9 - 1};
+      int bx[6];
+      for (int d = 0; d < 3; ++d) {
+        bx[2 * d] = dd[d] > 0 ? hb - gp : 0;
+        bx[2 * d + 1] = dd[d] < 0 ? gp : hb;
+      }
+      auto inside = [](const int *a, const int *c) {  // a within c
+        return a[0] >= c[0] && a[1] <= c[1] && a[2] >= c[2] && a[3] <= c[3] && a[4] >= c[4] && a[5] <= c[5];
+      };
+      bool covered = false;
+      for (int q = 0; q < n && !covered; ++q) covered = inside(bx, pbox[q]);
+      if (covered) continue;
+      int w = 0;
+      for (int q = 0; q < n; ++q)
+        if (!inside(pbox[q], bx)) {
+          for (int v = 0; v < 6; ++v) pbox[w][v] = pbox[q][v];
+          ++w;
+        }
+      for (int v = 0; v < 6; ++v) pbox[w][v] = bx[v];
+      n = w + 1;
     }
+    // two boxes whose bounding box is no larger than their volumes together
+    // become that box (wide shells: the face boxes nearly coincide)
+    auto vol = [](const int *a) { return (a[1] - a[0]) * (a[3] - a[2]) * (a[5] - a[4]); };
+    for (bool merged = true; merged;) {
+      merged = false;
+      for (int q = 0; q < n && !merged; ++q)
+        for (int u = q + 1; u < n && !merged; ++u) {
+          int bb[6];
+          for (int d = 0; d < 3; ++d) {
+            bb[2 * d] = min(pbox[q][2 * d], pbox[u][2 * d]);
+            bb[2 * d + 1] = max(pbox[q][2 * d + 1], pbox[u][2 * d + 1]);
+          }
+          if (vol(bb) <= vol(pbox[q]) + vol(pbox[u])) {
+            for (int v = 0; v < 6; ++v) pbox[q][v] = bb[v], pbox[u][v] = pbox[n - 1][v];
+            --n;
+            merged = true;
+          }
+        }
+    }
+    npb = n;
   }
   __syncthreads();
-  // Part 2: H^a coarsening of the padded block at every coarse point of the
-  // leaf, evaluated once and separably (x, then y, then z; zc coarse z-planes
-  // per chunk so the partial sums fit in shared memory), then written to each
+  // Part 2: H^a coarsening of the padded block at the coarse points of those
+  // boxes, evaluated separably (x, then y, then z; zc coarse z-planes per
+  // chunk so the partial sums fit in shared memory), then written to each
   // periodic image of the point that lies in the ghost shell (Gpush) of a
   // coarser neighbour.
   constexpr int hH = W::hwH;
-  const int hb = nb / 2, nf = nb - 1 + 2 * hH, Wg = nb + 2 * Gi;
-  TP *A = reinterpret_cast<TP *>(smraw);  // x-pass [nk][nf][hb]
-  for (int pz0 = 0; pz0 < hb; pz0 += zc) {
-    const int zn = min(zc, hb - pz0), k0 = 2 * pz0 - hH, nk = 2 * zn - 1 + 2 * hH;
-    TP *B = A + (size_t)nk * nf * hb;  // y-pass [nk][hb][hb]
-    for (int idx = threadIdx.x; idx < hb * nf * nk; idx += blockDim.x) {
-      const int px = idx % hb, j = (idx / hb) % nf - hH, k = idx / (hb * nf) + k0;
-      A[idx] = tap_sum<N, NT, FK_H>(Pb + (size_t)(2 * px + Gi) + Wd * ((j + Gi) + (size_t)Wd * (k + Gi)), 1);
-    }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < hb * hb * nk; idx += blockDim.x) {
-      const int px = idx % hb, py = (idx / hb) % hb, kk = idx / (hb * hb);
-      B[idx] = tap_sum<N, NT, FK_H>(A + ((size_t)kk * nf + 2 * py + hH) * hb + px, hb);
-    }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < hb * hb * zn; idx += blockDim.x) {
-      const int px = idx % hb, py = (idx / hb) % hb, pz = idx / (hb * hb);
-      const TP sv = tap_sum<N, NT, FK_H>(B + ((size_t)(2 * pz + hH) * hb + py) * hb + px, (long)hb * hb);
-      // coarse (level L-1) point, global index
-      const int G[3] = {ax / 2 + px, ay / 2 + py, az / 2 + pz0 + pz};
-      for (int ci = 0; ci < ncs; ++ci) {
-        const int c = cslots[ci];
-        // c-local offsets of every periodic image of G in c's shell (tiny
-        // periodic domains: c can see this leaf on both sides)
-        int cand[3][3], ncand[3];
-        bool any = true;
-        for (int d = 0; d < 3; ++d) {
-          const int Pn = period(t, L - 1, d);
-          const int off = pwrap(G[d] - __ldg(t.anc + 3 * c + d) * nb, Pn);
-          ncand[d] = 0;
-          for (int sh = -1; sh <= 1; ++sh) {
-            const int o = off + sh * Pn;
-            if (o >= -Gpush && o < nb + Gpush) cand[d][ncand[d]++] = o;
-          }
-          any &= ncand[d] > 0;
-        }
-        if (!any) continue;
-        for (int iz = 0; iz < ncand[2]; ++iz)
-          for (int iy = 0; iy < ncand[1]; ++iy)
-            for (int ix = 0; ix < ncand[0]; ++ix) {
-              const int lc[3] = {cand[0][ix], cand[1][iy], cand[2][iz]};
-              const bool inside = lc[0] >= 0 && lc[0] < nb && lc[1] >= 0 && lc[1] < nb && lc[2] >= 0 && lc[2] < nb;
-              if (inside) continue;
-              Q[(size_t)c * np + (lc[0] + Gi) + Wg * ((lc[1] + Gi) + (size_t)Wg * (lc[2] + Gi))] = sv;
-            }
+  const int Wg = nb + 2 * Gi;
+  TP *A = reinterpret_cast<TP *>(smraw);  // x-pass [nk][nfj][nx]
+  for (int e = 0; e < npb; ++e) {
+    const int x0 = pbox[e][0], nx = pbox[e][1] - x0, y0 = pbox[e][2], ny = pbox[e][3] - y0;
+    const int z0 = pbox[e][4], z1 = pbox[e][5];
+    const int nfj = 2 * ny - 1 + 2 * hH, jlo = 2 * y0 - hH;  // fine rows the y pass reads
+    const DivM dnx = divm(nx), dny = divm(ny), dnf = divm(nfj);
+    for (int pz0 = z0; pz0 < z1; pz0 += zc) {
+      const int zn = min(zc, z1 - pz0), k0 = 2 * pz0 - hH, nk = 2 * zn - 1 + 2 * hH;
+      TP *B = A + nk * nfj * nx;  // y-pass [nk][ny][nx]
+      for (int idx = threadIdx.x; idx < nx * nfj * nk; idx += blockDim.x) {
+        const int r = divq(idx, dnx), kr = divq(r, dnf);
+        const int px = x0 + idx - r * nx, j = jlo + r - kr * nfj, k = kr + k0;
+        A[idx] = tap_sum<N, NT, FK_H>(Pb + (2 * px + Gi) + Wd * ((j + Gi) + Wd * (k + Gi)), 1);
       }
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < nx * ny * nk; idx += blockDim.x) {
+        const int r = divq(idx, dnx), kk = divq(r, dny), px = idx - r * nx, py = r - kk * ny;
+        B[idx] = tap_sum<N, NT, FK_H>(A + (kk * nfj + 2 * py + hH) * nx + px, nx);
+      }
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < nx * ny * zn; idx += blockDim.x) {
+        const int r = divq(idx, dnx), pz = divq(r, dny), px = idx - r * nx, py = r - pz * ny;
+        const TP sv = tap_sum<N, NT, FK_H>(B + ((2 * pz + hH) * ny + py) * nx + px, nx * ny);
+        // coarse (level L-1) point, global index
+        const int G[3] = {ax / 2 + x0 + px, ay / 2 + y0 + py, az / 2 + pz0 + pz};
+        for (int ci = 0; ci < ncs; ++ci) {
+          const int c = cslots[ci];
+          // c-local offsets of every periodic image of G in c's shell (tiny
+          // periodic domains: c can see this leaf on both sides)
+          int cand[3][3], ncand[3];
+          bool any = true;
+          for (int d = 0; d < 3; ++d) {
+            const int Pn = period(t, L - 1, d);
+            const int off = pwrap(G[d] - __ldg(t.anc + 3 * c + d) * nb, Pn);
+            ncand[d] = 0;
+            for (int sh = -1; sh <= 1; ++sh) {
+              const int o = off + sh * Pn;
+              if (o >= -Gpush && o < nb + Gpush) cand[d][ncand[d]++] = o;
+            }
+            any &= ncand[d] > 0;
+          }
+          if (!any) continue;
+          for (int iz = 0; iz < ncand[2]; ++iz)
+            for (int iy = 0; iy < ncand[1]; ++iy)
+              for (int ix = 0; ix < ncand[0]; ++ix) {
+                const int lc[3] = {cand[0][ix], cand[1][iy], cand[2][iz]};
+                const bool inside = lc[0] >= 0 && lc[0] < nb && lc[1] >= 0 && lc[1] < nb && lc[2] >= 0 && lc[2] < nb;
+                if (inside) continue;
+                Q[(size_t)c * np + (lc[0] + Gi) + Wg * ((lc[1] + Gi) + (size_t)Wg * (lc[2] + Gi))] = sv;
+              }
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 
@@ -863,6 +1015,15 @@ static size_t sep_refine_elems(int N, int nb, int Gi) {
   return best;
 }
 
+// partial sums of the separable refinement of one whole side of the padded
+// block (Gi x Wd x Wd fine points, its coarse extents), the largest box the
+// kernel builds from merged regions
+static size_t side_refine_elems(int N, int nb, int Gi) {
+  const int ko = N - 1, wd = nb + 2 * Gi;
+  const int cw = ((nb + Gi - 1 + ko) >> 1) - ((-Gi - ko) >> 1) + 1;
+  return (size_t)Gi * cw * cw + (size_t)Gi * wd * cw;
+}
+
 // shared memory of the separable Part-2 coarsening for zc coarse z-planes
 template <int N, int NT>
 static size_t push_smem(int nb, int zc, size_t es) {
@@ -900,15 +1061,18 @@ __global__ void __launch_bounds__(512) k_merge(Tree t, TP *__restrict__ P, const
       ext[d] = dd[d] ? G : nb;
     }
     const int cnt = ext[0] * ext[1] * ext[2];
+    const DivM de0 = divm(ext[0]), de1 = divm(ext[1]);
     for (int p = threadIdx.x; p < cnt; p += blockDim.x) {
-      const int i = lo[0] + p % ext[0], j = lo[1] + (p / ext[0]) % ext[1], k = lo[2] + p / (ext[0] * ext[1]);
+      const int r = divq(p, de0), z = divq(r, de1);
+      const int i = lo[0] + p - r * ext[0], j = lo[1] + r - z * ext[1], k = lo[2] + z;
       const size_t q = (size_t)b * np + (i + Gi) + Wd * ((j + Gi) + (size_t)Wd * (k + Gi));
       P[q] = Q[q];
     }
   }
   if (phi_out && cmask[b]) {
+    const DivM dnb = divm(nb);
     for (int p = threadIdx.x; p < nb * nb * nb; p += blockDim.x) {
-      const int i = p % nb, j = (p / nb) % nb, k = p / (nb * nb);
+      const int r = divq(p, dnb), k = divq(r, dnb), i = p - r * nb, j = r - k * nb;
       if (!((i | j | k) & 1)) continue;  // 0-degree points are never substituted
       phi_out[(size_t)b * nb * nb * nb + p] =
           TO(P[(size_t)b * np + (i + Gi) + Wd * ((j + Gi) + (size_t)Wd * (k + Gi))]);
@@ -947,8 +1111,15 @@ int ghost_impl(mr_grid *g, const TI *phi_in, TI *phi_out, int G, TP *P, TP *Q, i
   int *err = g->counter + 1;
   const int nq = tq_hi<N>(nb, Gi) - tq_lo<N>(Gi) + 1;
   const size_t smT = (sizeof(TI) * (size_t)nq * nq * nq + 15) & ~(size_t)15;
-  const size_t smU = sizeof(TP) * sep_refine_elems(N, nb, Gi);
   const size_t budget = 220 * 1024;
+  // partial sums of the separable refinement: at least one region's, and up
+  // to a whole side of the padded block (the kernel merges the coarser
+  // regions into boxes that fit) as long as the occupancy stays (two CTAs
+  // per SM where one region's sums allow it)
+  const size_t smU1 = sizeof(TP) * sep_refine_elems(N, nb, Gi);
+  const size_t smUs = sizeof(TP) * side_refine_elems(N, nb, Gi);
+  const size_t target = smT + smU1 <= 110 * 1024 && sizeof(TP) == 4 ? 110 * 1024 : budget;
+  const size_t smU = std::max(smU1, std::min(smUs, target > smT ? (target - smT) & ~(size_t)15 : (size_t)0));
   // 2: coarse tile + separable refinement, 1: tile + per-point tensor sums,
   // 0: per-point sums through the owner map
   const int use_tile = smT + smU <= budget ? 2 : smT <= budget ? 1 : 0;
@@ -957,8 +1128,9 @@ int ghost_impl(mr_grid *g, const TI *phi_in, TI *phi_out, int G, TP *P, TP *Q, i
   const size_t smP = push_smem<N, NT>(nb, zc, sizeof(TP));
   if (smP > 227 * 1024) return MR_ERR_UNSUPPORTED;
   const size_t sm = std::max(use_tile == 2 ? smT + smU : use_tile ? smT : (size_t)0, smP);
-  if (sm > 48 * 1024 &&
-      check_cuda(cudaFuncSetAttribute(k_prep<TI, TP, N, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
+  // (set on every launch: the kernel's static shared memory counts against
+  // the 48 KB that needs no opt-in)
+  if (check_cuda(cudaFuncSetAttribute(k_prep<TI, TP, N, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
                  "k_prep smem"))
     return MR_ERR_CUDA;
   // The plain gather writes every region but the coarser leaves' of the

@@ -158,16 +158,17 @@ __device__ __forceinline__ F2 f2_split(double x) {
   return {__uint_as_float(hi), __uint_as_float(sgn | ((unsigned)le << 23) | (((r << lz) >> 8) & 0x7fffffu))};
 }
 
-// x / d for 0 <= x, 2 <= d, x d < 2^32, as a multiply-high with
-// m = ceil(2^32 / d): x m / 2^32 = x/d + x e / (d 2^32) with e = m d - 2^32
-// < d, so the excess stays below 1/d and the floor is exact.  Every index
-// decomposition of one block (x < Wd^3, d <= Wd) is inside that range.
+// x / d for 0 <= x, 1 <= d, x d < 2^32, as a multiply-high with
+// m = ceil(2^32 / d) (d >= 2): x m / 2^32 = x/d + x e / (d 2^32) with
+// e = m d - 2^32 < d, so the excess stays below 1/d and the floor is exact;
+// d = 1 is selected.  Every index decomposition of one block (x < Wd^3,
+// d <= Wd) is inside that range.  divr: the remainder.
 struct DivM {
   unsigned m;
   int d;
 };
-__device__ __forceinline__ DivM divm(int d) { return {0xffffffffu / (unsigned)d + 1u, d}; }
-__device__ __forceinline__ int divq(int x, DivM v) { return (int)__umulhi((unsigned)x, v.m); }
+__host__ __device__ __forceinline__ DivM divm(int d) { return {d > 1 ? 0xffffffffu / (unsigned)d + 1u : 0u, d}; }
+__device__ __forceinline__ int divq(int x, DivM v) { return v.d > 1 ? (int)__umulhi((unsigned)x, v.m) : x; }
 
 // value of the field element type TI in the working precision TP
 template <typename TP>
@@ -219,7 +220,7 @@ __device__ __forceinline__ void for_taps(F f) {
 }
 // sum_t w(t) p[t * stride]
 template <int N, int NT, int KIND, typename TP>
-__device__ __forceinline__ TP tap_sum(const TP *p, long stride) {
+__device__ __forceinline__ TP tap_sum(const TP *p, int stride) {
   TP s = TP(0);
   for_taps<N, NT, KIND>([&](int t, double w) { s = racc(s, TP(w), p[t * stride]); });
   return s;
@@ -367,12 +368,14 @@ __device__ __forceinline__ void for_class_points(const BoxList &bl, F f) {
   for (int e = 0; e < bl.n; ++e) total += cnt3(e, nx, ny);
   if (!total) return;
   int e = 0, base = 0, cnt = cnt3(0, nx, ny);
+  DivM dx = divm(nx > 0 ? nx : 1), dy = divm(ny > 0 ? ny : 1);
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
     while (idx >= base + cnt) {
       base += cnt;
       cnt = cnt3(++e, nx, ny);
+      dx = divm(nx > 0 ? nx : 1), dy = divm(ny > 0 ? ny : 1);
     }
-    const int q = idx - base, qx = q % nx, qy = (q / nx) % ny, qz = q / (nx * ny);
+    const int q = idx - base, r = divq(q, dx), qz = divq(r, dy), qx = q - r * nx, qy = r - qz * ny;
     f(par_first(bl.lo[e][0], OX) + 2 * qx, par_first(bl.lo[e][1], OY) + 2 * qy,
       par_first(bl.lo[e][2], OZ) + 2 * qz);
   }
@@ -400,10 +403,15 @@ struct Tree {
   const int *map; // mdim[0]*mdim[1]*mdim[2]
   double tree_len;
   int indep;      // every tree is its own periodic domain (independent grids)
+  DivM dnb;       // division by nb
 };
 
+// g mod P in [0, P): one period off (every neighbourhood read) without a division
 __device__ __forceinline__ int pwrap(int g, int P) {
-  int r = g % P;
+  if ((unsigned)g < (unsigned)P) return g;
+  if (g < 0 && g >= -P) return g + P;
+  if (g >= P && g - P < P) return g - P;
+  const int r = g % P;
   return r < 0 ? r + P : r;
 }
 
@@ -428,9 +436,9 @@ __device__ __forceinline__ int period(const Tree &t, int L, int d) {
 // domain of leaf hb, the leaf whose neighbourhood is being read)
 __device__ __forceinline__ int owner(const Tree &t, int L, int gx, int gy, int gz, int hb) {
   const int s = t.M - L;
-  int cx = (wrap_pt(t, L, gx, 0, hb) << s) / t.nb;
-  int cy = (wrap_pt(t, L, gy, 1, hb) << s) / t.nb;
-  int cz = (wrap_pt(t, L, gz, 2, hb) << s) / t.nb;
+  const int cx = divq(wrap_pt(t, L, gx, 0, hb) << s, t.dnb);
+  const int cy = divq(wrap_pt(t, L, gy, 1, hb) << s, t.dnb);
+  const int cz = divq(wrap_pt(t, L, gz, 2, hb) << s, t.dnb);
   return __ldg(t.map + cx + t.mdim[0] * (cy + t.mdim[1] * cz));
 }
 
