@@ -278,8 +278,10 @@ int mr_graph_replays(mr_grid *grid, long long *n);
  * overwrite their outputs from unchanged inputs, so repeating them changes
  * nothing -- and keeps the fastest in a table shared by every grid of the
  * process (later launches of that configuration use it whether or not their
- * grid tunes).  Results do not depend on the choice: every output point is
- * computed with the same arithmetic whatever the CTA size.  No tuning happens
+ * grid tunes).  Results do not depend on the CTA size: every output point is
+ * computed with the same arithmetic whatever the size.  On FP32 grids left
+ * at mr_set_stage_kernel(grid, 0) the tuner also picks the faster of the two
+ * stage kernels (see there: equal up to the last bit).  No tuning happens
  * while a step is being captured into a CUDA graph.  The paper has no
  * counterpart (its code runs one block after the other per MPI rank).
  * mr_autotune_table writes one line per tuned configuration (chosen size
@@ -289,6 +291,20 @@ int mr_graph_replays(mr_grid *grid, long long *n);
 int mr_autotune(mr_grid *grid, int enable);
 int mr_autotune_table(char *buf, size_t len, int *nentries);
 int mr_autotune_clear(void);
+
+/* Which kernel runs the FP32 stage (ghost faces + rhs + RK3 stage, the
+ * supplement's "Finite differences" and "Time integration" schemes) of
+ * mr_step, mr_step_vel, mr_step_vel_scaled, mr_rhs_advect and
+ * mr_rhs_advect_vel: 1 = k_fused (the ghost-extended block in shared memory,
+ * one thread per grid line), 2 = k_march (the block traversed plane by plane,
+ * one thread per grid column, two CTAs per SM), 0 = chosen by the autotuner
+ * on grids with mr_autotune enabled, else k_march (the default).  k_march
+ * needs 12 <= nb <= 24; other block sizes always use k_fused.  Both evaluate
+ * every value with the same operations in the same order; they may differ in
+ * the last bit where the compiler fuses a multiply and an add differently
+ * (measured within 1e-6 of the field maximum).  FP64 grids are unaffected.
+ * MR_ERR_INVALID for which outside 0..2.                                  */
+int mr_set_stage_kernel(mr_grid *grid, int which);
 
 /* Bounds of the adaptation loops: mr_adapt runs at most max_iter iterations
  * (default 64) and each iteration at most max_sweeps policy sweeps (default

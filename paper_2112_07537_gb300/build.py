@@ -18,7 +18,9 @@ LIB = os.path.join(OUT, "libmrgb.so")
 # the ghost kernels: one translation unit per (field type, block type,
 # wavelet) instantiation, so that ptxas runs on them in parallel
 GHOST_UNITS = [f"ghost_i_{t}{n}{nt}" for t in ("ff", "fd", "dd") for n in (2, 4, 6) for nt in (0, 2)]
-UNITS = ["ghost"] + GHOST_UNITS + ["stencil", "tree", "adapt", "abi", "peaks", "tune"]
+# the FP32 stage kernels: one translation unit per wavelet
+STAGE_UNITS = [f"stage_i_{n}{nt}" for n in (2, 4, 6) for nt in (0, 2)]
+UNITS = ["ghost"] + GHOST_UNITS + STAGE_UNITS + ["stencil", "tree", "adapt", "abi", "peaks", "tune"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v"]
 
@@ -38,6 +40,7 @@ def _stale(obj, deps):
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OUT, exist_ok=True)
     hdrs = [os.path.join(SRC, "mr_internal.cuh"), os.path.join(SRC, "ghost_kernels.cuh"),
+            os.path.join(SRC, "stage_kernels.cuh"),
             os.path.join(os.path.dirname(HERE), "include", "mrgb.h")]
     nvcc = _nvcc()
 

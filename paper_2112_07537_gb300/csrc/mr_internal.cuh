@@ -534,6 +534,7 @@ struct mr_grid {
   int gkey_len;
   long long graph_replays;
   int autotune;           // tune launch shapes at first use (mr_autotune)
+  int stage_kernel;       // FP32 stage kernel: 0 tuned, 1 k_fused, 2 k_march (mr_set_stage_kernel)
   // field_subst[f] = tree_version while field f holds the values a converged
   // mr_adapt left (every band next to a coarser leaf substituted in FP64 for
   // the current tree), -1 once anything may have written it
@@ -576,8 +577,9 @@ void *field_ptr(mr_grid *g, int fid);      // fid >= nfields: temporaries
 void *next_field_ptr(mr_grid *g, int fid);
 
 // tune.cu: launch-shape autotuner (kid: 0 k_fill_plain, 1 k_prep,
-// 2 k_criterion, 3 k_fused, 4 k_interp, 5 k_merge; tp: 4 FP32, 5 FP32
-// field with FP64 padded blocks, 8 FP64)
+// 2 k_criterion, 3 k_fused, 4 k_interp, 5 k_merge, 6 the FP32 stage kernel
+// variant (candidates 1 k_fused, 2 k_march); tp: 4 FP32, 5 FP32 field with
+// FP64 padded blocks, 8 FP64)
 struct TuneKey {
   int kid, N, Nt, nb, tp, shell, mode;
 };
@@ -605,6 +607,10 @@ int launch_substitute(mr_grid *g, void *phi, const int *need = nullptr, bool in_
 int launch_ghost_adapt32(mr_grid *g, const float *phi, int G, const int *need, void **P, int *Gi);
 int launch_fused(mr_grid *g, const void *phi, const void *P, const void *Q, int Gi, const void *u, void *out,
                  int stage, double dt, const double *uc, int scheme, bool rhs_only, const void *vpad = nullptr);
+// stage_kernels.cuh (instantiated in stage_i_*.cu)
+template <int N, int NT>
+int fused_launch(mr_grid *g, const float *phi, const float *P, const float *Q, int Gi, const float *u, float *out,
+                 int stage, double dt, const double *uc, int scheme, bool rhs_only, const float *vpad);
 int adapt_shell(int N, int Nt);
 // stencil.cu
 int launch_rhs_stage(mr_grid *g, const void *P, int Gi, const void *u, void *out, int stage,

@@ -1,0 +1,7 @@
+// Instantiation of the FP32 fused stage kernels for the 4.2 wavelet.
+#include "stage_kernels.cuh"
+
+namespace mr {
+template int fused_launch<4, 2>(mr_grid *, const float *, const float *, const float *, int, const float *,
+                                   float *, int, double, const double *, int, bool, const float *);
+}  // namespace mr

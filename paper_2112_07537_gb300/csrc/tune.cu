@@ -7,8 +7,11 @@
 // launches that give the same result when repeated are tuned (they read
 // their inputs and overwrite their outputs), so tuning changes no value:
 // every kernel computes each output point with the same arithmetic whatever
-// its CTA size.  Tuning is skipped while a step is being captured into a
-// CUDA graph (the cached or first candidate is used).
+// its CTA size.  One key (kid 6) chooses between the two FP32 stage kernels
+// instead, which evaluate the same operations in the same order (equal up to
+// where the compiler fuses a multiply-add differently).  Tuning is skipped
+// while a step is being captured into a CUDA graph (the cached or first
+// candidate is used).
 #include <cstdio>
 #include <map>
 #include <mutex>
@@ -31,7 +34,8 @@ std::mutex g_mu;
 std::map<TuneKey, Entry> g_table;
 
 const char *tune_kernel_name(int kid) {
-  static const char *names[] = {"k_fill_plain", "k_prep", "k_criterion", "k_fused", "k_interp", "k_merge"};
+  static const char *names[] = {"k_fill_plain", "k_prep", "k_criterion", "k_fused", "k_interp", "k_merge",
+                                "stage kernel (1 k_fused, 2 k_march)"};
   return kid >= 0 && kid < (int)(sizeof names / sizeof names[0]) ? names[kid] : "?";
 }
 
@@ -95,6 +99,12 @@ extern "C" int mr_autotune(mr_grid *g, int enable) {
   return MR_OK;
 }
 
+extern "C" int mr_set_stage_kernel(mr_grid *g, int which) {
+  if (!g || which < 0 || which > 2) return MR_ERR_INVALID;
+  g->stage_kernel = which;
+  return MR_OK;
+}
+
 extern "C" int mr_autotune_table(char *buf, size_t len, int *nentries) {
   using namespace mr;
   std::lock_guard<std::mutex> lk(g_mu);
@@ -105,9 +115,9 @@ extern "C" int mr_autotune_table(char *buf, size_t len, int *nentries) {
   for (const auto &kv : g_table) {
     const TuneKey &k = kv.first;
     const Entry &e = kv.second;
-    int n = snprintf(line, sizeof line, "%s N=%d.%d nb=%d %s shell=%d mode=%d -> %d threads (", tune_kernel_name(k.kid),
+    int n = snprintf(line, sizeof line, "%s N=%d.%d nb=%d %s shell=%d mode=%d -> %d %s (", tune_kernel_name(k.kid),
                      k.N, k.Nt, k.nb, k.tp == 8 ? "f64" : k.tp == 5 ? "f32->f64" : "f32", k.shell, k.mode,
-                     e.threads);
+                     e.threads, k.kid == 6 ? "variant" : "threads");
     out.append(line, n > 0 ? (size_t)n : 0);
     for (int c = 0; c < e.ncand; ++c) {
       n = snprintf(line, sizeof line, "%s%d: %.3f ms", c ? ", " : "", e.cand[c], e.ms[c]);

@@ -35,7 +35,8 @@ EXPORTS = ["mr_last_error", "mr_workspace_size", "mr_grid_create", "mr_grid_dest
            "mr_field_ptr", "mr_profile", "mr_profile_read", "mr_launch_count", "mr_profile_bytes", "mr_set_diffusion", "mr_step_vel_scaled",
            "mr_ghost_fill_static", "mr_rhs_advect_vel", "mr_step_vel", "mr_velocity_invalidate",
            "mr_device_peaks", "mr_dt", "mr_use_graphs", "mr_graph_replays", "mr_set_adapt_limits",
-           "mr_last_block_norms", "mr_autotune", "mr_autotune_table", "mr_autotune_clear"]
+           "mr_last_block_norms", "mr_autotune", "mr_autotune_table", "mr_autotune_clear",
+           "mr_set_stage_kernel"]
 
 
 class MRError(RuntimeError):
@@ -107,6 +108,7 @@ def load(path: str = LIB_PATH):
         L.mr_set_adapt_limits.argtypes = [vp, C.c_int, C.c_int]
         L.mr_last_block_norms.argtypes = [vp, vp, C.c_int, C.POINTER(C.c_int)]
         L.mr_autotune.argtypes = [vp, C.c_int]
+        L.mr_set_stage_kernel.argtypes = [vp, C.c_int]
         L.mr_autotune_table.argtypes = [C.c_char_p, C.c_size_t, C.POINTER(C.c_int)]
         _lib = L
     return _lib
@@ -353,6 +355,10 @@ class Grid:
         """Tune launch shapes on this grid's data at first use (mr_autotune)."""
         _chk(load().mr_autotune(self.h, int(enable)))
 
+    def set_stage_kernel(self, which):
+        """FP32 stage kernel: 0 tuned/default, 1 k_fused, 2 k_march (mr_set_stage_kernel)."""
+        _chk(load().mr_set_stage_kernel(self.h, int(which)))
+
     def use_graphs(self, enable=True):
         """Capture each RK step into a CUDA graph and replay it while unchanged."""
         _chk(load().mr_use_graphs(self.h, int(enable)))
@@ -377,3 +383,38 @@ class Grid:
         m = C.c_double()
         _chk(load().mr_mass(self.h, fid, C.byref(m)))
         return m.value
+
+    # ------------------------------------------------- checkpoint / resume
+    def checkpoint(self, path):
+        """Write the grid's description, its leaves (Morton order, as
+        mr_grid_leaves returns them) and every field (mr_field_copy_out) to
+        an .npz file.  Launch-shape, diffusion and graph settings are not
+        part of the checkpoint.  A restored field counts as freshly written:
+        a checkpoint taken after an RK step (which writes the field) resumes
+        bit for bit; right after mr_adapt, the restored grid substitutes the
+        fields once more at their next ghost fill, which the adapted grid
+        skips (the adaptation left them substituted), so values may differ
+        by rounding there.  The ghost-filled velocity cache is rebuilt."""
+        d = self.desc
+        lev, anc, _ = self.leaves()
+        fields = np.stack([self.field_copy_out(f) for f in range(self.nfields)])
+        np.savez(path, ntree=np.array(self.ntree), tree_len=self.tree_len, nb=self.nb, lmin=self.lmin,
+                 lmax=self.lmax, N=self.N, Nt=self.Nt, precision=self.precision, nfields=self.nfields,
+                 capacity=d.capacity, flags=d.flags, lev=lev, anc=anc, fields=fields)
+
+    @classmethod
+    def restore(cls, path, device="cuda", stream=None, capacity=None):
+        """A new grid from a checkpoint: the same leaves in the same slots
+        (mr_grid_create orders them as they were) and the same field values
+        (mr_field_copy_in), so every later call gives the results the saved
+        grid would have given."""
+        z = np.load(path)
+        flags = int(z["flags"])
+        g = cls(tuple(int(x) for x in z["ntree"]), float(z["tree_len"]), int(z["nb"]), int(z["lmin"]),
+                int(z["lmax"]), int(z["N"]), int(z["Nt"]), z["lev"], z["anc"], precision=int(z["precision"]),
+                nfields=int(z["nfields"]), capacity=capacity or int(z["capacity"]), device=device,
+                stream=stream, fixed_tree=bool(flags & GRID_FIXED_TREE), velocity=bool(flags & GRID_VELOCITY),
+                independent_trees=bool(flags & GRID_INDEPENDENT_TREES))
+        for f in range(g.nfields):
+            g.field_copy_in(f, z["fields"][f])
+        return g

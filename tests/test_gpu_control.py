@@ -142,9 +142,13 @@ def test_adaptation_beyond_capacity_is_refused(mr):
 
 @pytest.mark.parametrize("prec", [0, 1])
 def test_autotuned_launches_give_identical_results(mr, prec):
-    """The autotuner changes CTA sizes only: ghost fills, RK steps with
+    """The autotuner changes launch shapes only: ghost fills, RK steps with
     velocity fields and an adaptation on a tuning grid equal those of an
-    untuned twin bit for bit, and the table lists the tuned shapes."""
+    untuned twin -- bit for bit, except that on FP32 grids the tuner also
+    picks the faster of the two stage kernels, which evaluate the same
+    operations in the same order but may round a multiply-add differently
+    where the compiler fuses it (fields within 1e-6 of their maximum) --
+    and the table lists the tuned shapes."""
     import torch
     mr.autotune_clear()
     nt, tl, nb = (2, 2, 2), 0.5, 16
@@ -177,12 +181,17 @@ def test_autotuned_launches_give_identical_results(mr, prec):
     assert np.array_equal(pads[0], pads[1])
     assert np.array_equal(grids[0].leaves()[0], grids[1].leaves()[0])
     for f in range(4):
-        assert np.array_equal(grids[0].field_copy_out(f), grids[1].field_copy_out(f))
+        a, b = grids[0].field_copy_out(f), grids[1].field_copy_out(f)
+        if prec == 1:
+            assert np.array_equal(a, b)
+        else:
+            assert np.abs(a.astype(np.float64) - b).max() <= 1e-6 * np.abs(a).max()
     table = mr.autotune_table()
     assert len(table) >= 4, table
     assert any(ln.startswith("k_criterion") for ln in table) and any(ln.startswith("k_prep") for ln in table)
     if prec == 0:  # the FP32 stage kernel (FP64 grids use the plain per-block stage)
         assert any(ln.startswith("k_fused") for ln in table)
+        assert any(ln.startswith("stage kernel") for ln in table)
 
 
 def test_substituted_field_tracking(mr):
@@ -228,3 +237,30 @@ def test_substituted_field_tracking(mr):
             ref = grids[0].field_copy_out(0).astype(np.float64)
             other = grids[2].field_copy_out(0).astype(np.float64)
             assert np.abs(other - ref).max() <= 1e-6 * np.abs(ref).max()
+
+
+def test_checkpoint_restore_resumes_bit_for_bit(mr, tmp_path):
+    """Checkpoint / resume: a grid restored from a checkpoint taken after an
+    adaptation and two RK3 steps continues exactly like the original (two
+    more steps and one more adaptation: same leaves, same field)."""
+    nt, tl, nb = (2, 2, 2), 0.5, 16
+    lev, anc = I.tree_config1()
+    g = mr.Grid(nt, tl, nb, 0, 2, 4, 2, lev, anc, precision=mr.F32, capacity=4000)
+    glev, ganc, _ = g.leaves()
+    xyz = I.point_coords(nt, tl, nb, glev, ganc)
+    g.field_copy_in(0, I.gaussian(xyz, (0.4, 0.4, 0.4), 0.04).astype(np.float32))
+    u = (1.0, 0.5, 0.25)
+    g.adapt(0, 1e-3, 1e-6)
+    for _ in range(2):
+        g.step(0, 1e-3, u, mr.WENOZ5)
+    path = tmp_path / "grid.npz"
+    g.checkpoint(path)
+    h = mr.Grid.restore(path)
+    assert np.array_equal(h.leaves()[2], g.leaves()[2])
+    assert np.array_equal(h.field_copy_out(0), g.field_copy_out(0))
+    for x in (g, h):
+        for _ in range(2):
+            x.step(0, 1e-3, u, mr.WENOZ5)
+        x.adapt(0, 1e-3, 1e-6)
+    assert np.array_equal(h.leaves()[2], g.leaves()[2])
+    assert np.array_equal(h.field_copy_out(0), g.field_copy_out(0))
