@@ -13,8 +13,11 @@
  *
  * Conventions (where the paper leaves a choice open, the reading taken is
  * stated at the function that implements it):
- *  - forest of nt[0] x nt[1] x nt[2] trees of edge tree_len, periodic in every
- *    direction; a leaf block at level L has anchor a (in units of blocks at
+ *  - forest of nt[0] x nt[1] x nt[2] trees of edge tree_len, periodic along
+ *    every axis with periodic[d] = 1; along another axis the domain ends at
+ *    x = 0 and x = nt[d] tree_len, and ghost values beyond it come from the
+ *    boundary condition bc (Sec. 2.4, og_bc_value); a leaf block at level L
+ *    has anchor a (in units of blocks at
  *    level L) and nb^3 points; point i of the block sits at (a*nb + i) * h_L,
  *    h_L = tree_len / (nb * 2^L) (vertex-aligned layout, Sec. 2.2: coarse
  *    point k coincides with fine point 2k);
@@ -211,7 +214,15 @@ typedef struct {
   int nleaf;
   const int32_t *lev; /* [nleaf] */
   const int32_t *anc; /* [3*nleaf], anchor (x,y,z) at the leaf's own level */
+  int periodic[3];    /* 1: periodic axis; 0: physical boundaries at both ends */
+  int bc;             /* boundary condition of the non-periodic axes (OG_BC_*) */
 } og_grid;
+
+/* Boundary conditions (Sec. 2.4: polynomial interpolation at the order of the
+ * wavelet, evaluated with Neville's algorithm).                            */
+#define OG_BC_EXTRAP 0    /* extrapolation through the N nearest grid points  */
+#define OG_BC_DIRICHLET0 1 /* zero value at the boundary + N-1 grid points   */
+#define OG_BC_ZERO 2      /* plain zeros                                    */
 
 typedef struct {
   const og_grid *g;
@@ -230,6 +241,9 @@ static int ctx_init(og_ctx *c, const og_grid *g) {
   c->g = g;
   if (g->nb < 4 || g->nb % 2) return OG_ERR_INVALID;
   if (og_wavelet_get(g->N, g->Nt, &c->w)) return OG_ERR_INVALID;
+  for (int d = 0; d < 3; ++d)
+    if (g->periodic[d] != 0 && g->periodic[d] != 1) return OG_ERR_INVALID;
+  if (g->bc < OG_BC_EXTRAP || g->bc > OG_BC_ZERO) return OG_ERR_INVALID;
   c->maxlev = 0;
   for (int i = 0; i < g->nleaf; ++i) {
     if (g->lev[i] < 0 || g->lev[i] > OG_MAXL) return OG_ERR_INVALID;
@@ -256,6 +270,53 @@ static int ctx_init(og_ctx *c, const og_grid *g) {
 
 /* number of level-L points along dimension d */
 static long npts(const og_ctx *c, int L, int d) { return (long)c->g->nt[d] * c->g->nb << L; }
+
+/* First axis along which level-L point g lies beyond a physical boundary,
+ * or -1 when the point is in the domain (periodic axes never end).         */
+static int outside_axis(const og_ctx *c, int L, const long g[3]) {
+  for (int d = 0; d < 3; ++d)
+    if (!c->g->periodic[d] && (g[d] < 0 || g[d] >= npts(c, L, d))) return d;
+  return -1;
+}
+
+/* Neville's algorithm: the value at x of the polynomial of degree n-1 through
+ * (xs[i], ys[i]), i < n (Press et al., "Numerical Recipes", Sec. 3.2): the
+ * tableau p[i] <- ((x - xs[i+m]) p[i] + (xs[i] - x) p[i+1]) / (xs[i] - xs[i+m]). */
+static double neville(int n, const double *xs, const double *ys, double x) {
+  double p[8];
+  for (int i = 0; i < n; ++i) p[i] = ys[i];
+  for (int m = 1; m < n; ++m)
+    for (int i = 0; i + m < n; ++i)
+      p[i] = ((x - xs[i + m]) * p[i] + (xs[i] - x) * p[i + 1]) / (xs[i] - xs[i + m]);
+  return p[0];
+}
+
+/* Nodes of the boundary condition (Sec. 2.4) for a point at level-L index q
+ * beyond a physical boundary of axis d (n = npts): the grid indices whose
+ * values the boundary polynomial passes through (*nfix of them), plus, for
+ * the zero-value condition, the boundary position itself with value 0.  The
+ * layout is vertex-aligned, so the lower boundary x = 0 is grid point 0 and
+ * the upper boundary x = n h is one spacing beyond the last grid point.    */
+static int bc_nodes(const og_ctx *c, long q, long n, long *idx, double *xs, int *nfix) {
+  const int N = c->g->N;
+  const int lower = q < 0;
+  int m = 0;
+  if (c->g->bc == OG_BC_EXTRAP) {
+    for (int i = 0; i < N; ++i) idx[m] = lower ? i : n - 1 - i, xs[m] = (double)idx[m], ++m;
+    *nfix = 0;
+  } else if (c->g->bc == OG_BC_DIRICHLET0) {
+    /* boundary node first (value 0), then the N-1 nearest grid points that
+     * are not on the boundary */
+    xs[0] = lower ? 0.0 : (double)n;
+    idx[0] = -1;
+    m = 1;
+    for (int i = 1; i < N; ++i) idx[m] = lower ? i : n - i, xs[m] = (double)idx[m], ++m;
+    *nfix = 1;
+  } else {
+    return -1;
+  }
+  return m;
+}
 
 /* The leaf whose (half-open) region contains level-L point g (wrapped).
  * Searches every level; exactly one leaf matches in a valid forest.        */
@@ -311,6 +372,34 @@ static int coarse_value(const og_ctx *c, const double *phi, int Lq, const long q
   return leaf_value(c, phi, o, Lq, q, out);
 }
 
+/* T(q) with the boundary condition at the coarse level (Alg. SM1: the
+ * boundary conditions are applied to the coarse buffer before refinement):
+ * beyond a physical boundary, the value of the boundary polynomial through
+ * the buffer's values at the nodes (bc_nodes) along the first such axis,
+ * each node itself taken the same way along the remaining axes.          */
+static int coarse_value_bc(const og_ctx *c, const double *phi, int Lq, const long q[3], double *out) {
+  const int d = outside_axis(c, Lq, q);
+  if (d < 0) return coarse_value(c, phi, Lq, q, out);
+  if (c->g->bc == OG_BC_ZERO) return *out = 0.0, OG_OK;
+  long idx[8];
+  double xs[8], ys[8];
+  int nfix;
+  const int m = bc_nodes(c, q[d], npts(c, Lq, d), idx, xs, &nfix);
+  if (m < 0) return OG_ERR_INVALID;
+  for (int i = 0; i < m; ++i) {
+    if (i < nfix) {
+      ys[i] = 0.0;
+      continue;
+    }
+    long qq[3] = {q[0], q[1], q[2]};
+    qq[d] = idx[i];
+    int e = coarse_value_bc(c, phi, Lq, qq, &ys[i]);
+    if (e) return e;
+  }
+  *out = neville(m, xs, ys, (double)q[d]);
+  return OG_OK;
+}
+
 /* Refinement with zero details (Sec. 2.2.3, Table SM1/SM2 synthesis filters):
  * the value at level-L point g from level-(L-1) values, tensor product of
  * J^s (even coordinate) or K^s (odd coordinate) over the interleaved array
@@ -330,7 +419,7 @@ static int refine_point(const og_ctx *c, const double *phi, int L, const long g[
         /* g+o is even (possibly negative): the division is exact */
         long q[3] = {(g[0] + ox) / 2, (g[1] + oy) / 2, (g[2] + oz) / 2};
         double t;
-        int e = coarse_value(c, phi, L - 1, q, &t);
+        int e = coarse_value_bc(c, phi, L - 1, q, &t);
         if (e) return e;
         s += wgt * t;
       }
@@ -345,6 +434,7 @@ static int refine_point(const og_ctx *c, const double *phi, int L, const long g[
  * Part 2 overwrites).                                                      */
 static int part1_value(const og_ctx *c, const double *phi, int b, const long g[3], double *out) {
   int L = c->g->lev[b];
+  if (outside_axis(c, L, g) >= 0) return *out = 0.0, OG_OK; /* set by the boundary condition */
   int o = owner(c, L, g);
   if (o < 0) return OG_ERR_INVALID;
   int Lo = c->g->lev[o];
@@ -368,6 +458,7 @@ static int coarse_dirs(const og_ctx *c, int b, int mask[27]) {
         long g[3];
         for (int d = 0; d < 3; ++d)
           g[d] = (long)c->g->anc[3 * b + d] * nb + (dd[d] < 0 ? -1 : dd[d] > 0 ? nb : 0);
+        if (outside_axis(c, L, g) >= 0) continue; /* beyond a physical boundary */
         int o = owner(c, L, g);
         if (o < 0) return OG_ERR_INVALID;
         if (c->g->lev[o] < L - 1 || c->g->lev[o] > L + 1) return OG_ERR_BALANCE;
@@ -427,6 +518,60 @@ static void substitute_block(const og_ctx *c, const int mask[27], double *P, int
 
 static int imax(int a, int b) { return a > b ? a : b; }
 
+/* Value of padded point (i,j,k) of leaf b under the boundary condition, from
+ * the padded block P (shell G) of the same leaf: inside the domain the stored
+ * value; beyond a physical boundary the boundary polynomial (Sec. 2.4)
+ * through the values at the nodes along the first such axis, each node taken
+ * the same way along the remaining axes.                                   */
+static int pad_bc_value(const og_ctx *c, const double *P, int G, int b, const int p[3], double *out) {
+  const int nb = c->g->nb, L = c->g->lev[b], W = nb + 2 * G;
+  long g[3];
+  for (int d = 0; d < 3; ++d) g[d] = (long)c->g->anc[3 * b + d] * nb + p[d];
+  const int d = outside_axis(c, L, g);
+  if (d < 0) return *out = P[PIDX(p[0], p[1], p[2], G, W)], OG_OK;
+  if (c->g->bc == OG_BC_ZERO) return *out = 0.0, OG_OK;
+  long idx[8];
+  double xs[8], ys[8];
+  int nfix;
+  const int m = bc_nodes(c, g[d], npts(c, L, d), idx, xs, &nfix);
+  if (m < 0) return OG_ERR_INVALID;
+  for (int i = 0; i < m; ++i) {
+    if (i < nfix) {
+      ys[i] = 0.0;
+      continue;
+    }
+    int pp[3] = {p[0], p[1], p[2]};
+    pp[d] = (int)(idx[i] - (long)c->g->anc[3 * b + d] * nb);
+    if (pp[d] < -G || pp[d] >= nb + G) return OG_ERR_INVALID;
+    int e = pad_bc_value(c, P, G, b, pp, &ys[i]);
+    if (e) return e;
+  }
+  *out = neville(m, xs, ys, (double)g[d]);
+  return OG_OK;
+}
+
+/* The boundary condition on every point of leaf b's padded block beyond a
+ * physical boundary (in place: such points are computed from points inside
+ * the domain only).                                                        */
+static int apply_bc_pad(const og_ctx *c, double *P, int G, int b) {
+  const int nb = c->g->nb, L = c->g->lev[b], W = nb + 2 * G;
+  for (int k = -G; k < nb + G; ++k)
+    for (int j = -G; j < nb + G; ++j)
+      for (int i = -G; i < nb + G; ++i) {
+        long g[3] = {(long)c->g->anc[3 * b] * nb + i, (long)c->g->anc[3 * b + 1] * nb + j,
+                     (long)c->g->anc[3 * b + 2] * nb + k};
+        if (outside_axis(c, L, g) < 0) continue;
+        const int p[3] = {i, j, k};
+        double v;
+        int e = pad_bc_value(c, P, G, b, p, &v);
+        if (e) return e;
+        P[PIDX(i, j, k, G, W)] = v;
+      }
+  return OG_OK;
+}
+
+static int has_boundary(const og_grid *g) { return !g->periodic[0] || !g->periodic[1] || !g->periodic[2]; }
+
 /*
  * Ghost fill (Alg. SM1 then Alg. SM2):
  *   1. every leaf builds its padded block: interior, same-level copies,
@@ -436,6 +581,13 @@ static int imax(int a, int b) { return a > b ? a : b; }
  *      on its padded block; the substituted interior is the new field;
  *   3. every point owned by a finer leaf F is replaced by the coarsening
  *      (tensor H^a) of F's padded block from step 2.
+ * With physical boundaries (Sec. 2.4 and Alg. SM1/SM2: the boundary
+ * condition is applied to the coarse buffer before refinement, to the block
+ * before substitution and coarsening, and once more when every ghost is
+ * known): step 1 refines coarse values that lie beyond a boundary from the
+ * boundary condition at the coarse level (coarse_value_bc); the points of
+ * each padded block beyond a boundary take the boundary condition after
+ * step 1 and again after step 3.
  * out_pad: nleaf*(nb+2G)^3, phi_out: nleaf*nb^3 (may alias phi_in).
  */
 int og_ghost_fill(const og_grid *g, const double *phi_in, int G, double *out_pad, double *phi_out) {
@@ -466,6 +618,9 @@ int og_ghost_fill(const og_grid *g, const double *phi_in, int G, double *out_pad
           P1[b * npi + PIDX(i, j, k, Gi, Wi)] = v;
         }
   }
+  /* boundary condition on the blocks before substitution and coarsening */
+  if (has_boundary(g))
+    for (int b = 0; b < g->nleaf && !e; ++b) e = apply_bc_pad(&c, P1 + b * npi, Gi, b);
   /* step 2 */
   for (int b = 0; b < g->nleaf && !e; ++b) {
     int mask[27];
@@ -481,8 +636,8 @@ int og_ghost_fill(const og_grid *g, const double *phi_in, int G, double *out_pad
         for (int i = -G; i < nb + G && !e; ++i) {
           double v = P1[b * npi + PIDX(i, j, k, Gi, Wi)];
           int inside = i >= 0 && i < nb && j >= 0 && j < nb && k >= 0 && k < nb;
-          if (!inside) {
-            long gg[3] = {(long)a[0] * nb + i, (long)a[1] * nb + j, (long)a[2] * nb + k};
+          long gg[3] = {(long)a[0] * nb + i, (long)a[1] * nb + j, (long)a[2] * nb + k};
+          if (!inside && outside_axis(&c, L, gg) < 0) {
             int F = owner(&c, L, gg);
             if (F < 0) { e = OG_ERR_INVALID; break; }
             if (g->lev[F] == L + 1) {
@@ -490,8 +645,11 @@ int og_ghost_fill(const og_grid *g, const double *phi_in, int G, double *out_pad
               long fl[3];
               for (int d = 0; d < 3; ++d) {
                 long P = npts(&c, L + 1, d);
-                long off = pmod(2 * gg[d] - (long)g->anc[3 * F + d] * nb, P);
-                if (off >= P / 2) off -= P; /* nearest periodic image */
+                long off = 2 * gg[d] - (long)g->anc[3 * F + d] * nb;
+                if (g->periodic[d]) {
+                  off = pmod(off, P);
+                  if (off >= P / 2) off -= P; /* nearest periodic image */
+                }
                 fl[d] = off;
               }
               double s = 0.0;
@@ -514,6 +672,9 @@ int og_ghost_fill(const og_grid *g, const double *phi_in, int G, double *out_pad
           if (out_pad) out_pad[b * np + PIDX(i, j, k, G, W)] = v;
         }
   }
+  /* boundary condition once every ghost is known */
+  if (!e && out_pad && has_boundary(g))
+    for (int b = 0; b < g->nleaf && !e; ++b) e = apply_bc_pad(&c, out_pad + b * np, G, b);
   if (!e && phi_out)
     for (int b = 0; b < g->nleaf; ++b)
       for (int k = 0; k < nb; ++k)
@@ -864,8 +1025,8 @@ static double detail_at(const og_ctx *c, const double *P, int G, int i, int j, i
   return bz;
 }
 
-/* Per-leaf max |gamma| over [-ext_f, nb-1+ext_b]^3 from a padded field whose
- * shell covers the detail reach.                                           */
+/* Per-leaf max |gamma| over [-ext_f, nb-1+ext_b]^3 (the part inside the
+ * domain) from a padded field whose shell covers the detail reach.        */
 int og_criterion(const og_grid *g, const double *pad, int G, double *maxdet) {
   og_ctx c;
   int e = ctx_init(&c, g);
@@ -881,6 +1042,11 @@ int og_criterion(const og_grid *g, const double *pad, int G, double *maxdet) {
       for (int j = -c.w.ext_f; j <= nb - 1 + c.w.ext_b; ++j)
         for (int i = -c.w.ext_f; i <= nb - 1 + c.w.ext_b; ++i) {
           if (!((i | j | k) & 1)) continue;
+          /* the extended region stops at a physical boundary (reading: no
+           * detail exists beyond the domain) */
+          const long gp[3] = {(long)g->anc[3 * b] * nb + i, (long)g->anc[3 * b + 1] * nb + j,
+                              (long)g->anc[3 * b + 2] * nb + k};
+          if (outside_axis(&c, g->lev[b], gp) >= 0) continue;
           double v = fabs(detail_at(&c, pad + b * np, G, i, j, k));
           if (v > m) m = v;
         }
@@ -953,6 +1119,7 @@ int og_status(double maxdet, double eps_r, double eps_c) {
  *    neighbour is finer, and no same-level neighbour refines.              */
 int og_policy(const og_grid *g, const int32_t *refined, int8_t *st) {
   og_ctx c;
+  if (has_boundary(g)) return OG_ERR_INVALID; /* adaptation: periodic forests only */
   int e = ctx_init(&c, g);
   if (e) return e;
   int nbr[256];
@@ -1215,7 +1382,7 @@ int og_adapt_iter_fields(const og_grid *g, int nf, const double *const *phi, dou
                          double *const *phi_out, int32_t *refined_out, int *n_changed, double *maxdet_out,
                          int8_t *status_out) {
   og_ctx c;
-  if (nf < 1) return OG_ERR_INVALID;
+  if (nf < 1 || has_boundary(g)) return OG_ERR_INVALID; /* adaptation: periodic forests only */
   int e = ctx_init(&c, g);
   if (e) return e;
   const int nb = g->nb, G = og_adapt_shell(g->N, g->Nt), W = nb + 2 * G;

@@ -28,6 +28,7 @@ _SRC = os.path.join(_HERE, "mr_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 CONS3, CONS5, WENOZ5 = 0, 1, 2
+BC_EXTRAP, BC_DIRICHLET0, BC_ZERO = 0, 1, 2
 FINER, SAME, COARSER = 1, 0, -1
 
 
@@ -54,7 +55,7 @@ class _Grid(C.Structure):
     _fields_ = [("nt", C.c_int * 3), ("tree_len", C.c_double), ("nb", C.c_int),
                 ("N", C.c_int), ("Nt", C.c_int), ("lmin", C.c_int), ("lmax", C.c_int),
                 ("nleaf", C.c_int), ("lev", C.POINTER(C.c_int32)),
-                ("anc", C.POINTER(C.c_int32))]
+                ("anc", C.POINTER(C.c_int32)), ("periodic", C.c_int * 3), ("bc", C.c_int)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -104,7 +105,9 @@ def _d(a):
 
 @dataclass
 class Grid:
-    """A forest of octrees (periodic) with its leaves: lev[n], anc[n,3]."""
+    """A forest of octrees with its leaves: lev[n], anc[n,3]; periodic along
+    the axes with periodic[d] = 1, else bounded with boundary condition bc
+    (BC_EXTRAP, BC_DIRICHLET0 or BC_ZERO, Sec. 2.4)."""
     nt: tuple
     tree_len: float
     nb: int
@@ -114,6 +117,8 @@ class Grid:
     lmax: int
     lev: np.ndarray
     anc: np.ndarray
+    periodic: tuple = (1, 1, 1)
+    bc: int = 0
 
     def __post_init__(self):
         self.lev = np.ascontiguousarray(self.lev, dtype=np.int32)
@@ -130,12 +135,14 @@ class Grid:
         s.lmin, s.lmax, s.nleaf = self.lmin, self.lmax, self.nleaf
         s.lev = self.lev.ctypes.data_as(_ip)
         s.anc = self.anc.ctypes.data_as(_ip)
+        s.periodic[:] = [int(p) for p in self.periodic]
+        s.bc = int(self.bc)
         self._keep = s
         return C.byref(s)
 
     def with_leaves(self, lev, anc):
         return Grid(self.nt, self.tree_len, self.nb, self.N, self.Nt, self.lmin, self.lmax,
-                    lev, anc)
+                    lev, anc, self.periodic, self.bc)
 
 
 def _check(e, what):
