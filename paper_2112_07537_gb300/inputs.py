@@ -69,6 +69,17 @@ def balance(nt, lev, anc, max_iter=64):
     raise RuntimeError("balance did not converge")
 
 
+def bounded_test_tree(nt=(4, 4, 4)):
+    """A 3-level 2:1 tree whose refinement reaches the domain faces: level 1
+    in the trees with x-index <= 1 and y-index 1..2 (a slab on the x = 0
+    face), level 2 in the level-1 leaf at (0, 2, 0) (on the x = 0, z = 0
+    edge), then balanced."""
+    lev, anc = uniform_leaves(nt, 0)
+    lev, anc = refine_leaves(lev, anc, (anc[:, 0] <= 1) & (anc[:, 1] >= 1) & (anc[:, 1] <= 2))
+    lev, anc = refine_leaves(lev, anc, (lev == 1) & np.all(anc == (0, 2, 0), axis=1))
+    return balance(nt, lev, anc)
+
+
 def block_centres(nt, tree_len, lev, anc):
     size = tree_len / (1 << lev.astype(np.int64))
     return (anc + 0.5) * size[:, None], size

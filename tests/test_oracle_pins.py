@@ -757,10 +757,13 @@ from math import comb
 
 
 def _bounded_grid(oracle_mod, N, Nt, nb, bc, periodic=(0, 0, 0)):
-    """_poly_grid's 3-level tree (refinement touching every face of the
-    4x4x4 forest) with physical boundaries."""
-    g = _poly_grid(oracle_mod, N, Nt, nb)
-    return oracle_mod.Grid(g.nt, g.tree_len, nb, N, Nt, g.lmin, g.lmax, g.lev, g.anc, periodic, bc)
+    """A 3-level 2:1 tree on the 4x4x4 forest of edge 1 with physical
+    boundaries: a level-1 slab on the x = 0 face and a level-2 corner block
+    on the x = 0, z = 0 edge, so that coarse-to-fine and fine-to-coarse
+    ghosts meet the boundary."""
+    nt, tl = (4, 4, 4), 0.25
+    lev, anc = I.bounded_test_tree(nt)
+    return oracle_mod.Grid(nt, tl, nb, N, Nt, 0, 4, lev, anc, periodic, bc)
 
 
 @pytest.mark.parametrize("N", [2, 4, 6])
@@ -863,8 +866,8 @@ def test_boundary_with_compact_support_equals_periodic(oracle_mod):
     condition does not matter -- three RK3 steps of a narrow Gaussian in the
     middle of the bounded forest equal those on the periodic forest."""
     N, Nt, nb = 4, 2, 16
-    gp = _poly_grid(oracle_mod, N, Nt, nb)
     gb = _bounded_grid(oracle_mod, N, Nt, nb, oracle_mod.BC_EXTRAP)
+    gp = oracle_mod.Grid(gb.nt, gb.tree_len, nb, N, Nt, gb.lmin, gb.lmax, gb.lev, gb.anc)
     xyz = I.point_coords(gp.nt, gp.tree_len, nb, gp.lev, gp.anc)
     f = I.gaussian(xyz, (0.55, 0.5, 0.45), 0.06)
     u = (1.0, 0.5, -0.25)
