@@ -116,6 +116,27 @@ typedef struct {
  * are separate runs); each tree computes exactly what a one-tree grid with
  * the same leaves and values computes. */
 #define MR_GRID_INDEPENDENT_TREES 4
+/* Physical boundaries (Sec. 2.4): the domain ends at x_d = 0 and
+ * x_d = ntree[d] * tree_len along each axis d flagged here instead of
+ * wrapping around.  Ghost values beyond a boundary come from a polynomial of
+ * degree < N (the wavelet's order) through grid values next to it, applied
+ * as the paper orders it: to the coarse values before refinement, to each
+ * block before substitution and coarsening, and once more when every ghost
+ * is known.  The layout is vertex-aligned, so the lower boundary is grid
+ * point 0 and the upper boundary lies one spacing beyond the last point.
+ * Condition (default: extrapolation through the N nearest points):
+ * MR_GRID_BC_DIRICHLET0 -- zero value: through 0 at the boundary and the
+ * N-1 nearest points off it; MR_GRID_BC_ZERO -- plain zeros.  Such grids run
+ * a general point-wise ghost path (one thread per padded point, the tensor
+ * sums of Alg. SM1/SM2 evaluated directly) and the per-block stage kernel;
+ * the criterion's extended region stops at the boundary.  mr_adapt,
+ * mr_adapt_iter and mr_ghost_fill_static return MR_ERR_UNSUPPORTED on them,
+ * as does MR_GRID_INDEPENDENT_TREES combined with a bounded axis. */
+#define MR_GRID_BOUNDED_X 8
+#define MR_GRID_BOUNDED_Y 16
+#define MR_GRID_BOUNDED_Z 32
+#define MR_GRID_BC_DIRICHLET0 64
+#define MR_GRID_BC_ZERO 128
 
 typedef struct {
   int nleaf;

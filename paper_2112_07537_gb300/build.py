@@ -20,7 +20,7 @@ LIB = os.path.join(OUT, "libmrgb.so")
 GHOST_UNITS = [f"ghost_i_{t}{n}{nt}" for t in ("ff", "fd", "dd") for n in (2, 4, 6) for nt in (0, 2)]
 # the FP32 stage kernels: one translation unit per wavelet
 STAGE_UNITS = [f"stage_i_{n}{nt}" for n in (2, 4, 6) for nt in (0, 2)]
-UNITS = ["ghost"] + GHOST_UNITS + STAGE_UNITS + ["stencil", "tree", "adapt", "abi", "peaks", "tune"]
+UNITS = ["ghost"] + GHOST_UNITS + STAGE_UNITS + ["boundary", "stencil", "tree", "adapt", "abi", "peaks", "tune"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v"]
 

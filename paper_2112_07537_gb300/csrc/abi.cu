@@ -59,6 +59,10 @@ Tree tree_view(const mr_grid *g) {
   t.tree_len = g->desc.tree_len;
   t.indep = (g->desc.flags & MR_GRID_INDEPENDENT_TREES) ? 1 : 0;
   t.dnb = divm(t.nb);
+  t.bnd = ((g->desc.flags & MR_GRID_BOUNDED_X) ? 1 : 0) | ((g->desc.flags & MR_GRID_BOUNDED_Y) ? 2 : 0) |
+          ((g->desc.flags & MR_GRID_BOUNDED_Z) ? 4 : 0);
+  t.bc = (g->desc.flags & MR_GRID_BC_ZERO) ? MR_BC_ZERO : (g->desc.flags & MR_GRID_BC_DIRICHLET0) ? MR_BC_DIRICHLET0
+                                                                                                 : MR_BC_EXTRAP;
   return t;
 }
 
@@ -105,6 +109,11 @@ static int layout(const mr_grid_desc *d, Layout *L, int *shell_rk, int *shell_ad
   if (!((d->wav_N == 2 || d->wav_N == 4 || d->wav_N == 6) && (d->wav_Nt == 0 || d->wav_Nt == 2)))
     return MR_ERR_INVALID;
   if (d->precision != MR_F32 && d->precision != MR_F64) return MR_ERR_INVALID;
+  // one boundary condition at most; independent trees wrap onto themselves
+  if ((d->flags & MR_GRID_BC_DIRICHLET0) && (d->flags & MR_GRID_BC_ZERO)) return MR_ERR_INVALID;
+  if ((d->flags & MR_GRID_INDEPENDENT_TREES) &&
+      (d->flags & (MR_GRID_BOUNDED_X | MR_GRID_BOUNDED_Y | MR_GRID_BOUNDED_Z)))
+    return MR_ERR_UNSUPPORTED;
   if (d->nfields < 1 || d->capacity < 1 || d->lmax < 0 || d->lmax > MR_MAX_LEVEL || d->lmin < 0 ||
       d->lmin > d->lmax || !(d->tree_len > 0))
     return MR_ERR_INVALID;
@@ -464,6 +473,13 @@ static int adapt_ok(mr_grid *g) {
   return 1;
 }
 
+// the adaptation runs on periodic forests only
+static int adapt_refused(mr_grid *g) {
+  if (!grid_bounded(g)) return 0;
+  set_error("adaptation of grids with physical boundaries is not supported");
+  return 1;
+}
+
 // FP64 ghost fill (the adaptation path) into a double padded buffer.
 int mr_ghost_fill64(mr_grid *g, int fid, int G, double *padded) {
   if (!fid_ok(g, fid)) return MR_ERR_INVALID;
@@ -483,7 +499,7 @@ int mr_rhs_advect(mr_grid *g, int phi, const double *u, int out, int scheme) {
   field_written(g, phi);
   field_written(g, out);
   void *f = field_ptr(g, phi);
-  if (g->desc.precision == MR_F32) {
+  if (g->desc.precision == MR_F32 && !grid_bounded(g)) {
     int Gi;
     int e = launch_prep32(g, f, &Gi);
     if (!e) e = launch_fused(g, f, g->padP, g->padQ, Gi, nullptr, field_ptr(g, out), 0, 0.0, u, scheme, true);
@@ -548,7 +564,7 @@ int mr_rhs_advect_vel(mr_grid *g, int phi, const int *vel, int out, int scheme) 
   int e = velocity_cache(g, vel);
   if (e) return e;
   void *f = field_ptr(g, phi);
-  if (g->desc.precision == MR_F32) {
+  if (g->desc.precision == MR_F32 && !grid_bounded(g)) {
     int Gi;
     e = launch_prep32(g, f, &Gi);
     if (!e) e = launch_fused(g, f, g->padP, g->padQ, Gi, nullptr, field_ptr(g, out), 0, 0.0, nullptr, scheme, true,
@@ -636,7 +652,7 @@ static int step_vel_body(mr_grid *g, int phi, double dt, int scheme, const doubl
   for (int s = 0; s < 3 && !e; ++s) {
     int Gi;
     g->vel_scale = scale[s];
-    if (g->desc.precision == MR_F32) {
+    if (g->desc.precision == MR_F32 && !grid_bounded(g)) {
       e = launch_prep32(g, src[s], &Gi);
       if (!e) e = launch_fused(g, src[s], g->padP, g->padQ, Gi, un, dst[s], s, dt, nullptr, scheme, false, g->vpad);
       if (!e && s == 0) e = launch_writeback32(g, Gi, un);
@@ -655,7 +671,7 @@ static int step_body(mr_grid *g, int phi, double dt, const double *u, int scheme
   void *y1 = field_ptr(g, g->desc.nfields), *y2 = field_ptr(g, g->desc.nfields + 1);
   void *src[3] = {un, y1, y2};
   void *dst[3] = {y1, y2, un};
-  const bool fused = g->desc.precision == MR_F32;
+  const bool fused = g->desc.precision == MR_F32 && !grid_bounded(g);
   for (int s = 0; s < 3; ++s) {
     int Gi, e;
     if (fused) {
@@ -760,12 +776,13 @@ int mr_criterion(mr_grid *g, int fid, double *maxdet) {
   void *f = field_ptr(g, fid);
   int e = launch_ghost(g, f, f, adapt_shell(g->desc.wav_N, g->desc.wav_Nt), true, &P, &Gi);
   if (e) return e;
+  if (grid_bounded(g)) return launch_criterion_bounded(g, (const double *)P, Gi, maxdet);
   return launch_criterion(g, (const double *)P, Gi, maxdet);
 }
 
 int mr_adapt_iter(mr_grid *g, int crit, double er, double ec, int flags, int *nch) {
   if (!fid_ok(g, crit)) return MR_ERR_INVALID;
-  if (!adapt_ok(g)) return MR_ERR_UNSUPPORTED;
+  if (!adapt_ok(g) || adapt_refused(g)) return MR_ERR_UNSUPPORTED;
   field_written(g, crit);
   int n = 0;
   int e = adapt_iteration(g, crit, er, ec, flags, &n);
@@ -775,7 +792,7 @@ int mr_adapt_iter(mr_grid *g, int crit, double er, double ec, int flags, int *nc
 
 int mr_adapt(mr_grid *g, int crit, double er, double ec, int flags, int *nch) {
   if (!fid_ok(g, crit)) return MR_ERR_INVALID;
-  if (!adapt_ok(g)) return MR_ERR_UNSUPPORTED;
+  if (!adapt_ok(g) || adapt_refused(g)) return MR_ERR_UNSUPPORTED;
   int total = 0;
   field_written(g, crit);  // the criterion field changes between adaptations
   if (check_cuda(cudaMemsetAsync(g->refined, 0, 4 * (size_t)g->desc.capacity, g->stream), "refined reset"))

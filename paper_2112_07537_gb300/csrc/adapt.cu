@@ -505,16 +505,6 @@ __global__ void __launch_bounds__(512) k_interp(Tree to, const int *__restrict__
 }
 
 // ------------------------------------------------------------- update
-__device__ __forceinline__ bool in_band_dev(int mask, int i, int j, int k, int nb, int ef, int eb) {
-  for (int m = 0; m < 27; ++m) {
-    if (!((mask >> m) & 1)) continue;
-    const int d0 = m % 3 - 1, d1 = (m / 3) % 3 - 1, d2 = m / 9 - 1;
-    if ((d0 < 0 ? i < eb : d0 > 0 ? i >= nb - ef : true) && (d1 < 0 ? j < eb : d1 > 0 ? j >= nb - ef : true) &&
-        (d2 < 0 ? k < eb : d2 > 0 ? k >= nb - ef : true))
-      return true;
-  }
-  return false;
-}
 
 // Directions of newly coarsened neighbours (one level coarser) of unchanged
 // new leaves; 0 for other leaves.

@@ -99,6 +99,10 @@ int launch_ghost(mr_grid *g, const void *phi_in, void *phi_out, int G, bool fp64
   *Gi = gi;
   if (p_is64) *p_is64 = fp64 || g->desc.precision == MR_F64;
   const bool f32 = g->desc.precision == MR_F32;
+  if (grid_bounded(g)) {  // physical boundaries: the general point-wise path (every leaf)
+    *P = fp64 ? (void *)g->padP64 : g->padP;
+    return ghost_bounded(g, phi_in, phi_out, G, fp64, *P, fp64 ? (void *)g->padQ64 : g->padQ, gi);
+  }
   if (fp64) {
     *P = g->padP64;
     if (f32)
@@ -236,6 +240,10 @@ extern "C" int mr_ghost_fill_static(mr_grid *g, int fid, int G, void *padded) {
   const int nb = g->desc.nb;
   if (G < 1 || G > MR_MAX_SHELL) return MR_ERR_INVALID;
   if (G > nb / 2) return MR_ERR_BALANCE;
+  if (grid_bounded(g)) {
+    set_error("mr_ghost_fill_static: grids with physical boundaries are not supported");
+    return MR_ERR_UNSUPPORTED;
+  }
   int dev = -1;
   if (check_cuda(cudaGetDevice(&dev), "cudaGetDevice")) return MR_ERR_CUDA;
   if (dev != g->dev || dev < 0 || dev >= 256) {

@@ -404,7 +404,12 @@ struct Tree {
   double tree_len;
   int indep;      // every tree is its own periodic domain (independent grids)
   DivM dnb;       // division by nb
+  int bnd;        // bit d: axis d ends at physical boundaries (not periodic)
+  int bc;         // their boundary condition: MR_BC_EXTRAP, _DIRICHLET0, _ZERO
 };
+
+// boundary conditions of bounded axes (Sec. 2.4), from the grid flags
+enum { MR_BC_EXTRAP = 0, MR_BC_DIRICHLET0 = 1, MR_BC_ZERO = 2 };
 
 // g mod P in [0, P): one period off (every neighbourhood read) without a division
 __device__ __forceinline__ int pwrap(int g, int P) {
@@ -417,6 +422,33 @@ __device__ __forceinline__ int pwrap(int g, int P) {
 
 // points along dimension d at level L
 __device__ __forceinline__ int npts(const Tree &t, int L, int d) { return (t.nt[d] * t.nb) << L; }
+
+// floor(a / 2) for any integer a
+__device__ __forceinline__ int floordiv2(int a) { return a >= 0 ? a / 2 : -((-a + 1) / 2); }
+
+// level-L point g lies beyond a physical boundary along dimension d
+__device__ __forceinline__ bool beyond(const Tree &t, int L, int g, int d) {
+  return ((t.bnd >> d) & 1) && (unsigned)g >= (unsigned)npts(t, L, d);
+}
+__device__ __forceinline__ bool beyond3(const Tree &t, int L, const int *g) {
+  return beyond(t, L, g[0], 0) || beyond(t, L, g[1], 1) || beyond(t, L, g[2], 2);
+}
+
+// Substitution band of a block (Sec. 2.2.4, depth from Table 2.2's coarse
+// region extension, mirrored): bit m of mask marks a coarser neighbour in
+// direction m = (dx+1) + 3(dy+1) + 9(dz+1); block-local point (i, j, k) is in
+// the band when, for some such direction, it lies within eb of the -side
+// faces and ef of the +side faces the direction points to.
+__device__ __forceinline__ bool in_band_dev(int mask, int i, int j, int k, int nb, int ef, int eb) {
+  for (int m = 0; m < 27; ++m) {
+    if (!((mask >> m) & 1)) continue;
+    const int d0 = m % 3 - 1, d1 = (m / 3) % 3 - 1, d2 = m / 9 - 1;
+    if ((d0 < 0 ? i < eb : d0 > 0 ? i >= nb - ef : true) && (d1 < 0 ? j < eb : d1 > 0 ? j >= nb - ef : true) &&
+        (d2 < 0 ? k < eb : d2 > 0 ? k >= nb - ef : true))
+      return true;
+  }
+  return false;
+}
 
 // Level-L point g along dimension d wrapped into the periodic domain of leaf
 // hb: the whole forest, or -- independent trees -- hb's own tree.
@@ -612,6 +644,12 @@ template <int N, int NT>
 int fused_launch(mr_grid *g, const float *phi, const float *P, const float *Q, int Gi, const float *u, float *out,
                  int stage, double dt, const double *uc, int scheme, bool rhs_only, const float *vpad);
 int adapt_shell(int N, int Nt);
+// boundary.cu: grids with physical boundaries (the general point-wise path)
+int ghost_bounded(mr_grid *g, const void *phi_in, void *phi_out, int G, bool fp64, void *P, void *Q, int Gi);
+int launch_criterion_bounded(mr_grid *g, const double *P, int Gi, double *maxdet);
+inline bool grid_bounded(const mr_grid *g) {
+  return (g->desc.flags & (MR_GRID_BOUNDED_X | MR_GRID_BOUNDED_Y | MR_GRID_BOUNDED_Z)) != 0;
+}
 // stencil.cu
 int launch_rhs_stage(mr_grid *g, const void *P, int Gi, const void *u, void *out, int stage,
                      double dt, const double *uc, int scheme, bool rhs_only, const void *vpad = nullptr);

@@ -89,8 +89,6 @@ __device__ __forceinline__ T lap_at(const T *c, const int *stride, int diff) {
   return s;
 }
 
-__device__ __forceinline__ int floordiv2(int a) { return a >= 0 ? a / 2 : -((-a + 1) / 2); }
-
 // ---------------------------------------------------------------------------
 // The six face slabs (3 deep) that the 1D WENO/CONS stencils of leaf b read,
 // face f = 2*axis + (0: -side, 1: +side):

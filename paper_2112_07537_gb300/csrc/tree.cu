@@ -61,6 +61,7 @@ __global__ void k_check_balance(Tree t, int *err) {
             else if (dd[d] > 0) g[d] = base[d] + span;
             else g[d] = base[d] + cc[d] * (span / 2);  // one point per adjacent child cell
           }
+          if (beyond3(t, Ls, g)) continue;  // no neighbour beyond a physical boundary
           const int o = owner(t, Ls, g[0], g[1], g[2], b);
           const int Lo = __ldg(t.lev + o);
           if (Lo > L + 1 || Lo < L - 1) atomicOr(err, 256);

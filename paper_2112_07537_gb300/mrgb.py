@@ -25,6 +25,9 @@ INIT_COMPACT_GAUSSIAN, INIT_DEFORMATION, INIT_GAUSSIAN_SUM_ADD = 4, 5, 6
 GRID_FIXED_TREE = 1
 GRID_VELOCITY = 2
 GRID_INDEPENDENT_TREES = 4
+GRID_BOUNDED_X, GRID_BOUNDED_Y, GRID_BOUNDED_Z = 8, 16, 32
+GRID_BC_DIRICHLET0, GRID_BC_ZERO = 64, 128
+BC_EXTRAP, BC_DIRICHLET0, BC_ZERO = 0, 1, 2  # boundary conditions (flag bits above)
 NUM_KERNELS = 18
 
 # every entry point include/mrgb.h declares
@@ -159,11 +162,13 @@ def _on_dev(x):
 
 
 class Grid:
-    """A periodic forest of octrees of nb^3 blocks on one GPU (mr_grid)."""
+    """A forest of octrees of nb^3 blocks on one GPU (mr_grid): periodic, or
+    with physical boundaries along the axes with bounded[d] = 1 and boundary
+    condition bc (BC_EXTRAP, BC_DIRICHLET0 or BC_ZERO)."""
 
     def __init__(self, ntree, tree_len, nb, lmin, lmax, N, Nt, lev, anc, precision=F32,
                  nfields=1, capacity=None, device="cuda", stream=None, fixed_tree=False,
-                 velocity=False, independent_trees=False):
+                 velocity=False, independent_trees=False, bounded=(0, 0, 0), bc=BC_EXTRAP):
         import torch
         L = load()
         lev = np.ascontiguousarray(lev, np.int32)
@@ -179,7 +184,9 @@ class Grid:
         d.wav_N, d.wav_Nt, d.precision, d.nfields, d.capacity = N, Nt, precision, nfields, cap
         d.stream = s.cuda_stream
         d.flags = ((GRID_FIXED_TREE if fixed_tree else 0) | (GRID_VELOCITY if velocity else 0) |
-                   (GRID_INDEPENDENT_TREES if independent_trees else 0))
+                   (GRID_INDEPENDENT_TREES if independent_trees else 0) |
+                   sum(f for f, on in zip((GRID_BOUNDED_X, GRID_BOUNDED_Y, GRID_BOUNDED_Z), bounded) if on) |
+                   {BC_EXTRAP: 0, BC_DIRICHLET0: GRID_BC_DIRICHLET0, BC_ZERO: GRID_BC_ZERO}[bc])
         self.desc = d
         nbytes = C.c_size_t()
         _chk(L.mr_workspace_size(C.byref(d), C.byref(nbytes)))
@@ -414,7 +421,9 @@ class Grid:
                 int(z["lmax"]), int(z["N"]), int(z["Nt"]), z["lev"], z["anc"], precision=int(z["precision"]),
                 nfields=int(z["nfields"]), capacity=capacity or int(z["capacity"]), device=device,
                 stream=stream, fixed_tree=bool(flags & GRID_FIXED_TREE), velocity=bool(flags & GRID_VELOCITY),
-                independent_trees=bool(flags & GRID_INDEPENDENT_TREES))
+                independent_trees=bool(flags & GRID_INDEPENDENT_TREES),
+                bounded=tuple(int(bool(flags & f)) for f in (GRID_BOUNDED_X, GRID_BOUNDED_Y, GRID_BOUNDED_Z)),
+                bc=BC_ZERO if flags & GRID_BC_ZERO else BC_DIRICHLET0 if flags & GRID_BC_DIRICHLET0 else BC_EXTRAP)
         for f in range(g.nfields):
             g.field_copy_in(f, z["fields"][f])
         return g
