@@ -1064,7 +1064,8 @@ int og_criterion(const og_grid *g, const double *pad, int G, double *maxdet) {
 #define OG_SAME 0
 #define OG_COARSER (-1)
 
-/* Leaves that touch leaf b across a face, an edge or a corner (periodic).
+/* Leaves that touch leaf b across a face, an edge or a corner (across
+ * periodic faces; none beyond a physical boundary).
  * Under 2:1 balance every such neighbour is at most one level finer, so one
  * probe per level-(L+1) cell adjacent to b finds them all.                  */
 static int neighbours(const og_ctx *c, int b, int *out, int cap) {
@@ -1089,6 +1090,7 @@ static int neighbours(const og_ctx *c, int b, int *out, int cap) {
                 else if (dd[d] > 0) g[d] = base + 2L * nb;
                 else g[d] = base + (long)cc[d] * nb;
               }
+              if (outside_axis(c, L + 1, g) >= 0) continue; /* beyond a physical boundary */
               int o = owner(c, L + 1, g);
               if (o < 0) return OG_ERR_INVALID;
               if (o == b) continue;
@@ -1119,7 +1121,6 @@ int og_status(double maxdet, double eps_r, double eps_c) {
  *    neighbour is finer, and no same-level neighbour refines.              */
 int og_policy(const og_grid *g, const int32_t *refined, int8_t *st) {
   og_ctx c;
-  if (has_boundary(g)) return OG_ERR_INVALID; /* adaptation: periodic forests only */
   int e = ctx_init(&c, g);
   if (e) return e;
   int nbr[256];
@@ -1290,6 +1291,7 @@ static int apply_tree_change(const og_ctx *c, const og_grid *gn, const int8_t *s
       long gg[3];
       for (int d = 0; d < 3; ++d)
         gg[d] = (long)g->anc[3 * b + d] * nb + (dd[d] < 0 ? -1 : dd[d] > 0 ? nb : 0);
+      if (outside_axis(&cn, L, gg) >= 0) continue;
       int o = owner(&cn, L, gg);
       if (o >= 0 && lev_out[o] == L - 1 && newly_coarse[o]) nmask[(size_t)F * 27 + m] = 1;
     }
@@ -1312,6 +1314,7 @@ static int apply_tree_change(const og_ctx *c, const og_grid *gn, const int8_t *s
           inD[q] = 0;
           if (!((i | j | k) & 1)) continue;
           long gg[3] = {(long)a[0] * nb + i, (long)a[1] * nb + j, (long)a[2] * nb + k};
+          if (outside_axis(&cn, L, gg) >= 0) continue; /* no detail beyond the domain */
           int o = owner(&cn, L, gg);
           if (o < 0) { e = OG_ERR_INVALID; break; }
           if (lev_out[o] == L - 1 && newly_coarse[o]) {
@@ -1382,7 +1385,7 @@ int og_adapt_iter_fields(const og_grid *g, int nf, const double *const *phi, dou
                          double *const *phi_out, int32_t *refined_out, int *n_changed, double *maxdet_out,
                          int8_t *status_out) {
   og_ctx c;
-  if (nf < 1 || has_boundary(g)) return OG_ERR_INVALID; /* adaptation: periodic forests only */
+  if (nf < 1) return OG_ERR_INVALID;
   int e = ctx_init(&c, g);
   if (e) return e;
   const int nb = g->nb, G = og_adapt_shell(g->N, g->Nt), W = nb + 2 * G;

@@ -879,8 +879,30 @@ def test_boundary_with_compact_support_equals_periodic(oracle_mod):
     assert np.abs(a - b).max() <= 1e-14 * np.abs(a).max()
 
 
-def test_boundary_grids_refuse_adaptation(oracle_mod):
-    g = _bounded_grid(oracle_mod, 4, 2, 16, oracle_mod.BC_EXTRAP, periodic=(1, 0, 1))
-    f = np.zeros((g.nleaf, 16, 16, 16))
-    with pytest.raises(RuntimeError):
-        oracle_mod.adapt_iter(g, f, 1e-3, 1e-5)
+@pytest.mark.parametrize("N,Nt", [(4, 2), (4, 0)])
+def test_boundary_adaptation_is_the_dense_transform_of_a_polynomial(oracle_mod, N, Nt):
+    """Adaptation with physical boundaries (Alg. SM3 with the boundary
+    condition in every ghost fill): a polynomial of degree < N (<= 1 for
+    lifted H^a) has no details anywhere, so every block of the 3-level tree
+    whose refinement meets the faces coarsens down to level 0 (the criterion
+    is rounding, far below eps_c = 1e-5), and the coarsened values stay the
+    polynomial's samples; refined once everywhere, the children reproduce it
+    too.  (Rounding: ghosts beyond corners carry the extrapolation weights'
+    growth, ~1e-8 here.)"""
+    nb = 16
+    g = _bounded_grid(oracle_mod, N, Nt, nb, oracle_mod.BC_EXTRAP)
+    deg = N - 1 if Nt == 0 else 1
+    co = np.random.default_rng(4).normal(size=64)
+    f = I.polynomial(I.point_coords(g.nt, g.tree_len, nb, g.lev, g.anc), co, deg)
+    gc, fc = g, f
+    for _ in range(3):
+        out = oracle_mod.adapt_iter(gc, fc, 1e9, 1e-5)
+        gc, fc = out[0], out[1]
+    assert np.all(gc.lev == 0) and gc.nleaf == 64
+    ref = I.polynomial(I.point_coords(gc.nt, gc.tree_len, nb, gc.lev, gc.anc), co, deg)
+    assert np.abs(fc - ref).max() < 1e-6 * np.abs(ref).max()
+    up = oracle_mod.adapt_iter(gc, fc, -1.0, -2.0)  # every block refines once
+    gu, fu = up[0], up[1]
+    assert np.all(gu.lev == 1)
+    ref = I.polynomial(I.point_coords(gu.nt, gu.tree_len, nb, gu.lev, gu.anc), co, deg)
+    assert np.abs(fu - ref).max() < 1e-6 * np.abs(ref).max()
