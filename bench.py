@@ -468,6 +468,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain form of the workload")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) measurement")
     ap.add_argument("--no-autotune", action="store_true", help="default launch shapes (no autotuner)")
+    ap.add_argument("--stage-kernel", type=int, default=0, choices=[0, 1, 2],
+                    help="FP32 stage kernel: 0 tuned, 1 k_fused, 2 k_march")
     ap.add_argument("--workload", default="large",
                     choices=["large", "adaptive-small", "deformation", "batched"] + sorted(WORKLOADS))
     ap.add_argument("--wavelet", default="4.2", choices=["2.2", "4.2", "6.2", "4.0", "6.0"],
@@ -502,6 +504,8 @@ def main():
     g, lmax, umax = make_grid(args, mrgb, stream, prec, args.capacity)
     if not args.no_autotune:
         g.autotune(True)  # launch shapes tuned on this grid during the warm-up steps
+    if args.stage_kernel:
+        g.set_stage_kernel(args.stage_kernel)  # FP32 stage kernel forced (profiling)
     step = Stepper(args, mrgb, g, lmax, umax)
     r = timed(args, g, step, stream, W, dist)
     ms, psu_count, prof, stats0, stats1 = r["ms"], r["psu"], r["prof"], r["stats0"], r["stats1"]

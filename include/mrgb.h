@@ -129,9 +129,12 @@ typedef struct {
  * N-1 nearest points off it; MR_GRID_BC_ZERO -- plain zeros.  Such grids run
  * a general point-wise ghost path (one thread per padded point, the tensor
  * sums of Alg. SM1/SM2 evaluated directly) and the per-block stage kernel;
- * the criterion's extended region stops at the boundary.  mr_adapt,
- * mr_adapt_iter and mr_ghost_fill_static return MR_ERR_UNSUPPORTED on them,
- * as does MR_GRID_INDEPENDENT_TREES combined with a bounded axis. */
+ * the criterion's extended region stops at the boundary, neighbours and the
+ * update step never reach beyond it, and every adaptation iteration
+ * ghost-fills every field in full with FP64 padded blocks.
+ * mr_ghost_fill_static returns MR_ERR_UNSUPPORTED on them, and
+ * mr_grid_create / mr_workspace_size refuse MR_GRID_INDEPENDENT_TREES
+ * combined with a bounded axis (MR_ERR_UNSUPPORTED). */
 #define MR_GRID_BOUNDED_X 8
 #define MR_GRID_BOUNDED_Y 16
 #define MR_GRID_BOUNDED_Z 32

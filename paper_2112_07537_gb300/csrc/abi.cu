@@ -473,12 +473,6 @@ static int adapt_ok(mr_grid *g) {
   return 1;
 }
 
-// the adaptation runs on periodic forests only
-static int adapt_refused(mr_grid *g) {
-  if (!grid_bounded(g)) return 0;
-  set_error("adaptation of grids with physical boundaries is not supported");
-  return 1;
-}
 
 // FP64 ghost fill (the adaptation path) into a double padded buffer.
 int mr_ghost_fill64(mr_grid *g, int fid, int G, double *padded) {
@@ -782,7 +776,7 @@ int mr_criterion(mr_grid *g, int fid, double *maxdet) {
 
 int mr_adapt_iter(mr_grid *g, int crit, double er, double ec, int flags, int *nch) {
   if (!fid_ok(g, crit)) return MR_ERR_INVALID;
-  if (!adapt_ok(g) || adapt_refused(g)) return MR_ERR_UNSUPPORTED;
+  if (!adapt_ok(g)) return MR_ERR_UNSUPPORTED;
   field_written(g, crit);
   int n = 0;
   int e = adapt_iteration(g, crit, er, ec, flags, &n);
@@ -792,7 +786,7 @@ int mr_adapt_iter(mr_grid *g, int crit, double er, double ec, int flags, int *nc
 
 int mr_adapt(mr_grid *g, int crit, double er, double ec, int flags, int *nch) {
   if (!fid_ok(g, crit)) return MR_ERR_INVALID;
-  if (!adapt_ok(g) || adapt_refused(g)) return MR_ERR_UNSUPPORTED;
+  if (!adapt_ok(g)) return MR_ERR_UNSUPPORTED;
   int total = 0;
   field_written(g, crit);  // the criterion field changes between adaptations
   if (check_cuda(cudaMemsetAsync(g->refined, 0, 4 * (size_t)g->desc.capacity, g->stream), "refined reset"))

@@ -339,6 +339,7 @@ __global__ void k_policy(Tree t, const int8_t *__restrict__ sin, int8_t *__restr
           int g[3];
           for (int d = 0; d < 3; ++d)
             g[d] = dd[d] < 0 ? base[d] - 1 : dd[d] > 0 ? base[d] + span : base[d] + cc[d] * (span / 2);
+          if (beyond3(t, Ls, g)) continue;  // no neighbour beyond a physical boundary
           const int o = owner(t, Ls, g[0], g[1], g[2], b);
           if (o == b) continue;
           const int Lo = __ldg(t.lev + o), so = sin[o];
@@ -519,6 +520,7 @@ __global__ void k_newmask(Tree tn, const int *src, int *nmask) {
       const int dd[3] = {m % 3 - 1, (m / 3) % 3 - 1, m / 9 - 1};
       int g[3];
       for (int d = 0; d < 3; ++d) g[d] = __ldg(tn.anc + 3 * q + d) * nb + (dd[d] < 0 ? -1 : dd[d] > 0 ? nb : 0);
+      if (beyond3(tn, L, g)) continue;
       const int o = owner(tn, L, g[0], g[1], g[2], q);
       if (__ldg(tn.lev + o) == L - 1 && src[2 * o] == KIND_PARENT) mask |= 1 << m;
     }
@@ -552,11 +554,13 @@ __global__ void __launch_bounds__(1024) k_update_gamma(Tree tn, const int *__res
     const int dd[3] = {r % 3 - 1, (r / 3) % 3 - 1, r / 9 - 1};
     int g[3];
     for (int d = 0; d < 3; ++d) g[d] = __ldg(tn.anc + 3 * q + d) * nb + (dd[d] < 0 ? -1 : dd[d] > 0 ? nb : 0);
-    const int o = owner(tn, L, g[0], g[1], g[2], q);
-    const int Lo = __ldg(tn.lev + o), ko = src[2 * o];
-    int v = 0;
-    if (Lo == L - 1 && ko == KIND_PARENT) v = -1;
-    else if (Lo == L && ko == KIND_COPY) v = nmask[o];
+    int v = 0;  // regions beyond a physical boundary hold no details
+    if (!beyond3(tn, L, g)) {
+      const int o = owner(tn, L, g[0], g[1], g[2], q);
+      const int Lo = __ldg(tn.lev + o), ko = src[2 * o];
+      if (Lo == L - 1 && ko == KIND_PARENT) v = -1;
+      else if (Lo == L && ko == KIND_COPY) v = nmask[o];
+    }
     rD[r] = v;
     if (v) atomicOr(&any, 1);
   }
@@ -691,6 +695,7 @@ __device__ __forceinline__ void for_each_nbr(const Tree &t, int b, F f) {
           int g[3];
           for (int d = 0; d < 3; ++d)
             g[d] = dd[d] < 0 ? base[d] - 1 : dd[d] > 0 ? base[d] + span : base[d] + cc[d] * (span / 2);
+          if (beyond3(t, Ls, g)) continue;
           const int o = owner(t, Ls, g[0], g[1], g[2], b);
           if (o != b) f(o);
         }
@@ -796,7 +801,10 @@ int adapt_iteration(mr_grid *g, int crit, double er, double ec, int flags, int *
   int e = launch_ghost(g, field_ptr(g, crit), field_ptr(g, crit), G, true, &Pv, &Gi);
   if (e) return e;
   const double *P = (const double *)Pv;
-  e = launch_criterion(g, P, Gi, g->maxdet);
+  // grids with physical boundaries take the general point-wise paths: the
+  // bounded criterion, and full ghost fills (with write-back) of every field
+  const bool bnd = grid_bounded(g);
+  e = bnd ? launch_criterion_bounded(g, P, Gi, g->maxdet) : launch_criterion(g, P, Gi, g->maxdet);
   if (e) return e;
   // the norms this iteration decides with (mr_last_block_norms)
   if (check_cuda(cudaMemcpyAsync(g->mdlast, g->maxdet, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, st),
@@ -838,14 +846,15 @@ int adapt_iteration(mr_grid *g, int crit, double er, double ec, int flags, int *
   const int changed = hc[0], nn = hc[1];
   if (check_cuda(cudaGetLastError(), "policy")) return MR_ERR_CUDA;
   // the other fields of an FP32 grid adapt in FP32 unless asked otherwise
-  const bool f32 = g->desc.precision == MR_F32, o32 = f32 && !(flags & MR_ADAPT_OTHERS_FP64);
+  const bool f32 = g->desc.precision == MR_F32, o32 = f32 && !bnd && !(flags & MR_ADAPT_OTHERS_FP64);
   if (changed == 0) {
     // Alg. SM3 step 1 ghost-fills every field in every iteration; with no
     // leaf changing, what remains of it for the other fields is the
     // substitution next to coarser leaves, which overwrites their values
     for (int fid = 0; fid < g->desc.nfields; ++fid) {
       if (fid == crit) continue;
-      e = launch_substitute(g, field_ptr(g, fid), nullptr, false, o32);
+      e = bnd ? launch_ghost(g, field_ptr(g, fid), field_ptr(g, fid), G, true, &Pv, &Gi)
+              : launch_substitute(g, field_ptr(g, fid), nullptr, false, o32);
       if (e) return e;
     }
     return MR_OK;
@@ -895,7 +904,11 @@ int adapt_iteration(mr_grid *g, int crit, double er, double ec, int flags, int *
       if (e) return e;
       continue;
     }
-    if (pass > 0) {
+    if (pass > 0 && bnd) {
+      e = launch_ghost(g, field_ptr(g, fid), field_ptr(g, fid), G, true, &Pv, &Gi);
+      if (e) return e;
+      P = (const double *)Pv;
+    } else if (pass > 0) {
       e = launch_ghost(g, field_ptr(g, fid), nullptr, G, true, &Pv, &Gi, nullptr, need2);
       if (!e) e = launch_substitute(g, field_ptr(g, fid), nullptr, true);
       if (e) return e;

@@ -2,7 +2,8 @@
 through the C ABI: ghost fill, block criterion and RK3 steps on the 3-level
 tree whose refinement meets the domain faces (inputs.bounded_test_tree),
 bounded along every axis or along x only, with the extrapolation, zero-value
-and plain-zero conditions.
+and plain-zero conditions; and adaptation iterations (Alg. SM3) on such
+grids.
 
 Tolerance.  The device evaluates the boundary polynomial with its Lagrange
 weights, the oracle with Neville's algorithm: the same polynomial, rounded
@@ -173,13 +174,56 @@ def test_bounded_velocity_field_step(mr, oracle_mod):
     assert err <= _tol(N, 3, 1, 1), err
 
 
+# bounded axes chosen so that no block norm lies within 10x the bound of a
+# threshold (the bound grows with the number of bounded axes; the all-axes
+# 4.2 bound, ~1e-6, would cover norms near eps_c = 1e-7)
+@pytest.mark.parametrize("N,Nt,bounded", [(4, 2, (1, 0, 0)), (4, 0, (1, 0, 1)), (2, 2, (1, 1, 1))])
+def test_bounded_adaptation_matches_oracle(mr, oracle_mod, N, Nt, bounded):
+    """Alg. SM3 iterations with physical boundaries on two FP64 fields (the
+    criterion field and a second one refined, coarsened and updated by its
+    decisions): a narrow Gaussian on the x = 0 face refines the blocks there,
+    the smooth level-1/2 region coarsens.  Trees and statuses exactly as the
+    oracle's; fields within the ghost tolerance (the refinement of children
+    reads ghosts beyond the boundary)."""
+    nb, lmax = 16, 4
+    lev, anc = I.bounded_test_tree(NT)
+    g = mr.Grid(NT, TL, nb, 0, lmax, N, Nt, lev, anc, precision=mr.F64, nfields=2, bounded=bounded,
+                capacity=8000)
+    glev, ganc, _ = g.leaves()
+    periodic = tuple(0 if b else 1 for b in bounded)
+    og = oracle_mod.Grid(NT, TL, nb, N, Nt, 0, lmax, glev, ganc, periodic, 0)
+    x, y, z = I.point_coords(NT, TL, nb, glev, ganc)
+    phi = np.exp(-((x - 0.02) ** 2 + (y - 0.6) ** 2 + (z - 0.55) ** 2) / 0.06 ** 2)
+    psi = np.cos(3.0 * x) * np.exp(0.5 * y - 0.2 * z)
+    g.field_copy_in(0, phi)
+    g.field_copy_in(1, psi)
+    er, ec = 1e-3, 1e-7
+    tol = _tol(N, oracle_mod.adapt_shell(N, Nt), sum(bounded), 1)
+    refined = None
+    cur, fields = og, [phi, psi]
+    for it in range(4):
+        Ga = oracle_mod.adapt_shell(N, Nt)
+        norms = oracle_mod.criterion(cur, oracle_mod.ghost_fill(cur, fields[0], Ga)[0], Ga)
+        # no block norm within the tolerance of a threshold: decisions unique
+        assert np.all(np.abs(norms - er) > 10 * tol) and np.all(np.abs(norms - ec) > 10 * tol)
+        og2, ofields, refined, onch, _, st = oracle_mod.adapt_iter_fields(cur, fields, er, ec, refined)
+        nch = g.adapt_iter(0, er, ec)
+        assert nch == onch
+        lev2, anc2, _ = g.leaves()
+        assert np.array_equal(lev2, og2.lev) and np.array_equal(anc2, og2.anc)
+        for f in range(2):
+            got = g.field_copy_out(f)
+            assert np.abs(got - ofields[f]).max() <= tol * np.abs(ofields[f]).max(), (it, f)
+        if it == 0:
+            assert (st == 1).any() and (st == -1).any()
+        cur, fields = og2, [g.field_copy_out(0), g.field_copy_out(1)]
+        if nch == 0:
+            break
+
+
 def test_bounded_grids_refuse_what_they_do_not_support(mr):
     lev, anc = I.bounded_test_tree(NT)
     g = mr.Grid(NT, TL, 16, 0, 4, 4, 2, lev, anc, precision=mr.F64, bounded=(1, 0, 0), capacity=2000)
-    with pytest.raises(mr.MRError):
-        g.adapt(0, 1e-3, 1e-5)
-    with pytest.raises(mr.MRError):
-        g.adapt_iter(0, 1e-3, 1e-5)
     with pytest.raises(mr.MRError):
         g.ghost_fill_static(0, 3)
     lev1, anc1 = I.uniform_leaves((1, 1, 1), 1)
