@@ -28,30 +28,23 @@ __device__ __forceinline__ float wdiv(float a, float b) { return __fdividef(a, b
 __device__ __forceinline__ double wdiv(double a, double b) { return a / b; }
 
 // Interface flux F_{i+1/2} from f[0..5] = f_{i-2..i+3} (Tables SM3 / SM4).
+// The reconstruction biased to the right (upwind from i+1) is the mirror
+// image of the one biased to the left: the same formulas on the reversed
+// stencil f_{i+3..i-1}.  So the upwind choice only selects the five inputs
+// and every lane of a warp runs one code path whatever its interface
+// velocity's sign.
 template <typename T, int SCHEME>
 __device__ __forceinline__ T iface_flux(const T *f, bool left) {
+  const T a = left ? f[0] : f[5], b = left ? f[1] : f[4], c = left ? f[2] : f[3], d = left ? f[3] : f[2],
+          e = left ? f[4] : f[1];
   if (SCHEME == MR_CONS3) {
-    if (left) {
-      const T s0 = T(-0.5) * f[1] + T(1.5) * f[2], s1 = T(0.5) * f[2] + T(0.5) * f[3];
-      return T(1.0 / 3) * s0 + T(2.0 / 3) * s1;
-    }
-    const T s0 = T(0.5) * f[2] + T(0.5) * f[3], s1 = T(1.5) * f[3] - T(0.5) * f[4];
-    return T(2.0 / 3) * s0 + T(1.0 / 3) * s1;
+    const T s0 = T(-0.5) * b + T(1.5) * c, s1 = T(0.5) * c + T(0.5) * d;
+    return T(1.0 / 3) * s0 + T(2.0 / 3) * s1;
   }
-  T a, b, c, d, e, g0, g1, g2, s0, s1, s2;
-  if (left) {
-    a = f[0], b = f[1], c = f[2], d = f[3], e = f[4];
-    s0 = T(1.0 / 3) * a - T(7.0 / 6) * b + T(11.0 / 6) * c;
-    s1 = T(-1.0 / 6) * b + T(5.0 / 6) * c + T(1.0 / 3) * d;
-    s2 = T(1.0 / 3) * c + T(5.0 / 6) * d - T(1.0 / 6) * e;
-    g0 = T(0.1), g1 = T(0.6), g2 = T(0.3);
-  } else {
-    a = f[1], b = f[2], c = f[3], d = f[4], e = f[5];
-    s0 = T(-1.0 / 6) * a + T(5.0 / 6) * b + T(1.0 / 3) * c;
-    s1 = T(1.0 / 3) * b + T(5.0 / 6) * c - T(1.0 / 6) * d;
-    s2 = T(11.0 / 6) * c - T(7.0 / 6) * d + T(1.0 / 3) * e;
-    g0 = T(0.3), g1 = T(0.6), g2 = T(0.1);
-  }
+  const T s0 = T(1.0 / 3) * a - T(7.0 / 6) * b + T(11.0 / 6) * c;
+  const T s1 = T(-1.0 / 6) * b + T(5.0 / 6) * c + T(1.0 / 3) * d;
+  const T s2 = T(1.0 / 3) * c + T(5.0 / 6) * d - T(1.0 / 6) * e;
+  const T g0 = T(0.1), g1 = T(0.6), g2 = T(0.3);
   if (SCHEME == MR_CONS5) return g0 * s0 + g1 * s1 + g2 * s2;
   const T t0 = a - T(4) * b + T(3) * c, u0 = a - T(2) * b + c;
   const T t1 = d - b, u1 = b - T(2) * c + d;
