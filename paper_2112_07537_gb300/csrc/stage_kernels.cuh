@@ -82,6 +82,31 @@ __device__ __forceinline__ T lap_at(const T *c, const int *stride, int diff) {
   return s;
 }
 
+// Zero-detail refinement (J^s / K^s) from the coarse tile Tt of the slab
+// points [lo, lo + ext) whose block-local coordinates have parities
+// (PX, PY, PZ); put(f, c, v) stores each value.
+template <int N, int NT, bool PX, bool PY, bool PZ, typename Put>
+__device__ __forceinline__ void refine_class(int f, const int *lo, const int *ext, const int *q0, const int *nqd,
+                                             const float *Tt, int *err, Put put) {
+  const bool par[3] = {PX, PY, PZ};
+  int first[3], n[3];
+  for (int d = 0; d < 3; ++d) {
+    first[d] = lo[d] + (((lo[d] & 1) != 0) != par[d] ? 1 : 0);
+    n[d] = first[d] < lo[d] + ext[d] ? (lo[d] + ext[d] - first[d] + 1) / 2 : 0;
+  }
+  const int cnt = n[0] * n[1] * n[2];
+  for (int p = threadIdx.x; p < cnt; p += blockDim.x) {
+    const int r = p / n[0];
+    const int c[3] = {first[0] + 2 * (p - r * n[0]), first[1] + 2 * (r % n[1]), first[2] + 2 * (r / n[1])};
+    const float s = refine_sum<N, NT, PX, PY, PZ, float>([&](int ox, int oy, int oz) -> float {
+      const int tx = floordiv2(c[0] + ox) - q0[0], ty = floordiv2(c[1] + oy) - q0[1], tz = floordiv2(c[2] + oz) - q0[2];
+      return Tt[tx + nqd[0] * (ty + nqd[1] * tz)];
+    });
+    if (s != s) atomicOr(err, 2);
+    put(f, c, s);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // The six face slabs (3 deep) that the 1D WENO/CONS stencils of leaf b read,
 // face f = 2*axis + (0: -side, 1: +side):
@@ -167,17 +192,16 @@ __device__ __forceinline__ void stage_faces(const Tree &t, int b, int L, const i
         Tt[p] = v;
       }
       __syncthreads();
-      for (int p = threadIdx.x; p < cnt; p += blockDim.x) {
-        int c[3];
-        slab(p, c);
-        const float s = refine_dispatch<N, NT, float>(c[0] & 1, c[1] & 1, c[2] & 1, [&](int ox, int oy, int oz) -> float {
-          const int tx = floordiv2(c[0] + ox) - q0[0], ty = floordiv2(c[1] + oy) - q0[1],
-                    tz = floordiv2(c[2] + oz) - q0[2];
-          return Tt[tx + nqd[0] * (ty + nqd[1] * tz)];
-        });
-        if (s != s) atomicOr(err, 2);
-        put(f, c, s);
-      }
+      // one parity class at a time, so that every lane of a warp evaluates
+      // the same refinement sum
+      refine_class<N, NT, false, false, false>(f, lo, ext, q0, nqd, Tt, err, put);
+      refine_class<N, NT, true, false, false>(f, lo, ext, q0, nqd, Tt, err, put);
+      refine_class<N, NT, false, true, false>(f, lo, ext, q0, nqd, Tt, err, put);
+      refine_class<N, NT, true, true, false>(f, lo, ext, q0, nqd, Tt, err, put);
+      refine_class<N, NT, false, false, true>(f, lo, ext, q0, nqd, Tt, err, put);
+      refine_class<N, NT, true, false, true>(f, lo, ext, q0, nqd, Tt, err, put);
+      refine_class<N, NT, false, true, true>(f, lo, ext, q0, nqd, Tt, err, put);
+      refine_class<N, NT, true, true, true>(f, lo, ext, q0, nqd, Tt, err, put);
     }
   }
 }
