@@ -322,7 +322,8 @@ int mr_autotune_clear(void);
  * mr_rhs_advect_vel: 1 = k_fused (the ghost-extended block in shared memory,
  * one thread per grid line), 2 = k_march (the block traversed plane by plane,
  * one thread per grid column, two CTAs per SM), 0 = chosen by the autotuner
- * on grids with mr_autotune enabled, else k_march (the default).  k_march
+ * on grids with mr_autotune enabled (the faster of the two for that
+ * configuration), else k_fused (the default).  k_march
  * needs 12 <= nb <= 24; other block sizes always use k_fused.  Both evaluate
  * every value with the same operations in the same order; they may differ in
  * the last bit where the compiler fuses a multiply and an add differently
