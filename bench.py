@@ -412,6 +412,23 @@ class Stepper:
         return 3 * pts
 
 
+def max_over_ranks(ms, dist, device="cuda"):
+    """The job's time: the largest of the ranks' timed regions (every rank
+    receives it).  Without a process group, the rank's own time."""
+    if not dist:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, ms):
+    """Whole-job throughput: every rank processes units_per_rank units (weak
+    scaling, independent replicas), the job takes ms."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 def timed(args, g, step, stream, W, dist):
     """W warm-up steps, then args.steps timed steps between CUDA events on the
     grid's stream, with clocks sampled during the timed region."""
@@ -448,10 +465,7 @@ def timed(args, g, step, stream, W, dist):
     # algorithmic bytes of the ghost reconstruction: the pre-pass (id 0) and
     # the plain gather (id 1) share one fill, so they are timed together
     ghost_bytes = g.profile_bytes(0) + g.profile_bytes(1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist)
     return dict(ms=ms, psu=psu, launches=launches, prof=prof, ghost_bytes=ghost_bytes, stats0=stats0,
                 stats1=g.query(), clocks=summarize_clocks(samples))
 
@@ -555,7 +569,7 @@ def main():
                      "graph_replays": g.graph_replays(), "leaves": g.nleaf}
         g.use_graphs(False)
 
-    psu = world * psu_count / (ms / 1e3)
+    psu = whole_job_rate(world, psu_count, ms)
     hbm, src = peaks()
     try:
         cpk = mrgb.device_peaks()
@@ -690,7 +704,7 @@ def main():
         a64 = copy.copy(args)
         a64.steps = max(2, min(args.steps, 8) // 2 * 2)
         r64 = timed(a64, g64, step64, stream, 3, None)
-        v64 = world * r64["psu"] / (r64["ms"] / 1e3)
+        v64 = whole_job_rate(world, r64["psu"], r64["ms"])
         line["fp64_plain"] = {"value": v64, "unit": UNIT, "ms_per_step": r64["ms"] / a64.steps,
                               "leaves": [r64["stats0"].nleaf, r64["stats1"].nleaf], "steps": a64.steps,
                               "warmup": 3,
