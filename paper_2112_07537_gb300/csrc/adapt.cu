@@ -451,6 +451,23 @@ __global__ void k_emit(int n, int M, const int8_t *st, const int *pos, const int
 // New leaf values: copy, zero-detail refinement of the parent's padded block
 // (J^s / K^s), or tensor H^a coarsening of the 8 children's padded blocks,
 // in the padded blocks' precision TP.
+// Child ch of a refined parent (Sec. 2.2.3, zero-detail refinement with
+// J^s / K^s of the parent's padded block Pp): the points of the child whose
+// local indices have parities (PX, PY, PZ).
+template <int N, int NT, bool PX, bool PY, bool PZ, typename TP, typename TO, typename PI>
+__device__ __forceinline__ void interp_class(const TP *Pp, int ch, int nb, PI pidx, TO *out) {
+  const int h = nb / 2, cnt = h * h * h;
+  for (int p = threadIdx.x; p < cnt; p += blockDim.x) {
+    const int r = p / h;
+    const int i = 2 * (p - r * h) + PX, j = 2 * (r % h) + PY, k = 2 * (r / h) + PZ;
+    const int f[3] = {(ch & 1) * nb + i, ((ch >> 1) & 1) * nb + j, ((ch >> 2) & 1) * nb + k};
+    const TP acc = refine_sum<N, NT, PX, PY, PZ, TP>([&](int ox, int oy, int oz) {
+      return Pp[pidx((f[0] + ox) / 2, (f[1] + oy) / 2, (f[2] + oz) / 2)];
+    });
+    out[i + nb * (j + nb * k)] = TO(acc);
+  }
+}
+
 template <typename TO, typename TP, int N, int NT>
 __global__ void __launch_bounds__(512) k_interp(Tree to, const int *__restrict__ src,
                                                 const TP *__restrict__ P, int Gi,
@@ -468,14 +485,17 @@ __global__ void __launch_bounds__(512) k_interp(Tree to, const int *__restrict__
   } else if (kind == KIND_CHILD) {
     const int par = s >> 3, ch = s & 7;
     const TP *Pp = P + (size_t)par * np;
-    for (int p = threadIdx.x; p < (int)nb3; p += blockDim.x) {
-      const int i = p % nb, j = (p / nb) % nb, k = p / (nb * nb);
-      const int f[3] = {(ch & 1) * nb + i, ((ch >> 1) & 1) * nb + j, ((ch >> 2) & 1) * nb + k};
-      const TP acc = refine_dispatch<N, NT, TP>(f[0] & 1, f[1] & 1, f[2] & 1, [&](int ox, int oy, int oz) {
-        return Pp[pidx((f[0] + ox) / 2, (f[1] + oy) / 2, (f[2] + oz) / 2)];
-      });
-      out[p] = TO(acc);
-    }
+    // one parity class of the child's points at a time (the parity of the
+    // parent-grid index equals the child's, nb being even), so that every
+    // lane of a warp evaluates the same refinement sum
+    interp_class<N, NT, false, false, false>(Pp, ch, nb, pidx, out);
+    interp_class<N, NT, true, false, false>(Pp, ch, nb, pidx, out);
+    interp_class<N, NT, false, true, false>(Pp, ch, nb, pidx, out);
+    interp_class<N, NT, true, true, false>(Pp, ch, nb, pidx, out);
+    interp_class<N, NT, false, false, true>(Pp, ch, nb, pidx, out);
+    interp_class<N, NT, true, false, true>(Pp, ch, nb, pidx, out);
+    interp_class<N, NT, false, true, true>(Pp, ch, nb, pidx, out);
+    interp_class<N, NT, true, true, true>(Pp, ch, nb, pidx, out);
   } else {
     // children of the new parent in the old tree (level L = parent level + 1)
     __shared__ int chs[8];
