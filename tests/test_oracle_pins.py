@@ -794,13 +794,18 @@ def test_boundary_extrapolation_weights(oracle_mod, N):
     # x-ghosts between the two trees are copies, y/z ghosts periodic copies
     assert pad[0][G, G, G + nb] == fx[nb] and pad[1][G, G, G - 1] == fx[nb - 1]
     assert pad[0][G - 1, G, G + 2] == f[0][nb - 1, 0, 2]
+    # zero value: the same N nodes with the boundary node's value set to 0,
+    # so the ghost one spacing beyond is sum_{j>=1} (-1)^j C(N, j+1) f_j
+    # (N = 4: -6 f1 + 4 f2 - f3); the upper boundary point itself is 0
+    g0 = oracle_mod.Grid(nt, tl, nb, N, 0, 0, 0, lev, anc, (0, 1, 1), oracle_mod.BC_DIRICHLET0)
+    pad0, _ = oracle_mod.ghost_fill(g0, f, G)
+    lower0 = sum(w[j] * fx[j] for j in range(1, N))
+    upper0 = sum(w[j] * fx[n - j] for j in range(1, N))
+    assert abs(pad0[0][G, G, G - 1] - lower0) <= 1e-12 * 2 ** N * np.abs(fx).max()
+    assert abs(pad0[1][G, G, G + nb]) <= 1e-13 * np.abs(fx).max()
+    assert abs(pad0[1][G, G, G + nb + 1] - upper0) <= 1e-12 * 2 ** N * np.abs(fx).max()
     if N == 4:
-        g0 = oracle_mod.Grid(nt, tl, nb, N, 0, 0, 0, lev, anc, (0, 1, 1), oracle_mod.BC_DIRICHLET0)
-        pad0, _ = oracle_mod.ghost_fill(g0, f, G)
-        assert abs(pad0[0][G, G, G - 1] - (-6 * fx[1] + 4 * fx[2] - fx[3])) <= 1e-12 * 16 * np.abs(fx).max()
-        assert abs(pad0[1][G, G, G + nb]) <= 1e-13 * np.abs(fx).max()
-        assert abs(pad0[1][G, G, G + nb + 1] - (-6 * fx[n - 1] + 4 * fx[n - 2] - fx[n - 3])) \
-            <= 1e-12 * 16 * np.abs(fx).max()
+        assert w[1:] == [-6, 4, -1]
         gz = oracle_mod.Grid(nt, tl, nb, N, 0, 0, 0, lev, anc, (0, 1, 1), oracle_mod.BC_ZERO)
         padz, _ = oracle_mod.ghost_fill(gz, f, G)
         assert np.all(padz[0][:, :, :G] == 0) and np.all(padz[1][:, :, G + nb:] == 0)
